@@ -1,0 +1,28 @@
+"""Shape checks for the seeded input generators (no method arithmetic)."""
+import numpy as np
+
+import synth
+
+
+def test_grid_counts():
+    n, s, d, w = synth.grid2d(48)
+    assert n == 2304 and s.size == 4512 and w is None
+    assert np.all(s < d)
+
+
+def test_ba_counts_and_determinism():
+    n, s, d, _ = synth.barabasi_albert(3000, 5, seed=2)
+    assert s.size == 15 + 5 * (3000 - 6)
+    key = np.minimum(s, d).astype(np.int64) * n + np.maximum(s, d)
+    assert np.unique(key).size == key.size  # simple graph
+    n2, s2, d2, _ = synth.barabasi_albert(3000, 5, seed=2)
+    assert np.array_equal(s, s2) and np.array_equal(d, d2)
+
+
+def test_rmat_lcc():
+    n, s, d, _ = synth.rmat(12, seed=3)
+    assert n <= 4096 and np.all(s < d)
+    import scipy.sparse as sp
+    import scipy.sparse.csgraph as cg
+    a = sp.coo_matrix((np.ones(s.size), (s, d)), shape=(n, n))
+    assert cg.connected_components(a, directed=False)[0] == 1
