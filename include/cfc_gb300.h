@@ -1,0 +1,266 @@
+/*
+ * cfc_gb300.h -- C ABI of the GB300 Laplacian-solver / current-flow
+ * closeness library.
+ *
+ * Method: Bergamini, Wegner, Lukarski, Meyerhenke, "Estimating Current-Flow
+ * Closeness Centrality with a Multigrid Laplacian Solver" (arXiv:1607.02955).
+ * Notation follows the paper: G = (V, E, w) connected, undirected, weighted
+ * (Sec. 2); L = D - A its Laplacian (Sec. 2); supplies b with sum 0 and
+ * potentials L p = b (Eq. system); effective resistance
+ * d_ER(u, v) = p_uv(u) - p_uv(v) (Sec. 4); electrical farness
+ * f(v) = sum_{w != v} d_ER(v, w) and current-flow closeness
+ * c_ER(v) = (n - 1) / f(v) (Eq. closeness2).
+ *
+ * Conventions shared by every call
+ *  - Every call returns a lap_status_t; none aborts, prints or throws.
+ *    lap_status_string() names a status.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  All device work of a call is ordered on it.  Calls that write
+ *    host memory synchronise the stream before returning; calls that only
+ *    write device memory return without synchronising.
+ *  - Pointers documented "host or device" may be either; the library asks
+ *    the CUDA driver which one (cudaPointerGetAttributes).  Device pointers
+ *    must be on the current device.
+ *  - Inputs are read, never kept: the caller keeps ownership of every array
+ *    it passes.  A lap_hierarchy_t is owned by the library until
+ *    lap_hierarchy_destroy().
+ *  - Dense n x k blocks are row-major with the k columns of a row
+ *    contiguous (element (i, j) at [i * k + j]).
+ *  - Sizes: 2 <= n < 2^31 and 2 * m < 2^31 (32-bit row pointers).
+ *  - A hierarchy may be used by one call at a time (it holds the solve
+ *    workspace); distinct hierarchies may run concurrently on distinct
+ *    streams.
+ */
+#ifndef CFC_GB300_H
+#define CFC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LAP_OK = 0,
+    LAP_EINVAL = 1,    /* bad argument: size, index range, weight <= 0 or not finite, NULL */
+    LAP_ENOTCONN = 2,  /* the graph is not connected (Sec. 2 assumes connected G) */
+    LAP_ENOMEM = 3,    /* a device allocation failed; nothing leaked */
+    LAP_ENOCONV = 4,   /* a solve hit its iteration cap; outputs hold the best iterate */
+    LAP_ECUDA = 5,     /* a CUDA runtime error (the text is kept, see lap_last_error) */
+    LAP_EBUDGET = 6,   /* request exceeds a documented maximum */
+    LAP_ENOTIMPL = 7
+} lap_status_t;
+
+/* Arithmetic of a solve. */
+enum {
+    LAP_FP64 = 0,                     /* FP64 PCG + FP64 V-cycle */
+    LAP_FP32_REFINED = 1,             /* FP32 PCG + V-cycle inside FP64 iterative refinement */
+    LAP_FP32_BF16COARSE_REFINED = 2   /* as 1, with BF16 edge weights on levels >= 1 */
+};
+
+/* Smoother of the V-cycle. */
+enum { LAP_SMOOTH_JACOBI = 0, LAP_SMOOTH_CHEBYSHEV = 1 };
+
+typedef struct {
+    int32_t coarse_max;   /* stop coarsening at n_l <= coarse_max (default 64, at most 256) */
+    int32_t max_levels;   /* cap on levels incl. the finest (default 24); 1 = no coarsening */
+    int32_t agg_passes;   /* pairwise-matching passes per level (default 2: aggregates of ~4) */
+    int32_t match_rounds; /* handshake rounds per pass (default 4) */
+} lap_hier_opts_t;
+
+typedef struct {
+    int32_t precision;    /* LAP_FP64 | LAP_FP32_REFINED | LAP_FP32_BF16COARSE_REFINED */
+    double tol;           /* per-column ||b - L x||_2 / ||b||_2 target (default 1e-8) */
+    int32_t max_outer;    /* refinement steps (default 8) */
+    int32_t max_inner;    /* PCG iterations per refinement step (default 200) */
+    double inner_tol;     /* inner PCG relative residual (default 1e-4) */
+    int32_t k_tile;       /* columns per tile: 0 = autotune, else 16, 32, 64 or 128 */
+    int32_t smoother;     /* LAP_SMOOTH_JACOBI | LAP_SMOOTH_CHEBYSHEV (default Chebyshev) */
+    int32_t nu_pre;       /* smoothing steps before the coarse correction (default 2) */
+    int32_t nu_post;      /* smoothing steps after (default 2) */
+    int32_t check_every;  /* inner iterations between host convergence reads (default 4) */
+    int32_t levels_used;  /* use at most this many levels of the hierarchy (0 = all) */
+} lap_solve_opts_t;
+
+typedef struct {
+    int32_t outer_iters;
+    int32_t inner_iters;        /* total over all refinement steps */
+    double max_rel_residual;    /* max over columns of the final FP64 ||b - Lx|| / ||b|| */
+} lap_solve_info_t;
+
+typedef struct {
+    int64_t n, m;               /* nodes, undirected edges after merging duplicates */
+    int32_t levels;
+    int32_t coarse_n;           /* size of the dense coarsest level (0 if none) */
+    int64_t level_n[32];
+    int64_t level_nnz[32];      /* off-diagonal entries of each level's CSR */
+    double setup_ms;            /* device time of lap_build_hierarchy */
+} lap_hier_info_t;
+
+typedef struct lap_hierarchy lap_hierarchy_t;
+
+/* Fill defaults into an options struct. */
+void lap_default_hier_opts(lap_hier_opts_t *o);
+void lap_default_solve_opts(lap_solve_opts_t *o);
+
+/*
+ * lap_build_hierarchy -- ingest G and build the multigrid hierarchy.
+ * Sec. 2 (graph model, L = D - A), Sec. 3.1 and Sec. 6.1 (an algebraic
+ * multigrid Laplacian solver; the paper's LAMG coarsens by elimination and
+ * affinity-based aggregation -- this library aggregates by pairwise matching
+ * on edge strength w_ij / max(D_ii, D_jj)).
+ *   n           number of nodes, 2 <= n < 2^31
+ *   m           number of input edges (m >= 1)
+ *   src, dst    int32[m], host or device: edge endpoints in [0, n).
+ *               Self-loops are dropped; edge direction is ignored;
+ *               repeated pairs are merged with their weights summed
+ *               (parallel conductances) (Sec. 6.3).
+ *   w           double[m], host or device, or NULL for unit weights; each
+ *               weight finite and > 0 (conductances, Sec. 2).
+ *   opts        NULL = defaults.
+ *   out         receives the hierarchy on LAP_OK, NULL otherwise.
+ * Errors: LAP_EINVAL (sizes, NULL, endpoint out of range, bad weight);
+ * LAP_ENOTCONN (G not connected, Sec. 2); LAP_ENOMEM; LAP_ECUDA.
+ * Synchronises `stream`.
+ */
+lap_status_t lap_build_hierarchy(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                                 const double *w, const lap_hier_opts_t *opts, void *stream,
+                                 lap_hierarchy_t **out);
+
+/* Release every device and host resource of h (NULL is a no-op). */
+void lap_hierarchy_destroy(lap_hierarchy_t *h);
+
+/* Sizes of h's levels. */
+lap_status_t lap_hierarchy_info(const lap_hierarchy_t *h, lap_hier_info_t *info);
+
+/*
+ * lap_solve_multi -- solve L X = B for k right-hand sides at once (Eq.
+ * system; Sec. 3.1: iterate until the relative residual is below tol).
+ * Each column is an independent system (its own CG step lengths): results
+ * do not depend on k, the tile width or the other columns.
+ *   k    number of columns, 1 <= k <= 4096
+ *   B    device double[n * k] row-major.  Each column is projected onto
+ *        range(L) = 1-perp first (the null space span{1} of L, Sec. 2).
+ *   X    device double[n * k] row-major, output: the zero-mean solution
+ *        L^+ B of every column.  May not alias B.
+ *   o    NULL = defaults.  info may be NULL.
+ * Errors: LAP_EINVAL; LAP_ENOCONV (some column above tol after max_outer
+ * refinement steps; X holds the best iterate, info the residual); LAP_ENOMEM;
+ * LAP_ECUDA.  Synchronises `stream` (convergence is read on the host).
+ */
+lap_status_t lap_solve_multi(lap_hierarchy_t *h, int32_t k, const double *B, double *X,
+                             const lap_solve_opts_t *o, void *stream, lap_solve_info_t *info);
+
+/*
+ * cfc_jl_rhs -- Algorithm 1, steps 1-2: Y = Q W^{1/2} B with Q a k x m
+ * matrix of +-1/sqrt(k) entries drawn from Philox4x64-10 (Sec. 5.2).
+ * Edge e = {u < v} (ids: lexicographic rank of (u, v) after merging) has
+ * B(e, u) = +1, B(e, v) = -1.  Sign of Q[i, e]: bit (i % 64) of word
+ * (i % 256) / 64 of Philox4x64-10(counter = (e, i / 256, 0, 0),
+ * key = (seed, 0x4A4C)); bit 0 -> +1/sqrt(k), 1 -> -1/sqrt(k).
+ *   Y    device double[n * k], row-major: Y[u * k + i] = (Q W^{1/2} B)_{i,u},
+ *        i.e. column i of this block is row i of the paper's k x n Y.
+ */
+lap_status_t cfc_jl_rhs(lap_hierarchy_t *h, int32_t k, uint64_t seed, double *Y, void *stream);
+
+/*
+ * cfc_farness_jl -- the projection estimator of Sec. 5.2 / Algorithm 1:
+ * build Y (cfc_jl_rhs), solve L z_i = Y_i for the k rows (lap_solve_multi),
+ * and return f~(v) = sum_{w != v} ||Z_{.,v} - Z_{.,w}||^2 for each query node,
+ * evaluated in O(nk) as sum_i [n Z_iv^2 - 2 Z_iv S_i + T_i] with
+ * S_i = sum_w Z_iw, T_i = sum_w Z_iw^2 (FP64).  The closeness estimate is
+ * (n - 1) / f~(v).
+ *   k        JL dimension; k <= 0 means k = ceil(ln(n) / eps^2) (Sec. 6.4)
+ *   eps      used only when k <= 0
+ *   q        number of query nodes, 1 <= q <= n
+ *   nodes    int32[q], host or device
+ *   farness  double[q], host or device, output
+ * Errors: as lap_solve_multi; LAP_EINVAL for a node out of range.
+ */
+lap_status_t cfc_farness_jl(lap_hierarchy_t *h, int32_t k, double eps, uint64_t seed, int32_t q,
+                            const int32_t *nodes, double *farness, const lap_solve_opts_t *o,
+                            void *stream);
+
+/*
+ * cfc_sample_pivots -- the pivot set S of Sec. 5.1: a uniform n_pivots-subset
+ * of V without replacement (all of V: a query node may be a pivot), drawn on
+ * the device by Floyd's algorithm; Floyd step s (s = 0..n_pivots-1, range
+ * [0, n - n_pivots + s]) draws floor(u * range / 2^64) with u = word 0 of
+ * Philox4x64-10(counter = (s, 0, 0, 0), key = (seed, 0x534D50)).
+ *   pivots  int32[n_pivots], host or device, output, ascending.
+ */
+lap_status_t cfc_sample_pivots(lap_hierarchy_t *h, int32_t n_pivots, uint64_t seed, int32_t *pivots,
+                               void *stream);
+
+/*
+ * cfc_farness_sampled -- the sampling estimator of Sec. 5.1: with S from
+ * cfc_sample_pivots, f^(v) = (n / |S|) sum_{s in S} d_ER(v, s), the unbiased
+ * farness estimate of Proposition 1.  d_ER(v, s) is evaluated from column
+ * solves x_u = L^+ (e_u - 1/n) for u in S and the query nodes:
+ * d_ER(v, s) = x_v(v) - x_v(s) - x_s(v) + x_s(s), algebraically the
+ * potential difference of the pair system L p = e_v - e_s (Eq. system).
+ * Closeness: (n - 1) / f^(v) (equal to (k/n)(n-1)/f~(v, S) of Sec. 5.1).
+ *   n_pivots 1 <= n_pivots <= n;  q, nodes, farness as cfc_farness_jl.
+ */
+lap_status_t cfc_farness_sampled(lap_hierarchy_t *h, int32_t n_pivots, uint64_t seed, int32_t q,
+                                 const int32_t *nodes, double *farness, const lap_solve_opts_t *o,
+                                 void *stream);
+
+/*
+ * cfc_exact_small -- exact electrical farness and current-flow closeness of
+ * every node of a small graph (Sec. 4, Eq. closeness2), in FP64 on the
+ * device, from the dense pseudoinverse L^+ = (L + J/n)^{-1} - J/n:
+ * f(v) = n L^+_vv + tr(L^+) (equal to sum_w [L^+_vv - 2 L^+_vw + L^+_ww]
+ * since L^+ 1 = 0), c(v) = (n - 1) / f(v).
+ *   n <= 16384 (the dense n x n FP64 matrix is held on the device);
+ *   src, dst, w as lap_build_hierarchy;
+ *   farness   double[n], host or device, output
+ *   closeness double[n], host or device, output, or NULL
+ * Errors: LAP_EINVAL, LAP_EBUDGET (n too large), LAP_ENOTCONN, LAP_ENOMEM,
+ * LAP_ECUDA.  Synchronises `stream`.
+ */
+lap_status_t cfc_exact_small(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                             const double *w, double *farness, double *closeness, void *stream);
+
+/* Human-readable name of a status. */
+const char *lap_status_string(lap_status_t s);
+
+/* Text of the last CUDA error seen by this thread ("" if none). */
+const char *lap_last_error(void);
+
+/*
+ * Instrumentation (no counterpart in the paper).  Counts every kernel this
+ * library launches; when timing is on, brackets each launch of the kernel
+ * families below with CUDA events on the launching stream and accumulates
+ * the device time and the algorithmic bytes (each operand read once,
+ * each result written once) of those launches.
+ */
+enum {
+    LAP_KF_SPMV_FINE = 0,     /* FP32 L*p of the PCG at the finest level */
+    LAP_KF_SMOOTH_FINE = 1,   /* FP32 smoother steps at the finest level */
+    LAP_KF_RESTRICT_FINE = 2, /* residual + restriction at the finest level */
+    LAP_KF_BLAS1 = 3,         /* PCG vector updates and dot products (finest level) */
+    LAP_KF_COARSE_LEVELS = 4, /* every V-cycle kernel below the finest level */
+    LAP_KF_RESID64 = 5,       /* FP64 outer residual */
+    LAP_KF_SETUP = 6,         /* ingest + hierarchy */
+    LAP_KF_CFC = 7,           /* RHS generation and farness reductions */
+    LAP_KF_COUNT = 8
+};
+
+typedef struct {
+    uint64_t launches_total;          /* every kernel launch since the last reset */
+    uint64_t launches[LAP_KF_COUNT];
+    double ms[LAP_KF_COUNT];          /* event-timed device ms (timing on only) */
+    double bytes[LAP_KF_COUNT];       /* algorithmic bytes of the timed launches */
+} lap_stats_t;
+
+void lap_stats_reset(void);
+void lap_stats_set_timing(int32_t on);
+/* Synchronises the pending timing events, then copies the counters. */
+lap_status_t lap_stats_read(lap_stats_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CFC_GB300_H */

@@ -1,0 +1,299 @@
+"""ctypes binding of include/cfc_gb300.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+lib_path = os.path.join(_HERE, "lib", "libcfc_gb300.so")
+
+LAP_OK, LAP_EINVAL, LAP_ENOTCONN, LAP_ENOMEM, LAP_ENOCONV, LAP_ECUDA, LAP_EBUDGET, LAP_ENOTIMPL = range(8)
+LAP_FP64, LAP_FP32_REFINED, LAP_FP32_BF16COARSE_REFINED = 0, 1, 2
+LAP_SMOOTH_JACOBI, LAP_SMOOTH_CHEBYSHEV = 0, 1
+KERNEL_FAMILIES = ["spmv_fine", "smooth_fine", "restrict_fine", "blas1", "coarse_levels", "resid64", "setup",
+                   "cfc"]
+
+SYMBOLS = [
+    "lap_default_hier_opts", "lap_default_solve_opts", "lap_build_hierarchy", "lap_hierarchy_destroy",
+    "lap_hierarchy_info", "lap_solve_multi", "cfc_jl_rhs", "cfc_farness_jl", "cfc_sample_pivots",
+    "cfc_farness_sampled", "cfc_exact_small", "lap_status_string", "lap_last_error", "lap_stats_reset",
+    "lap_stats_set_timing", "lap_stats_read",
+]
+
+
+class HierOpts(C.Structure):
+    _fields_ = [("coarse_max", C.c_int32), ("max_levels", C.c_int32), ("agg_passes", C.c_int32),
+                ("match_rounds", C.c_int32)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("max_outer", C.c_int32),
+                ("max_inner", C.c_int32), ("inner_tol", C.c_double), ("k_tile", C.c_int32),
+                ("smoother", C.c_int32), ("nu_pre", C.c_int32), ("nu_post", C.c_int32),
+                ("check_every", C.c_int32), ("levels_used", C.c_int32)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("outer_iters", C.c_int32), ("inner_iters", C.c_int32), ("max_rel_residual", C.c_double)]
+
+
+class HierInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("m", C.c_int64), ("levels", C.c_int32), ("coarse_n", C.c_int32),
+                ("level_n", C.c_int64 * 32), ("level_nnz", C.c_int64 * 32), ("setup_ms", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("launches_total", C.c_uint64), ("launches", C.c_uint64 * 8), ("ms", C.c_double * 8),
+                ("bytes", C.c_double * 8)]
+
+
+class LapError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {lap_status_string(status)}" + (f" ({detail})" if detail else ""))
+
+
+_lib = None
+
+
+def lib():
+    """Load libcfc_gb300.so.  Raises RuntimeError when it has not been built:
+    there is no fallback implementation."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(lib_path):
+        raise RuntimeError(f"{lib_path} is missing: build it with "
+                           "paper_1607_02955_gb300.build_ext.build() (needs nvcc)")
+    L = C.CDLL(lib_path)
+    vp, i32, i64, u64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
+    L.lap_default_hier_opts.argtypes = [C.POINTER(HierOpts)]
+    L.lap_default_hier_opts.restype = None
+    L.lap_default_solve_opts.argtypes = [C.POINTER(SolveOpts)]
+    L.lap_default_solve_opts.restype = None
+    L.lap_build_hierarchy.argtypes = [i64, i64, vp, vp, vp, C.POINTER(HierOpts), vp, C.POINTER(vp)]
+    L.lap_build_hierarchy.restype = C.c_int
+    L.lap_hierarchy_destroy.argtypes = [vp]
+    L.lap_hierarchy_destroy.restype = None
+    L.lap_hierarchy_info.argtypes = [vp, C.POINTER(HierInfo)]
+    L.lap_hierarchy_info.restype = C.c_int
+    L.lap_solve_multi.argtypes = [vp, i32, vp, vp, C.POINTER(SolveOpts), vp, C.POINTER(SolveInfo)]
+    L.lap_solve_multi.restype = C.c_int
+    L.cfc_jl_rhs.argtypes = [vp, i32, u64, vp, vp]
+    L.cfc_jl_rhs.restype = C.c_int
+    L.cfc_farness_jl.argtypes = [vp, i32, dbl, u64, i32, vp, vp, C.POINTER(SolveOpts), vp]
+    L.cfc_farness_jl.restype = C.c_int
+    L.cfc_sample_pivots.argtypes = [vp, i32, u64, vp, vp]
+    L.cfc_sample_pivots.restype = C.c_int
+    L.cfc_farness_sampled.argtypes = [vp, i32, u64, i32, vp, vp, C.POINTER(SolveOpts), vp]
+    L.cfc_farness_sampled.restype = C.c_int
+    L.cfc_exact_small.argtypes = [i64, i64, vp, vp, vp, vp, vp, vp]
+    L.cfc_exact_small.restype = C.c_int
+    L.lap_status_string.argtypes = [C.c_int]
+    L.lap_status_string.restype = C.c_char_p
+    L.lap_last_error.argtypes = []
+    L.lap_last_error.restype = C.c_char_p
+    L.lap_stats_reset.argtypes = []
+    L.lap_stats_reset.restype = None
+    L.lap_stats_set_timing.argtypes = [i32]
+    L.lap_stats_set_timing.restype = None
+    L.lap_stats_read.argtypes = [C.POINTER(Stats)]
+    L.lap_stats_read.restype = C.c_int
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    L = lib()
+    return [s for s in SYMBOLS if hasattr(L, s)]
+
+
+# ------------------------------------------------------------------ marshalling
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return C.c_void_p(0)
+
+
+def _ptr(x, dtype):
+    """Pointer of a torch tensor (any device) or numpy array of the given
+    numpy dtype; None -> NULL.  Returns (pointer, keep-alive object)."""
+    if x is None:
+        return C.c_void_p(0), None
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            want = {np.int32: torch.int32, np.float64: torch.float64}[dtype]
+            if x.dtype != want or not x.is_contiguous():
+                raise TypeError(f"expected a contiguous {want} tensor")
+            return C.c_void_p(x.data_ptr()), x
+    except ImportError:
+        pass
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return C.c_void_p(a.ctypes.data), a
+
+
+def _check(st, where, allow=()):
+    if st != LAP_OK and st not in allow:
+        detail = lib().lap_last_error().decode(errors="replace")
+        raise LapError(st, where, detail)
+    return st
+
+
+def lap_status_string(status: int) -> str:
+    return lib().lap_status_string(int(status)).decode()
+
+
+def lap_last_error() -> str:
+    return lib().lap_last_error().decode(errors="replace")
+
+
+def lap_default_hier_opts(**kw) -> HierOpts:
+    o = HierOpts()
+    lib().lap_default_hier_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def lap_default_solve_opts(**kw) -> SolveOpts:
+    o = SolveOpts()
+    lib().lap_default_solve_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Hierarchy:
+    """Owns a lap_hierarchy_t; destroyed with the object or by destroy()."""
+
+    def __init__(self, handle: int, n: int):
+        self.handle = C.c_void_p(handle)
+        self.n = n
+
+    def destroy(self):
+        if self.handle and self.handle.value:
+            lib().lap_hierarchy_destroy(self.handle)
+            self.handle = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def lap_build_hierarchy(n, src, dst, w=None, opts: HierOpts | None = None, stream=None) -> Hierarchy:
+    ps, ks = _ptr(src, np.int32)
+    pd, kd = _ptr(dst, np.int32)
+    pw, kw = _ptr(w, np.float64)
+    m = len(src) if not hasattr(src, "numel") else src.numel()
+    out = C.c_void_p(0)
+    st = lib().lap_build_hierarchy(int(n), int(m), ps, pd, pw, C.byref(opts) if opts is not None else None,
+                                   _stream(stream), C.byref(out))
+    _check(st, "lap_build_hierarchy")
+    return Hierarchy(out.value, int(n))
+
+
+def lap_hierarchy_destroy(h: Hierarchy):
+    h.destroy()
+
+
+def lap_hierarchy_info(h: Hierarchy) -> dict:
+    info = HierInfo()
+    _check(lib().lap_hierarchy_info(h.handle, C.byref(info)), "lap_hierarchy_info")
+    L = info.levels
+    return {"n": info.n, "m": info.m, "levels": L, "coarse_n": info.coarse_n,
+            "level_n": list(info.level_n[:L]), "level_nnz": list(info.level_nnz[:L]), "setup_ms": info.setup_ms}
+
+
+def lap_solve_multi(h: Hierarchy, B, X, opts: SolveOpts | None = None, stream=None, allow_noconv=False) -> dict:
+    """B, X: contiguous FP64 CUDA tensors of shape (n, k)."""
+    k = 1 if B.dim() == 1 else B.shape[1]
+    pb, kb = _ptr(B, np.float64)
+    px, kx = _ptr(X, np.float64)
+    info = SolveInfo()
+    st = lib().lap_solve_multi(h.handle, int(k), pb, px, C.byref(opts) if opts is not None else None,
+                               _stream(stream), C.byref(info))
+    _check(st, "lap_solve_multi", allow=(LAP_ENOCONV,) if allow_noconv else ())
+    return {"status": st, "outer_iters": info.outer_iters, "inner_iters": info.inner_iters,
+            "max_rel_residual": info.max_rel_residual}
+
+
+def cfc_jl_rhs(h: Hierarchy, k: int, seed: int, Y, stream=None):
+    py, ky = _ptr(Y, np.float64)
+    _check(lib().cfc_jl_rhs(h.handle, int(k), int(seed), py, _stream(stream)), "cfc_jl_rhs")
+    return Y
+
+
+def _out_f64(out, q):
+    return np.empty(q, np.float64) if out is None else out
+
+
+def cfc_farness_jl(h: Hierarchy, k: int, seed: int, nodes, eps: float = 0.0, opts: SolveOpts | None = None,
+                   out=None, stream=None):
+    q = len(nodes)
+    pn, kn = _ptr(nodes, np.int32)
+    out = _out_f64(out, q)
+    po, ko = _ptr(out, np.float64)
+    st = lib().cfc_farness_jl(h.handle, int(k), float(eps), int(seed), int(q), pn, po,
+                              C.byref(opts) if opts is not None else None, _stream(stream))
+    _check(st, "cfc_farness_jl")
+    return out
+
+
+def cfc_sample_pivots(h: Hierarchy, n_pivots: int, seed: int, out=None, stream=None):
+    out = np.empty(n_pivots, np.int32) if out is None else out
+    po, ko = _ptr(out, np.int32)
+    _check(lib().cfc_sample_pivots(h.handle, int(n_pivots), int(seed), po, _stream(stream)), "cfc_sample_pivots")
+    return out
+
+
+def cfc_farness_sampled(h: Hierarchy, n_pivots: int, seed: int, nodes, opts: SolveOpts | None = None, out=None,
+                        stream=None):
+    q = len(nodes)
+    pn, kn = _ptr(nodes, np.int32)
+    out = _out_f64(out, q)
+    po, ko = _ptr(out, np.float64)
+    st = lib().cfc_farness_sampled(h.handle, int(n_pivots), int(seed), int(q), pn, po,
+                                   C.byref(opts) if opts is not None else None, _stream(stream))
+    _check(st, "cfc_farness_sampled")
+    return out
+
+
+def cfc_exact_small(n, src, dst, w=None, stream=None):
+    """Returns (farness, closeness) as numpy arrays."""
+    ps, ks = _ptr(src, np.int32)
+    pd, kd = _ptr(dst, np.int32)
+    pw, kw = _ptr(w, np.float64)
+    m = len(src)
+    f = np.empty(n, np.float64)
+    c = np.empty(n, np.float64)
+    st = lib().cfc_exact_small(int(n), int(m), ps, pd, pw, C.c_void_p(f.ctypes.data), C.c_void_p(c.ctypes.data),
+                               _stream(stream))
+    _check(st, "cfc_exact_small")
+    return f, c
+
+
+def lap_stats_reset():
+    lib().lap_stats_reset()
+
+
+def lap_stats_set_timing(on: bool):
+    lib().lap_stats_set_timing(1 if on else 0)
+
+
+def lap_stats_read() -> dict:
+    s = Stats()
+    _check(lib().lap_stats_read(C.byref(s)), "lap_stats_read")
+    return {"launches_total": int(s.launches_total),
+            "families": {name: {"launches": int(s.launches[i]), "ms": s.ms[i], "bytes": s.bytes[i]}
+                         for i, name in enumerate(KERNEL_FAMILIES)}}

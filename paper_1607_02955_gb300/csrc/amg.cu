@@ -1,0 +1,518 @@
+// Multigrid hierarchy of aggregation type (Sec. 3.1, Sec. 6.1: the paper's
+// LAMG coarsens by elimination of low-degree nodes and by aggregation driven
+// by an affinity measure; this build aggregates by parallel pairwise
+// matching on the edge strength s_ij = w_ij / max(D_ii, D_jj)).
+//
+// Per level: a few handshake rounds of locally-dominant-edge matching (each
+// unmatched node proposes its strongest unmatched neighbour; mutual
+// proposals pair up), leftover nodes join the aggregate of their strongest
+// matched neighbour, and `agg_passes` such passes are composed (two passes:
+// aggregates of about four nodes).  With the piecewise-constant
+// prolongation P of an aggregation, P^T L P is exactly the Laplacian of the
+// quotient graph (edge weights between aggregates summed, edges inside an
+// aggregate dropped), so the Galerkin operator is built by a sort-and-merge
+// of the aggregated edge list.  The coarsest level (n_c <= coarse_max) is
+// solved by the dense FP64 inverse of L_c + J/n_c, which equals L_c^+ on
+// zero-sum vectors.
+#include <algorithm>
+#include <cmath>
+
+#include "internal.h"
+
+struct lap_hierarchy;
+
+namespace cfc {
+
+namespace {
+
+int grid_for(int64_t work, int threads = kBlock) {
+    int64_t g = (work + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > 152 * 32) g = 152 * 32;
+    return (int)g;
+}
+
+int bits_for(int64_t n) {
+    int b = 1;
+    while ((int64_t(1) << b) < n) ++b;
+    return b;
+}
+
+#define GRID_LOOP(i, count) \
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (count); i += (int64_t)gridDim.x * blockDim.x)
+
+__device__ __forceinline__ uint32_t edge_hash(uint32_t a, uint32_t b) {
+    // symmetric in (a, b): the same edge gets the same tie-break from both ends
+    uint32_t lo = min(a, b), hi = max(a, b);
+    uint64_t x = ((uint64_t)lo << 32) | hi;
+    x ^= x >> 33;
+    x *= 0xff51afd7ed558ccdull;
+    x ^= x >> 33;
+    x *= 0xc4ceb9fe1a85ec53ull;
+    x ^= x >> 33;
+    return (uint32_t)x;
+}
+
+// priority of edge (i, j): strength first, then the hash
+__device__ __forceinline__ bool better(float s, uint32_t h, float bs, uint32_t bh) {
+    return s > bs || (s == bs && h > bh);
+}
+
+__global__ void k_propose(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                          const double *__restrict__ w, const double *__restrict__ deg, int32_t n,
+                          const int32_t *__restrict__ match, int32_t *__restrict__ prop) {
+    GRID_LOOP(i, n) {
+        if (match[i] >= 0) {
+            prop[i] = -1;
+            continue;
+        }
+        const double di = deg[i];
+        int32_t best = -1;
+        float bs = -1.f;
+        uint32_t bh = 0;
+        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            const int32_t j = col[e];
+            if (match[j] >= 0) continue;
+            const float s = (float)(w[e] / fmax(di, deg[j]));
+            const uint32_t h = edge_hash((uint32_t)i, (uint32_t)j);
+            if (best < 0 || better(s, h, bs, bh)) {
+                best = j;
+                bs = s;
+                bh = h;
+            }
+        }
+        prop[i] = best;
+    }
+}
+
+__global__ void k_accept(const int32_t *__restrict__ prop, int32_t n, int32_t *__restrict__ match) {
+    GRID_LOOP(i, n) {
+        const int32_t j = prop[i];
+        if (j >= 0 && prop[j] == (int32_t)i) match[i] = j;
+    }
+}
+
+// leader of each node's aggregate: min of a matched pair; a leftover joins
+// its strongest matched neighbour's pair; otherwise it stays alone
+__global__ void k_leaders(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                          const double *__restrict__ w, const double *__restrict__ deg, int32_t n,
+                          const int32_t *__restrict__ match, int32_t *__restrict__ leader,
+                          int32_t *__restrict__ is_leader) {
+    GRID_LOOP(i, n) {
+        const int32_t mi = match[i];
+        int32_t l;
+        if (mi >= 0) {
+            l = min((int32_t)i, mi);
+        } else {
+            const double di = deg[i];
+            int32_t best = -1;
+            float bs = -1.f;
+            uint32_t bh = 0;
+            for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+                const int32_t j = col[e];
+                if (match[j] < 0) continue;
+                const float s = (float)(w[e] / fmax(di, deg[j]));
+                const uint32_t h = edge_hash((uint32_t)i, (uint32_t)j);
+                if (best < 0 || better(s, h, bs, bh)) {
+                    best = j;
+                    bs = s;
+                    bh = h;
+                }
+            }
+            l = best >= 0 ? min(best, match[best]) : (int32_t)i;
+        }
+        leader[i] = l;
+        is_leader[i] = (l == (int32_t)i) ? 1 : 0;
+    }
+}
+
+__global__ void k_assign(const int32_t *__restrict__ leader, const int32_t *__restrict__ lid, int32_t n,
+                         int32_t *__restrict__ agg) {
+    GRID_LOOP(i, n) agg[i] = lid[leader[i]];
+}
+
+__global__ void k_compose(int32_t *__restrict__ agg, const int32_t *__restrict__ agg2, int32_t n) {
+    GRID_LOOP(i, n) agg[i] = agg2[agg[i]];
+}
+
+// Galerkin: flags of fine entries that cross aggregates
+__global__ void k_cross_flags(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, int32_t n,
+                              const int32_t *__restrict__ agg, int32_t *__restrict__ flag) {
+    GRID_LOOP(i, n) {
+        const int32_t I = agg[i];
+        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) flag[e] = (agg[col[e]] != I) ? 1 : 0;
+    }
+}
+
+__global__ void k_cross_emit(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, int32_t n,
+                             const int32_t *__restrict__ agg, const int32_t *__restrict__ flag,
+                             const int32_t *__restrict__ pos, int b, uint64_t *__restrict__ keys,
+                             uint32_t *__restrict__ vals) {
+    GRID_LOOP(i, n) {
+        const uint64_t I = (uint32_t)agg[i];
+        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            if (!flag[e]) continue;
+            keys[pos[e]] = (I << b) | (uint32_t)agg[col[e]];
+            vals[pos[e]] = (uint32_t)e;
+        }
+    }
+}
+
+__global__ void k_heads(const uint64_t *__restrict__ keys, int64_t len, int32_t *__restrict__ head) {
+    GRID_LOOP(i, len) head[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
+}
+
+__global__ void k_merge(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                        const int32_t *__restrict__ head, const int32_t *__restrict__ hpos, int64_t len, int b,
+                        const double *__restrict__ w, int32_t *__restrict__ col, double *__restrict__ wout,
+                        int32_t *__restrict__ rowcnt) {
+    GRID_LOOP(i, len) {
+        if (!head[i]) continue;
+        const uint64_t key = keys[i];
+        double s = 0.0;
+        for (int64_t j = i; j < len && keys[j] == key; ++j) s += w[vals[j]];
+        const int32_t o = hpos[i];
+        col[o] = (int32_t)(key & ((uint64_t(1) << b) - 1));
+        wout[o] = s;
+        atomicAdd(&rowcnt[key >> b], 1);
+    }
+}
+
+__global__ void k_set_last(int32_t *p, int32_t idx, int32_t v) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) p[idx] = v;
+}
+
+__global__ void k_row_sums(const int32_t *__restrict__ rowptr, const double *__restrict__ w, int32_t n,
+                           double *__restrict__ deg) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n;
+         r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        double s = 0.0;
+        for (int e = rowptr[r] + lane; e < rowptr[r + 1]; e += 32) s += w[e];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) deg[r] = s;
+    }
+}
+
+__global__ void k_iota_keys(const int32_t *__restrict__ agg, int32_t n, uint64_t *__restrict__ keys,
+                            uint32_t *__restrict__ vals, int32_t *__restrict__ cnt) {
+    GRID_LOOP(i, n) {
+        keys[i] = (uint32_t)agg[i];
+        vals[i] = (uint32_t)i;
+        atomicAdd(&cnt[agg[i]], 1);
+    }
+}
+
+__global__ void k_u32_to_i32(const uint32_t *__restrict__ a, int32_t *__restrict__ b, int32_t n) {
+    GRID_LOOP(i, n) b[i] = (int32_t)a[i];
+}
+
+// FP32 copies, inverse degrees, long-row flags
+__global__ void k_finish(const int32_t *__restrict__ rowptr, const double *__restrict__ w64,
+                         const double *__restrict__ deg64, int32_t n, int64_t nnz, float *__restrict__ w32,
+                         float *__restrict__ deg32, float *__restrict__ dinv32, double *__restrict__ dinv64,
+                         int32_t *__restrict__ nchunk) {
+    GRID_LOOP(e, nnz) w32[e] = (float)w64[e];
+    GRID_LOOP(i, n) {
+        const double d = deg64[i];
+        deg32[i] = (float)d;
+        dinv32[i] = (float)(1.0 / d);
+        dinv64[i] = 1.0 / d;
+        const int len = rowptr[i + 1] - rowptr[i];
+        nchunk[i] = len > kLongRow ? (len + kLongRow - 1) / kLongRow : 0;
+    }
+}
+
+__global__ void k_long_index(const int32_t *__restrict__ nchunk, int32_t n, int32_t *__restrict__ is_long) {
+    GRID_LOOP(i, n) is_long[i] = nchunk[i] > 0 ? 1 : 0;
+}
+
+__global__ void k_fill_chunks(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ nchunk,
+                              const int32_t *__restrict__ cfirst, const int32_t *__restrict__ lidx, int32_t n,
+                              int32_t *__restrict__ chunk_row, int32_t *__restrict__ chunk_begin,
+                              int32_t *__restrict__ chunk_long, int32_t *__restrict__ long_first) {
+    GRID_LOOP(i, n) {
+        const int c = nchunk[i];
+        if (!c) continue;
+        const int f = cfirst[i], l = lidx[i];
+        long_first[l] = f;
+        for (int t = 0; t < c; ++t) {
+            chunk_row[f + t] = (int32_t)i;
+            chunk_begin[f + t] = rowptr[i] + t * kLongRow;
+            chunk_long[f + t] = l;
+        }
+    }
+}
+
+// dense M = L_c + J/n_c
+__global__ void k_fill(double *__restrict__ M, int64_t count, double v) {
+    GRID_LOOP(t, count) M[t] = v;
+}
+
+__global__ void k_dense_scatter(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                const double *__restrict__ w, const double *__restrict__ deg, int32_t n,
+                                double *__restrict__ M) {
+    GRID_LOOP(i, n) {
+        M[i * (int64_t)n + i] += deg[i];
+        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) M[i * (int64_t)n + col[e]] -= w[e];
+    }
+}
+
+// In-place Gauss-Jordan inversion of an SPD matrix (no pivoting needed),
+// whole matrix in shared memory, one CTA.  Step k: scale row k by 1/a_kk
+// with the identity column stored in place, then eliminate column k from
+// every other row.  A pivot <= 0 flags a singular (disconnected) matrix.
+__global__ void __launch_bounds__(1024) k_gj_smem(double *__restrict__ A, int n, int *__restrict__ flag) {
+    extern __shared__ double sm[];
+    double *a = sm;           // n*n
+    double *fc = sm + n * n;  // column k saved
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) a[t] = A[t];
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        const double akk = a[k * n + k];
+        if (!(akk > 0.0)) {
+            if (threadIdx.x == 0) atomicOr(flag, 1);
+            return;
+        }
+        const double piv = 1.0 / akk;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) fc[i] = a[i * n + k];
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += blockDim.x) a[k * n + j] = (j == k ? 1.0 : a[k * n + j]) * piv;
+        __syncthreads();
+        for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+            const int i = t / n, j = t - (t / n) * n;
+            if (i == k) continue;
+            const double cur = (j == k) ? 0.0 : a[t];
+            a[t] = cur - fc[i] * a[k * n + j];
+        }
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) A[t] = a[t];
+}
+
+// global-memory Gauss-Jordan: two launches per pivot
+__global__ void k_gj_pivot(const double *__restrict__ A, int n, int k, double *__restrict__ rowk,
+                           double *__restrict__ colk, int *__restrict__ flag) {
+    const double akk = A[(int64_t)k * n + k];
+    const double piv = akk > 0.0 ? 1.0 / akk : 0.0;
+    if (!(akk > 0.0) && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(flag, 1);
+    GRID_LOOP(j, n) {
+        rowk[j] = (j == k ? 1.0 : A[(int64_t)k * n + j]) * piv;
+        colk[j] = (j == k) ? 0.0 : A[(int64_t)j * n + k];
+    }
+}
+
+__global__ void k_gj_update(double *__restrict__ A, int n, int k, const double *__restrict__ rowk,
+                            const double *__restrict__ colk) {
+    GRID_LOOP(t, (int64_t)n * n) {
+        const int64_t i = t / n, j = t - i * n;
+        if (i == k) {
+            A[t] = rowk[j];
+        } else {
+            const double cur = (j == k) ? 0.0 : A[t];
+            A[t] = cur - colk[i] * rowk[j];
+        }
+    }
+}
+
+struct Graph64 {
+    int32_t n = 0;
+    int64_t nnz = 0;
+    DBuf<int32_t> rowptr, col;
+    DBuf<double> w, deg;
+};
+
+// one pairwise-matching pass: agg[n], returns the number of aggregates
+int32_t pairwise_pass(const int32_t *rowptr, const int32_t *col, const double *w, const double *deg, int32_t n,
+                      int rounds, int32_t *agg, cudaStream_t s) {
+    DBuf<int32_t> match(n, s), prop(n, s), leader(n, s), isl(n, s), lid(n, s);
+    CFC_CUDA(cudaMemsetAsync(match.get(), 0xff, n * sizeof(int32_t), s));
+    for (int r = 0; r < rounds; ++r) {
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_propose, grid_for(n), kBlock, 0, rowptr, col, w, deg, n, match.get(),
+                   prop.get());
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_accept, grid_for(n), kBlock, 0, prop.get(), n, match.get());
+    }
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_leaders, grid_for(n), kBlock, 0, rowptr, col, w, deg, n, match.get(),
+               leader.get(), isl.get());
+    const int64_t nc = scan_exclusive_i32(isl.get(), lid.get(), n, s);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_assign, grid_for(n), kBlock, 0, leader.get(), lid.get(), n, agg);
+    return (int32_t)nc;
+}
+
+// quotient graph of (rowptr, col, w) under agg (nc aggregates)
+void contract(const int32_t *rowptr, const int32_t *col, const double *w, int32_t n, int64_t nnz,
+              const int32_t *agg, int32_t nc, bool persistent, Graph64 &out, cudaStream_t s) {
+    DBuf<int32_t> flag(nnz, s), pos(nnz, s);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_cross_flags, grid_for(n), kBlock, 0, rowptr, col, n, agg, flag.get());
+    const int64_t len = scan_exclusive_i32(flag.get(), pos.get(), nnz, s);
+    const int b = bits_for(nc);
+    out.n = nc;
+    auto alloc_i = [&](DBuf<int32_t> &d, size_t c) { persistent ? d.alloc_persistent(c) : d.alloc(c, s); };
+    auto alloc_d = [&](DBuf<double> &d, size_t c) { persistent ? d.alloc_persistent(c) : d.alloc(c, s); };
+    alloc_i(out.rowptr, nc + 1);
+    alloc_d(out.deg, nc);
+    DBuf<int32_t> rowcnt(nc + 1, s);
+    rowcnt.zero(s);
+    if (len == 0) {
+        out.nnz = 0;
+        alloc_i(out.col, 1);
+        alloc_d(out.w, 1);
+        CFC_CUDA(cudaMemsetAsync(out.rowptr.get(), 0, (nc + 1) * sizeof(int32_t), s));
+        CFC_CUDA(cudaMemsetAsync(out.deg.get(), 0, nc * sizeof(double), s));
+        return;
+    }
+    DBuf<uint64_t> keys(len, s);
+    DBuf<uint32_t> vals(len, s);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_cross_emit, grid_for(n), kBlock, 0, rowptr, col, n, agg, flag.get(),
+               pos.get(), b, keys.get(), vals.get());
+    flag.release();
+    pos.release();
+    radix_sort_pairs(keys.get(), vals.get(), len, 2 * b, s);
+    DBuf<int32_t> head(len, s), hpos(len, s);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_heads, grid_for(len), kBlock, 0, keys.get(), len, head.get());
+    const int64_t cnnz = scan_exclusive_i32(head.get(), hpos.get(), len, s);
+    out.nnz = cnnz;
+    alloc_i(out.col, cnnz);
+    alloc_d(out.w, cnnz);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_merge, grid_for(len), kBlock, 0, keys.get(), vals.get(), head.get(),
+               hpos.get(), len, b, w, out.col.get(), out.w.get(), rowcnt.get());
+    scan_exclusive_i32(rowcnt.get(), out.rowptr.get(), nc, s);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_set_last, 1, 1, 0, out.rowptr.get(), nc, (int32_t)cnnz);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_row_sums, grid_for(32 * (int64_t)nc), kBlock, 0, out.rowptr.get(),
+               out.w.get(), nc, out.deg.get());
+}
+
+}  // namespace
+
+void finish_level(Level &L, cudaStream_t s) {
+    const int32_t n = L.n;
+    const int64_t nnz = L.nnz;
+    L.w32.alloc_persistent(std::max<int64_t>(nnz, 1));
+    L.deg32.alloc_persistent(n);
+    L.dinv32.alloc_persistent(n);
+    L.dinv64.alloc_persistent(n);
+    DBuf<int32_t> nchunk(n, s), cfirst(n, s), isl(n, s), lidx(n, s);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_finish, grid_for(std::max<int64_t>(nnz, n)), kBlock, 0, L.rowptr.get(),
+               L.w64.get(), L.deg64.get(), n, nnz, L.w32.get(), L.deg32.get(), L.dinv32.get(), L.dinv64.get(),
+               nchunk.get());
+    L.n_chunks = (int32_t)scan_exclusive_i32(nchunk.get(), cfirst.get(), n, s);
+    if (L.n_chunks == 0) {
+        L.n_long = 0;
+        return;
+    }
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_long_index, grid_for(n), kBlock, 0, nchunk.get(), n, isl.get());
+    L.n_long = (int32_t)scan_exclusive_i32(isl.get(), lidx.get(), n, s);
+    L.chunk_row.alloc_persistent(L.n_chunks);
+    L.chunk_begin.alloc_persistent(L.n_chunks);
+    L.chunk_long.alloc_persistent(L.n_chunks);
+    L.long_first.alloc_persistent(L.n_long + 1);
+    L.long_count.alloc_persistent((size_t)L.n_long * kMaxTiles);
+    L.long_count.zero(s);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_fill_chunks, grid_for(n), kBlock, 0, L.rowptr.get(), nchunk.get(),
+               cfirst.get(), lidx.get(), n, L.chunk_row.get(), L.chunk_begin.get(), L.chunk_long.get(),
+               L.long_first.get());
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_set_last, 1, 1, 0, L.long_first.get(), L.n_long, L.n_chunks);
+}
+
+void dense_spd_inverse_small(double *A, int n, int *d_flag, cudaStream_t s) {
+    const size_t smem = (size_t)(n * n + n) * sizeof(double);
+    CFC_CUDA(cudaFuncSetAttribute(k_gj_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_gj_smem, 1, 1024, smem, A, n, d_flag);
+}
+
+void dense_spd_inverse_large(double *A, int n, int *d_flag, cudaStream_t s) {
+    DBuf<double> rowk(n, s), colk(n, s);
+    for (int k = 0; k < n; ++k) {
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_gj_pivot, grid_for(n), kBlock, 0, A, n, k, rowk.get(), colk.get(),
+                   d_flag);
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_gj_update, grid_for((int64_t)n * n), kBlock, 0, A, n, k, rowk.get(),
+                   colk.get());
+    }
+}
+
+void build_dense(const int32_t *rowptr, const int32_t *col, const double *w, const double *deg, int32_t n,
+                 double *M, cudaStream_t s) {
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_fill, grid_for((int64_t)n * n), kBlock, 0, M, (int64_t)n * n, 1.0 / n);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_dense_scatter, grid_for(n), kBlock, 0, rowptr, col, w, deg, n, M);
+}
+
+void build_levels(lap_hierarchy &h, Csr64 &fine, const lap_hier_opts_t &o, cudaStream_t s) {
+    h.lv.clear();
+    h.lv.emplace_back();
+    {
+        Level &L0 = h.lv.back();
+        L0.n = fine.n;
+        L0.nnz = fine.nnz;
+        L0.rowptr = std::move(fine.rowptr);
+        L0.col = std::move(fine.col);
+        L0.w64 = std::move(fine.w);
+        L0.deg64 = std::move(fine.deg);
+    }
+    const int coarse_max = std::min(256, std::max(2, o.coarse_max));
+    const int max_levels = std::max(1, std::min(32, o.max_levels));
+    while ((int)h.lv.size() < max_levels && h.lv.back().n > coarse_max) {
+        Level &F = h.lv.back();
+        const int32_t n = F.n;
+        DBuf<int32_t> agg;
+        agg.alloc_persistent(n);
+        int32_t nc = pairwise_pass(F.rowptr.get(), F.col.get(), F.w64.get(), F.deg64.get(), n,
+                                   std::max(1, o.match_rounds), agg.get(), s);
+        for (int p = 1; p < o.agg_passes && nc > coarse_max; ++p) {
+            Graph64 mid;
+            contract(F.rowptr.get(), F.col.get(), F.w64.get(), n, F.nnz, agg.get(), nc, false, mid, s);
+            DBuf<int32_t> agg2(nc, s);
+            const int32_t nc2 = pairwise_pass(mid.rowptr.get(), mid.col.get(), mid.w.get(), mid.deg.get(), nc,
+                                              std::max(1, o.match_rounds), agg2.get(), s);
+            CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_compose, grid_for(n), kBlock, 0, agg.get(), agg2.get(), n);
+            nc = nc2;
+        }
+        if (nc >= n || (double)nc > 0.9 * n) break;  // coarsening stalled
+        Graph64 C;
+        contract(F.rowptr.get(), F.col.get(), F.w64.get(), n, F.nnz, agg.get(), nc, true, C, s);
+        // members of each aggregate in ascending node order (stable sort by aggregate)
+        {
+            DBuf<uint64_t> keys(n, s);
+            DBuf<uint32_t> vals(n, s);
+            DBuf<int32_t> cnt(nc + 1, s);
+            cnt.zero(s);
+            CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_iota_keys, grid_for(n), kBlock, 0, agg.get(), n, keys.get(),
+                       vals.get(), cnt.get());
+            radix_sort_pairs(keys.get(), vals.get(), n, bits_for(nc), s);
+            F.mem.alloc_persistent(n);
+            F.mem_ptr.alloc_persistent(nc + 1);
+            CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_u32_to_i32, grid_for(n), kBlock, 0, vals.get(), F.mem.get(), n);
+            scan_exclusive_i32(cnt.get(), F.mem_ptr.get(), nc, s);
+            CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_set_last, 1, 1, 0, F.mem_ptr.get(), nc, n);
+        }
+        F.agg = std::move(agg);
+        Level Cl;
+        Cl.n = nc;
+        Cl.nnz = C.nnz;
+        Cl.rowptr = std::move(C.rowptr);
+        Cl.col = std::move(C.col);
+        Cl.w64 = std::move(C.w);
+        Cl.deg64 = std::move(C.deg);
+        h.lv.push_back(std::move(Cl));
+    }
+    for (auto &L : h.lv) finish_level(L, s);
+    // dense coarsest solve
+    Level &Lc = h.lv.back();
+    h.coarse_n = 0;
+    if (Lc.n <= 256) {
+        const int nc = Lc.n;
+        h.coarse_inv.alloc_persistent((size_t)nc * nc);
+        build_dense(Lc.rowptr.get(), Lc.col.get(), Lc.w64.get(), Lc.deg64.get(), nc, h.coarse_inv.get(), s);
+        DBuf<int> flag(1, s);
+        flag.zero(s);
+        if (nc <= 160) dense_spd_inverse_small(h.coarse_inv.get(), nc, flag.get(), s);
+        else dense_spd_inverse_large(h.coarse_inv.get(), nc, flag.get(), s);
+        int hf = 0;
+        CFC_CUDA(cudaMemcpyAsync(&hf, flag.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+        CFC_CUDA(cudaStreamSynchronize(s));
+        CFC_REQUIRE(hf == 0, LAP_ENOTCONN, "coarsest operator singular: graph not connected");
+        h.coarse_n = nc;
+    }
+}
+
+}  // namespace cfc

@@ -1,0 +1,345 @@
+// The C ABI (include/cfc_gb300.h): argument checks, error translation,
+// hierarchy handles, and the launch counters / event timers.
+#include <atomic>
+#include <chrono>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+namespace cfc {
+
+namespace {
+thread_local std::string t_last_error;
+
+// ---------------------------------------------------------------- stats
+std::atomic<uint64_t> g_launches_total{0};
+std::atomic<uint64_t> g_launches[LAP_KF_COUNT];
+std::atomic<int> g_timing{0};
+
+struct Pending {
+    int family;
+    double bytes;
+    cudaEvent_t a, b;
+};
+std::mutex g_mu;
+std::vector<Pending> g_pending;
+std::vector<cudaEvent_t> g_free_events;
+double g_ms[LAP_KF_COUNT];
+double g_bytes[LAP_KF_COUNT];
+
+cudaEvent_t get_event() {
+    if (!g_free_events.empty()) {
+        cudaEvent_t e = g_free_events.back();
+        g_free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    CFC_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+// folds completed timings into the totals (caller holds g_mu)
+void drain_locked() {
+    for (auto &p : g_pending) {
+        float ms = 0.f;
+        CFC_CUDA(cudaEventSynchronize(p.b));
+        CFC_CUDA(cudaEventElapsedTime(&ms, p.a, p.b));
+        g_ms[p.family] += ms;
+        g_bytes[p.family] += p.bytes;
+        g_free_events.push_back(p.a);
+        g_free_events.push_back(p.b);
+    }
+    g_pending.clear();
+}
+}  // namespace
+
+void set_last_error(const std::string &s) { t_last_error = s; }
+
+void count_launch() { g_launches_total.fetch_add(1, std::memory_order_relaxed); }
+
+LaunchScope::LaunchScope(int fam, cudaStream_t s, double algorithmic_bytes)
+    : family(fam), stream(s), bytes(algorithmic_bytes) {
+    g_launches_total.fetch_add(1, std::memory_order_relaxed);
+    g_launches[fam].fetch_add(1, std::memory_order_relaxed);
+    if (g_timing.load(std::memory_order_relaxed)) {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (g_pending.size() > 65536) drain_locked();
+        start = get_event();
+        if (cudaEventRecord(start, s) != cudaSuccess) {
+            cudaGetLastError();
+            g_free_events.push_back(start);
+            start = nullptr;
+        }
+    }
+}
+
+LaunchScope::~LaunchScope() {
+    if (!start) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaEvent_t stop = nullptr;
+    if (!g_free_events.empty()) {
+        stop = g_free_events.back();
+        g_free_events.pop_back();
+    } else if (cudaEventCreate(&stop) != cudaSuccess) {
+        cudaGetLastError();
+        g_free_events.push_back(start);
+        return;
+    }
+    if (cudaEventRecord(stop, stream) != cudaSuccess) {
+        cudaGetLastError();
+        g_free_events.push_back(start);
+        g_free_events.push_back(stop);
+        return;
+    }
+    g_pending.push_back(Pending{family, bytes, start, stop});
+}
+
+bool is_device_pointer(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+LevelView view(const Level &L) {
+    LevelView v;
+    v.n = L.n;
+    v.rowptr = L.rowptr.get();
+    v.col = L.col.get();
+    v.w32 = L.w32.get();
+    v.deg32 = L.deg32.get();
+    v.dinv32 = L.dinv32.get();
+    v.w64 = L.w64.get();
+    v.deg64 = L.deg64.get();
+    v.dinv64 = L.dinv64.get();
+    v.n_chunks = L.n_chunks;
+    v.n_long = L.n_long;
+    v.chunk_row = L.chunk_row.get();
+    v.chunk_begin = L.chunk_begin.get();
+    v.chunk_long = L.chunk_long.get();
+    v.long_first = L.long_first.get();
+    v.long_count = L.long_count.get();
+    return v;
+}
+
+template <class F>
+lap_status_t guard(F &&f) {
+    try {
+        t_last_error.clear();
+        return f();
+    } catch (const Error &e) {
+        t_last_error = e.what;
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        t_last_error = "host allocation failed";
+        return LAP_ENOMEM;
+    } catch (...) {
+        t_last_error = "unknown error";
+        return LAP_ECUDA;
+    }
+}
+
+}  // namespace cfc
+
+using namespace cfc;
+
+extern "C" {
+
+void lap_default_hier_opts(lap_hier_opts_t *o) {
+    if (!o) return;
+    o->coarse_max = 64;
+    o->max_levels = 24;
+    o->agg_passes = 2;
+    o->match_rounds = 4;
+}
+
+void lap_default_solve_opts(lap_solve_opts_t *o) {
+    if (!o) return;
+    o->precision = LAP_FP32_REFINED;
+    o->tol = 1e-8;
+    o->max_outer = 8;
+    o->max_inner = 200;
+    o->inner_tol = 1e-4;
+    o->k_tile = 0;
+    o->smoother = LAP_SMOOTH_CHEBYSHEV;
+    o->nu_pre = 2;
+    o->nu_post = 2;
+    o->check_every = 4;
+    o->levels_used = 0;
+}
+
+const char *lap_status_string(lap_status_t s) {
+    switch (s) {
+        case LAP_OK: return "LAP_OK";
+        case LAP_EINVAL: return "LAP_EINVAL: invalid argument";
+        case LAP_ENOTCONN: return "LAP_ENOTCONN: graph is not connected";
+        case LAP_ENOMEM: return "LAP_ENOMEM: out of memory";
+        case LAP_ENOCONV: return "LAP_ENOCONV: iteration cap reached before the tolerance";
+        case LAP_ECUDA: return "LAP_ECUDA: CUDA error";
+        case LAP_EBUDGET: return "LAP_EBUDGET: request exceeds a documented maximum";
+        case LAP_ENOTIMPL: return "LAP_ENOTIMPL: not implemented";
+    }
+    return "unknown status";
+}
+
+const char *lap_last_error(void) { return t_last_error.c_str(); }
+
+lap_status_t lap_build_hierarchy(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const double *w,
+                                 const lap_hier_opts_t *opts, void *stream, lap_hierarchy_t **out) {
+    return guard([&]() -> lap_status_t {
+        CFC_REQUIRE(out, LAP_EINVAL, "out must not be NULL");
+        *out = nullptr;
+        lap_hier_opts_t o;
+        lap_default_hier_opts(&o);
+        if (opts) o = *opts;
+        CFC_REQUIRE(o.agg_passes >= 1 && o.agg_passes <= 4, LAP_EINVAL, "agg_passes must be 1..4");
+        cudaStream_t s = (cudaStream_t)stream;
+        auto *h = new lap_hierarchy();
+        try {
+            CFC_CUDA(cudaGetDevice(&h->device));
+            cudaEvent_t e0, e1;
+            CFC_CUDA(cudaEventCreate(&e0));
+            CFC_CUDA(cudaEventCreate(&e1));
+            CFC_CUDA(cudaEventRecord(e0, s));
+            Csr64 g;
+            ingest(n, m, src, dst, w, s, g);
+            h->n = g.n;
+            h->m = g.m;
+            h->eid = std::move(g.eid);
+            build_levels(*h, g, o, s);
+            CFC_CUDA(cudaEventRecord(e1, s));
+            CFC_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CFC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            h->setup_ms = ms;
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            CFC_CUDA(cudaStreamSynchronize(s));
+        } catch (...) {
+            cudaStreamSynchronize(s);
+            delete h;
+            throw;
+        }
+        *out = h;
+        return LAP_OK;
+    });
+}
+
+void lap_hierarchy_destroy(lap_hierarchy_t *h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    delete h;
+}
+
+lap_status_t lap_hierarchy_info(const lap_hierarchy_t *h, lap_hier_info_t *info) {
+    return guard([&]() -> lap_status_t {
+        CFC_REQUIRE(h && info, LAP_EINVAL, "NULL argument");
+        std::memset(info, 0, sizeof(*info));
+        info->n = h->n;
+        info->m = h->m;
+        info->levels = (int32_t)h->lv.size();
+        info->coarse_n = h->coarse_n;
+        for (size_t l = 0; l < h->lv.size() && l < 32; ++l) {
+            info->level_n[l] = h->lv[l].n;
+            info->level_nnz[l] = h->lv[l].nnz;
+        }
+        info->setup_ms = h->setup_ms;
+        return LAP_OK;
+    });
+}
+
+static lap_solve_opts_t resolve_opts(const lap_solve_opts_t *o) {
+    lap_solve_opts_t r;
+    lap_default_solve_opts(&r);
+    if (o) r = *o;
+    return r;
+}
+
+lap_status_t lap_solve_multi(lap_hierarchy_t *h, int32_t k, const double *B, double *X, const lap_solve_opts_t *o,
+                             void *stream, lap_solve_info_t *info) {
+    return guard([&]() -> lap_status_t {
+        CFC_REQUIRE(h, LAP_EINVAL, "NULL hierarchy");
+        return solve_multi(h, k, B, X, resolve_opts(o), (cudaStream_t)stream, info);
+    });
+}
+
+lap_status_t cfc_jl_rhs(lap_hierarchy_t *h, int32_t k, uint64_t seed, double *Y, void *stream) {
+    return guard([&]() -> lap_status_t {
+        CFC_REQUIRE(h && Y, LAP_EINVAL, "NULL argument");
+        CFC_REQUIRE(k >= 1 && k <= 4096, LAP_EINVAL, "need 1 <= k <= 4096");
+        CFC_REQUIRE(is_device_pointer(Y), LAP_EINVAL, "Y must be a device pointer");
+        jl_rhs(h, k, k, seed, Y, (cudaStream_t)stream);
+        return LAP_OK;
+    });
+}
+
+lap_status_t cfc_farness_jl(lap_hierarchy_t *h, int32_t k, double eps, uint64_t seed, int32_t q,
+                            const int32_t *nodes, double *farness, const lap_solve_opts_t *o, void *stream) {
+    return guard([&]() -> lap_status_t {
+        CFC_REQUIRE(h, LAP_EINVAL, "NULL hierarchy");
+        return farness_jl(h, k, eps, seed, q, nodes, farness, resolve_opts(o), (cudaStream_t)stream);
+    });
+}
+
+lap_status_t cfc_sample_pivots(lap_hierarchy_t *h, int32_t n_pivots, uint64_t seed, int32_t *pivots,
+                               void *stream) {
+    return guard([&]() -> lap_status_t {
+        CFC_REQUIRE(h, LAP_EINVAL, "NULL hierarchy");
+        return pivots_api(h, n_pivots, seed, pivots, (cudaStream_t)stream);
+    });
+}
+
+lap_status_t cfc_farness_sampled(lap_hierarchy_t *h, int32_t n_pivots, uint64_t seed, int32_t q,
+                                 const int32_t *nodes, double *farness, const lap_solve_opts_t *o, void *stream) {
+    return guard([&]() -> lap_status_t {
+        CFC_REQUIRE(h, LAP_EINVAL, "NULL hierarchy");
+        return farness_sampled(h, n_pivots, seed, q, nodes, farness, resolve_opts(o), (cudaStream_t)stream);
+    });
+}
+
+lap_status_t cfc_exact_small(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const double *w,
+                             double *farness, double *closeness, void *stream) {
+    return guard([&]() -> lap_status_t {
+        return exact_small(n, m, src, dst, w, farness, closeness, (cudaStream_t)stream);
+    });
+}
+
+void lap_stats_reset(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    try {
+        drain_locked();
+    } catch (...) {
+    }
+    g_launches_total.store(0);
+    for (int f = 0; f < LAP_KF_COUNT; ++f) {
+        g_launches[f].store(0);
+        g_ms[f] = 0;
+        g_bytes[f] = 0;
+    }
+}
+
+void lap_stats_set_timing(int32_t on) { g_timing.store(on ? 1 : 0); }
+
+lap_status_t lap_stats_read(lap_stats_t *out) {
+    return guard([&]() -> lap_status_t {
+        CFC_REQUIRE(out, LAP_EINVAL, "NULL argument");
+        std::lock_guard<std::mutex> lk(g_mu);
+        drain_locked();
+        out->launches_total = g_launches_total.load();
+        for (int f = 0; f < LAP_KF_COUNT; ++f) {
+            out->launches[f] = g_launches[f].load();
+            out->ms[f] = g_ms[f];
+            out->bytes[f] = g_bytes[f];
+        }
+        return LAP_OK;
+    });
+}
+
+}  // extern "C"

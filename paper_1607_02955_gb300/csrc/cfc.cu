@@ -1,0 +1,426 @@
+// Current-flow closeness estimators on top of the block solver:
+//  * projection / JL estimator (Sec. 5.2, Algorithm 1): right-hand sides
+//    Y = Q W^{1/2} B generated on the device, k solves, farness reduction;
+//  * sampling estimator (Sec. 5.1): pivots by Floyd's algorithm on the
+//    device, column solves, unbiased farness (n/k) sum_s d_ER(v, s);
+//  * exact farness of small graphs from the dense pseudoinverse (Sec. 4).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+
+namespace cfc {
+
+namespace {
+
+constexpr uint64_t kTagJL = 0x4A4C;
+constexpr uint64_t kTagSample = 0x534D50;
+
+// Philox4x64-10 (Salmon et al., SC'11): 10 rounds of two 64x64->128-bit
+// multiplications, xor with the round key and a word permutation; the key
+// advances by the Weyl constants after each round.
+struct U64x4 {
+    uint64_t v[4];
+};
+__device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3, uint64_t k0,
+                                               uint64_t k1) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+        const uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+        const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += W0;
+        k1 += W1;
+    }
+    return U64x4{{c0, c1, c2, c3}};
+}
+
+#define GRID_LOOP(i, count) \
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (count); i += (int64_t)gridDim.x * blockDim.x)
+
+int grid_for(int64_t work, int threads = kBlock) {
+    int64_t g = (work + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > 152 * 32) g = 152 * 32;
+    return (int)g;
+}
+
+// 32 sign bits of Q for rows cb*32 .. cb*32+31 of edge id e: row i uses bit
+// (i % 64) of word (i % 256) / 64 of Philox(counter (e, i / 256, 0, 0), key (seed, JL))
+__device__ __forceinline__ uint32_t jl_bits32(uint64_t e, int cb, uint64_t seed) {
+    const int i0 = cb * 32;
+    const U64x4 r = philox4x64_10(e, (uint64_t)(i0 / 256), 0, 0, seed, kTagJL);
+    const uint64_t word = r.v[(i0 % 256) / 64];
+    return (uint32_t)(word >> (i0 % 64));
+}
+
+// sum over entries [e0, e1) of row u of sgn * sqrt(w) * q_{i,e} for 32 rows of Q
+__device__ __forceinline__ void jl_accum(const int32_t *col, const int32_t *eid, const double *w, int u, int e0,
+                                         int e1, int cb, uint64_t seed, double scale, double (&acc)[32]) {
+    for (int e = e0; e < e1; ++e) {
+        const int v = col[e];
+        const double sw = (u < v ? scale : -scale) * sqrt(w[e]);
+        const uint32_t bits = jl_bits32((uint64_t)eid[e], cb, seed);
+#pragma unroll
+        for (int t = 0; t < 32; ++t) acc[t] += ((bits >> t) & 1u) ? -sw : sw;
+    }
+}
+
+__global__ void k_jl_short(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                           const int32_t *__restrict__ eid, const double *__restrict__ w, int32_t n, int k, int ld,
+                           uint64_t seed, double scale, double *__restrict__ Y) {
+    const int ncb = (ld + 31) / 32;
+    GRID_LOOP(t, (int64_t)n * ncb) {
+        const int u = (int)(t / ncb), cb = (int)(t - (int64_t)u * ncb);
+        const int e0 = rowptr[u], e1 = rowptr[u + 1];
+        if (e1 - e0 > kLongRow) continue;
+        double acc[32];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) acc[q] = 0.0;
+        jl_accum(col, eid, w, u, e0, e1, cb, seed, scale, acc);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            const int c = cb * 32 + q;
+            if (c < ld) Y[(size_t)u * ld + c] = c < k ? acc[q] : 0.0;
+        }
+    }
+}
+
+__global__ void k_jl_chunks(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                            const int32_t *__restrict__ eid, const double *__restrict__ w,
+                            const int32_t *__restrict__ chunk_row, const int32_t *__restrict__ chunk_begin,
+                            int32_t n_chunks, int ld, uint64_t seed, double scale, double *__restrict__ part) {
+    const int ncb = (ld + 31) / 32;
+    GRID_LOOP(t, (int64_t)n_chunks * ncb) {
+        const int ch = (int)(t / ncb), cb = (int)(t - (int64_t)ch * ncb);
+        const int u = chunk_row[ch];
+        const int e0 = chunk_begin[ch], e1 = min(e0 + kLongRow, rowptr[u + 1]);
+        double acc[32];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) acc[q] = 0.0;
+        jl_accum(col, eid, w, u, e0, e1, cb, seed, scale, acc);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) part[((size_t)ch * ncb + cb) * 32 + q] = acc[q];
+    }
+}
+
+__global__ void k_jl_long(const int32_t *__restrict__ chunk_row, const int32_t *__restrict__ long_first,
+                          int32_t n_long, int k, int ld, const double *__restrict__ part, double *__restrict__ Y) {
+    const int ncb = (ld + 31) / 32;
+    GRID_LOOP(t, (int64_t)n_long * ncb) {
+        const int li = (int)(t / ncb), cb = (int)(t - (int64_t)li * ncb);
+        const int f0 = long_first[li], f1 = long_first[li + 1];
+        const int u = chunk_row[f0];
+        for (int q = 0; q < 32; ++q) {
+            const int c = cb * 32 + q;
+            if (c >= ld) break;
+            double s = 0.0;
+            for (int f = f0; f < f1; ++f) s += part[((size_t)f * ncb + cb) * 32 + q];
+            Y[(size_t)u * ld + c] = c < k ? s : 0.0;
+        }
+    }
+}
+
+// per-column sums S_i = sum_w Z_wi and T_i = sum_w Z_wi^2 (FP64, fixed order):
+// block partials, then one warp per column
+constexpr int kRedRows = 8;
+__global__ void k_colsum2_part(const double *__restrict__ Z, int64_t n, int k, int ld, double *__restrict__ part) {
+    // blockDim = (32, kRedRows); grid = (P, ceil(k/32))
+    const int c = blockIdx.y * 32 + threadIdx.x;
+    double s = 0.0, t = 0.0;
+    if (c < k) {
+        for (int64_t i = (int64_t)blockIdx.x * kRedRows + threadIdx.y; i < n; i += (int64_t)gridDim.x * kRedRows) {
+            const double z = Z[i * ld + c];
+            s += z;
+            t += z * z;
+        }
+    }
+    __shared__ double ss[kRedRows][32], tt[kRedRows][32];
+    ss[threadIdx.y][threadIdx.x] = s;
+    tt[threadIdx.y][threadIdx.x] = t;
+    __syncthreads();
+    if (threadIdx.y == 0 && c < k) {
+        double a = 0.0, b = 0.0;
+        for (int r = 0; r < kRedRows; ++r) {
+            a += ss[r][threadIdx.x];
+            b += tt[r][threadIdx.x];
+        }
+        part[((size_t)c * gridDim.x + blockIdx.x) * 2 + 0] = a;
+        part[((size_t)c * gridDim.x + blockIdx.x) * 2 + 1] = b;
+    }
+}
+
+__global__ void k_colsum2_final(const double *__restrict__ part, int P, int k, double *__restrict__ S,
+                                double *__restrict__ T) {
+    const int c = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (c >= k) return;
+    double a = 0.0, b = 0.0;
+    for (int p = lane; p < P; p += 32) {
+        a += part[((size_t)c * P + p) * 2 + 0];
+        b += part[((size_t)c * P + p) * 2 + 1];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+        S[c] = a;
+        T[c] = b;
+    }
+}
+
+// f(v) = sum_i [n Z_vi^2 - 2 Z_vi S_i + T_i]: one warp per query node
+__global__ void k_jl_farness(const double *__restrict__ Z, int64_t n, int k, int ld, const double *__restrict__ S,
+                             const double *__restrict__ T, const int32_t *__restrict__ nodes, int q,
+                             double *__restrict__ f) {
+    const int t = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (t >= q) return;
+    const int64_t v = nodes[t];
+    double a = 0.0;
+    for (int i = lane; i < k; i += 32) {
+        const double z = Z[v * ld + i];
+        a += (double)n * z * z - 2.0 * z * S[i] + T[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if (lane == 0) f[t] = a;
+}
+
+__global__ void k_check_nodes(const int32_t *__restrict__ nodes, int q, int32_t n, int32_t *__restrict__ bad) {
+    GRID_LOOP(t, q) {
+        if (nodes[t] < 0 || nodes[t] >= n) atomicOr(bad, 1);
+    }
+}
+
+// Floyd's algorithm (Bentley & Floyd 1987), one warp: step s draws
+// t uniform in [0, n - kk + s] and inserts t unless present, else the top
+// value n - kk + s.  Membership is tested by all lanes in parallel.
+__global__ void k_floyd(int64_t n, int kk, uint64_t seed, int32_t *__restrict__ out) {
+    extern __shared__ int32_t S[];
+    const int lane = threadIdx.x;
+    for (int s = 0; s < kk; ++s) {
+        const uint64_t j = (uint64_t)(n - kk + s);
+        int32_t tval = 0;
+        if (lane == 0) {
+            const U64x4 r = philox4x64_10((uint64_t)s, 0, 0, 0, seed, kTagSample);
+            tval = (int32_t)__umul64hi(r.v[0], j + 1);
+        }
+        tval = __shfl_sync(0xffffffffu, tval, 0);
+        bool found = false;
+        for (int u = lane; u < s; u += 32) found |= (S[u] == tval);
+        found = __any_sync(0xffffffffu, found);
+        if (lane == 0) S[s] = found ? (int32_t)j : tval;
+        __syncwarp();
+    }
+    // ascending order: rank of each element (values are distinct)
+    for (int a = lane; a < kk; a += 32) {
+        const int32_t x = S[a];
+        int rank = 0;
+        for (int b = 0; b < kk; ++b) rank += (S[b] < x) ? 1 : 0;
+        out[rank] = x;
+    }
+}
+
+// column c of B is e_{U_c}, U = [pivots..., query nodes...]
+__global__ void k_unit_columns(const int32_t *__restrict__ piv, int kk, const int32_t *__restrict__ nodes, int q,
+                               int ld, double *__restrict__ B) {
+    GRID_LOOP(c, kk + q) {
+        const int u = c < kk ? piv[c] : nodes[c - kk];
+        B[(size_t)u * ld + c] = 1.0;
+    }
+}
+
+// f^(v) = (n/k) sum_s [x_v(v) - x_v(s) - x_s(v) + x_s(s)]: one warp per query node
+__global__ void k_sample_farness(const double *__restrict__ X, int64_t n, int ld, const int32_t *__restrict__ piv,
+                                 int kk, const int32_t *__restrict__ nodes, int q, double *__restrict__ f) {
+    const int t = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (t >= q) return;
+    const int64_t v = nodes[t];
+    const int cv = kk + t;
+    const double xvv = X[v * ld + cv];
+    double a = 0.0;
+    for (int i = lane; i < kk; i += 32) {
+        const int64_t sv = piv[i];
+        if (sv == v) continue;  // d_ER(v, v) = 0
+        a += xvv - X[sv * ld + cv] - X[v * ld + i] + X[sv * ld + i];
+    }
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if (lane == 0) f[t] = a * ((double)n / kk);
+}
+
+// exact: f(v) = n L+_vv + tr L+ with L+ = M^{-1} - J/n
+__global__ void k_trace(const double *__restrict__ Minv, int n, double *__restrict__ tr) {
+    __shared__ double sm[1024];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += Minv[(size_t)i * n + i];
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) tr[0] = sm[0];
+}
+
+__global__ void k_exact_farness(const double *__restrict__ Minv, int n, const double *__restrict__ tr,
+                                double *__restrict__ f, double *__restrict__ c) {
+    GRID_LOOP(v, n) {
+        const double lpv = Minv[(size_t)v * n + v] - 1.0 / n;
+        const double trl = tr[0] - 1.0;
+        const double fv = (double)n * lpv + trl;
+        f[v] = fv;
+        if (c) c[v] = (double)(n - 1) / fv;
+    }
+}
+
+void copy_out(double *dst, const double *dsrc, size_t count, cudaStream_t s) {
+    const cudaMemcpyKind kind = is_device_pointer(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CFC_CUDA(cudaMemcpyAsync(dst, dsrc, count * sizeof(double), kind, s));
+}
+
+void copy_out_i32(int32_t *dst, const int32_t *dsrc, size_t count, cudaStream_t s) {
+    const cudaMemcpyKind kind = is_device_pointer(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CFC_CUDA(cudaMemcpyAsync(dst, dsrc, count * sizeof(int32_t), kind, s));
+}
+
+const int32_t *nodes_to_device(const int32_t *nodes, int q, int32_t n, DBuf<int32_t> &tmp, cudaStream_t s) {
+    CFC_REQUIRE(nodes, LAP_EINVAL, "nodes must not be NULL");
+    const int32_t *d = nodes;
+    if (!is_device_pointer(nodes)) {
+        tmp.alloc(q, s);
+        CFC_CUDA(cudaMemcpyAsync(tmp.get(), nodes, q * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        d = tmp.get();
+    }
+    DBuf<int32_t> bad(1, s);
+    bad.zero(s);
+    CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_check_nodes, grid_for(q), kBlock, 0, d, q, n, bad.get());
+    int32_t hb = 0;
+    CFC_CUDA(cudaMemcpyAsync(&hb, bad.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CFC_CUDA(cudaStreamSynchronize(s));
+    CFC_REQUIRE(hb == 0, LAP_EINVAL, "query node out of range");
+    return d;
+}
+
+}  // namespace
+
+void jl_rhs(lap_hierarchy *h, int k, int ld, uint64_t seed, double *Y, cudaStream_t s) {
+    const Level &L = h->lv[0];
+    const int n = L.n;
+    const int ncb = (ld + 31) / 32;
+    const double scale = 1.0 / std::sqrt((double)k);
+    const double bytes = (double)L.nnz * (4 + 4 + 8) + (double)n * 4 + (double)n * ld * 8;
+    CFC_LAUNCH(LAP_KF_CFC, s, bytes, k_jl_short, grid_for((int64_t)n * ncb, 128), 128, 0, L.rowptr.get(),
+               L.col.get(), h->eid.get(), L.w64.get(), n, k, ld, seed, scale, Y);
+    if (L.n_chunks > 0) {
+        DBuf<double> part((size_t)L.n_chunks * ncb * 32, s);
+        CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_jl_chunks, grid_for((int64_t)L.n_chunks * ncb, 128), 128, 0,
+                   L.rowptr.get(), L.col.get(), h->eid.get(), L.w64.get(), L.chunk_row.get(), L.chunk_begin.get(),
+                   L.n_chunks, ld, seed, scale, part.get());
+        CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_jl_long, grid_for((int64_t)L.n_long * ncb, 128), 128, 0,
+                   L.chunk_row.get(), L.long_first.get(), L.n_long, k, ld, part.get(), Y);
+    }
+}
+
+lap_status_t farness_jl(lap_hierarchy *h, int32_t k, double eps, uint64_t seed, int32_t q, const int32_t *nodes,
+                        double *farness, const lap_solve_opts_t &o, cudaStream_t s) {
+    const int64_t n = h->lv[0].n;
+    if (k <= 0) {
+        CFC_REQUIRE(eps > 0 && std::isfinite(eps), LAP_EINVAL, "k <= 0 needs eps > 0");
+        k = (int32_t)std::ceil(std::log((double)n) / (eps * eps));
+    }
+    CFC_REQUIRE(k >= 1 && k <= 4096, LAP_EINVAL, "need 1 <= k <= 4096");
+    CFC_REQUIRE(q >= 1 && q <= n, LAP_EINVAL, "need 1 <= q <= n");
+    CFC_REQUIRE(farness, LAP_EINVAL, "farness must not be NULL");
+    DBuf<int32_t> ntmp;
+    const int32_t *dn = nodes_to_device(nodes, q, (int32_t)n, ntmp, s);
+    DBuf<double> Y((size_t)n * k, s), Z((size_t)n * k, s);
+    jl_rhs(h, k, k, seed, Y.get(), s);
+    lap_status_t st = solve_multi(h, k, Y.get(), Z.get(), o, s, nullptr);
+    if (st != LAP_OK && st != LAP_ENOCONV) return st;
+    const int P = std::min<int64_t>(2 * num_sms_public(), (n + kRedRows - 1) / kRedRows);
+    DBuf<double> part((size_t)k * P * 2, s), S(k, s), T(k, s), f(q, s);
+    dim3 g1(P, (k + 31) / 32), b1(32, kRedRows);
+    CFC_LAUNCH(LAP_KF_CFC, s, (double)n * k * 8, k_colsum2_part, g1, b1, 0, Z.get(), n, k, k, part.get());
+    CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_colsum2_final, (k + 7) / 8, 256, 0, part.get(), P, k, S.get(), T.get());
+    CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_jl_farness, (q + 7) / 8, 256, 0, Z.get(), n, k, k, S.get(), T.get(), dn, q,
+               f.get());
+    copy_out(farness, f.get(), q, s);
+    CFC_CUDA(cudaStreamSynchronize(s));
+    return st;
+}
+
+void sample_pivots(int64_t n, int32_t kk, uint64_t seed, int32_t *dpiv, cudaStream_t s) {
+    CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_floyd, 1, 32, (size_t)kk * sizeof(int32_t), n, kk, seed, dpiv);
+}
+
+lap_status_t pivots_api(lap_hierarchy *h, int32_t kk, uint64_t seed, int32_t *pivots, cudaStream_t s) {
+    const int64_t n = h->lv[0].n;
+    CFC_REQUIRE(kk >= 1 && kk <= n && kk <= 8192, LAP_EINVAL, "need 1 <= n_pivots <= min(n, 8192)");
+    CFC_REQUIRE(pivots, LAP_EINVAL, "pivots must not be NULL");
+    DBuf<int32_t> d(kk, s);
+    sample_pivots(n, kk, seed, d.get(), s);
+    copy_out_i32(pivots, d.get(), kk, s);
+    CFC_CUDA(cudaStreamSynchronize(s));
+    return LAP_OK;
+}
+
+lap_status_t farness_sampled(lap_hierarchy *h, int32_t kk, uint64_t seed, int32_t q, const int32_t *nodes,
+                             double *farness, const lap_solve_opts_t &o, cudaStream_t s) {
+    const int64_t n = h->lv[0].n;
+    CFC_REQUIRE(kk >= 1 && kk <= n, LAP_EINVAL, "need 1 <= n_pivots <= n");
+    CFC_REQUIRE(q >= 1 && q <= n, LAP_EINVAL, "need 1 <= q <= n");
+    CFC_REQUIRE(kk + q <= 4096, LAP_EBUDGET, "n_pivots + q must be <= 4096 columns");
+    CFC_REQUIRE(farness, LAP_EINVAL, "farness must not be NULL");
+    DBuf<int32_t> ntmp;
+    const int32_t *dn = nodes_to_device(nodes, q, (int32_t)n, ntmp, s);
+    const int kc = kk + q;
+    DBuf<int32_t> piv(kk, s);
+    sample_pivots(n, kk, seed, piv.get(), s);
+    DBuf<double> B((size_t)n * kc, s), X((size_t)n * kc, s), f(q, s);
+    B.zero(s);
+    CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_unit_columns, grid_for(kc), kBlock, 0, piv.get(), kk, dn, q, kc, B.get());
+    lap_status_t st = solve_multi(h, kc, B.get(), X.get(), o, s, nullptr);
+    if (st != LAP_OK && st != LAP_ENOCONV) return st;
+    CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_sample_farness, (q + 7) / 8, 256, 0, X.get(), n, kc, piv.get(), kk, dn, q,
+               f.get());
+    copy_out(farness, f.get(), q, s);
+    CFC_CUDA(cudaStreamSynchronize(s));
+    return st;
+}
+
+lap_status_t exact_small(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const double *w,
+                         double *farness, double *closeness, cudaStream_t s) {
+    CFC_REQUIRE(n >= 2, LAP_EINVAL, "need n >= 2");
+    CFC_REQUIRE(n <= 16384, LAP_EBUDGET, "cfc_exact_small holds n x n doubles: n <= 16384");
+    CFC_REQUIRE(farness, LAP_EINVAL, "farness must not be NULL");
+    Csr64 g;
+    ingest(n, m, src, dst, w, s, g);
+    DBuf<double> M((size_t)n * n, s), tr(1, s), f(n, s), c(n, s);
+    build_dense(g.rowptr.get(), g.col.get(), g.w.get(), g.deg.get(), (int32_t)n, M.get(), s);
+    DBuf<int> flag(1, s);
+    flag.zero(s);
+    if (n <= 160) dense_spd_inverse_small(M.get(), (int)n, flag.get(), s);
+    else dense_spd_inverse_large(M.get(), (int)n, flag.get(), s);
+    int hf = 0;
+    CFC_CUDA(cudaMemcpyAsync(&hf, flag.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    CFC_CUDA(cudaStreamSynchronize(s));
+    CFC_REQUIRE(hf == 0, LAP_ENOTCONN, "L + J/n is singular: graph not connected");
+    CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_trace, 1, 1024, 0, M.get(), (int)n, tr.get());
+    CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_exact_farness, grid_for(n), kBlock, 0, M.get(), (int)n, tr.get(), f.get(),
+               closeness ? c.get() : nullptr);
+    copy_out(farness, f.get(), n, s);
+    if (closeness) copy_out(closeness, c.get(), n, s);
+    CFC_CUDA(cudaStreamSynchronize(s));
+    return LAP_OK;
+}
+
+}  // namespace cfc

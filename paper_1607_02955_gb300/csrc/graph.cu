@@ -1,0 +1,261 @@
+// Graph ingest (Sec. 2, Sec. 6.3): edge list -> symmetric CSR of the
+// adjacency weights of G, with self-loops dropped, edge directions ignored
+// and repeated pairs merged (weights summed: parallel conductances), the
+// degree vector D_ii = sum_j w_ij, the undirected edge id of each CSR entry
+// (lexicographic rank of (min, max), the orientation used for the incidence
+// matrix B of Sec. 5.2) and the connectivity check (Sec. 2 assumes G
+// connected).
+#include "internal.h"
+
+namespace cfc {
+
+namespace {
+
+__global__ void k_validate(const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+                           const double *__restrict__ w, int64_t m, int32_t n, int32_t *__restrict__ flag,
+                           int32_t *__restrict__ keep) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = src[e], v = dst[e];
+        bool ok = u >= 0 && v >= 0 && u < n && v < n;
+        if (w) {
+            const double x = w[e];
+            ok = ok && isfinite(x) && x > 0.0;
+        }
+        if (!ok) atomicOr(flag, 1);
+        keep[e] = (ok && u != v) ? 1 : 0;
+    }
+}
+
+// two CSR candidates per kept edge: (u, v) and (v, u); key = row * 2^b + col
+__global__ void k_emit_pairs(const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+                             const int32_t *__restrict__ keep, const int32_t *__restrict__ pos, int64_t m, int b,
+                             uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        if (!keep[e]) continue;
+        const uint64_t u = (uint32_t)src[e], v = (uint32_t)dst[e];
+        const int64_t p = 2 * (int64_t)pos[e];
+        keys[p] = (u << b) | v;
+        vals[p] = (uint32_t)e;
+        keys[p + 1] = (v << b) | u;
+        vals[p + 1] = (uint32_t)e;
+    }
+}
+
+__global__ void k_heads(const uint64_t *__restrict__ keys, int64_t len, int32_t *__restrict__ head) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+        head[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
+}
+
+// one thread per merged entry: sums the weights of its run of equal keys in
+// sorted (stable) order
+__global__ void k_merge(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                        const int32_t *__restrict__ head, const int32_t *__restrict__ hpos, int64_t len, int b,
+                        const double *__restrict__ w, int32_t *__restrict__ col, double *__restrict__ wout,
+                        int32_t *__restrict__ rowcnt, int32_t *__restrict__ row_of) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+        if (!head[i]) continue;
+        const uint64_t key = keys[i];
+        double s = 0.0;
+        for (int64_t j = i; j < len && keys[j] == key; ++j) s += w ? w[vals[j]] : 1.0;
+        const int32_t o = hpos[i];
+        const int32_t r = (int32_t)(key >> b);
+        col[o] = (int32_t)(key & ((uint64_t(1) << b) - 1));
+        row_of[o] = r;
+        wout[o] = s;
+        atomicAdd(&rowcnt[r], 1);
+    }
+}
+
+__global__ void k_finish_rowptr(int32_t *rowptr, int32_t n, int32_t nnz) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) rowptr[n] = nnz;
+}
+
+// D_ii = sum_j w_ij: one warp per row, fixed-order lane-strided sums + tree
+__global__ void k_row_sums(const int32_t *__restrict__ rowptr, const double *__restrict__ w, int32_t n,
+                           double *__restrict__ deg) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n;
+         r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        double s = 0.0;
+        for (int e = rowptr[r] + lane; e < rowptr[r + 1]; e += 32) s += w[e];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) deg[r] = s;
+    }
+}
+
+__global__ void k_upper_flags(const int32_t *__restrict__ row_of, const int32_t *__restrict__ col, int64_t nnz,
+                              int32_t *__restrict__ up) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * blockDim.x)
+        up[i] = row_of[i] < col[i] ? 1 : 0;
+}
+
+// the lower entry (r, c), r > c, takes the id of its mirror (c, r), found by
+// binary search in the sorted row c
+__global__ void k_mirror_eid(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ row_of,
+                             const int32_t *__restrict__ col, int64_t nnz, int32_t *__restrict__ eid) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = row_of[i], c = col[i];
+        if (r < c) continue;
+        int lo = rowptr[c], hi = rowptr[c + 1] - 1;
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (col[mid] < r) lo = mid + 1;
+            else hi = mid;
+        }
+        eid[i] = eid[lo];
+    }
+}
+
+// ---------------------------------------------------------------- connectivity
+// Lock-free union-find with hooking of the larger root under the smaller by
+// compare-and-swap and path halving (the scheme of Jaiganesh & Burtscher's
+// ECL-CC).  Parent pointers only ever point to smaller ids, so every find
+// terminates.
+__device__ __forceinline__ int32_t uf_find(int32_t *par, int32_t x) {
+    while (true) {
+        const int32_t p = __ldcg(par + x);
+        if (p == x) return x;
+        const int32_t gp = __ldcg(par + p);
+        if (gp != p) __stcg(par + x, gp);
+        x = gp;
+    }
+}
+
+__global__ void k_uf_init(int32_t *par, int32_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        par[i] = (int32_t)i;
+}
+
+__global__ void k_uf_hook(const int32_t *__restrict__ row_of, const int32_t *__restrict__ col, int64_t nnz,
+                          int32_t *par) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = row_of[i], v = col[i];
+        if (u > v) continue;
+        int32_t ru = uf_find(par, u), rv = uf_find(par, v);
+        while (ru != rv) {
+            if (ru < rv) {
+                int32_t t = ru;
+                ru = rv;
+                rv = t;
+            }
+            const int32_t old = atomicCAS(par + ru, ru, rv);
+            if (old == ru) break;
+            ru = uf_find(par, ru);
+            rv = uf_find(par, rv);
+        }
+    }
+}
+
+__global__ void k_uf_count_roots(const int32_t *par, int32_t n, int32_t *count) {
+    int32_t c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        c += (__ldcg(par + i) == (int32_t)i) ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+int grid_for(int64_t work, int threads = kBlock) {
+    int64_t g = (work + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > 152 * 32) g = 152 * 32;
+    return (int)g;
+}
+
+int bits_for(int64_t n) {
+    int b = 1;
+    while ((int64_t(1) << b) < n) ++b;
+    return b;
+}
+
+template <typename T>
+const T *to_device(const T *p, int64_t count, DBuf<T> &tmp, cudaStream_t s) {
+    if (!p || is_device_pointer(p)) return p;
+    tmp.alloc(count, s);
+    CFC_CUDA(cudaMemcpyAsync(tmp.get(), p, count * sizeof(T), cudaMemcpyHostToDevice, s));
+    return tmp.get();
+}
+
+}  // namespace
+
+void ingest(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const double *w, cudaStream_t s,
+            Csr64 &out) {
+    CFC_REQUIRE(src && dst, LAP_EINVAL, "src/dst must not be NULL");
+    CFC_REQUIRE(n >= 2 && n < (int64_t(1) << 31) - 1, LAP_EINVAL, "need 2 <= n < 2^31");
+    CFC_REQUIRE(m >= 1 && 2 * m < (int64_t(1) << 31) - 1, LAP_EINVAL, "need 1 <= m and 2m < 2^31");
+    DBuf<int32_t> ts, td;
+    DBuf<double> tw;
+    const int32_t *ds = to_device(src, m, ts, s);
+    const int32_t *dd = to_device(dst, m, td, s);
+    const double *dw = to_device(w, m, tw, s);
+
+    DBuf<int32_t> flag(1, s), keep(m, s), pos(m, s);
+    flag.zero(s);
+    const double eb = (double)m * (8.0 + (w ? 8.0 : 0.0));
+    CFC_LAUNCH(LAP_KF_SETUP, s, eb, k_validate, grid_for(m), kBlock, 0, ds, dd, dw, m, (int32_t)n, flag.get(),
+               keep.get());
+    int32_t hflag = 0;
+    CFC_CUDA(cudaMemcpyAsync(&hflag, flag.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CFC_CUDA(cudaStreamSynchronize(s));
+    CFC_REQUIRE(hflag == 0, LAP_EINVAL, "edge endpoint out of range or weight not finite and > 0");
+
+    const int64_t kept = scan_exclusive_i32(keep.get(), pos.get(), m, s);
+    CFC_REQUIRE(kept > 0, LAP_ENOTCONN, "graph has no edges besides self-loops");
+    const int64_t len = 2 * kept;
+    const int b = bits_for(n);
+    DBuf<uint64_t> keys(len, s);
+    DBuf<uint32_t> vals(len, s);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_emit_pairs, grid_for(m), kBlock, 0, ds, dd, keep.get(), pos.get(), m, b,
+               keys.get(), vals.get());
+    keep.release();
+    pos.release();
+    radix_sort_pairs(keys.get(), vals.get(), len, 2 * b, s);
+
+    DBuf<int32_t> head(len, s), hpos(len, s);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_heads, grid_for(len), kBlock, 0, keys.get(), len, head.get());
+    const int64_t nnz = scan_exclusive_i32(head.get(), hpos.get(), len, s);
+
+    out.n = (int32_t)n;
+    out.nnz = nnz;
+    out.m = nnz / 2;
+    out.rowptr.alloc_persistent(n + 1);
+    out.col.alloc_persistent(nnz);
+    out.w.alloc_persistent(nnz);
+    out.deg.alloc_persistent(n);
+    out.eid.alloc_persistent(nnz);
+    DBuf<int32_t> rowcnt(n + 1, s), row_of(nnz, s);
+    rowcnt.zero(s);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_merge, grid_for(len), kBlock, 0, keys.get(), vals.get(), head.get(),
+               hpos.get(), len, b, dw, out.col.get(), out.w.get(), rowcnt.get(), row_of.get());
+    keys.release();
+    vals.release();
+    head.release();
+    hpos.release();
+    scan_exclusive_i32(rowcnt.get(), out.rowptr.get(), n, s);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_finish_rowptr, 1, 1, 0, out.rowptr.get(), (int32_t)n, (int32_t)nnz);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_row_sums, grid_for(32 * n), kBlock, 0, out.rowptr.get(), out.w.get(),
+               (int32_t)n, out.deg.get());
+
+    // edge ids: lexicographic rank among the upper entries (row < col)
+    DBuf<int32_t> up(nnz, s);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_upper_flags, grid_for(nnz), kBlock, 0, row_of.get(), out.col.get(), nnz,
+               up.get());
+    scan_exclusive_i32(up.get(), out.eid.get(), nnz, s);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_mirror_eid, grid_for(nnz), kBlock, 0, out.rowptr.get(), row_of.get(),
+               out.col.get(), nnz, out.eid.get());
+
+    // connectivity
+    DBuf<int32_t> par(n, s), roots(1, s);
+    roots.zero(s);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_uf_init, grid_for(n), kBlock, 0, par.get(), (int32_t)n);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_uf_hook, grid_for(nnz), kBlock, 0, row_of.get(), out.col.get(), nnz,
+               par.get());
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_uf_count_roots, grid_for(n), kBlock, 0, par.get(), (int32_t)n,
+               roots.get());
+    int32_t hroots = 0;
+    CFC_CUDA(cudaMemcpyAsync(&hroots, roots.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CFC_CUDA(cudaStreamSynchronize(s));
+    CFC_REQUIRE(hroots == 1, LAP_ENOTCONN, "graph is not connected");
+}
+
+}  // namespace cfc

@@ -1,0 +1,221 @@
+// Internal declarations shared by the library's translation units.
+// Nothing here is part of the C ABI (include/cfc_gb300.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cfc_gb300.h"
+
+struct lap_hierarchy;
+
+namespace cfc {
+
+// ------------------------------------------------------------------ errors
+struct Error {
+    lap_status_t status;
+    std::string what;
+};
+
+void set_last_error(const std::string &s);
+
+#define CFC_CUDA(call)                                                                         \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            if (e_ == cudaErrorMemoryAllocation) {                                             \
+                cudaGetLastError();                                                            \
+                throw ::cfc::Error{LAP_ENOMEM, "out of device memory"};                        \
+            }                                                                                  \
+            throw ::cfc::Error{LAP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+        }                                                                                      \
+    } while (0)
+
+#define CFC_REQUIRE(cond, st, msg)                  \
+    do {                                            \
+        if (!(cond)) throw ::cfc::Error{(st), (msg)}; \
+    } while (0)
+
+// ------------------------------------------------------------------ launches
+// Every kernel launch goes through a LaunchScope so the library
+// can count its launches and, when timing is on, time the families of
+// include/cfc_gb300.h with CUDA events on the launching stream.
+struct LaunchScope {
+    int family;
+    cudaStream_t stream;
+    double bytes;
+    cudaEvent_t start = nullptr;
+    LaunchScope(int family, cudaStream_t s, double algorithmic_bytes);
+    ~LaunchScope();
+};
+void count_launch();
+
+#define CFC_LAUNCH(family, stream, bytes, kernel, grid, block, smem, ...)       \
+    do {                                                                       \
+        ::cfc::LaunchScope scope_((family), (stream), (bytes));                \
+        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);            \
+        CFC_CUDA(cudaGetLastError());                                          \
+    } while (0)
+
+// ------------------------------------------------------------------ memory
+// Device buffers owned by the library.  All allocations are stream-ordered
+// (cudaMallocAsync) and freed the same way.
+template <typename T>
+struct DBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    cudaStream_t s = nullptr;
+    bool async = false;
+    DBuf() = default;
+    DBuf(size_t count, cudaStream_t stream) { alloc(count, stream); }
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    DBuf(DBuf &&o) noexcept : p(o.p), n(o.n), s(o.s), async(o.async) { o.p = nullptr; o.n = 0; }
+    DBuf &operator=(DBuf &&o) noexcept {
+        if (this != &o) {
+            release();
+            p = o.p; n = o.n; s = o.s; async = o.async;
+            o.p = nullptr; o.n = 0;
+        }
+        return *this;
+    }
+    // stream-ordered temporary, freed on the same stream
+    void alloc(size_t count, cudaStream_t stream) {
+        release();
+        s = stream;
+        n = count;
+        async = true;
+        if (count) CFC_CUDA(cudaMallocAsync((void **)&p, count * sizeof(T) + 16, stream));
+    }
+    // long-lived buffer (hierarchy data, workspace): plain cudaMalloc / cudaFree
+    void alloc_persistent(size_t count) {
+        release();
+        n = count;
+        async = false;
+        if (count) CFC_CUDA(cudaMalloc((void **)&p, count * sizeof(T) + 16));
+    }
+    void zero(cudaStream_t stream) const {
+        if (n) CFC_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), stream));
+    }
+    void release() noexcept {
+        if (p) {
+            if (async) cudaFreeAsync(p, s);
+            else cudaFree(p);
+        }
+        p = nullptr;
+        n = 0;
+    }
+    ~DBuf() { release(); }
+    T *get() const { return p; }
+};
+
+bool is_device_pointer(const void *p);
+
+// ------------------------------------------------------------------ graph levels
+// One level of the multigrid hierarchy: the Laplacian L = D - A of a graph in
+// CSR form holding only the off-diagonal adjacency weights w_ij > 0 (the
+// matrix entries are -w_ij) plus the degree vector D_ii = sum_j w_ij.
+struct Level {
+    int32_t n = 0;
+    int64_t nnz = 0;
+    DBuf<int32_t> rowptr, col;
+    DBuf<double> w64, deg64, dinv64;
+    DBuf<float> w32, deg32, dinv32;
+    // rows longer than kLongRow nonzeros are split into chunks of kLongRow
+    int32_t n_long = 0, n_chunks = 0;
+    DBuf<int32_t> chunk_row;     // [n_chunks] row of each chunk
+    DBuf<int32_t> chunk_begin;   // [n_chunks] first nonzero of the chunk
+    DBuf<int32_t> chunk_long;    // [n_chunks] index of the chunk's long row
+    DBuf<int32_t> long_first;    // [n_long + 1] first chunk of each long row
+    DBuf<uint32_t> long_count;   // [n_long * max_tiles] arrival counters (zero between launches)
+    // map to the next coarser level (empty at the coarsest)
+    DBuf<int32_t> agg;           // [n] aggregate (coarse node) of each node
+    DBuf<int32_t> mem_ptr, mem;  // members of each coarse node, ascending
+};
+
+constexpr int kLongRow = 64;     // row split threshold (nonzeros)
+constexpr int kMaxTiles = 64;    // column tiles per launch (k <= 64 * 64)
+constexpr int kBlock = 256;
+
+// Device view of a level passed by value to kernels.
+struct LevelView {
+    int32_t n;
+    const int32_t *rowptr, *col;
+    const float *w32, *deg32, *dinv32;
+    const double *w64, *deg64, *dinv64;
+    int32_t n_chunks, n_long;
+    const int32_t *chunk_row, *chunk_begin, *chunk_long, *long_first;
+    uint32_t *long_count;
+};
+LevelView view(const Level &L);
+
+// ------------------------------------------------------------------ primitives (prims.cu)
+// Exclusive prefix sum of n int32 or int64 values; returns the total.
+int64_t scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
+int64_t scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
+// Stable LSD radix sort of (key, value) pairs on the low `bits` key bits.
+// keys/vals are sorted in place (scratch is allocated internally).
+void radix_sort_pairs(uint64_t *keys, uint32_t *vals, int64_t n, int bits, cudaStream_t s);
+
+// ------------------------------------------------------------------ ingest (graph.cu)
+struct Csr64 {
+    int32_t n = 0;
+    int64_t nnz = 0;
+    DBuf<int32_t> rowptr, col, eid;   // eid: undirected edge id of each entry
+    DBuf<double> w, deg;
+    int64_t m = 0;                    // undirected edges after merging
+};
+// Edge list (host or device) -> symmetric CSR, merged, loop-free, with the
+// connectivity check.  Throws Error on invalid input / disconnected graph.
+void ingest(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const double *w,
+            cudaStream_t s, Csr64 &out);
+
+// ------------------------------------------------------------------ hierarchy (amg.cu)
+void build_levels(lap_hierarchy &h, Csr64 &fine, const lap_hier_opts_t &o, cudaStream_t s);
+void finish_level(Level &L, cudaStream_t s);  // FP32 copies, inverse degrees, long-row split
+
+// dense SPD inverse (in place, FP64, row-major n x n) -- used for the
+// coarsest level (single CTA, n <= 160) and cfc_exact_small (global memory).
+void dense_spd_inverse_small(double *A, int n, int *d_flag, cudaStream_t s);
+void dense_spd_inverse_large(double *A, int n, int *d_flag, cudaStream_t s);
+
+}  // namespace cfc
+
+// ------------------------------------------------------------------ handle
+struct lap_hierarchy {
+    int device = 0;
+    int64_t n = 0, m = 0;
+    std::vector<cfc::Level> lv;
+    cfc::DBuf<int32_t> eid;           // level-0 undirected edge id of each CSR entry
+    int32_t coarse_n = 0;             // dense coarsest size (0: none)
+    cfc::DBuf<double> coarse_inv;     // (L_c + J/n_c)^{-1}, row-major
+    double setup_ms = 0;
+    // solve workspace, grown on demand
+    cfc::DBuf<char> ws;
+    size_t ws_bytes = 0;
+    bool ws_dirty = true;             // workspace counters need zeroing
+    cudaStream_t ws_stream = nullptr;
+};
+
+namespace cfc {
+// solve.cu
+lap_status_t solve_multi(lap_hierarchy *h, int32_t k, const double *B, double *X,
+                         const lap_solve_opts_t &o, cudaStream_t s, lap_solve_info_t *info);
+int num_sms_public();
+int32_t *pinned_scratch();  // per-thread pinned host buffer of 8192 int32
+// amg.cu
+void build_dense(const int32_t *rowptr, const int32_t *col, const double *w, const double *deg, int32_t n,
+                 double *M, cudaStream_t s);
+// cfc.cu
+void jl_rhs(lap_hierarchy *h, int k, int ld, uint64_t seed, double *Y, cudaStream_t s);
+lap_status_t farness_jl(lap_hierarchy *h, int32_t k, double eps, uint64_t seed, int32_t q, const int32_t *nodes,
+                        double *farness, const lap_solve_opts_t &o, cudaStream_t s);
+lap_status_t pivots_api(lap_hierarchy *h, int32_t kk, uint64_t seed, int32_t *pivots, cudaStream_t s);
+lap_status_t farness_sampled(lap_hierarchy *h, int32_t kk, uint64_t seed, int32_t q, const int32_t *nodes,
+                             double *farness, const lap_solve_opts_t &o, cudaStream_t s);
+lap_status_t exact_small(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const double *w,
+                         double *farness, double *closeness, cudaStream_t s);
+}  // namespace cfc

@@ -1,0 +1,819 @@
+// Block solve of L X = B (Eq. system) for k right-hand sides: FP64 iterative
+// refinement around a column-independent preconditioned CG (Sec. 3.1: CG,
+// relative-residual stopping rule) whose preconditioner is one V-cycle of
+// the aggregation hierarchy built in amg.cu.
+//
+//   outer (FP64):  r = b - L x ;  stop when ||r_j|| <= tol ||b_j|| for all j
+//                  d = PCG(L, r) in Tin (FP32, or FP64 in LAP_FP64 mode)
+//                  x += d
+//   inner PCG:     per column j its own alpha_j, beta_j (columns never mix)
+//   V-cycle:       Chebyshev (or damped Jacobi) smoothing with D^{-1},
+//                  residual, restriction (sum over each aggregate),
+//                  recursion, dense FP64 coarsest solve, prolongation,
+//                  the same smoothing again (a symmetric preconditioner).
+//
+// L is singular with null space span{1} (Sec. 2): b is projected to zero
+// mean once, the search directions are projected every iteration, and the
+// result is returned with zero mean.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+#include "rowops.cuh"
+
+namespace cfc {
+
+namespace {
+
+// ====================================================================== ops
+// q = L p ; sum p.q ; alpha = rz / pq
+template <typename T>
+struct OpSpmvDot {
+    using V = typename Vec<T>::V;
+    static constexpr int VW = Vec<T>::W;
+    LevelView A;
+    const T *p;
+    T *q;
+    int ld;
+    const double *rz;
+    double *alpha;
+    const int32_t *active;
+    __device__ V gather(int j, int c0) const { return vldg<T>(p + (size_t)j * ld + c0); }
+    template <class Acc>
+    __device__ void epi(int i, int c0, V s, Acc &acc) const {
+        const V x = gather(i, c0);
+        const T d = ldeg<T>(A, i);
+        V y;
+#pragma unroll
+        for (int v = 0; v < VW; ++v) {
+            vel(y, v) = d * vel(x, v) - vel(s, v);
+            acc[0][v] += (double)vel(x, v) * (double)vel(y, v);
+        }
+        vst<T>(q + (size_t)i * ld + c0, y);
+    }
+    __device__ void fin(int c, const double *sums) const {
+        const double pq = sums[0];
+        alpha[c] = (active[c] && pq > 0.0) ? rz[c] / pq : 0.0;
+    }
+};
+
+// FP64 outer residual r = b - L x, written in the inner type; sum r^2;
+// relres_j = ||r_j|| / ||b_j|| ; active_j = relres_j > tol
+template <typename Tin>
+struct OpResid64 {
+    using V = double2;
+    static constexpr int VW = 2;
+    LevelView A;
+    const double *x;
+    const double *b;
+    Tin *r;
+    int ld;
+    const double *bnorm;
+    double *relres;
+    int32_t *active;
+    double tol;
+    __device__ V gather(int j, int c0) const { return vldg<double>(x + (size_t)j * ld + c0); }
+    template <class Acc>
+    __device__ void epi(int i, int c0, V s, Acc &acc) const {
+        const V xi = gather(i, c0);
+        const V bi = vldg<double>(b + (size_t)i * ld + c0);
+        const double d = ldeg<double>(A, i);
+#pragma unroll
+        for (int v = 0; v < VW; ++v) {
+            const double rv = vel(bi, v) - (d * vel(xi, v) - vel(s, v));
+            acc[0][v] += rv * rv;
+            r[(size_t)i * ld + c0 + v] = (Tin)rv;
+        }
+    }
+    __device__ void fin(int c, const double *sums) const {
+        const double bn = bnorm[c];
+        const double rr = bn > 0.0 ? sqrt(sums[0]) / bn : 0.0;
+        relres[c] = rr;
+        active[c] = (bn > 0.0 && rr > tol) ? 1 : 0;
+    }
+};
+
+// Chebyshev / Jacobi step: out = x + c (x - xp) + e D^{-1} (b - L x), in place on xp
+template <typename T>
+struct OpSmooth {
+    using V = typename Vec<T>::V;
+    static constexpr int VW = Vec<T>::W;
+    LevelView A;
+    const T *x;
+    T *xp;
+    const T *b;
+    int ld;
+    T c, e;
+    bool xp_zero;  // the previous iterate is the zero initial guess
+    __device__ V gather(int j, int c0) const { return vldg<T>(x + (size_t)j * ld + c0); }
+    template <class Acc>
+    __device__ void epi(int i, int c0, V s, Acc &) const {
+        const V xi = gather(i, c0);
+        const V bi = vld<T>(b + (size_t)i * ld + c0);
+        const T d = ldeg<T>(A, i), di = ldinv<T>(A, i);
+        V out;
+        if (c != T(0)) {
+            const V pi = xp_zero ? vzero<V>() : vld<T>(xp + (size_t)i * ld + c0);
+#pragma unroll
+            for (int v = 0; v < VW; ++v)
+                vel(out, v) = vel(xi, v) + c * (vel(xi, v) - vel(pi, v)) +
+                              e * di * (vel(bi, v) - (d * vel(xi, v) - vel(s, v)));
+        } else {
+#pragma unroll
+            for (int v = 0; v < VW; ++v)
+                vel(out, v) = vel(xi, v) + e * di * (vel(bi, v) - (d * vel(xi, v) - vel(s, v)));
+        }
+        vst<T>(xp + (size_t)i * ld + c0, out);
+    }
+    __device__ void fin(int, const double *) const {}
+};
+
+// r = b - L x
+template <typename T>
+struct OpResid {
+    using V = typename Vec<T>::V;
+    static constexpr int VW = Vec<T>::W;
+    LevelView A;
+    const T *x;
+    const T *b;
+    T *r;
+    int ld;
+    __device__ V gather(int j, int c0) const { return vldg<T>(x + (size_t)j * ld + c0); }
+    template <class Acc>
+    __device__ void epi(int i, int c0, V s, Acc &) const {
+        const V xi = gather(i, c0);
+        const V bi = vld<T>(b + (size_t)i * ld + c0);
+        const T d = ldeg<T>(A, i);
+        V out;
+#pragma unroll
+        for (int v = 0; v < VW; ++v) vel(out, v) = vel(bi, v) - (d * vel(xi, v) - vel(s, v));
+        vst<T>(r + (size_t)i * ld + c0, out);
+    }
+    __device__ void fin(int, const double *) const {}
+};
+
+// ---------------------------------------------------------------- row-local ops
+// x = e D^{-1} b  (first smoothing step from a zero guess)
+template <typename T>
+struct OpJacobiZero {
+    using V = typename Vec<T>::V;
+    static constexpr int VW = Vec<T>::W;
+    LevelView A;
+    const T *b;
+    T *x;
+    int ld;
+    T e;
+    template <class Acc>
+    __device__ void row(int i, int c0, Acc &) const {
+        const V bi = vld<T>(b + (size_t)i * ld + c0);
+        const T di = e * ldinv<T>(A, i);
+        V out;
+#pragma unroll
+        for (int v = 0; v < VW; ++v) vel(out, v) = di * vel(bi, v);
+        vst<T>(x + (size_t)i * ld + c0, out);
+    }
+    __device__ void fin(int, const double *) const {}
+};
+
+// coarse b_c[I] = sum over the members i of aggregate I of r[i]
+template <typename T>
+struct OpRestrict {
+    using V = typename Vec<T>::V;
+    const int32_t *mem_ptr, *mem;
+    const T *r;
+    T *bc;
+    int ld;
+    template <class Acc>
+    __device__ void row(int I, int c0, Acc &) const {
+        V s = vzero<V>();
+        for (int t = __ldg(mem_ptr + I); t < __ldg(mem_ptr + I + 1); ++t)
+            s = vadd(s, vld<T>(r + (size_t)__ldg(mem + t) * ld + c0));
+        vst<T>(bc + (size_t)I * ld + c0, s);
+    }
+    __device__ void fin(int, const double *) const {}
+};
+
+// x[i] += gamma * xc[agg[i]]
+template <typename T>
+struct OpProlong {
+    using V = typename Vec<T>::V;
+    static constexpr int VW = Vec<T>::W;
+    const int32_t *agg;
+    const T *xc;
+    T *x;
+    int ld;
+    T gamma;
+    template <class Acc>
+    __device__ void row(int i, int c0, Acc &) const {
+        const V c = vld<T>(xc + (size_t)__ldg(agg + i) * ld + c0);
+        V xi = vld<T>(x + (size_t)i * ld + c0);
+#pragma unroll
+        for (int v = 0; v < VW; ++v) vel(xi, v) += gamma * vel(c, v);
+        vst<T>(x + (size_t)i * ld + c0, xi);
+    }
+    __device__ void fin(int, const double *) const {}
+};
+
+// x += alpha p ; r -= alpha q ; sum r^2 -> inner convergence flags
+template <typename T>
+struct OpUpdateXR {
+    using V = typename Vec<T>::V;
+    static constexpr int VW = Vec<T>::W;
+    T *x, *r;
+    const T *p, *q;
+    int ld;
+    const double *alpha;
+    int32_t *active;
+    const double *rr0;
+    double tol2;
+    template <class Acc>
+    __device__ void row(int i, int c0, Acc &acc) const {
+        const size_t o = (size_t)i * ld + c0;
+        V xi = vld<T>(x + o), ri = vld<T>(r + o);
+        const V pi = vld<T>(p + o), qi = vld<T>(q + o);
+#pragma unroll
+        for (int v = 0; v < VW; ++v) {
+            const T a = (T)alpha[c0 + v];
+            vel(xi, v) += a * vel(pi, v);
+            vel(ri, v) -= a * vel(qi, v);
+            acc[0][v] += (double)vel(ri, v) * (double)vel(ri, v);
+        }
+        vst<T>(x + o, xi);
+        vst<T>(r + o, ri);
+    }
+    __device__ void fin(int c, const double *sums) const {
+        if (active[c] && !(sums[0] > tol2 * rr0[c])) active[c] = 0;
+    }
+};
+
+// sums r.z, z, r (and r.r when init) -> mu = mean(z), rz = r.(z - mu), beta
+template <typename T, bool Init>
+struct OpDotRZ {
+    using V = typename Vec<T>::V;
+    static constexpr int VW = Vec<T>::W;
+    const T *r, *z;
+    int ld;
+    double inv_n;
+    double *rz, *beta, *mu, *rr0;
+    int32_t *active;
+    const int32_t *active_out;
+    template <class Acc>
+    __device__ void row(int i, int c0, Acc &acc) const {
+        const size_t o = (size_t)i * ld + c0;
+        const V ri = vld<T>(r + o), zi = vld<T>(z + o);
+#pragma unroll
+        for (int v = 0; v < VW; ++v) {
+            const double a = vel(ri, v), b = vel(zi, v);
+            acc[0][v] += a * b;
+            acc[1][v] += b;
+            acc[2][v] += a;
+            if constexpr (Init) acc[3][v] += a * a;
+        }
+    }
+    __device__ void fin(int c, const double *s) const {
+        const double m = s[1] * inv_n;
+        const double rzn = s[0] - m * s[2];
+        mu[c] = m;
+        if constexpr (Init) {
+            rr0[c] = s[3];
+            active[c] = (active_out[c] && s[3] > 0.0) ? 1 : 0;
+            beta[c] = 0.0;
+        } else {
+            beta[c] = (active[c] && rz[c] != 0.0) ? rzn / rz[c] : 0.0;
+        }
+        rz[c] = rzn;
+    }
+};
+
+// p = (z - mu) + beta p
+template <typename T>
+struct OpUpdateP {
+    using V = typename Vec<T>::V;
+    static constexpr int VW = Vec<T>::W;
+    const T *z;
+    T *p;
+    int ld;
+    const double *mu, *beta;
+    template <class Acc>
+    __device__ void row(int i, int c0, Acc &) const {
+        const size_t o = (size_t)i * ld + c0;
+        const V zi = vld<T>(z + o);
+        V pi = vld<T>(p + o);
+#pragma unroll
+        for (int v = 0; v < VW; ++v)
+            vel(pi, v) = (vel(zi, v) - (T)mu[c0 + v]) + (T)beta[c0 + v] * vel(pi, v);
+        vst<T>(p + o, pi);
+    }
+    __device__ void fin(int, const double *) const {}
+};
+
+// x64 += d (active columns only)
+template <typename Tin>
+struct OpAddCorr {
+    using V = double2;
+    static constexpr int VW = 2;
+    double *x;
+    const Tin *d;
+    int ld;
+    const int32_t *active;
+    template <class Acc>
+    __device__ void row(int i, int c0, Acc &) const {
+        const size_t o = (size_t)i * ld + c0;
+        V xi = vld<double>(x + o);
+#pragma unroll
+        for (int v = 0; v < VW; ++v)
+            if (active[c0 + v]) vel(xi, v) += (double)d[o + v];
+        vst<double>(x + o, xi);
+    }
+    __device__ void fin(int, const double *) const {}
+};
+
+// column sums of an FP64 block -> mean
+struct OpColMean64 {
+    using V = double2;
+    const double *a;
+    int ld;
+    double inv_n;
+    double *mean;
+    template <class Acc>
+    __device__ void row(int i, int c0, Acc &acc) const {
+        const V ai = vld<double>(a + (size_t)i * ld + c0);
+        acc[0][0] += ai.x;
+        acc[0][1] += ai.y;
+    }
+    __device__ void fin(int c, const double *s) const { mean[c] = s[0] * inv_n; }
+};
+
+// out = a - mean (in place allowed), sum out^2 -> norm
+struct OpSubMean64 {
+    using V = double2;
+    const double *a;
+    double *out;
+    int ld;
+    const double *mean;
+    double *norm;  // may be null
+    template <class Acc>
+    __device__ void row(int i, int c0, Acc &acc) const {
+        const size_t o = (size_t)i * ld + c0;
+        V ai = vld<double>(a + o);
+        ai.x -= mean[c0];
+        ai.y -= mean[c0 + 1];
+        acc[0][0] += ai.x * ai.x;
+        acc[0][1] += ai.y * ai.y;
+        vst<double>(out + o, ai);
+    }
+    __device__ void fin(int c, const double *s) const {
+        if (norm) norm[c] = sqrt(s[0]);
+    }
+};
+
+// ---------------------------------------------------------------- plain kernels
+__global__ void k_copy_pad(const double *__restrict__ src, int k, double *__restrict__ dst, int ld, int64_t n) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * ld; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / ld;
+        const int c = (int)(t - i * ld);
+        dst[t] = c < k ? src[i * k + c] : 0.0;
+    }
+}
+
+__global__ void k_copy_unpad(const double *__restrict__ src, int ld, double *__restrict__ dst, int k, int64_t n) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * k; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / k;
+        const int c = (int)(t - i * k);
+        dst[t] = src[i * ld + c];
+    }
+}
+
+// x_c = M^{-1} b_c with the dense FP64 inverse (coarsest level), FP64 sums
+template <typename T>
+__global__ void k_coarse_dense(const double *__restrict__ Minv, int nc, const T *__restrict__ b, T *__restrict__ x,
+                               int ld, int k) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nc * k; t += gridDim.x * blockDim.x) {
+        const int I = t / k, c = t - (t / k) * k;
+        const double *row = Minv + (size_t)I * nc;
+        double s = 0.0;
+        for (int J = 0; J < nc; ++J) s += row[J] * (double)b[(size_t)J * ld + c];
+        x[(size_t)I * ld + c] = (T)s;
+    }
+}
+
+int g_num_sms = 0;
+int num_sms() {
+    if (!g_num_sms) {
+        int dev = 0;
+        CFC_CUDA(cudaGetDevice(&dev));
+        CFC_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+        if (g_num_sms <= 0) g_num_sms = 1;
+    }
+    return g_num_sms;
+}
+
+// ====================================================================== solver
+struct ColState {
+    double *bnorm, *relres, *alpha, *beta, *rz, *rr0, *mu;
+    int32_t *active_out, *active_in;
+};
+
+template <typename Tin, int KT>
+struct Solver {
+    static constexpr int K64 = KT > 64 ? 64 : KT;  // FP64 tile: at most 32 lanes of double2
+    static constexpr int G64 = K64 / 2;
+    static constexpr int RPB64 = kBlock / G64;
+
+    lap_hierarchy *h;
+    cudaStream_t s;
+    int ld, ntiles, ntiles64, nlev, k;
+    const lap_solve_opts_t &o;
+    // workspace
+    double *b64, *x64;
+    std::vector<Tin *> lb, lx, lt;  // per level: rhs, iterate, scratch
+    Tin *r, *z, *p, *q, *t0;        // finest-level PCG vectors (+ lb[0] = r, lx[0] = z)
+    Tin *chunk_part;
+    double *chunk_part64;
+    RedBuf rb;
+    ColState cs;
+    int32_t *h_active;  // pinned
+    std::vector<double> cheb_c, cheb_e;
+    double gamma = 1.0;
+    int nu_pre, nu_post;
+
+    Solver(lap_hierarchy *h_, cudaStream_t s_, int k_, int ld_, const lap_solve_opts_t &o_)
+        : h(h_), s(s_), ld(ld_), ntiles(ld_ / KT), ntiles64(ld_ / K64), k(k_), o(o_) {
+        nlev = (int)h->lv.size();
+        if (o.levels_used > 0) nlev = std::min(nlev, o.levels_used);
+        nu_pre = std::max(1, o.nu_pre);
+        nu_post = std::max(1, o.nu_post);
+        setup_smoother();
+    }
+
+    void setup_smoother() {
+        // D^{-1} L of a Laplacian has its spectrum in [0, 2] (Gershgorin).
+        const int nu = std::max(nu_pre, nu_post);
+        cheb_c.assign(nu, 0.0);
+        cheb_e.assign(nu, 0.0);
+        if (o.smoother == LAP_SMOOTH_JACOBI) {
+            for (int t = 0; t < nu; ++t) cheb_e[t] = 2.0 / 3.0;
+            return;
+        }
+        const double hi = 2.0, lo = hi / 4.0;  // smooth the upper part of the spectrum
+        const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+        double rho = 1.0 / sigma;
+        cheb_e[0] = 1.0 / theta;
+        cheb_c[0] = 0.0;
+        for (int t = 1; t < nu; ++t) {
+            const double rn = 1.0 / (2.0 * sigma - rho);
+            cheb_c[t] = rn * rho;
+            cheb_e[t] = 2.0 * rn / delta;
+            rho = rn;
+        }
+    }
+
+    int red_grid(int nvb) const { return std::max(1, std::min(nvb, 2 * num_sms())); }
+    int plain_grid(int nvb) const { return std::max(1, std::min(nvb, 8 * num_sms())); }
+
+    static double vec_bytes(int64_t n, int ld, int nvec, int elem) { return (double)n * ld * elem * nvec; }
+    static double mat_bytes(const Level &L, int wb) {
+        return (double)L.nnz * (4.0 + wb) + (double)L.n * (4.0 + 2.0 * wb);
+    }
+
+    // ---------------- generic launches
+    template <typename T, int NR, class Op>
+    void rowop(int fam, const Level &L, const Op &op, T *cpart, double bytes) {
+        constexpr int G = KT / Vec<T>::W;
+        constexpr int RPB = kBlock / G;
+        const int nvb_short = (L.n + RPB - 1) / RPB;
+        const int nvb_long = (L.n_chunks + RPB - 1) / RPB;
+        const int nvb = nvb_short + nvb_long;
+        const int gx = NR > 0 ? red_grid(nvb) : plain_grid(nvb);
+        dim3 grid(gx, ntiles);
+        CFC_LAUNCH(fam, s, bytes, (k_rowop<T, KT, NR, Op>), grid, kBlock, 0, view(L), op, nvb_short, nvb, cpart, ld,
+                   rb);
+    }
+    template <typename T, int NR, class Op>
+    void rows(int fam, int64_t n, const Op &op, double bytes) {
+        constexpr int G = KT / Vec<T>::W;
+        constexpr int RPB = kBlock / G;
+        const int nvb = (int)((n + RPB - 1) / RPB);
+        const int gx = NR > 0 ? red_grid(nvb) : plain_grid(nvb);
+        dim3 grid(gx, ntiles);
+        CFC_LAUNCH(fam, s, bytes, (k_rows<T, KT, NR, Op>), grid, kBlock, 0, (int)n, op, rb);
+    }
+
+    int fam_level(int l, int fine_fam) const { return l == 0 ? fine_fam : LAP_KF_COARSE_LEVELS; }
+
+    // ---------------- V-cycle on level l: b = lb[l] -> x = lx[l]
+    void vcycle(int l) {
+        const Level &L = h->lv[l];
+        const int et = (int)sizeof(Tin);
+        const int wb = et;
+        const bool coarsest = (l == nlev - 1);
+        if (coarsest && h->coarse_n == L.n && l == (int)h->lv.size() - 1) {
+            const int nc = L.n;
+            const int threads = 128;
+            const int blocks = std::max(1, std::min((nc * ld + threads - 1) / threads, 8 * num_sms()));
+            CFC_LAUNCH(LAP_KF_COARSE_LEVELS, s, (double)nc * nc * 8 + 2.0 * nc * ld * et, k_coarse_dense<Tin>,
+                       blocks, threads, 0, h->coarse_inv.get(), nc, lb[l], lx[l], ld, ld);
+            return;
+        }
+        // pre-smoothing from zero
+        Tin *cur = lx[l], *oth = lt[l];
+        rows<Tin, 0>(fam_level(l, LAP_KF_SMOOTH_FINE), L.n,
+                     OpJacobiZero<Tin>{view(L), lb[l], cur, ld, (Tin)cheb_e[0]},
+                     vec_bytes(L.n, ld, 2, et) + L.n * (double)wb);
+        const int npre = coarsest ? std::max(nu_pre, 4) : nu_pre;
+        for (int t = 1; t < npre; ++t) {
+            const int ti = std::min(t, (int)cheb_c.size() - 1);
+            rowop<Tin, 0>(fam_level(l, LAP_KF_SMOOTH_FINE), L,
+                          OpSmooth<Tin>{view(L), cur, oth, lb[l], ld, (Tin)cheb_c[ti], (Tin)cheb_e[ti], t == 1},
+                          chunk_part, mat_bytes(L, wb) + vec_bytes(L.n, ld, t == 1 ? 3 : 4, et));
+            std::swap(cur, oth);
+        }
+        if (coarsest) {
+            lx[l] = cur;
+            lt[l] = oth;
+            return;
+        }
+        // residual into oth, restrict to level l+1
+        rowop<Tin, 0>(fam_level(l, LAP_KF_RESTRICT_FINE), L, OpResid<Tin>{view(L), cur, lb[l], oth, ld}, chunk_part,
+                      mat_bytes(L, wb) + vec_bytes(L.n, ld, 3, et));
+        const Level &C = h->lv[l + 1];
+        rows<Tin, 0>(fam_level(l, LAP_KF_RESTRICT_FINE), C.n,
+                     OpRestrict<Tin>{L.mem_ptr.get(), L.mem.get(), oth, lb[l + 1], ld},
+                     vec_bytes(L.n, ld, 1, et) + vec_bytes(C.n, ld, 1, et) + 4.0 * (L.n + C.n));
+        vcycle(l + 1);
+        rows<Tin, 0>(LAP_KF_COARSE_LEVELS, L.n, OpProlong<Tin>{L.agg.get(), lx[l + 1], cur, ld, (Tin)gamma},
+                     vec_bytes(L.n, ld, 2, et) + vec_bytes(C.n, ld, 1, et) + 4.0 * L.n);
+        // post-smoothing (the same polynomial: symmetric V-cycle)
+        for (int t = 0; t < nu_post; ++t) {
+            const int ti = std::min(t, (int)cheb_c.size() - 1);
+            rowop<Tin, 0>(fam_level(l, LAP_KF_SMOOTH_FINE), L,
+                          OpSmooth<Tin>{view(L), cur, oth, lb[l], ld, (Tin)cheb_c[ti], (Tin)cheb_e[ti], false},
+                          chunk_part, mat_bytes(L, wb) + vec_bytes(L.n, ld, t ? 4 : 3, et));
+            std::swap(cur, oth);
+        }
+        lx[l] = cur;
+        lt[l] = oth;
+    }
+
+    // z = M^{-1} r  (the result may land in either of the two finest-level
+    // buffers; z and t0 are swapped accordingly)
+    void precond() {
+        lb[0] = r;
+        lx[0] = z;
+        lt[0] = t0;
+        vcycle(0);
+        z = lx[0];
+        t0 = lt[0];
+    }
+
+    // inner PCG on the finest level: solves L d = r, d in lx... returns iterations
+    int inner_pcg(Tin *d, int max_inner, double inner_tol) {
+        const Level &L0 = h->lv[0];
+        const int et = (int)sizeof(Tin);
+        const int64_t n = L0.n;
+        const double vb1 = vec_bytes(n, ld, 1, et);
+        CFC_CUDA(cudaMemsetAsync(d, 0, (size_t)n * ld * et, s));
+        precond();
+        rows<Tin, 4>(LAP_KF_BLAS1, n,
+                     OpDotRZ<Tin, true>{r, z, ld, 1.0 / n, cs.rz, cs.beta, cs.mu, cs.rr0, cs.active_in, cs.active_out},
+                     2 * vb1);
+        rows<Tin, 0>(LAP_KF_BLAS1, n, OpUpdateP<Tin>{z, p, ld, cs.mu, cs.beta}, 3 * vb1);
+        const int check = std::max(1, o.check_every);
+        int it = 0;
+        for (it = 1; it <= max_inner; ++it) {
+            rowop<Tin, 1>(LAP_KF_SPMV_FINE, L0, OpSpmvDot<Tin>{view(L0), p, q, ld, cs.rz, cs.alpha, cs.active_in},
+                          chunk_part, mat_bytes(L0, et) + 2 * vb1);
+            rows<Tin, 1>(LAP_KF_BLAS1, n,
+                         OpUpdateXR<Tin>{d, r, p, q, ld, cs.alpha, cs.active_in, cs.rr0, inner_tol * inner_tol},
+                         6 * vb1);
+            if (it % check == 0 || it == max_inner) {
+                CFC_CUDA(cudaMemcpyAsync(h_active, cs.active_in, ld * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+                CFC_CUDA(cudaStreamSynchronize(s));
+                int na = 0;
+                for (int c = 0; c < ld; ++c) na += h_active[c] ? 1 : 0;
+                if (na == 0) break;
+                if (it == max_inner) break;
+            }
+            precond();
+            rows<Tin, 3>(LAP_KF_BLAS1, n,
+                         OpDotRZ<Tin, false>{r, z, ld, 1.0 / n, cs.rz, cs.beta, cs.mu, cs.rr0, cs.active_in,
+                                             cs.active_out},
+                         2 * vb1);
+            rows<Tin, 0>(LAP_KF_BLAS1, n, OpUpdateP<Tin>{z, p, ld, cs.mu, cs.beta}, 3 * vb1);
+        }
+        return std::min(it, max_inner);
+    }
+
+    lap_status_t run(const double *B, double *X, lap_solve_info_t *info) {
+        const Level &L0 = h->lv[0];
+        const int64_t n = L0.n;
+        const double v64 = vec_bytes(n, ld, 1, 8);
+        // b64 = B (padded), projected to zero mean; bnorm
+        {
+            const int64_t tot = n * ld;
+            const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 8 * num_sms());
+            CFC_LAUNCH(LAP_KF_BLAS1, s, v64 * 2, k_copy_pad, blocks, 256, 0, B, k, b64, ld, n);
+        }
+        rowsd<1>(n, OpColMean64{b64, ld, 1.0 / n, cs.mu}, v64);
+        rowsd<1>(n, OpSubMean64{b64, b64, ld, cs.mu, cs.bnorm}, 2 * v64);
+        CFC_CUDA(cudaMemsetAsync(x64, 0, (size_t)n * ld * 8, s));
+
+        int outer = 0, inner_total = 0;
+        bool converged = false;
+        double maxrel = 0.0;
+        std::vector<double> hrel(ld);
+        for (outer = 0;; ++outer) {
+            // FP64 residual, written to r in the inner type
+            {
+                constexpr int RPB = RPB64;
+                const int nvb_short = (L0.n + RPB - 1) / RPB;
+                const int nvb_long = (L0.n_chunks + RPB - 1) / RPB;
+                const int nvb = nvb_short + nvb_long;
+                dim3 grid(red_grid(nvb), ntiles64);
+                using Op = OpResid64<Tin>;
+                Op op{view(L0), x64, b64, r, ld, cs.bnorm, cs.relres, cs.active_out, o.tol};
+                CFC_LAUNCH(LAP_KF_RESID64, s, mat_bytes(L0, 8) + 2 * v64 + vec_bytes(n, ld, 1, sizeof(Tin)),
+                           (k_rowop<double, K64, 1, Op>), grid, kBlock, 0, view(L0), op, nvb_short, nvb, chunk_part64,
+                           ld, rb);
+            }
+            CFC_CUDA(cudaMemcpyAsync(h_active, cs.active_out, ld * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            CFC_CUDA(cudaMemcpyAsync(hrel.data(), cs.relres, ld * sizeof(double), cudaMemcpyDeviceToHost, s));
+            CFC_CUDA(cudaStreamSynchronize(s));
+            int na = 0;
+            maxrel = 0.0;
+            for (int c = 0; c < ld; ++c) {
+                na += h_active[c] ? 1 : 0;
+                maxrel = std::max(maxrel, hrel[c]);
+            }
+            if (na == 0) {
+                converged = true;
+                break;
+            }
+            if (outer >= o.max_outer) break;
+            // inner solve of L d = r; d lives in lt-independent buffer `dbuf`
+            const double itol = (o.precision == LAP_FP64) ? std::max(o.tol * 0.5, 1e-15) : o.inner_tol;
+            inner_total += inner_pcg(dbuf, o.max_inner, itol);
+            rowsd<0>(n, OpAddCorr<Tin>{x64, dbuf, ld, cs.active_out}, 2 * v64 + vec_bytes(n, ld, 1, sizeof(Tin)));
+        }
+        // zero-mean result, copied out unpadded
+        rowsd<1>(n, OpColMean64{x64, ld, 1.0 / n, cs.mu}, v64);
+        rowsd<1>(n, OpSubMean64{x64, x64, ld, cs.mu, nullptr}, 2 * v64);
+        {
+            const int64_t tot = n * k;
+            const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 8 * num_sms());
+            CFC_LAUNCH(LAP_KF_BLAS1, s, v64 * 2, k_copy_unpad, blocks, 256, 0, x64, ld, X, k, n);
+        }
+        CFC_CUDA(cudaStreamSynchronize(s));
+        if (info) {
+            info->outer_iters = outer;
+            info->inner_iters = inner_total;
+            info->max_rel_residual = maxrel;
+        }
+        return converged ? LAP_OK : LAP_ENOCONV;
+    }
+
+    template <int NR, class Op>
+    void rowsd(int64_t n, const Op &op, double bytes) {
+        const int nvb = (int)((n + RPB64 - 1) / RPB64);
+        const int gx = NR > 0 ? red_grid(nvb) : plain_grid(nvb);
+        dim3 grid(gx, ntiles64);
+        CFC_LAUNCH(LAP_KF_BLAS1, s, bytes, (k_rows<double, K64, NR, Op>), grid, kBlock, 0, (int)n, op, rb);
+    }
+
+    Tin *dbuf = nullptr;
+};
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+template <typename Tin, int KT>
+lap_status_t run_solver(lap_hierarchy *h, int32_t k, const double *B, double *X, const lap_solve_opts_t &o,
+                        cudaStream_t s, lap_solve_info_t *info) {
+    const int ld = ((k + KT - 1) / KT) * KT;
+    const int ntiles = ld / KT;
+    CFC_REQUIRE(ntiles <= kMaxTiles, LAP_EBUDGET, "too many column tiles");
+    Solver<Tin, KT> S(h, s, k, ld, o);
+    const int nlev = S.nlev;
+    // workspace layout
+    const int64_t n0 = h->lv[0].n;
+    int64_t max_chunks = 0;
+    for (int l = 0; l < nlev; ++l) max_chunks = std::max<int64_t>(max_chunks, h->lv[l].n_chunks);
+    std::vector<size_t> sizes;
+    sizes.push_back(align_up(n0 * ld * 8));  // b64
+    sizes.push_back(align_up(n0 * ld * 8));  // x64
+    sizes.push_back(align_up(n0 * ld * sizeof(Tin)));  // r
+    sizes.push_back(align_up(n0 * ld * sizeof(Tin)));  // z
+    sizes.push_back(align_up(n0 * ld * sizeof(Tin)));  // p
+    sizes.push_back(align_up(n0 * ld * sizeof(Tin)));  // q
+    sizes.push_back(align_up(n0 * ld * sizeof(Tin)));  // d
+    sizes.push_back(align_up(n0 * ld * sizeof(Tin)));  // t0
+    for (int l = 1; l < nlev; ++l)
+        for (int v = 0; v < 3; ++v) sizes.push_back(align_up((size_t)h->lv[l].n * ld * sizeof(Tin)));
+    sizes.push_back(align_up(std::max<int64_t>(max_chunks, 1) * ld * 8));  // chunk partials (FP64 size)
+    const int P = 2 * num_sms();
+    sizes.push_back(align_up((size_t)ntiles * 4 * KT * P * 8));  // reduction partials
+    sizes.push_back(align_up(kMaxTiles * 4));                     // counters
+    sizes.push_back(align_up(ld * 8) * 7);                        // column doubles
+    sizes.push_back(align_up(ld * 4) * 2);                        // column flags
+    size_t total = 0;
+    for (size_t z : sizes) total += z;
+    if (h->ws_bytes < total) {
+        h->ws.release();
+        h->ws.alloc_persistent(total);
+        h->ws_bytes = total;
+        h->ws_dirty = true;
+    }
+    char *base = h->ws.get();
+    size_t off = 0;
+    auto take = [&](size_t idx) {
+        char *p = base + off;
+        off += sizes[idx];
+        return p;
+    };
+    size_t idx = 0;
+    S.b64 = (double *)take(idx++);
+    S.x64 = (double *)take(idx++);
+    S.r = (Tin *)take(idx++);
+    S.z = (Tin *)take(idx++);
+    S.p = (Tin *)take(idx++);
+    S.q = (Tin *)take(idx++);
+    S.dbuf = (Tin *)take(idx++);
+    S.t0 = (Tin *)take(idx++);
+    Tin *t0 = S.t0;
+    S.lb.assign(nlev, nullptr);
+    S.lx.assign(nlev, nullptr);
+    S.lt.assign(nlev, nullptr);
+    S.lb[0] = S.r;
+    S.lx[0] = S.z;
+    S.lt[0] = t0;
+    for (int l = 1; l < nlev; ++l) {
+        S.lb[l] = (Tin *)take(idx++);
+        S.lx[l] = (Tin *)take(idx++);
+        S.lt[l] = (Tin *)take(idx++);
+    }
+    S.chunk_part = (Tin *)take(idx);
+    S.chunk_part64 = (double *)take(idx++);
+    S.rb.part = (double *)take(idx++);
+    S.rb.counter = (uint32_t *)take(idx++);
+    {
+        char *cd = take(idx++);
+        const size_t st = align_up(ld * 8);
+        S.cs.bnorm = (double *)(cd + 0 * st);
+        S.cs.relres = (double *)(cd + 1 * st);
+        S.cs.alpha = (double *)(cd + 2 * st);
+        S.cs.beta = (double *)(cd + 3 * st);
+        S.cs.rz = (double *)(cd + 4 * st);
+        S.cs.rr0 = (double *)(cd + 5 * st);
+        S.cs.mu = (double *)(cd + 6 * st);
+        char *cf = take(idx++);
+        S.cs.active_out = (int32_t *)cf;
+        S.cs.active_in = (int32_t *)(cf + align_up(ld * 4));
+    }
+    if (h->ws_dirty) {
+        // arrival counters must start at zero; every kernel leaves them at zero
+        CFC_CUDA(cudaMemsetAsync(S.rb.counter, 0, kMaxTiles * 4, s));
+        h->ws_dirty = false;
+    }
+    CFC_CUDA(cudaMemsetAsync(S.cs.active_in, 0, ld * 4, s));
+    S.h_active = pinned_scratch();
+    return S.run(B, X, info);
+}
+
+}  // namespace
+
+int num_sms_public() { return num_sms(); }
+
+int32_t *pinned_scratch() {
+    thread_local int32_t *buf = nullptr;
+    if (!buf) CFC_CUDA(cudaMallocHost((void **)&buf, 8192 * sizeof(int32_t)));
+    return buf;
+}
+
+lap_status_t solve_multi(lap_hierarchy *h, int32_t k, const double *B, double *X, const lap_solve_opts_t &o,
+                         cudaStream_t s, lap_solve_info_t *info) {
+    CFC_REQUIRE(k >= 1 && k <= 4096, LAP_EINVAL, "need 1 <= k <= 4096");
+    CFC_REQUIRE(B && X && B != X, LAP_EINVAL, "B and X must be distinct device buffers");
+    CFC_REQUIRE(is_device_pointer(B) && is_device_pointer(X), LAP_EINVAL, "B and X must be device pointers");
+    CFC_REQUIRE(o.tol > 0 && o.max_outer >= 0 && o.max_inner >= 1, LAP_EINVAL, "bad solve options");
+    int kt = o.k_tile;
+    const bool fp64 = (o.precision == LAP_FP64);
+    if (kt == 0) kt = (k >= 64) ? 64 : (k > 16 ? 32 : 16);
+    if (fp64 && kt > 64) kt = 64;
+    while ((k + kt - 1) / kt > kMaxTiles) kt *= 2;
+    CFC_REQUIRE(kt == 16 || kt == 32 || kt == 64 || (kt == 128 && !fp64), LAP_EINVAL, "k_tile must be 16/32/64/128");
+    if (fp64) {
+        switch (kt) {
+            case 16: return run_solver<double, 16>(h, k, B, X, o, s, info);
+            case 32: return run_solver<double, 32>(h, k, B, X, o, s, info);
+            default: return run_solver<double, 64>(h, k, B, X, o, s, info);
+        }
+    }
+    switch (kt) {
+        case 16: return run_solver<float, 16>(h, k, B, X, o, s, info);
+        case 32: return run_solver<float, 32>(h, k, B, X, o, s, info);
+        case 64: return run_solver<float, 64>(h, k, B, X, o, s, info);
+        default: return run_solver<float, 128>(h, k, B, X, o, s, info);
+    }
+}
+
+}  // namespace cfc

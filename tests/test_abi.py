@@ -1,0 +1,64 @@
+"""CPU checks of the boundary: the library builds, loads and exports every
+function include/cfc_gb300.h declares (no compute calls without a GPU), and
+the product path does not touch the oracle."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "cfc_gb300.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b((?:lap|cfc)_[a-z0-9_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_1607_02955_gb300 import build_ext
+    build_ext.build()
+    import paper_1607_02955_gb300 as P
+    return P
+
+
+def test_library_exports_every_declared_symbol(P):
+    import ctypes
+    L = ctypes.CDLL(P.lib_path)
+    decl = _declared()
+    assert len(decl) >= 15
+    missing = [s for s in decl if not hasattr(L, s)]
+    assert not missing, missing
+    assert set(decl) == set(P._binding.SYMBOLS)
+
+
+def test_status_strings_and_defaults(P):
+    assert P.lap_status_string(P.LAP_OK) == "LAP_OK"
+    assert "not connected" in P.lap_status_string(P.LAP_ENOTCONN)
+    o = P.lap_default_solve_opts()
+    assert o.tol == 1e-8 and o.precision == P.LAP_FP32_REFINED
+    h = P.lap_default_hier_opts()
+    assert h.coarse_max == 64 and h.agg_passes == 2
+
+
+def test_product_does_not_import_oracle():
+    pkg = os.path.join(ROOT, "paper_1607_02955_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle", txt, flags=re.M), f
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith(".py"):
+            txt = open(os.path.join(ROOT, "oracle", f)).read()
+            assert not re.search(r"^\s*(import|from)\s+paper_1607_02955_gb300", txt, flags=re.M), f
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    from paper_1607_02955_gb300 import _binding
+    monkeypatch.setattr(_binding, "lib_path", str(tmp_path / "absent.so"))
+    monkeypatch.setattr(_binding, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        _binding.lib()

@@ -1,0 +1,248 @@
+"""Parity of the CUDA path (called through the C ABI) with the CPU oracle.
+
+Tolerances: the solver stops at a per-column relative residual of 1e-8
+(FP64 outer residual); farness estimates must match the oracle to relative
+error <= 1e-6 in the FP64-refined modes, the dense exact path to 1e-9,
+integer outputs (pivots) bit for bit.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import cg as ocg
+from oracle import dense, jl, sampling
+from oracle.graph import canonical_graph, laplacian
+
+pytestmark = pytest.mark.gpu
+
+FARNESS_RTOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def P():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1607_02955_gb300 import build_ext
+    build_ext.build()
+    import paper_1607_02955_gb300 as P
+    torch.cuda.init()
+    return P
+
+
+def _graph(gen, weighted=True, seed=7):
+    n, s, d, _ = gen
+    w = synth.uniform_weights(s.size, seed=seed) if weighted else None
+    return n, s, d, w
+
+
+def _rel(a, b):
+    return np.max(np.abs(np.asarray(a) - np.asarray(b)) / np.maximum(np.abs(np.asarray(b)), 1e-300))
+
+
+# ------------------------------------------------------------------ ingest / hierarchy
+def test_hierarchy_sizes(P):
+    n, s, d, w = _graph(synth.grid2d(48))
+    h = P.lap_build_hierarchy(n, s, d, w)
+    info = P.lap_hierarchy_info(h)
+    assert info["n"] == 2304 and info["m"] == 4512
+    assert info["level_nnz"][0] == 2 * 4512
+    assert info["levels"] >= 2
+    assert info["coarse_n"] == info["level_n"][-1] <= 64
+    for a, b in zip(info["level_n"], info["level_n"][1:]):
+        assert b < a
+
+
+def test_duplicates_selfloops_merged(P):
+    # parallel edges add, self-loops vanish, orientation is ignored
+    src = np.array([0, 1, 1, 2, 2, 3, 0], np.int32)
+    dst = np.array([1, 0, 2, 2, 3, 0, 1], np.int32)
+    w = np.array([1.0, 2.0, 4.0, 9.0, 1.0, 1.0, 3.0])
+    f, c = P.cfc_exact_small(4, src, dst, w)
+    g = canonical_graph(4, src, dst, w)
+    np.testing.assert_allclose(f, dense.farness(g), rtol=1e-12)
+    np.testing.assert_allclose(c, dense.closeness(g), rtol=1e-12)
+
+
+@pytest.mark.parametrize("bad", ["disconnected", "range", "weight", "nan"])
+def test_input_errors(P, bad):
+    src = np.array([0, 1, 2], np.int32)
+    dst = np.array([1, 2, 3], np.int32)
+    w = np.ones(3)
+    n = 4
+    want = P.LAP_EINVAL
+    if bad == "disconnected":
+        n, want = 6, P.LAP_ENOTCONN
+    elif bad == "range":
+        dst = np.array([1, 2, 4], np.int32)
+    elif bad == "weight":
+        w = np.array([1.0, 0.0, 1.0])
+    else:
+        w = np.array([1.0, np.nan, 1.0])
+    with pytest.raises(P.LapError) as e:
+        P.lap_build_hierarchy(n, src, dst, w)
+    assert e.value.status == want
+
+
+# ------------------------------------------------------------------ JL right-hand sides
+@pytest.mark.parametrize("k", [32, 5, 300])
+def test_jl_rhs_matches_oracle(P, k):
+    import torch
+    n, s, d, w = _graph(synth.barabasi_albert(1500, 5, seed=3))  # hubs: split rows
+    g = canonical_graph(n, s, d, w)
+    h = P.lap_build_hierarchy(n, s, d, w)
+    Y = torch.empty((n, k), dtype=torch.float64, device="cuda")
+    P.cfc_jl_rhs(h, k, 11, Y)
+    Yo = jl.jl_rhs(g, k, 11).T
+    np.testing.assert_allclose(Y.cpu().numpy(), Yo, rtol=0, atol=1e-13 * np.abs(Yo).max())
+
+
+# ------------------------------------------------------------------ solver
+SOLVE_CASES = [
+    ("grid48", lambda: synth.grid2d(48), 32),
+    ("ba3000", lambda: synth.barabasi_albert(3000, 5, seed=2), 17),
+    ("star", lambda: synth.star_graph(700), 8),
+    ("path", lambda: synth.path_graph(400), 16),
+    ("er", lambda: synth.erdos_renyi_connected(500, 0.02, seed=5), 70),
+]
+
+
+@pytest.mark.parametrize("name,gen,k", SOLVE_CASES)
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_solve_matches_dense_pinv(P, name, gen, k, precision):
+    import torch
+    n, s, d, w = _graph(gen())
+    g = canonical_graph(n, s, d, w)
+    h = P.lap_build_hierarchy(n, s, d, w)
+    rng = np.random.default_rng(1)
+    B = rng.standard_normal((n, k))
+    Bt = torch.tensor(B, device="cuda")
+    Xt = torch.empty_like(Bt)
+    opts = P.lap_default_solve_opts(precision=P.LAP_FP64 if precision == "fp64" else P.LAP_FP32_REFINED)
+    info = P.lap_solve_multi(h, Bt, Xt, opts)
+    assert info["max_rel_residual"] <= 1e-8
+    X = Xt.cpu().numpy()
+    Bp = B - B.mean(axis=0)
+    # independent residual check in FP64 on the CPU
+    R = Bp - laplacian(g) @ X
+    assert np.all(np.linalg.norm(R, axis=0) <= 1.01e-8 * np.linalg.norm(Bp, axis=0))
+    np.testing.assert_allclose(X.mean(axis=0), 0, atol=1e-12 * np.abs(X).max())
+    Xd = dense.pinv(g) @ Bp
+    err = np.linalg.norm(X - Xd, axis=0) / np.linalg.norm(Xd, axis=0)
+    # ||x - x*|| / ||x*|| <= kappa * ||r|| / ||b||, kappa = lambda_max / lambda_2 on 1-perp
+    lam = np.linalg.eigvalsh(laplacian(g).toarray())
+    kappa = lam[-1] / lam[1]
+    assert err.max() <= kappa * 1.01e-8, (err.max(), kappa)
+
+
+def test_solve_is_deterministic_and_column_independent(P):
+    import torch
+    n, s, d, w = _graph(synth.barabasi_albert(4000, 5, seed=9))
+    h = P.lap_build_hierarchy(n, s, d, w)
+    B = torch.randn((n, 48), dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+    X1, X2 = torch.empty_like(B), torch.empty_like(B)
+    o = P.lap_default_solve_opts(k_tile=16)
+    P.lap_solve_multi(h, B, X1, o)
+    P.lap_solve_multi(h, B, X2, o)
+    assert torch.equal(X1, X2)
+    # the first 16 columns alone give the same bits (same tile width)
+    Xs = torch.empty((n, 16), dtype=torch.float64, device="cuda")
+    P.lap_solve_multi(h, B[:, :16].contiguous(), Xs, o)
+    assert torch.equal(Xs, X1[:, :16])
+
+
+def test_solve_noconv_reports(P):
+    import torch
+    n, s, d, w = _graph(synth.grid2d(40))
+    h = P.lap_build_hierarchy(n, s, d, w)
+    B = torch.randn((n, 4), dtype=torch.float64, device="cuda")
+    X = torch.empty_like(B)
+    o = P.lap_default_solve_opts(max_outer=1, max_inner=2, inner_tol=1e-2)
+    info = P.lap_solve_multi(h, B, X, o, allow_noconv=True)
+    assert info["status"] == P.LAP_ENOCONV and info["max_rel_residual"] > 1e-8
+    assert torch.isfinite(X).all()
+
+
+# ------------------------------------------------------------------ estimators
+@pytest.mark.parametrize("gen,k", [(lambda: synth.grid2d(48), 32), (lambda: synth.barabasi_albert(2000, 5, 4), 64),
+                                   (lambda: synth.star_graph(300), 24)])
+def test_farness_jl_matches_oracle(P, gen, k):
+    n, s, d, w = _graph(gen())
+    g = canonical_graph(n, s, d, w)
+    h = P.lap_build_hierarchy(n, s, d, w)
+    nodes = np.array([0, 1, n // 2, n - 1], np.int32)
+    f = P.cfc_farness_jl(h, k, 1, nodes)
+    fo = jl.jl_farness(g, k, 1, nodes.tolist(), solver="dense")
+    assert _rel(f, fo) <= FARNESS_RTOL
+
+
+def test_farness_jl_eps_rule(P):
+    n, s, d, w = _graph(synth.grid2d(20))
+    g = canonical_graph(n, s, d, w)
+    h = P.lap_build_hierarchy(n, s, d, w)
+    f = P.cfc_farness_jl(h, 0, 3, [5], eps=0.5)
+    k = jl.k_from_eps(n, 0.5)
+    assert _rel(f, jl.jl_farness(g, k, 3, [5])) <= FARNESS_RTOL
+
+
+@pytest.mark.parametrize("n,kk,seed", [(2304, 200, 1), (100, 100, 2), (5000, 7, 3), (64, 1, 4)])
+def test_pivots_bit_exact(P, n, kk, seed):
+    ns, s, d, w = _graph(synth.path_graph(n))
+    h = P.lap_build_hierarchy(ns, s, d, w)
+    piv = P.cfc_sample_pivots(h, kk, seed)
+    assert np.array_equal(piv, sampling.floyd_pivots(n, kk, seed))
+
+
+@pytest.mark.parametrize("gen,kk", [(lambda: synth.grid2d(30), 20), (lambda: synth.barabasi_albert(1200, 5, 6), 50)])
+def test_farness_sampled_matches_pair_solves(P, gen, kk):
+    n, s, d, w = _graph(gen())
+    g = canonical_graph(n, s, d, w)
+    h = P.lap_build_hierarchy(n, s, d, w)
+    nodes = np.array([3, n - 2, 17], np.int32)
+    f = P.cfc_farness_sampled(h, kk, 9, nodes)
+    fo = sampling.sampled_farness(g, kk, 9, nodes.tolist(), solver="dense")
+    assert _rel(f, fo) <= FARNESS_RTOL
+
+
+def test_farness_sampled_all_pivots_is_exact(P):
+    n, s, d, w = _graph(synth.barabasi_albert(90, 3, seed=1))
+    g = canonical_graph(n, s, d, w)
+    h = P.lap_build_hierarchy(n, s, d, w)
+    f = P.cfc_farness_sampled(h, n, 5, [0, 45, 89])
+    assert _rel(f, dense.farness(g)[[0, 45, 89]]) <= FARNESS_RTOL
+
+
+@pytest.mark.parametrize("gen", [lambda: synth.grid2d(48), lambda: synth.barabasi_albert(1000, 5, 2),
+                                 lambda: synth.complete_graph(30), lambda: synth.path_graph(2)])
+def test_exact_small_matches_dense_oracle(P, gen):
+    n, s, d, w = _graph(gen())
+    g = canonical_graph(n, s, d, w)
+    f, c = P.cfc_exact_small(n, s, d, w)
+    fo = dense.farness(g)
+    assert _rel(f, fo) <= 1e-9
+    assert _rel(c, dense.closeness(g, fo)) <= 1e-9
+
+
+def test_exact_small_cross_checked_by_cg_solves(P):
+    # exact farness (dense L+) against n CG solves with b = e_v - 1/n (Sec. 4 exact methods)
+    n, s, d, w = _graph(synth.grid2d(12, 10))
+    g = canonical_graph(n, s, d, w)
+    f, _ = P.cfc_exact_small(n, s, d, w)
+    X, _, _ = ocg.cg_solve(laplacian(g), np.eye(n), tol=1e-13)
+    fo = n * np.diag(X) + np.trace(X)
+    assert _rel(f, fo) <= 1e-8
+
+
+# ------------------------------------------------------------------ full-size sampled parity
+@pytest.mark.slow
+def test_ba100k_jl_node0_matches_oracle(P):
+    """The 100k-node Barabasi-Albert configuration with k = 64 in the
+    benchmark's launch configuration (default options): farness of node 0
+    against the oracle's FP64 CG (1e-12) on the same right-hand sides."""
+    n, s, d, _ = synth.barabasi_albert(100000, 5, seed=2)
+    w = synth.uniform_weights(s.size, seed=2)
+    g = canonical_graph(n, s, d, w)
+    h = P.lap_build_hierarchy(n, s, d, w)
+    f = P.cfc_farness_jl(h, 64, 1, [0])
+    fo = jl.jl_farness(g, 64, 1, [0], solver="cg", tol=1e-12)
+    assert _rel(f, fo) <= FARNESS_RTOL
