@@ -1,0 +1,322 @@
+"""Benchmark: right-hand sides solved per second to relative residual 1e-8.
+
+One step is one pass of the whole hot path on the 100k-node Barabasi-Albert
+workload (5 edges per new node, weights uniform in [1, 2), seed 2): ingest
+of the edge list and construction of the multigrid hierarchy
+(lap_build_hierarchy), generation of the k = 64 Johnson-Lindenstrauss
+right-hand sides, the block solve to ||b - Lx|| <= 1e-8 ||b|| per column in
+FP32 PCG + V-cycle inside FP64 refinement, and the farness reduction for
+node 0 (cfc_farness_jl).  value = 64 * N / step time.
+
+--impl reference times the CPU FP64 oracle on the same workload and metric.
+Run with torchrun for N > 1 GPUs: every rank solves its own independent
+instance (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "RHS solved/s to rel. residual 1e-8"
+WORKLOADS = {
+    "ba100k_jl64": dict(kind="ba", n=100000, m_per=5, seed=2, k=64, jl_seed=1, nodes=[0]),
+    "grid48_jl32": dict(kind="grid", a=48, k=32, jl_seed=1, nodes=[0]),
+    "rmat20_jl64": dict(kind="rmat", scale=20, seed=3, k=64, jl_seed=1, nodes=[0]),
+}
+
+
+def make_graph(wl):
+    if wl["kind"] == "ba":
+        n, s, d, _ = synth.barabasi_albert(wl["n"], wl["m_per"], seed=wl["seed"])
+        w = synth.uniform_weights(s.size, seed=wl["seed"])
+    elif wl["kind"] == "grid":
+        n, s, d, w = synth.grid2d(wl["a"])
+    else:
+        n, s, d, w = synth.rmat(wl["scale"], seed=wl["seed"])
+    return n, s, d, w
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            j = json.load(fh)
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    def __init__(self, gpu_index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args, wl, rank, world):
+    """CPU oracle on the same workload: JL farness with the oracle's FP64 CG
+    to relative residual 1e-8, timed on the host cores."""
+    if rank != 0:
+        return
+    from oracle import jl
+    from oracle.graph import canonical_graph
+    n, s, d, w = make_graph(wl)
+    k = wl["k"]
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        g = canonical_graph(n, s, d, w)
+        jl.jl_farness(g, k, wl["jl_seed"], wl["nodes"], solver="cg", tol=1e-8)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    sec = sum(times) / len(times)
+    value = k / sec
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "k": k, "n": n, "m": int(s.size)},
+            "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": cores, "kind": "oracle",
+                             "sample": f"full {args.workload} step (canonical graph, {k} JL RHS, FP64 Jacobi-CG "
+                                       f"to 1e-8, farness of node 0) per step"},
+            "e2e": {"value": value, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(wl):
+    """Oracle on a bounded sample of the workload: 8 of the k JL columns."""
+    from oracle import jl
+    from oracle.cg import cg_solve
+    from oracle.graph import canonical_graph, laplacian
+    n, s, d, w = make_graph(wl)
+    ks = 8
+    t0 = time.perf_counter()
+    g = canonical_graph(n, s, d, w)
+    Y = jl.jl_rhs(g, wl["k"], wl["jl_seed"])[:ks]
+    cg_solve(laplacian(g), Y.T, tol=1e-8)
+    sec = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": ks / sec, "unit": "RHS/s", "cores": cores, "kind": "oracle",
+            "sample": f"{ks} of the {wl['k']} JL right-hand sides (canonical graph + RHS + FP64 Jacobi-CG to 1e-8)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ba100k_jl64", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--levels", type=int, default=-1, help="levels_used override (-1 = tuned default)")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, wl, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    torch.cuda.init()
+    import paper_1607_02955_gb300 as P
+    from paper_1607_02955_gb300 import build_ext
+    build_ext.build()
+
+    n, s, d, w = make_graph(wl)
+    k = wl["k"]
+    nodes = np.array(wl["nodes"], np.int32)
+    dev = torch.device("cuda", local)
+    src_d = torch.tensor(s, dtype=torch.int32, device=dev)
+    dst_d = torch.tensor(d, dtype=torch.int32, device=dev)
+    w_d = torch.tensor(w, dtype=torch.float64, device=dev) if w is not None else None
+    nodes_d = torch.tensor(nodes, device=dev)
+    far_d = torch.empty(len(nodes), dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    sp = stream.cuda_stream
+    sopts = P.lap_default_solve_opts()
+    if args.levels >= 0:
+        sopts.levels_used = args.levels
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+
+    def step_device():
+        h = P.lap_build_hierarchy(n, src_d, dst_d, w_d, stream=sp)
+        P.cfc_farness_jl(h, k, wl["jl_seed"], nodes_d, opts=sopts, out=far_d, stream=sp)
+        h.destroy()
+
+    # host-buffer variant: pinned host inputs, result read back to the host
+    src_h = torch.tensor(s, dtype=torch.int32).pin_memory()
+    dst_h = torch.tensor(d, dtype=torch.int32).pin_memory()
+    w_h = torch.tensor(w, dtype=torch.float64).pin_memory() if w is not None else None
+    far_h = torch.empty(len(nodes), dtype=torch.float64).pin_memory()
+
+    def step_host():
+        h = P.lap_build_hierarchy(n, src_h, dst_h, w_h, stream=sp)
+        P.cfc_farness_jl(h, k, wl["jl_seed"], nodes, opts=sopts, out=far_h, stream=sp)
+        h.destroy()
+
+    def timed(step, K, instrument=False):
+        total = 0.0
+        with torch.cuda.stream(stream):
+            for _ in range(K):
+                flush.fill_(1.0)
+                torch.cuda.synchronize()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                step()
+                b.record(stream)
+                b.synchronize()
+                total += a.elapsed_time(b)
+        return total
+
+    for _ in range(args.warmup):
+        step_device()
+        step_host()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    P.lap_stats_reset()
+    ms_total = timed(step_device, args.steps)
+    stats = P.lap_stats_read()
+    clocks = clk.stop()
+    torch.cuda.synchronize()
+    barrier(world)
+    ms_total = max_over_ranks(ms_total, world)
+    ms_step = ms_total / args.steps
+    value = k * world / (ms_step / 1e3)
+    launches = stats["launches_total"]
+
+    # end to end through the C ABI with host buffers
+    barrier(world)
+    ms_e2e = max_over_ranks(timed(step_host, args.steps) / args.steps, world)
+    e2e_value = k * world / (ms_e2e / 1e3)
+    h2d = int(s.size) * (4 + 4 + (8 if w is not None else 0)) + len(nodes) * 4
+    d2h = len(nodes) * 8
+
+    # instrumented pass: per-kernel-family device time by CUDA events on the launch stream
+    P.lap_stats_reset()
+    P.lap_stats_set_timing(True)
+    timed(step_device, args.steps)
+    fam = P.lap_stats_read()["families"]
+    P.lap_stats_set_timing(False)
+    solve_fams = {kf: v for kf, v in fam.items() if v["ms"] > 0}
+    dom = max(solve_fams, key=lambda kf: solve_fams[kf]["ms"])
+    peak, peak_src = read_peaks()
+    dm = fam[dom]
+    achieved = (dm["bytes"] / 1e9) / (dm["ms"] / 1e3) if dm["ms"] > 0 else 0.0
+
+    # setup alone (ingest + hierarchy) and solver iteration counts, for context
+    h = P.lap_build_hierarchy(n, src_d, dst_d, w_d, stream=sp)
+    hinfo = P.lap_hierarchy_info(h)
+    Y = torch.empty((n, k), dtype=torch.float64, device=dev)
+    X = torch.empty_like(Y)
+    P.cfc_jl_rhs(h, k, wl["jl_seed"], Y, stream=sp)
+    sinfo = P.lap_solve_multi(h, Y, X, sopts, stream=sp)
+    h.destroy()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "m": int(s.size), "k": k,
+                       "query_nodes": wl["nodes"], "tol": 1e-8, "precision": "fp32 V-cycle/PCG in fp64 refinement",
+                       "setup_included": True, "l2": "flushed between steps (256 MiB write, untimed)",
+                       "levels": hinfo["levels"], "level_n": hinfo["level_n"], "setup_ms": hinfo["setup_ms"],
+                       "outer_iters": sinfo["outer_iters"], "inner_iters": sinfo["inner_iters"],
+                       "max_rel_residual": sinfo["max_rel_residual"],
+                       "parallelism": f"{world} independent replicas"},
+            "e2e": {"value": e2e_value, "unit": "RHS/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "kernel_family": dom, "achieved": achieved, "peak": peak,
+                         "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "launches": dm["launches"], "ms": dm["ms"]},
+            "family_ms_per_step": {kf: v["ms"] / args.steps for kf, v in fam.items()},
+            "clocks": clocks,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(wl)
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

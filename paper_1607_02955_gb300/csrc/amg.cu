@@ -53,35 +53,60 @@ __device__ __forceinline__ uint32_t edge_hash(uint32_t a, uint32_t b) {
     return (uint32_t)x;
 }
 
-// priority of edge (i, j): strength first, then the hash
-__device__ __forceinline__ bool better(float s, uint32_t h, float bs, uint32_t bh) {
-    return s > bs || (s == bs && h > bh);
+// priority of edge (i, j): strength first, then the hash, then the smaller j
+struct Cand {
+    float s;
+    uint32_t h;
+    int32_t j;
+};
+__device__ __forceinline__ bool better(const Cand &a, const Cand &b) {
+    if (a.j < 0) return false;
+    if (b.j < 0) return true;
+    if (a.s != b.s) return a.s > b.s;
+    if (a.h != b.h) return a.h > b.h;
+    return a.j < b.j;
+}
+__device__ __forceinline__ Cand warp_best(Cand c) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        Cand o{__shfl_down_sync(0xffffffffu, c.s, d), __shfl_down_sync(0xffffffffu, c.h, d),
+               __shfl_down_sync(0xffffffffu, c.j, d)};
+        if (better(o, c)) c = o;
+    }
+    return c;
+}
+
+#define WARP_ROW_LOOP(i, count)                                                              \
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < (count);       \
+         i += ((int64_t)gridDim.x * blockDim.x) >> 5)
+
+// strongest neighbour of row i among those with (match[j] < 0) == want_unmatched;
+// one warp per row, lanes stride over the row
+__device__ __forceinline__ Cand best_neighbour(const int32_t *rowptr, const int32_t *col, const double *w,
+                                               const double *deg, const int32_t *match, int32_t i,
+                                               bool want_unmatched) {
+    const int lane = threadIdx.x & 31;
+    const double di = deg[i];
+    Cand b{-1.f, 0u, -1};
+    for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) {
+        const int32_t j = col[e];
+        if ((match[j] < 0) != want_unmatched) continue;
+        Cand c{(float)(w[e] / fmax(di, deg[j])), edge_hash((uint32_t)i, (uint32_t)j), j};
+        if (better(c, b)) b = c;
+    }
+    return warp_best(b);
 }
 
 __global__ void k_propose(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                           const double *__restrict__ w, const double *__restrict__ deg, int32_t n,
                           const int32_t *__restrict__ match, int32_t *__restrict__ prop) {
-    GRID_LOOP(i, n) {
+    WARP_ROW_LOOP(i, n) {
         if (match[i] >= 0) {
-            prop[i] = -1;
+            if ((threadIdx.x & 31) == 0) prop[i] = -1;
             continue;
         }
-        const double di = deg[i];
-        int32_t best = -1;
-        float bs = -1.f;
-        uint32_t bh = 0;
-        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
-            const int32_t j = col[e];
-            if (match[j] >= 0) continue;
-            const float s = (float)(w[e] / fmax(di, deg[j]));
-            const uint32_t h = edge_hash((uint32_t)i, (uint32_t)j);
-            if (best < 0 || better(s, h, bs, bh)) {
-                best = j;
-                bs = s;
-                bh = h;
-            }
-        }
-        prop[i] = best;
+        const Cand b = best_neighbour(rowptr, col, w, deg, match, (int32_t)i, true);
+        if ((threadIdx.x & 31) == 0) prop[i] = b.j;
     }
 }
 
@@ -98,31 +123,19 @@ __global__ void k_leaders(const int32_t *__restrict__ rowptr, const int32_t *__r
                           const double *__restrict__ w, const double *__restrict__ deg, int32_t n,
                           const int32_t *__restrict__ match, int32_t *__restrict__ leader,
                           int32_t *__restrict__ is_leader) {
-    GRID_LOOP(i, n) {
+    WARP_ROW_LOOP(i, n) {
         const int32_t mi = match[i];
         int32_t l;
         if (mi >= 0) {
             l = min((int32_t)i, mi);
         } else {
-            const double di = deg[i];
-            int32_t best = -1;
-            float bs = -1.f;
-            uint32_t bh = 0;
-            for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
-                const int32_t j = col[e];
-                if (match[j] < 0) continue;
-                const float s = (float)(w[e] / fmax(di, deg[j]));
-                const uint32_t h = edge_hash((uint32_t)i, (uint32_t)j);
-                if (best < 0 || better(s, h, bs, bh)) {
-                    best = j;
-                    bs = s;
-                    bh = h;
-                }
-            }
-            l = best >= 0 ? min(best, match[best]) : (int32_t)i;
+            const Cand b = best_neighbour(rowptr, col, w, deg, match, (int32_t)i, false);
+            l = b.j >= 0 ? min(b.j, match[b.j]) : (int32_t)i;
         }
-        leader[i] = l;
-        is_leader[i] = (l == (int32_t)i) ? 1 : 0;
+        if ((threadIdx.x & 31) == 0) {
+            leader[i] = l;
+            is_leader[i] = (l == (int32_t)i) ? 1 : 0;
+        }
     }
 }
 
@@ -138,9 +151,10 @@ __global__ void k_compose(int32_t *__restrict__ agg, const int32_t *__restrict__
 // Galerkin: flags of fine entries that cross aggregates
 __global__ void k_cross_flags(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, int32_t n,
                               const int32_t *__restrict__ agg, int32_t *__restrict__ flag) {
-    GRID_LOOP(i, n) {
+    const int lane = threadIdx.x & 31;
+    WARP_ROW_LOOP(i, n) {
         const int32_t I = agg[i];
-        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) flag[e] = (agg[col[e]] != I) ? 1 : 0;
+        for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) flag[e] = (agg[col[e]] != I) ? 1 : 0;
     }
 }
 
@@ -148,9 +162,10 @@ __global__ void k_cross_emit(const int32_t *__restrict__ rowptr, const int32_t *
                              const int32_t *__restrict__ agg, const int32_t *__restrict__ flag,
                              const int32_t *__restrict__ pos, int b, uint64_t *__restrict__ keys,
                              uint32_t *__restrict__ vals) {
-    GRID_LOOP(i, n) {
+    const int lane = threadIdx.x & 31;
+    WARP_ROW_LOOP(i, n) {
         const uint64_t I = (uint32_t)agg[i];
-        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) {
             if (!flag[e]) continue;
             keys[pos[e]] = (I << b) | (uint32_t)agg[col[e]];
             vals[pos[e]] = (uint32_t)e;
@@ -329,12 +344,12 @@ int32_t pairwise_pass(const int32_t *rowptr, const int32_t *col, const double *w
     DBuf<int32_t> match(n, s), prop(n, s), leader(n, s), isl(n, s), lid(n, s);
     CFC_CUDA(cudaMemsetAsync(match.get(), 0xff, n * sizeof(int32_t), s));
     for (int r = 0; r < rounds; ++r) {
-        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_propose, grid_for(n), kBlock, 0, rowptr, col, w, deg, n, match.get(),
-                   prop.get());
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_propose, grid_for(32 * (int64_t)n), kBlock, 0, rowptr, col, w, deg, n,
+                   match.get(), prop.get());
         CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_accept, grid_for(n), kBlock, 0, prop.get(), n, match.get());
     }
-    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_leaders, grid_for(n), kBlock, 0, rowptr, col, w, deg, n, match.get(),
-               leader.get(), isl.get());
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_leaders, grid_for(32 * (int64_t)n), kBlock, 0, rowptr, col, w, deg, n,
+               match.get(), leader.get(), isl.get());
     const int64_t nc = scan_exclusive_i32(isl.get(), lid.get(), n, s);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_assign, grid_for(n), kBlock, 0, leader.get(), lid.get(), n, agg);
     return (int32_t)nc;
@@ -344,7 +359,8 @@ int32_t pairwise_pass(const int32_t *rowptr, const int32_t *col, const double *w
 void contract(const int32_t *rowptr, const int32_t *col, const double *w, int32_t n, int64_t nnz,
               const int32_t *agg, int32_t nc, bool persistent, Graph64 &out, cudaStream_t s) {
     DBuf<int32_t> flag(nnz, s), pos(nnz, s);
-    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_cross_flags, grid_for(n), kBlock, 0, rowptr, col, n, agg, flag.get());
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_cross_flags, grid_for(32 * (int64_t)n), kBlock, 0, rowptr, col, n, agg,
+               flag.get());
     const int64_t len = scan_exclusive_i32(flag.get(), pos.get(), nnz, s);
     const int b = bits_for(nc);
     out.n = nc;
@@ -364,8 +380,8 @@ void contract(const int32_t *rowptr, const int32_t *col, const double *w, int32_
     }
     DBuf<uint64_t> keys(len, s);
     DBuf<uint32_t> vals(len, s);
-    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_cross_emit, grid_for(n), kBlock, 0, rowptr, col, n, agg, flag.get(),
-               pos.get(), b, keys.get(), vals.get());
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_cross_emit, grid_for(32 * (int64_t)n), kBlock, 0, rowptr, col, n, agg,
+               flag.get(), pos.get(), b, keys.get(), vals.get());
     flag.release();
     pos.release();
     radix_sort_pairs(keys.get(), vals.get(), len, 2 * b, s);

@@ -97,6 +97,27 @@ LaunchScope::~LaunchScope() {
     g_pending.push_back(Pending{family, bytes, start, stop});
 }
 
+cudaMemPool_t library_pool() {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    CFC_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p;
+        CFC_CUDA(cudaMemPoolCreate(&p, &props));
+        uint64_t thr = ~uint64_t(0);
+        CFC_CUDA(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &thr));
+        pools[dev] = p;
+    }
+    return pools[dev];
+}
+
 bool is_device_pointer(const void *p) {
     if (!p) return false;
     cudaPointerAttributes a;

@@ -61,6 +61,11 @@ void count_launch();
     } while (0)
 
 // ------------------------------------------------------------------ memory
+// The library's own stream-ordered memory pool (one per device), with a
+// release threshold high enough that freed blocks stay reserved for reuse:
+// repeated builds and solves then allocate without reaching the driver.
+cudaMemPool_t library_pool();
+
 // Device buffers owned by the library.  All allocations are stream-ordered
 // (cudaMallocAsync) and freed the same way.
 template <typename T>
@@ -88,23 +93,22 @@ struct DBuf {
         s = stream;
         n = count;
         async = true;
-        if (count) CFC_CUDA(cudaMallocAsync((void **)&p, count * sizeof(T) + 16, stream));
+        if (count) CFC_CUDA(cudaMallocFromPoolAsync((void **)&p, count * sizeof(T) + 16, library_pool(), stream));
     }
-    // long-lived buffer (hierarchy data, workspace): plain cudaMalloc / cudaFree
+    // long-lived buffer (hierarchy data, workspace): taken from the pool on
+    // the legacy default stream and returned there when released
     void alloc_persistent(size_t count) {
         release();
         n = count;
-        async = false;
-        if (count) CFC_CUDA(cudaMalloc((void **)&p, count * sizeof(T) + 16));
+        async = true;
+        s = nullptr;
+        if (count) CFC_CUDA(cudaMallocFromPoolAsync((void **)&p, count * sizeof(T) + 16, library_pool(), nullptr));
     }
     void zero(cudaStream_t stream) const {
         if (n) CFC_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), stream));
     }
     void release() noexcept {
-        if (p) {
-            if (async) cudaFreeAsync(p, s);
-            else cudaFree(p);
-        }
+        if (p) cudaFreeAsync(p, s);
         p = nullptr;
         n = 0;
     }
@@ -136,7 +140,7 @@ struct Level {
     DBuf<int32_t> mem_ptr, mem;  // members of each coarse node, ascending
 };
 
-constexpr int kLongRow = 64;     // row split threshold (nonzeros)
+constexpr int kLongRow = 64;     // row split threshold and chunk length (nonzeros)
 constexpr int kMaxTiles = 64;    // column tiles per launch (k <= 64 * 64)
 constexpr int kBlock = 256;
 
@@ -196,7 +200,6 @@ struct lap_hierarchy {
     // solve workspace, grown on demand
     cfc::DBuf<char> ws;
     size_t ws_bytes = 0;
-    bool ws_dirty = true;             // workspace counters need zeroing
     cudaStream_t ws_stream = nullptr;
 };
 

@@ -99,13 +99,26 @@ template <>
 __device__ __forceinline__ double ldinv<double>(const LevelView &A, int i) { return __ldg(A.dinv64 + i); }
 
 // ------------------------------------------------------------------ reductions
+// Two-level, fixed-order cross-block reduction.  Blocks are grouped in teams
+// of kTeam consecutive blocks; the last block of a team to arrive sums the
+// team's partials (in block order), and the last team to arrive sums the
+// team partials (in team order) and runs the per-column finalisation.  No
+// block waits for another, and the order of every sum is fixed.
+constexpr int kTeam = 32;
+constexpr int kMaxTeams = 128;
+
 struct RedBuf {
-    double *part;       // [ntiles][NR*KT][P]
-    uint32_t *counter;  // [ntiles], zero between launches
+    double *part;            // [ntiles][NR*KT][P]
+    double *team_part;       // [ntiles][NR*KT][kMaxTeams]
+    uint32_t *counter;       // [kMaxTiles], zero between launches
+    uint32_t *team_counter;  // [kMaxTiles][kMaxTeams], zero between launches
 };
 
-template <int KT, int NR, int VW, int RPB, class Op>
-__device__ __forceinline__ void block_reduce_finalize(double (&acc)[NR][VW], int lane, int grp, RedBuf rb,
+// acc holds this thread's partial sums in the kernel's arithmetic type (FP32
+// partials over a few rows: FP64 per element would run on GB300's narrow
+// FP64 pipe); the block, team and final stages add in FP64.
+template <int KT, int NR, int VW, int RPB, typename TA, class Op>
+__device__ __forceinline__ void block_reduce_finalize(TA (&acc)[NR][VW], int lane, int grp, RedBuf rb,
                                                       Op &op) {
     constexpr int NO = NR * KT;
     __shared__ double sm[RPB][NO];
@@ -114,7 +127,7 @@ __device__ __forceinline__ void block_reduce_finalize(double (&acc)[NR][VW], int
 #pragma unroll
     for (int r = 0; r < NR; ++r)
 #pragma unroll
-        for (int v = 0; v < VW; ++v) sm[grp][r * KT + lane * VW + v] = acc[r][v];
+        for (int v = 0; v < VW; ++v) sm[grp][r * KT + lane * VW + v] = (double)acc[r][v];
     __syncthreads();
     const int tile = blockIdx.y;
     const int P = gridDim.x;
@@ -125,21 +138,48 @@ __device__ __forceinline__ void block_reduce_finalize(double (&acc)[NR][VW], int
     }
     __threadfence();
     __syncthreads();
+    const int team = blockIdx.x / kTeam;
+    const int team_size = min(kTeam, P - team * kTeam);
+    const int nteams = (P + kTeam - 1) / kTeam;
     if (threadIdx.x == 0) {
-        const uint32_t t = atomicAdd(rb.counter + tile, 1u);
-        is_last = (t == (uint32_t)P - 1);
+        const uint32_t t = atomicAdd(rb.team_counter + tile * kMaxTeams + team, 1u);
+        is_last = (t == (uint32_t)team_size - 1);
     }
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    const int wl = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int o = wid; o < NO; o += nw) {
-        const double *src = rb.part + ((size_t)tile * NO + o) * P;
-        double s = 0.0;
-        for (int p = wl; p < P; p += 32) s += __ldcg(src + p);
+    // team stage: one thread per output, the team's partials loaded together
+    for (int o = threadIdx.x; o < NO; o += blockDim.x) {
+        const double *src = rb.part + ((size_t)tile * NO + o) * P + team * kTeam;
+        double v[kTeam];
 #pragma unroll
-        for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d);
-        if (wl == 0) fin[o] = s;
+        for (int i = 0; i < kTeam; ++i) v[i] = (i < team_size) ? __ldcg(src + i) : 0.0;
+        double t = 0.0;
+#pragma unroll
+        for (int i = 0; i < kTeam; ++i) t += v[i];
+        rb.team_part[((size_t)tile * NO + o) * kMaxTeams + team] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        rb.team_counter[tile * kMaxTeams + team] = 0;
+        const uint32_t t = atomicAdd(rb.counter + tile, 1u);
+        is_last = (t == (uint32_t)nteams - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    for (int o = threadIdx.x; o < NO; o += blockDim.x) {
+        const double *src = rb.team_part + ((size_t)tile * NO + o) * kMaxTeams;
+        double t = 0.0;
+        for (int t0 = 0; t0 < nteams; t0 += kTeam) {
+            double v[kTeam];
+#pragma unroll
+            for (int i = 0; i < kTeam; ++i) v[i] = (t0 + i < nteams) ? __ldcg(src + t0 + i) : 0.0;
+#pragma unroll
+            for (int i = 0; i < kTeam; ++i) t += v[i];
+        }
+        fin[o] = t;
     }
     __syncthreads();
     for (int c = threadIdx.x; c < KT; c += blockDim.x) {
@@ -149,6 +189,51 @@ __device__ __forceinline__ void block_reduce_finalize(double (&acc)[NR][VW], int
         op.fin(tile * KT + c, sums);
     }
     if (threadIdx.x == 0) rb.counter[tile] = 0;
+}
+
+// sum_{e in [e0, e1)} w_e x_{col(e)} for this lane's columns; eight gathers
+// in flight per lane
+template <typename T, class Op>
+__device__ __forceinline__ typename Vec<T>::V row_sum(const LevelView &A, const Op &op, int e0, int e1, int c0) {
+    using V = typename Vec<T>::V;
+    V s0 = vzero<V>(), s1 = vzero<V>();
+    int e = e0;
+    for (; e + 7 < e1; e += 8) {
+        int j[8];
+        T w[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            j[u] = __ldg(A.col + e + u);
+            w[u] = lw<T>(A, e + u);
+        }
+        V x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = op.gather(j[u], c0);
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+            vfma(s0, w[u], x[u]);
+            vfma(s1, w[u + 1], x[u + 1]);
+        }
+    }
+    if (e + 3 < e1) {
+        int j[4];
+        T w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            j[u] = __ldg(A.col + e + u);
+            w[u] = lw<T>(A, e + u);
+        }
+        V x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = op.gather(j[u], c0);
+        vfma(s0, w[0], x[0]);
+        vfma(s1, w[1], x[1]);
+        vfma(s0, w[2], x[2]);
+        vfma(s1, w[3], x[3]);
+        e += 4;
+    }
+    for (; e < e1; ++e) vfma(s0, lw<T>(A, e), op.gather(__ldg(A.col + e), c0));
+    return vadd(s0, s1);
 }
 
 // ------------------------------------------------------------------ SpMM-like row operator
@@ -168,11 +253,11 @@ __global__ void __launch_bounds__(kBlock) k_rowop(LevelView A, Op op, int nvb_sh
     const int lane = threadIdx.x % G, grp = threadIdx.x / G;
     const int tile = blockIdx.y;
     const int c0 = tile * KT + lane * VW;
-    double acc[NRA][VW];
+    T acc[NRA][VW];
 #pragma unroll
     for (int r = 0; r < NRA; ++r)
 #pragma unroll
-        for (int v = 0; v < VW; ++v) acc[r][v] = 0.0;
+        for (int v = 0; v < VW; ++v) acc[r][v] = T(0);
 
     for (int vb = blockIdx.x; vb < nvb_total; vb += gridDim.x) {
         if (vb < nvb_short) {
@@ -180,20 +265,7 @@ __global__ void __launch_bounds__(kBlock) k_rowop(LevelView A, Op op, int nvb_sh
             if (i < A.n) {
                 const int e0 = __ldg(A.rowptr + i), e1 = __ldg(A.rowptr + i + 1);
                 if (e1 - e0 <= kLongRow) {
-                    V s = vzero<V>();
-                    int e = e0;
-                    for (; e + 3 < e1; e += 4) {
-                        const int j0 = __ldg(A.col + e), j1 = __ldg(A.col + e + 1);
-                        const int j2 = __ldg(A.col + e + 2), j3 = __ldg(A.col + e + 3);
-                        const T w0 = lw<T>(A, e), w1 = lw<T>(A, e + 1), w2 = lw<T>(A, e + 2), w3 = lw<T>(A, e + 3);
-                        const V x0 = op.gather(j0, c0), x1 = op.gather(j1, c0);
-                        const V x2 = op.gather(j2, c0), x3 = op.gather(j3, c0);
-                        vfma(s, w0, x0);
-                        vfma(s, w1, x1);
-                        vfma(s, w2, x2);
-                        vfma(s, w3, x3);
-                    }
-                    for (; e < e1; ++e) vfma(s, lw<T>(A, e), op.gather(__ldg(A.col + e), c0));
+                    const V s = row_sum<T>(A, op, e0, e1, c0);
                     op.epi(i, c0, s, acc);
                 }
             }
@@ -205,8 +277,7 @@ __global__ void __launch_bounds__(kBlock) k_rowop(LevelView A, Op op, int nvb_sh
                 i = __ldg(A.chunk_row + ch);
                 const int e0 = __ldg(A.chunk_begin + ch);
                 const int e1 = min(e0 + kLongRow, __ldg(A.rowptr + i + 1));
-                V s = vzero<V>();
-                for (int e = e0; e < e1; ++e) vfma(s, lw<T>(A, e), op.gather(__ldg(A.col + e), c0));
+                const V s = row_sum<T>(A, op, e0, e1, c0);
                 vst<T>(chunk_part + (size_t)ch * ld_part + c0, s);
                 __threadfence();
             }
@@ -230,7 +301,7 @@ __global__ void __launch_bounds__(kBlock) k_rowop(LevelView A, Op op, int nvb_sh
             __syncwarp();
         }
     }
-    if constexpr (NR > 0) block_reduce_finalize<KT, NR, VW, RPB>(acc, lane, grp, rb, op);
+    if constexpr (NR > 0) block_reduce_finalize<KT, NR, VW, RPB, T>(acc, lane, grp, rb, op);
 }
 
 // ------------------------------------------------------------------ row-local kernels (no gathers)
@@ -243,13 +314,13 @@ __global__ void __launch_bounds__(kBlock) k_rows(int n, Op op, RedBuf rb) {
     constexpr int NRA = NR > 0 ? NR : 1;
     const int lane = threadIdx.x % G, grp = threadIdx.x / G;
     const int c0 = blockIdx.y * KT + lane * VW;
-    double acc[NRA][VW];
+    T acc[NRA][VW];
 #pragma unroll
     for (int r = 0; r < NRA; ++r)
 #pragma unroll
-        for (int v = 0; v < VW; ++v) acc[r][v] = 0.0;
+        for (int v = 0; v < VW; ++v) acc[r][v] = T(0);
     for (int i = blockIdx.x * RPB + grp; i < n; i += gridDim.x * RPB) op.row(i, c0, acc);
-    if constexpr (NR > 0) block_reduce_finalize<KT, NR, VW, RPB>(acc, lane, grp, rb, op);
+    if constexpr (NR > 0) block_reduce_finalize<KT, NR, VW, RPB, T>(acc, lane, grp, rb, op);
 }
 
 }  // namespace cfc

@@ -38,6 +38,7 @@ struct OpSpmvDot {
     int ld;
     const double *rz;
     double *alpha;
+    T *alpha_t;
     const int32_t *active;
     __device__ V gather(int j, int c0) const { return vldg<T>(p + (size_t)j * ld + c0); }
     template <class Acc>
@@ -48,13 +49,14 @@ struct OpSpmvDot {
 #pragma unroll
         for (int v = 0; v < VW; ++v) {
             vel(y, v) = d * vel(x, v) - vel(s, v);
-            acc[0][v] += (double)vel(x, v) * (double)vel(y, v);
+            acc[0][v] += vel(x, v) * vel(y, v);
         }
         vst<T>(q + (size_t)i * ld + c0, y);
     }
     __device__ void fin(int c, const double *sums) const {
         const double pq = sums[0];
         alpha[c] = (active[c] && pq > 0.0) ? rz[c] / pq : 0.0;
+        alpha_t[c] = (T)alpha[c];
     }
 };
 
@@ -94,8 +96,38 @@ struct OpResid64 {
     }
 };
 
-// Chebyshev / Jacobi step: out = x + c (x - xp) + e D^{-1} (b - L x), in place on xp
+// PCG scalars from the sums r.z, sum z, sum r (and r.r at the start):
+// mu = mean(z) (the projection of z onto 1-perp), rz = r.(z - mu),
+// beta = rz / rz_old; Init also records rr0 = r.r and the active columns.
 template <typename T>
+struct DotState {
+    double inv_n;
+    double *rz, *beta, *mu, *rr0;
+    T *beta_t, *mu_t;
+    int32_t *active;
+    const int32_t *active_out;
+    template <bool Init>
+    __device__ void fin(int c, const double *s) const {
+        const double m = s[1] * inv_n;
+        const double rzn = s[0] - m * s[2];
+        mu[c] = m;
+        if constexpr (Init) {
+            rr0[c] = s[3];
+            active[c] = (active_out[c] && s[3] > 0.0) ? 1 : 0;
+            beta[c] = 0.0;
+        } else {
+            beta[c] = (active[c] && rz[c] != 0.0) ? rzn / rz[c] : 0.0;
+        }
+        rz[c] = rzn;
+        mu_t[c] = (T)m;
+        beta_t[c] = (T)beta[c];
+    }
+};
+
+// Chebyshev / Jacobi step: out = x + c (x - xp) + e D^{-1} (b - L x), in place
+// on xp.  With NR = 3 (4 when Init) the step also accumulates b.out, sum out,
+// sum b (and b.b) for the PCG scalars (b is the PCG residual at level 0).
+template <typename T, int NR = 0, bool Init = false>
 struct OpSmooth {
     using V = typename Vec<T>::V;
     static constexpr int VW = Vec<T>::W;
@@ -106,9 +138,10 @@ struct OpSmooth {
     int ld;
     T c, e;
     bool xp_zero;  // the previous iterate is the zero initial guess
+    DotState<T> ds;
     __device__ V gather(int j, int c0) const { return vldg<T>(x + (size_t)j * ld + c0); }
     template <class Acc>
-    __device__ void epi(int i, int c0, V s, Acc &) const {
+    __device__ void epi(int i, int c0, V s, Acc &acc) const {
         const V xi = gather(i, c0);
         const V bi = vld<T>(b + (size_t)i * ld + c0);
         const T d = ldeg<T>(A, i), di = ldinv<T>(A, i);
@@ -125,8 +158,19 @@ struct OpSmooth {
                 vel(out, v) = vel(xi, v) + e * di * (vel(bi, v) - (d * vel(xi, v) - vel(s, v)));
         }
         vst<T>(xp + (size_t)i * ld + c0, out);
+        if constexpr (NR > 0) {
+#pragma unroll
+            for (int v = 0; v < VW; ++v) {
+                acc[0][v] += vel(bi, v) * vel(out, v);
+                acc[1][v] += vel(out, v);
+                acc[2][v] += vel(bi, v);
+                if constexpr (Init) acc[NR - 1][v] += vel(bi, v) * vel(bi, v);
+            }
+        }
     }
-    __device__ void fin(int, const double *) const {}
+    __device__ void fin(int c, const double *sums) const {
+        if constexpr (NR > 0) ds.template fin<Init>(c, sums);
+    }
 };
 
 // r = b - L x
@@ -215,15 +259,19 @@ struct OpProlong {
     __device__ void fin(int, const double *) const {}
 };
 
-// x += alpha p ; r -= alpha q ; sum r^2 -> inner convergence flags
+// x += alpha p ; r -= alpha q ; sum r^2 -> inner convergence flags; when z1
+// is set, also the preconditioner's first smoothing step z1 = e D^{-1} r
 template <typename T>
 struct OpUpdateXR {
     using V = typename Vec<T>::V;
     static constexpr int VW = Vec<T>::W;
     T *x, *r;
     const T *p, *q;
+    T *z1;
+    LevelView A;
+    T e0;
     int ld;
-    const double *alpha;
+    const T *alpha_t;
     int32_t *active;
     const double *rr0;
     double tol2;
@@ -232,81 +280,105 @@ struct OpUpdateXR {
         const size_t o = (size_t)i * ld + c0;
         V xi = vld<T>(x + o), ri = vld<T>(r + o);
         const V pi = vld<T>(p + o), qi = vld<T>(q + o);
+        const V a = vld<T>(alpha_t + c0);
 #pragma unroll
         for (int v = 0; v < VW; ++v) {
-            const T a = (T)alpha[c0 + v];
-            vel(xi, v) += a * vel(pi, v);
-            vel(ri, v) -= a * vel(qi, v);
-            acc[0][v] += (double)vel(ri, v) * (double)vel(ri, v);
+            vel(xi, v) += vel(a, v) * vel(pi, v);
+            vel(ri, v) -= vel(a, v) * vel(qi, v);
+            acc[0][v] += vel(ri, v) * vel(ri, v);
         }
         vst<T>(x + o, xi);
         vst<T>(r + o, ri);
+        if (z1) {
+            const T di = e0 * ldinv<T>(A, i);
+            V zi;
+#pragma unroll
+            for (int v = 0; v < VW; ++v) vel(zi, v) = di * vel(ri, v);
+            vst<T>(z1 + o, zi);
+        }
     }
     __device__ void fin(int c, const double *sums) const {
         if (active[c] && !(sums[0] > tol2 * rr0[c])) active[c] = 0;
     }
 };
 
-// sums r.z, z, r (and r.r when init) -> mu = mean(z), rz = r.(z - mu), beta
+// sums r.z, z, r (and r.r when Init) -> the PCG scalars (DotState)
 template <typename T, bool Init>
 struct OpDotRZ {
     using V = typename Vec<T>::V;
     static constexpr int VW = Vec<T>::W;
     const T *r, *z;
     int ld;
-    double inv_n;
-    double *rz, *beta, *mu, *rr0;
-    int32_t *active;
-    const int32_t *active_out;
+    DotState<T> ds;
     template <class Acc>
     __device__ void row(int i, int c0, Acc &acc) const {
         const size_t o = (size_t)i * ld + c0;
         const V ri = vld<T>(r + o), zi = vld<T>(z + o);
 #pragma unroll
         for (int v = 0; v < VW; ++v) {
-            const double a = vel(ri, v), b = vel(zi, v);
+            const T a = vel(ri, v), b = vel(zi, v);
             acc[0][v] += a * b;
             acc[1][v] += b;
             acc[2][v] += a;
             if constexpr (Init) acc[3][v] += a * a;
         }
     }
-    __device__ void fin(int c, const double *s) const {
-        const double m = s[1] * inv_n;
-        const double rzn = s[0] - m * s[2];
-        mu[c] = m;
-        if constexpr (Init) {
-            rr0[c] = s[3];
-            active[c] = (active_out[c] && s[3] > 0.0) ? 1 : 0;
-            beta[c] = 0.0;
-        } else {
-            beta[c] = (active[c] && rz[c] != 0.0) ? rzn / rz[c] : 0.0;
-        }
-        rz[c] = rzn;
-    }
+    __device__ void fin(int c, const double *s) const { ds.template fin<Init>(c, s); }
 };
 
-// p = (z - mu) + beta p
-template <typename T>
+// p = (z - mu) + beta p   (First: p = z - mu; the old p is not read)
+template <typename T, bool First>
 struct OpUpdateP {
     using V = typename Vec<T>::V;
     static constexpr int VW = Vec<T>::W;
     const T *z;
     T *p;
     int ld;
-    const double *mu, *beta;
+    const T *mu_t, *beta_t;
     template <class Acc>
     __device__ void row(int i, int c0, Acc &) const {
         const size_t o = (size_t)i * ld + c0;
         const V zi = vld<T>(z + o);
-        V pi = vld<T>(p + o);
+        const V m = vld<T>(mu_t + c0);
+        V pi;
+        if constexpr (First) {
 #pragma unroll
-        for (int v = 0; v < VW; ++v)
-            vel(pi, v) = (vel(zi, v) - (T)mu[c0 + v]) + (T)beta[c0 + v] * vel(pi, v);
+            for (int v = 0; v < VW; ++v) vel(pi, v) = vel(zi, v) - vel(m, v);
+        } else {
+            const V bt = vld<T>(beta_t + c0);
+            pi = vld<T>(p + o);
+#pragma unroll
+            for (int v = 0; v < VW; ++v) vel(pi, v) = (vel(zi, v) - vel(m, v)) + vel(bt, v) * vel(pi, v);
+        }
         vst<T>(p + o, pi);
     }
     __device__ void fin(int, const double *) const {}
 };
+
+// first outer step (x = 0): r = b in the inner type
+template <typename Tin>
+struct OpCastB {
+    using V = double2;
+    const double *b;
+    Tin *r;
+    int ld;
+    template <class Acc>
+    __device__ void row(int i, int c0, Acc &) const {
+        const size_t o = (size_t)i * ld + c0;
+        const V bi = vld<double>(b + o);
+        r[o] = (Tin)bi.x;
+        r[o + 1] = (Tin)bi.y;
+    }
+    __device__ void fin(int, const double *) const {}
+};
+
+__global__ void k_init_cols(const double *__restrict__ bnorm, double *__restrict__ relres,
+                            int32_t *__restrict__ active, int ld) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ld; c += gridDim.x * blockDim.x) {
+        relres[c] = bnorm[c] > 0.0 ? 1.0 : 0.0;
+        active[c] = bnorm[c] > 0.0 ? 1 : 0;
+    }
+}
 
 // x64 += d (active columns only)
 template <typename Tin>
@@ -412,6 +484,7 @@ int num_sms() {
 // ====================================================================== solver
 struct ColState {
     double *bnorm, *relres, *alpha, *beta, *rz, *rr0, *mu;
+    void *alpha_t, *beta_t, *mu_t;  // the same scalars in the inner arithmetic type
     int32_t *active_out, *active_in;
 };
 
@@ -469,8 +542,8 @@ struct Solver {
         }
     }
 
-    int red_grid(int nvb) const { return std::max(1, std::min(nvb, 2 * num_sms())); }
-    int plain_grid(int nvb) const { return std::max(1, std::min(nvb, 8 * num_sms())); }
+    int red_grid(int nvb) const { return std::max(1, std::min(nvb, 16 * num_sms())); }
+    int plain_grid(int nvb) const { return std::max(1, std::min(nvb, 32 * num_sms())); }
 
     static double vec_bytes(int64_t n, int ld, int nvec, int elem) { return (double)n * ld * elem * nvec; }
     static double mat_bytes(const Level &L, int wb) {
@@ -502,8 +575,39 @@ struct Solver {
 
     int fam_level(int l, int fine_fam) const { return l == 0 ? fine_fam : LAP_KF_COARSE_LEVELS; }
 
-    // ---------------- V-cycle on level l: b = lb[l] -> x = lx[l]
-    void vcycle(int l) {
+    // one smoothing step at level l (cur -> oth, swapped); at level 0 the
+    // step may also produce the PCG dot products (dot = 1: update, 2: init)
+    void smooth_step(int l, Tin *&cur, Tin *&oth, int t, bool xp_zero, int dot) {
+        const Level &L = h->lv[l];
+        const int et = (int)sizeof(Tin);
+        const int ti = std::min(t, (int)cheb_c.size() - 1);
+        const double bytes = mat_bytes(L, et) + vec_bytes(L.n, ld, xp_zero || cheb_c[ti] == 0.0 ? 3 : 4, et);
+        const Tin c = (Tin)cheb_c[ti], e = (Tin)cheb_e[ti];
+        const int fam = fam_level(l, LAP_KF_SMOOTH_FINE);
+        if (dot == 0) {
+            rowop<Tin, 0>(fam, L, OpSmooth<Tin>{view(L), cur, oth, lb[l], ld, c, e, xp_zero, {}}, chunk_part, bytes);
+        } else if (dot == 1) {
+            rowop<Tin, 3>(fam, L, OpSmooth<Tin, 3, false>{view(L), cur, oth, lb[l], ld, c, e, xp_zero, dstate()},
+                          chunk_part, bytes);
+        } else {
+            rowop<Tin, 4>(fam, L, OpSmooth<Tin, 4, true>{view(L), cur, oth, lb[l], ld, c, e, xp_zero, dstate()},
+                          chunk_part, bytes);
+        }
+        std::swap(cur, oth);
+    }
+
+    DotState<Tin> dstate() const {
+        return DotState<Tin>{1.0 / h->lv[0].n, cs.rz, cs.beta, cs.mu, cs.rr0, (Tin *)cs.beta_t, (Tin *)cs.mu_t,
+                             cs.active_in, cs.active_out};
+    }
+
+    bool level0_is_dense() const { return nlev == 1 && h->coarse_n == h->lv[0].n && h->lv.size() == 1; }
+
+    // ---------------- V-cycle on level l: b = lb[l] -> x = lx[l].
+    // first_done: x already holds the first smoothing step e D^{-1} b (fused
+    // into the PCG update); dot: the level-0 final step also computes the PCG
+    // dot products (1: update, 2: init).  Returns true when it did.
+    bool vcycle(int l, bool first_done = false, int dot = 0) {
         const Level &L = h->lv[l];
         const int et = (int)sizeof(Tin);
         const int wb = et;
@@ -514,25 +618,25 @@ struct Solver {
             const int blocks = std::max(1, std::min((nc * ld + threads - 1) / threads, 8 * num_sms()));
             CFC_LAUNCH(LAP_KF_COARSE_LEVELS, s, (double)nc * nc * 8 + 2.0 * nc * ld * et, k_coarse_dense<Tin>,
                        blocks, threads, 0, h->coarse_inv.get(), nc, lb[l], lx[l], ld, ld);
-            return;
+            return false;
         }
         // pre-smoothing from zero
         Tin *cur = lx[l], *oth = lt[l];
-        rows<Tin, 0>(fam_level(l, LAP_KF_SMOOTH_FINE), L.n,
-                     OpJacobiZero<Tin>{view(L), lb[l], cur, ld, (Tin)cheb_e[0]},
-                     vec_bytes(L.n, ld, 2, et) + L.n * (double)wb);
+        if (!first_done)
+            rows<Tin, 0>(fam_level(l, LAP_KF_SMOOTH_FINE), L.n,
+                         OpJacobiZero<Tin>{view(L), lb[l], cur, ld, (Tin)cheb_e[0]},
+                         vec_bytes(L.n, ld, 2, et) + L.n * (double)wb);
         const int npre = coarsest ? std::max(nu_pre, 4) : nu_pre;
+        bool dotted = false;
         for (int t = 1; t < npre; ++t) {
-            const int ti = std::min(t, (int)cheb_c.size() - 1);
-            rowop<Tin, 0>(fam_level(l, LAP_KF_SMOOTH_FINE), L,
-                          OpSmooth<Tin>{view(L), cur, oth, lb[l], ld, (Tin)cheb_c[ti], (Tin)cheb_e[ti], t == 1},
-                          chunk_part, mat_bytes(L, wb) + vec_bytes(L.n, ld, t == 1 ? 3 : 4, et));
-            std::swap(cur, oth);
+            const int d = (coarsest && t == npre - 1) ? dot : 0;
+            smooth_step(l, cur, oth, t, t == 1, d);
+            dotted = dotted || d;
         }
         if (coarsest) {
             lx[l] = cur;
             lt[l] = oth;
-            return;
+            return dotted;
         }
         // residual into oth, restrict to level l+1
         rowop<Tin, 0>(fam_level(l, LAP_KF_RESTRICT_FINE), L, OpResid<Tin>{view(L), cur, lb[l], oth, ld}, chunk_part,
@@ -546,47 +650,50 @@ struct Solver {
                      vec_bytes(L.n, ld, 2, et) + vec_bytes(C.n, ld, 1, et) + 4.0 * L.n);
         // post-smoothing (the same polynomial: symmetric V-cycle)
         for (int t = 0; t < nu_post; ++t) {
-            const int ti = std::min(t, (int)cheb_c.size() - 1);
-            rowop<Tin, 0>(fam_level(l, LAP_KF_SMOOTH_FINE), L,
-                          OpSmooth<Tin>{view(L), cur, oth, lb[l], ld, (Tin)cheb_c[ti], (Tin)cheb_e[ti], false},
-                          chunk_part, mat_bytes(L, wb) + vec_bytes(L.n, ld, t ? 4 : 3, et));
-            std::swap(cur, oth);
+            const int d = (t == nu_post - 1) ? dot : 0;
+            smooth_step(l, cur, oth, t, false, d);
+            dotted = dotted || d;
         }
         lx[l] = cur;
         lt[l] = oth;
+        return dotted;
     }
 
     // z = M^{-1} r  (the result may land in either of the two finest-level
-    // buffers; z and t0 are swapped accordingly)
-    void precond() {
+    // buffers; z and t0 are swapped accordingly).  Returns true when the PCG
+    // dot products were computed on the way.
+    bool precond(bool first_done, int dot) {
         lb[0] = r;
         lx[0] = z;
         lt[0] = t0;
-        vcycle(0);
+        const bool dotted = vcycle(0, first_done, dot);
         z = lx[0];
         t0 = lt[0];
+        return dotted;
     }
 
-    // inner PCG on the finest level: solves L d = r, d in lx... returns iterations
+    // inner PCG on the finest level: solves L d = r; returns iterations
     int inner_pcg(Tin *d, int max_inner, double inner_tol) {
         const Level &L0 = h->lv[0];
         const int et = (int)sizeof(Tin);
         const int64_t n = L0.n;
         const double vb1 = vec_bytes(n, ld, 1, et);
         CFC_CUDA(cudaMemsetAsync(d, 0, (size_t)n * ld * et, s));
-        precond();
-        rows<Tin, 4>(LAP_KF_BLAS1, n,
-                     OpDotRZ<Tin, true>{r, z, ld, 1.0 / n, cs.rz, cs.beta, cs.mu, cs.rr0, cs.active_in, cs.active_out},
-                     2 * vb1);
-        rows<Tin, 0>(LAP_KF_BLAS1, n, OpUpdateP<Tin>{z, p, ld, cs.mu, cs.beta}, 3 * vb1);
+        Tin *alpha_t = (Tin *)cs.alpha_t, *beta_t = (Tin *)cs.beta_t, *mu_t = (Tin *)cs.mu_t;
+        if (!precond(false, 2))
+            rows<Tin, 4>(LAP_KF_BLAS1, n, OpDotRZ<Tin, true>{r, z, ld, dstate()}, 2 * vb1);
+        rows<Tin, 0>(LAP_KF_BLAS1, n, OpUpdateP<Tin, true>{z, p, ld, mu_t, beta_t}, 2 * vb1);
+        const bool fuse_first = !level0_is_dense();
         const int check = std::max(1, o.check_every);
         int it = 0;
         for (it = 1; it <= max_inner; ++it) {
-            rowop<Tin, 1>(LAP_KF_SPMV_FINE, L0, OpSpmvDot<Tin>{view(L0), p, q, ld, cs.rz, cs.alpha, cs.active_in},
-                          chunk_part, mat_bytes(L0, et) + 2 * vb1);
+            rowop<Tin, 1>(LAP_KF_SPMV_FINE, L0,
+                          OpSpmvDot<Tin>{view(L0), p, q, ld, cs.rz, cs.alpha, alpha_t, cs.active_in}, chunk_part,
+                          mat_bytes(L0, et) + 2 * vb1);
             rows<Tin, 1>(LAP_KF_BLAS1, n,
-                         OpUpdateXR<Tin>{d, r, p, q, ld, cs.alpha, cs.active_in, cs.rr0, inner_tol * inner_tol},
-                         6 * vb1);
+                         OpUpdateXR<Tin>{d, r, p, q, fuse_first ? z : nullptr, view(L0), (Tin)cheb_e[0], ld, alpha_t,
+                                         cs.active_in, cs.rr0, inner_tol * inner_tol},
+                         (fuse_first ? 7 : 6) * vb1);
             if (it % check == 0 || it == max_inner) {
                 CFC_CUDA(cudaMemcpyAsync(h_active, cs.active_in, ld * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
                 CFC_CUDA(cudaStreamSynchronize(s));
@@ -595,12 +702,9 @@ struct Solver {
                 if (na == 0) break;
                 if (it == max_inner) break;
             }
-            precond();
-            rows<Tin, 3>(LAP_KF_BLAS1, n,
-                         OpDotRZ<Tin, false>{r, z, ld, 1.0 / n, cs.rz, cs.beta, cs.mu, cs.rr0, cs.active_in,
-                                             cs.active_out},
-                         2 * vb1);
-            rows<Tin, 0>(LAP_KF_BLAS1, n, OpUpdateP<Tin>{z, p, ld, cs.mu, cs.beta}, 3 * vb1);
+            if (!precond(fuse_first, 1))
+                rows<Tin, 3>(LAP_KF_BLAS1, n, OpDotRZ<Tin, false>{r, z, ld, dstate()}, 2 * vb1);
+            rows<Tin, 0>(LAP_KF_BLAS1, n, OpUpdateP<Tin, false>{z, p, ld, mu_t, beta_t}, 3 * vb1);
         }
         return std::min(it, max_inner);
     }
@@ -624,8 +728,12 @@ struct Solver {
         double maxrel = 0.0;
         std::vector<double> hrel(ld);
         for (outer = 0;; ++outer) {
-            // FP64 residual, written to r in the inner type
-            {
+            // FP64 residual, written to r in the inner type (x = 0 at the first step: r = b)
+            if (outer == 0) {
+                rowsd<0>(n, OpCastB<Tin>{b64, r, ld}, v64 + vec_bytes(n, ld, 1, sizeof(Tin)));
+                CFC_LAUNCH(LAP_KF_BLAS1, s, 0.0, k_init_cols, (ld + 255) / 256, 256, 0, cs.bnorm, cs.relres,
+                           cs.active_out, ld);
+            } else {
                 constexpr int RPB = RPB64;
                 const int nvb_short = (L0.n + RPB - 1) / RPB;
                 const int nvb_long = (L0.n_chunks + RPB - 1) / RPB;
@@ -699,6 +807,7 @@ lap_status_t run_solver(lap_hierarchy *h, int32_t k, const double *B, double *X,
     int64_t max_chunks = 0;
     for (int l = 0; l < nlev; ++l) max_chunks = std::max<int64_t>(max_chunks, h->lv[l].n_chunks);
     std::vector<size_t> sizes;
+    sizes.push_back(align_up(kMaxTiles * 4 + kMaxTiles * kMaxTeams * 4));  // arrival counters (first)
     sizes.push_back(align_up(n0 * ld * 8));  // b64
     sizes.push_back(align_up(n0 * ld * 8));  // x64
     sizes.push_back(align_up(n0 * ld * sizeof(Tin)));  // r
@@ -710,10 +819,10 @@ lap_status_t run_solver(lap_hierarchy *h, int32_t k, const double *B, double *X,
     for (int l = 1; l < nlev; ++l)
         for (int v = 0; v < 3; ++v) sizes.push_back(align_up((size_t)h->lv[l].n * ld * sizeof(Tin)));
     sizes.push_back(align_up(std::max<int64_t>(max_chunks, 1) * ld * 8));  // chunk partials (FP64 size)
-    const int P = 2 * num_sms();
-    sizes.push_back(align_up((size_t)ntiles * 4 * KT * P * 8));  // reduction partials
-    sizes.push_back(align_up(kMaxTiles * 4));                     // counters
-    sizes.push_back(align_up(ld * 8) * 7);                        // column doubles
+    const int P = 16 * num_sms();
+    sizes.push_back(align_up((size_t)ntiles * 4 * KT * P * 8));          // reduction partials
+    sizes.push_back(align_up((size_t)ntiles * 4 * KT * kMaxTeams * 8));  // team partials
+    sizes.push_back(align_up(ld * 8) * 10);                       // column scalars
     sizes.push_back(align_up(ld * 4) * 2);                        // column flags
     size_t total = 0;
     for (size_t z : sizes) total += z;
@@ -721,16 +830,18 @@ lap_status_t run_solver(lap_hierarchy *h, int32_t k, const double *B, double *X,
         h->ws.release();
         h->ws.alloc_persistent(total);
         h->ws_bytes = total;
-        h->ws_dirty = true;
     }
     char *base = h->ws.get();
     size_t off = 0;
-    auto take = [&](size_t idx) {
+    auto take = [&](size_t i) {
         char *p = base + off;
-        off += sizes[idx];
+        off += sizes[i];
+        if (off > total) throw Error{LAP_ECUDA, "internal: workspace layout overflow"};
         return p;
     };
     size_t idx = 0;
+    S.rb.counter = (uint32_t *)take(idx++);
+    S.rb.team_counter = S.rb.counter + kMaxTiles;
     S.b64 = (double *)take(idx++);
     S.x64 = (double *)take(idx++);
     S.r = (Tin *)take(idx++);
@@ -751,10 +862,13 @@ lap_status_t run_solver(lap_hierarchy *h, int32_t k, const double *B, double *X,
         S.lx[l] = (Tin *)take(idx++);
         S.lt[l] = (Tin *)take(idx++);
     }
-    S.chunk_part = (Tin *)take(idx);
-    S.chunk_part64 = (double *)take(idx++);
+    {
+        char *cp = take(idx++);  // one buffer, viewed in the inner type or FP64
+        S.chunk_part = (Tin *)cp;
+        S.chunk_part64 = (double *)cp;
+    }
     S.rb.part = (double *)take(idx++);
-    S.rb.counter = (uint32_t *)take(idx++);
+    S.rb.team_part = (double *)take(idx++);
     {
         char *cd = take(idx++);
         const size_t st = align_up(ld * 8);
@@ -765,15 +879,15 @@ lap_status_t run_solver(lap_hierarchy *h, int32_t k, const double *B, double *X,
         S.cs.rz = (double *)(cd + 4 * st);
         S.cs.rr0 = (double *)(cd + 5 * st);
         S.cs.mu = (double *)(cd + 6 * st);
+        S.cs.alpha_t = (void *)(cd + 7 * st);
+        S.cs.beta_t = (void *)(cd + 8 * st);
+        S.cs.mu_t = (void *)(cd + 9 * st);
         char *cf = take(idx++);
         S.cs.active_out = (int32_t *)cf;
         S.cs.active_in = (int32_t *)(cf + align_up(ld * 4));
     }
-    if (h->ws_dirty) {
-        // arrival counters must start at zero; every kernel leaves them at zero
-        CFC_CUDA(cudaMemsetAsync(S.rb.counter, 0, kMaxTiles * 4, s));
-        h->ws_dirty = false;
-    }
+    // arrival counters must start at zero (every kernel leaves them at zero)
+    CFC_CUDA(cudaMemsetAsync(S.rb.counter, 0, kMaxTiles * 4 + kMaxTiles * kMaxTeams * 4, s));
     CFC_CUDA(cudaMemsetAsync(S.cs.active_in, 0, ld * 4, s));
     S.h_active = pinned_scratch();
     return S.run(B, X, info);
