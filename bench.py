@@ -185,7 +185,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ba100k_jl64", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--levels", type=int, default=-1, help="levels_used override (-1 = tuned default)")
+    ap.add_argument("--levels", type=int, default=None,
+                    help="levels_used of the V-cycle (default: autotuned; -1: every level)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     rank, world, local = dist_setup(args.gpus)
@@ -212,7 +213,7 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     sp = stream.cuda_stream
     sopts = P.lap_default_solve_opts()
-    if args.levels >= 0:
+    if args.levels is not None:
         sopts.levels_used = args.levels
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
 
@@ -278,7 +279,7 @@ def main():
     timed(step_device, args.steps)
     fam = P.lap_stats_read()["families"]
     P.lap_stats_set_timing(False)
-    solve_fams = {kf: v for kf, v in fam.items() if v["ms"] > 0}
+    solve_fams = {kf: v for kf, v in fam.items() if v["ms"] > 0 and kf not in ("setup", "cfc")}
     dom = max(solve_fams, key=lambda kf: solve_fams[kf]["ms"])
     peak, peak_src = read_peaks()
     dm = fam[dom]
@@ -291,6 +292,7 @@ def main():
     X = torch.empty_like(Y)
     P.cfc_jl_rhs(h, k, wl["jl_seed"], Y, stream=sp)
     sinfo = P.lap_solve_multi(h, Y, X, sopts, stream=sp)
+    hinfo = P.lap_hierarchy_info(h)
     h.destroy()
 
     if rank == 0:
@@ -301,7 +303,7 @@ def main():
             "config": {"workload": args.workload, "n": n, "m": int(s.size), "k": k,
                        "query_nodes": wl["nodes"], "tol": 1e-8, "precision": "fp32 V-cycle/PCG in fp64 refinement",
                        "setup_included": True, "l2": "flushed between steps (256 MiB write, untimed)",
-                       "levels": hinfo["levels"], "level_n": hinfo["level_n"], "setup_ms": hinfo["setup_ms"],
+                       "levels_built": hinfo["levels"], "level_n": hinfo["level_n"], "setup_ms": hinfo["setup_ms"],
                        "outer_iters": sinfo["outer_iters"], "inner_iters": sinfo["inner_iters"],
                        "max_rel_residual": sinfo["max_rel_residual"],
                        "parallelism": f"{world} independent replicas"},

@@ -67,6 +67,8 @@ typedef struct {
     int32_t max_levels;   /* cap on levels incl. the finest (default 24); 1 = no coarsening */
     int32_t agg_passes;   /* pairwise-matching passes per level (default 2: aggregates of ~4) */
     int32_t match_rounds; /* handshake rounds per pass (default 4) */
+    int32_t eager;        /* 1: build every level now; 0 (default): build the coarse
+                             levels on the first solve that uses them */
 } lap_hier_opts_t;
 
 typedef struct {
@@ -80,7 +82,11 @@ typedef struct {
     int32_t nu_pre;       /* smoothing steps before the coarse correction (default 2) */
     int32_t nu_post;      /* smoothing steps after (default 2) */
     int32_t check_every;  /* inner iterations between host convergence reads (default 4) */
-    int32_t levels_used;  /* use at most this many levels of the hierarchy (0 = all) */
+    int32_t levels_used;  /* levels of the hierarchy the V-cycle uses: > 0 that many
+                             (at most), -1 every level, 0 (default) autotuned: the
+                             first solve for a graph size and configuration times
+                             complete solves with 1, 2, 3, 4 and all levels and the
+                             fastest converged depth is kept for the process */
 } lap_solve_opts_t;
 
 typedef struct {

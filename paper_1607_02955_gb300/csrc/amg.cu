@@ -235,7 +235,7 @@ __global__ void k_finish(const int32_t *__restrict__ rowptr, const double *__res
         dinv32[i] = (float)(1.0 / d);
         dinv64[i] = 1.0 / d;
         const int len = rowptr[i + 1] - rowptr[i];
-        nchunk[i] = len > kLongRow ? (len + kLongRow - 1) / kLongRow : 0;
+        nchunk[i] = len > kLongRow ? (len + kChunk - 1) / kChunk : 0;
     }
 }
 
@@ -246,15 +246,17 @@ __global__ void k_long_index(const int32_t *__restrict__ nchunk, int32_t n, int3
 __global__ void k_fill_chunks(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ nchunk,
                               const int32_t *__restrict__ cfirst, const int32_t *__restrict__ lidx, int32_t n,
                               int32_t *__restrict__ chunk_row, int32_t *__restrict__ chunk_begin,
-                              int32_t *__restrict__ chunk_long, int32_t *__restrict__ long_first) {
+                              int32_t *__restrict__ chunk_long, int32_t *__restrict__ long_first,
+                              int32_t *__restrict__ long_of_row) {
     GRID_LOOP(i, n) {
         const int c = nchunk[i];
+        long_of_row[i] = c ? lidx[i] : -1;
         if (!c) continue;
         const int f = cfirst[i], l = lidx[i];
         long_first[l] = f;
         for (int t = 0; t < c; ++t) {
             chunk_row[f + t] = (int32_t)i;
-            chunk_begin[f + t] = rowptr[i] + t * kLongRow;
+            chunk_begin[f + t] = rowptr[i] + t * kChunk;
             chunk_long[f + t] = l;
         }
     }
@@ -425,9 +427,10 @@ void finish_level(Level &L, cudaStream_t s) {
     L.long_first.alloc_persistent(L.n_long + 1);
     L.long_count.alloc_persistent((size_t)L.n_long * kMaxTiles);
     L.long_count.zero(s);
+    L.long_of_row.alloc_persistent(n);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_fill_chunks, grid_for(n), kBlock, 0, L.rowptr.get(), nchunk.get(),
                cfirst.get(), lidx.get(), n, L.chunk_row.get(), L.chunk_begin.get(), L.chunk_long.get(),
-               L.long_first.get());
+               L.long_first.get(), L.long_of_row.get());
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_set_last, 1, 1, 0, L.long_first.get(), L.n_long, L.n_chunks);
 }
 
@@ -453,21 +456,45 @@ void build_dense(const int32_t *rowptr, const int32_t *col, const double *w, con
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_dense_scatter, grid_for(n), kBlock, 0, rowptr, col, w, deg, n, M);
 }
 
-void build_levels(lap_hierarchy &h, Csr64 &fine, const lap_hier_opts_t &o, cudaStream_t s) {
+// Level 0 from the ingested graph; coarser levels are added by grow_levels.
+void init_levels(lap_hierarchy &h, Csr64 &fine, const lap_hier_opts_t &o, cudaStream_t s) {
     h.lv.clear();
     h.lv.emplace_back();
-    {
-        Level &L0 = h.lv.back();
-        L0.n = fine.n;
-        L0.nnz = fine.nnz;
-        L0.rowptr = std::move(fine.rowptr);
-        L0.col = std::move(fine.col);
-        L0.w64 = std::move(fine.w);
-        L0.deg64 = std::move(fine.deg);
-    }
+    Level &L0 = h.lv.back();
+    L0.n = fine.n;
+    L0.nnz = fine.nnz;
+    L0.rowptr = std::move(fine.rowptr);
+    L0.col = std::move(fine.col);
+    L0.w64 = std::move(fine.w);
+    L0.deg64 = std::move(fine.deg);
+    h.hopts = o;
+    h.complete = false;
+    h.coarse_n = 0;
+    finish_level(L0, s);
+    if (L0.n <= std::min(256, std::max(2, o.coarse_max)) || o.max_levels <= 1) grow_levels(h, 0, s);
+}
+
+// Coarsen until the hierarchy has `target` levels (0: until coarsening stops:
+// n_l <= coarse_max, the level cap, or a stall).  On completion the coarsest
+// level gets its dense inverse when it is small enough.
+void grow_levels(lap_hierarchy &h, int target, cudaStream_t s) {
+    if (h.complete) return;
+    const lap_hier_opts_t &o = h.hopts;
     const int coarse_max = std::min(256, std::max(2, o.coarse_max));
     const int max_levels = std::max(1, std::min(32, o.max_levels));
-    while ((int)h.lv.size() < max_levels && h.lv.back().n > coarse_max) {
+    bool stalled = false;
+    cudaEvent_t ev0, ev1;
+    CFC_CUDA(cudaEventCreate(&ev0));
+    CFC_CUDA(cudaEventCreate(&ev1));
+    struct EvGuard {
+        cudaEvent_t a, b;
+        ~EvGuard() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } evg{ev0, ev1};
+    while ((int)h.lv.size() < max_levels && h.lv.back().n > coarse_max && (target <= 0 || (int)h.lv.size() < target)) {
+        CFC_CUDA(cudaEventRecord(ev0, s));
         Level &F = h.lv.back();
         const int32_t n = F.n;
         DBuf<int32_t> agg;
@@ -483,7 +510,10 @@ void build_levels(lap_hierarchy &h, Csr64 &fine, const lap_hier_opts_t &o, cudaS
             CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_compose, grid_for(n), kBlock, 0, agg.get(), agg2.get(), n);
             nc = nc2;
         }
-        if (nc >= n || (double)nc > 0.9 * n) break;  // coarsening stalled
+        if (nc >= n || (double)nc > 0.9 * n) {  // coarsening stalled
+            stalled = true;
+            break;
+        }
         Graph64 C;
         contract(F.rowptr.get(), F.col.get(), F.w64.get(), n, F.nnz, agg.get(), nc, true, C, s);
         // members of each aggregate in ascending node order (stable sort by aggregate)
@@ -510,11 +540,21 @@ void build_levels(lap_hierarchy &h, Csr64 &fine, const lap_hier_opts_t &o, cudaS
         Cl.w64 = std::move(C.w);
         Cl.deg64 = std::move(C.deg);
         h.lv.push_back(std::move(Cl));
+        finish_level(h.lv.back(), s);
+        CFC_CUDA(cudaEventRecord(ev1, s));
+        CFC_CUDA(cudaEventSynchronize(ev1));
+        float ms = 0.f;
+        CFC_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+        h.level_ms.resize(h.lv.size(), 0.0);
+        h.level_ms[h.lv.size() - 1] = ms;
     }
-    for (auto &L : h.lv) finish_level(L, s);
+    const bool done = stalled || (int)h.lv.size() >= max_levels || h.lv.back().n <= coarse_max;
+    if (!done) return;
+    h.complete = true;
     // dense coarsest solve
     Level &Lc = h.lv.back();
     h.coarse_n = 0;
+    CFC_CUDA(cudaEventRecord(ev0, s));
     if (Lc.n <= 256) {
         const int nc = Lc.n;
         h.coarse_inv.alloc_persistent((size_t)nc * nc);
@@ -528,6 +568,12 @@ void build_levels(lap_hierarchy &h, Csr64 &fine, const lap_hier_opts_t &o, cudaS
         CFC_CUDA(cudaStreamSynchronize(s));
         CFC_REQUIRE(hf == 0, LAP_ENOTCONN, "coarsest operator singular: graph not connected");
         h.coarse_n = nc;
+        CFC_CUDA(cudaEventRecord(ev1, s));
+        CFC_CUDA(cudaEventSynchronize(ev1));
+        float ms = 0.f;
+        CFC_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+        h.level_ms.resize(h.lv.size(), 0.0);
+        h.level_ms.back() += ms;
     }
 }
 

@@ -146,6 +146,7 @@ LevelView view(const Level &L) {
     v.chunk_begin = L.chunk_begin.get();
     v.chunk_long = L.chunk_long.get();
     v.long_first = L.long_first.get();
+    v.long_of_row = L.long_of_row.get();
     v.long_count = L.long_count.get();
     return v;
 }
@@ -179,6 +180,7 @@ void lap_default_hier_opts(lap_hier_opts_t *o) {
     o->max_levels = 24;
     o->agg_passes = 2;
     o->match_rounds = 4;
+    o->eager = 0;
 }
 
 void lap_default_solve_opts(lap_solve_opts_t *o) {
@@ -234,7 +236,8 @@ lap_status_t lap_build_hierarchy(int64_t n, int64_t m, const int32_t *src, const
             h->n = g.n;
             h->m = g.m;
             h->eid = std::move(g.eid);
-            build_levels(*h, g, o, s);
+            init_levels(*h, g, o, s);
+            if (o.eager) grow_levels(*h, 0, s);
             CFC_CUDA(cudaEventRecord(e1, s));
             CFC_CUDA(cudaEventSynchronize(e1));
             float ms = 0.f;

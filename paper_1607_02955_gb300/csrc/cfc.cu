@@ -101,7 +101,7 @@ __global__ void k_jl_chunks(const int32_t *__restrict__ rowptr, const int32_t *_
     GRID_LOOP(t, (int64_t)n_chunks * ncb) {
         const int ch = (int)(t / ncb), cb = (int)(t - (int64_t)ch * ncb);
         const int u = chunk_row[ch];
-        const int e0 = chunk_begin[ch], e1 = min(e0 + kLongRow, rowptr[u + 1]);
+        const int e0 = chunk_begin[ch], e1 = min(e0 + kChunk, rowptr[u + 1]);
         double acc[32];
 #pragma unroll
         for (int q = 0; q < 32; ++q) acc[q] = 0.0;

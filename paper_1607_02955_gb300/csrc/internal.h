@@ -128,19 +128,21 @@ struct Level {
     DBuf<int32_t> rowptr, col;
     DBuf<double> w64, deg64, dinv64;
     DBuf<float> w32, deg32, dinv32;
-    // rows longer than kLongRow nonzeros are split into chunks of kLongRow
+    // rows longer than kLongRow nonzeros are split into chunks of kChunk
     int32_t n_long = 0, n_chunks = 0;
     DBuf<int32_t> chunk_row;     // [n_chunks] row of each chunk
     DBuf<int32_t> chunk_begin;   // [n_chunks] first nonzero of the chunk
     DBuf<int32_t> chunk_long;    // [n_chunks] index of the chunk's long row
     DBuf<int32_t> long_first;    // [n_long + 1] first chunk of each long row
+    DBuf<int32_t> long_of_row;   // [n] index of the row among the long rows, -1 if short
     DBuf<uint32_t> long_count;   // [n_long * max_tiles] arrival counters (zero between launches)
     // map to the next coarser level (empty at the coarsest)
     DBuf<int32_t> agg;           // [n] aggregate (coarse node) of each node
     DBuf<int32_t> mem_ptr, mem;  // members of each coarse node, ascending
 };
 
-constexpr int kLongRow = 64;     // row split threshold and chunk length (nonzeros)
+constexpr int kLongRow = 32;     // rows with more nonzeros are split into chunks
+constexpr int kChunk = 16;       // nonzeros per chunk of a split row
 constexpr int kMaxTiles = 64;    // column tiles per launch (k <= 64 * 64)
 constexpr int kBlock = 256;
 
@@ -151,7 +153,7 @@ struct LevelView {
     const float *w32, *deg32, *dinv32;
     const double *w64, *deg64, *dinv64;
     int32_t n_chunks, n_long;
-    const int32_t *chunk_row, *chunk_begin, *chunk_long, *long_first;
+    const int32_t *chunk_row, *chunk_begin, *chunk_long, *long_first, *long_of_row;
     uint32_t *long_count;
 };
 LevelView view(const Level &L);
@@ -178,7 +180,8 @@ void ingest(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const 
             cudaStream_t s, Csr64 &out);
 
 // ------------------------------------------------------------------ hierarchy (amg.cu)
-void build_levels(lap_hierarchy &h, Csr64 &fine, const lap_hier_opts_t &o, cudaStream_t s);
+void init_levels(lap_hierarchy &h, Csr64 &fine, const lap_hier_opts_t &o, cudaStream_t s);
+void grow_levels(lap_hierarchy &h, int target, cudaStream_t s);  // target 0: all
 void finish_level(Level &L, cudaStream_t s);  // FP32 copies, inverse degrees, long-row split
 
 // dense SPD inverse (in place, FP64, row-major n x n) -- used for the
@@ -194,6 +197,9 @@ struct lap_hierarchy {
     int64_t n = 0, m = 0;
     std::vector<cfc::Level> lv;
     cfc::DBuf<int32_t> eid;           // level-0 undirected edge id of each CSR entry
+    lap_hier_opts_t hopts{};
+    bool complete = false;            // coarsening finished (no further levels)
+    std::vector<double> level_ms;     // device time to build each level (level 0: ingest)
     int32_t coarse_n = 0;             // dense coarsest size (0: none)
     cfc::DBuf<double> coarse_inv;     // (L_c + J/n_c)^{-1}, row-major
     double setup_ms = 0;

@@ -20,64 +20,121 @@
 
 namespace cfc {
 
+// A lane owns VW consecutive columns held as two native 16-byte vectors
+// (8 floats or 4 doubles): two gathers of 16 bytes per neighbour per lane,
+// twice the rows in flight per thread of one-vector lanes.
+struct f8 {
+    float4 a, b;
+};
+struct d4 {
+    double2 a, b;
+};
+
 template <typename T>
 struct Vec;
 template <>
 struct Vec<float> {
-    using V = float4;
-    static constexpr int W = 4;
+    using V = f8;
+    static constexpr int W = 8;
 };
 template <>
 struct Vec<double> {
-    using V = double2;
-    static constexpr int W = 2;
+    using V = d4;
+    static constexpr int W = 4;
 };
 
 template <typename V>
 __device__ __forceinline__ V vzero();
 template <>
-__device__ __forceinline__ float4 vzero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ f8 vzero<f8>() {
+    return f8{make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+}
 template <>
-__device__ __forceinline__ double2 vzero<double2>() { return make_double2(0.0, 0.0); }
+__device__ __forceinline__ d4 vzero<d4>() {
+    return d4{make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+}
 
 template <typename T>
-__device__ __forceinline__ typename Vec<T>::V vld(const T *p) {
-    return *reinterpret_cast<const typename Vec<T>::V *>(p);
+__device__ __forceinline__ typename Vec<T>::V vld(const T *p);
+template <>
+__device__ __forceinline__ f8 vld<float>(const float *p) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+    return f8{q[0], q[1]};
+}
+template <>
+__device__ __forceinline__ d4 vld<double>(const double *p) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    return d4{q[0], q[1]};
 }
 template <typename T>
-__device__ __forceinline__ typename Vec<T>::V vldg(const T *p) {  // read-only path
-    return __ldg(reinterpret_cast<const typename Vec<T>::V *>(p));
+__device__ __forceinline__ typename Vec<T>::V vldg(const T *p);  // read-only path
+template <>
+__device__ __forceinline__ f8 vldg<float>(const float *p) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+    return f8{__ldg(q), __ldg(q + 1)};
+}
+template <>
+__device__ __forceinline__ d4 vldg<double>(const double *p) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    return d4{__ldg(q), __ldg(q + 1)};
 }
 template <typename T>
-__device__ __forceinline__ typename Vec<T>::V vldcg(const T *p) {  // L2, coherent across blocks
-    return __ldcg(reinterpret_cast<const typename Vec<T>::V *>(p));
+__device__ __forceinline__ typename Vec<T>::V vldcg(const T *p);  // L2, coherent across blocks
+template <>
+__device__ __forceinline__ f8 vldcg<float>(const float *p) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+    return f8{__ldcg(q), __ldcg(q + 1)};
+}
+template <>
+__device__ __forceinline__ d4 vldcg<double>(const double *p) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    return d4{__ldcg(q), __ldcg(q + 1)};
+}
+__device__ __forceinline__ void vst_(float *p, const f8 &v) {
+    float4 *q = reinterpret_cast<float4 *>(p);
+    q[0] = v.a;
+    q[1] = v.b;
+}
+__device__ __forceinline__ void vst_(double *p, const d4 &v) {
+    double2 *q = reinterpret_cast<double2 *>(p);
+    q[0] = v.a;
+    q[1] = v.b;
 }
 template <typename T>
-__device__ __forceinline__ void vst(T *p, typename Vec<T>::V v) {
-    *reinterpret_cast<typename Vec<T>::V *>(p) = v;
+__device__ __forceinline__ void vst(T *p, const typename Vec<T>::V &v) {
+    vst_(p, v);
 }
 
 // element access
-__device__ __forceinline__ float &vel(float4 &v, int i) { return (&v.x)[i]; }
-__device__ __forceinline__ double &vel(double2 &v, int i) { return (&v.x)[i]; }
-__device__ __forceinline__ float vel(const float4 &v, int i) { return (&v.x)[i]; }
-__device__ __forceinline__ double vel(const double2 &v, int i) { return (&v.x)[i]; }
+__device__ __forceinline__ float &vel(f8 &v, int i) { return i < 4 ? (&v.a.x)[i] : (&v.b.x)[i - 4]; }
+__device__ __forceinline__ double &vel(d4 &v, int i) { return i < 2 ? (&v.a.x)[i] : (&v.b.x)[i - 2]; }
+__device__ __forceinline__ float vel(const f8 &v, int i) { return i < 4 ? (&v.a.x)[i] : (&v.b.x)[i - 4]; }
+__device__ __forceinline__ double vel(const d4 &v, int i) { return i < 2 ? (&v.a.x)[i] : (&v.b.x)[i - 2]; }
 
 // s += a * x
-__device__ __forceinline__ void vfma(float4 &s, float a, const float4 &x) {
-    s.x = fmaf(a, x.x, s.x);
-    s.y = fmaf(a, x.y, s.y);
-    s.z = fmaf(a, x.z, s.z);
-    s.w = fmaf(a, x.w, s.w);
+__device__ __forceinline__ void vfma(f8 &s, float a, const f8 &x) {
+    s.a.x = fmaf(a, x.a.x, s.a.x);
+    s.a.y = fmaf(a, x.a.y, s.a.y);
+    s.a.z = fmaf(a, x.a.z, s.a.z);
+    s.a.w = fmaf(a, x.a.w, s.a.w);
+    s.b.x = fmaf(a, x.b.x, s.b.x);
+    s.b.y = fmaf(a, x.b.y, s.b.y);
+    s.b.z = fmaf(a, x.b.z, s.b.z);
+    s.b.w = fmaf(a, x.b.w, s.b.w);
 }
-__device__ __forceinline__ void vfma(double2 &s, double a, const double2 &x) {
-    s.x = fma(a, x.x, s.x);
-    s.y = fma(a, x.y, s.y);
+__device__ __forceinline__ void vfma(d4 &s, double a, const d4 &x) {
+    s.a.x = fma(a, x.a.x, s.a.x);
+    s.a.y = fma(a, x.a.y, s.a.y);
+    s.b.x = fma(a, x.b.x, s.b.x);
+    s.b.y = fma(a, x.b.y, s.b.y);
 }
-__device__ __forceinline__ float4 vadd(const float4 &a, const float4 &b) {
-    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+__device__ __forceinline__ f8 vadd(const f8 &x, const f8 &y) {
+    return f8{make_float4(x.a.x + y.a.x, x.a.y + y.a.y, x.a.z + y.a.z, x.a.w + y.a.w),
+              make_float4(x.b.x + y.b.x, x.b.y + y.b.y, x.b.z + y.b.z, x.b.w + y.b.w)};
 }
-__device__ __forceinline__ double2 vadd(const double2 &a, const double2 &b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ d4 vadd(const d4 &x, const d4 &y) {
+    return d4{make_double2(x.a.x + y.a.x, x.a.y + y.a.y), make_double2(x.b.x + y.b.x, x.b.y + y.b.y)};
+}
 
 template <typename T>
 __device__ __forceinline__ T lw(const LevelView &A, int e);
@@ -99,17 +156,25 @@ template <>
 __device__ __forceinline__ double ldinv<double>(const LevelView &A, int i) { return __ldg(A.dinv64 + i); }
 
 // ------------------------------------------------------------------ reductions
+// Per-column partial sums of this lane's columns, in registers:
+// acc.add(r, v, x) adds x to reduction r of the lane's column v.
+template <typename TA, int NR, int VW>
+struct RAcc {
+    TA a[NR > 0 ? NR : 1][VW];
+    __device__ __forceinline__ void add(int r, int v, TA x) { a[r][v] += x; }
+};
+
 // Two-level, fixed-order cross-block reduction.  Blocks are grouped in teams
 // of kTeam consecutive blocks; the last block of a team to arrive sums the
 // team's partials (in block order), and the last team to arrive sums the
 // team partials (in team order) and runs the per-column finalisation.  No
 // block waits for another, and the order of every sum is fixed.
 constexpr int kTeam = 32;
-constexpr int kMaxTeams = 128;
+constexpr int kMaxTeams = 1024;  // P <= kTeam * kMaxTeams blocks per tile
 
 struct RedBuf {
-    double *part;            // [ntiles][NR*KT][P]
-    double *team_part;       // [ntiles][NR*KT][kMaxTeams]
+    double *part;            // [ntiles][P][NR*KT]
+    double *team_part;       // [ntiles][kMaxTeams][NR*KT]
     uint32_t *counter;       // [kMaxTiles], zero between launches
     uint32_t *team_counter;  // [kMaxTiles][kMaxTeams], zero between launches
 };
@@ -117,65 +182,82 @@ struct RedBuf {
 // acc holds this thread's partial sums in the kernel's arithmetic type (FP32
 // partials over a few rows: FP64 per element would run on GB300's narrow
 // FP64 pipe); the block, team and final stages add in FP64.
-template <int KT, int NR, int VW, int RPB, typename TA, class Op>
-__device__ __forceinline__ void block_reduce_finalize(TA (&acc)[NR][VW], int lane, int grp, RedBuf rb,
-                                                      Op &op) {
+template <int KT, int NR, int VW, int G, typename TA, class Op>
+__device__ __forceinline__ void block_reduce_finalize(RAcc<TA, NR, VW> &acc, RedBuf rb, Op &op) {
     constexpr int NO = NR * KT;
-    __shared__ double sm[RPB][NO];
+    constexpr int NWARP = kBlock / 32;
+    __shared__ TA sm[NWARP][NO];
     __shared__ double fin[NO];
     __shared__ int is_last;
+    // warp stage: the row groups of a warp own the same columns; add them up
+    // with a fixed xor-shuffle tree, then group 0 of each warp stores them
+    const int wl = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int r = 0; r < NR; ++r)
 #pragma unroll
-        for (int v = 0; v < VW; ++v) sm[grp][r * KT + lane * VW + v] = (double)acc[r][v];
+        for (int v = 0; v < VW; ++v) {
+            TA x = acc.a[r][v];
+#pragma unroll
+            for (int d = G; d < 32; d <<= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
+            acc.a[r][v] = x;
+        }
+    if (wl < G) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+#pragma unroll
+            for (int v = 0; v < VW; ++v) sm[wid][r * KT + wl * VW + v] = acc.a[r][v];
+    }
     __syncthreads();
     const int tile = blockIdx.y;
     const int P = gridDim.x;
+    // block stage: partial of this block, stored contiguously ([tile][block][output])
     for (int o = threadIdx.x; o < NO; o += blockDim.x) {
-        double s = 0.0;
-        for (int g = 0; g < RPB; ++g) s += sm[g][o];
-        rb.part[((size_t)tile * NO + o) * P + blockIdx.x] = s;
+        TA s = TA(0);
+#pragma unroll
+        for (int g = 0; g < NWARP; ++g) s += sm[g][o];
+        rb.part[((size_t)tile * P + blockIdx.x) * NO + o] = (double)s;
     }
-    __threadfence();
-    __syncthreads();
     const int team = blockIdx.x / kTeam;
     const int team_size = min(kTeam, P - team * kTeam);
     const int nteams = (P + kTeam - 1) / kTeam;
+    // one release per block: barrier, then a device-scope fence and the ticket
+    __syncthreads();
     if (threadIdx.x == 0) {
+        __threadfence();
         const uint32_t t = atomicAdd(rb.team_counter + tile * kMaxTeams + team, 1u);
         is_last = (t == (uint32_t)team_size - 1);
+        if (is_last) __threadfence();
     }
     __syncthreads();
     if (!is_last) return;
-    __threadfence();
     // team stage: one thread per output, the team's partials loaded together
     for (int o = threadIdx.x; o < NO; o += blockDim.x) {
-        const double *src = rb.part + ((size_t)tile * NO + o) * P + team * kTeam;
+        const double *src = rb.part + ((size_t)tile * P + team * kTeam) * NO + o;
         double v[kTeam];
 #pragma unroll
-        for (int i = 0; i < kTeam; ++i) v[i] = (i < team_size) ? __ldcg(src + i) : 0.0;
+        for (int i = 0; i < kTeam; ++i) v[i] = (i < team_size) ? __ldcg(src + (size_t)i * NO) : 0.0;
         double t = 0.0;
 #pragma unroll
         for (int i = 0; i < kTeam; ++i) t += v[i];
-        rb.team_part[((size_t)tile * NO + o) * kMaxTeams + team] = t;
+        rb.team_part[((size_t)tile * kMaxTeams + team) * NO + o] = t;
     }
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         rb.team_counter[tile * kMaxTeams + team] = 0;
+        __threadfence();
         const uint32_t t = atomicAdd(rb.counter + tile, 1u);
         is_last = (t == (uint32_t)nteams - 1);
+        if (is_last) __threadfence();
     }
     __syncthreads();
     if (!is_last) return;
-    __threadfence();
     for (int o = threadIdx.x; o < NO; o += blockDim.x) {
-        const double *src = rb.team_part + ((size_t)tile * NO + o) * kMaxTeams;
+        const double *src = rb.team_part + (size_t)tile * kMaxTeams * NO + o;
         double t = 0.0;
         for (int t0 = 0; t0 < nteams; t0 += kTeam) {
             double v[kTeam];
 #pragma unroll
-            for (int i = 0; i < kTeam; ++i) v[i] = (t0 + i < nteams) ? __ldcg(src + t0 + i) : 0.0;
+            for (int i = 0; i < kTeam; ++i) v[i] = (t0 + i < nteams) ? __ldcg(src + (size_t)(t0 + i) * NO) : 0.0;
 #pragma unroll
             for (int i = 0; i < kTeam; ++i) t += v[i];
         }
@@ -191,31 +273,14 @@ __device__ __forceinline__ void block_reduce_finalize(TA (&acc)[NR][VW], int lan
     if (threadIdx.x == 0) rb.counter[tile] = 0;
 }
 
-// sum_{e in [e0, e1)} w_e x_{col(e)} for this lane's columns; eight gathers
-// in flight per lane
+// sum_{e in [e0, e1)} w_e x_{col(e)} for this lane's columns; four
+// neighbours (eight 16-byte gathers) in flight per lane
 template <typename T, class Op>
 __device__ __forceinline__ typename Vec<T>::V row_sum(const LevelView &A, const Op &op, int e0, int e1, int c0) {
     using V = typename Vec<T>::V;
     V s0 = vzero<V>(), s1 = vzero<V>();
     int e = e0;
-    for (; e + 7 < e1; e += 8) {
-        int j[8];
-        T w[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            j[u] = __ldg(A.col + e + u);
-            w[u] = lw<T>(A, e + u);
-        }
-        V x[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) x[u] = op.gather(j[u], c0);
-#pragma unroll
-        for (int u = 0; u < 8; u += 2) {
-            vfma(s0, w[u], x[u]);
-            vfma(s1, w[u + 1], x[u + 1]);
-        }
-    }
-    if (e + 3 < e1) {
+    for (; e + 3 < e1; e += 4) {
         int j[4];
         T w[4];
 #pragma unroll
@@ -230,7 +295,6 @@ __device__ __forceinline__ typename Vec<T>::V row_sum(const LevelView &A, const 
         vfma(s1, w[1], x[1]);
         vfma(s0, w[2], x[2]);
         vfma(s1, w[3], x[3]);
-        e += 4;
     }
     for (; e < e1; ++e) vfma(s0, lw<T>(A, e), op.gather(__ldg(A.col + e), c0));
     return vadd(s0, s1);
@@ -238,11 +302,31 @@ __device__ __forceinline__ typename Vec<T>::V row_sum(const LevelView &A, const 
 
 // ------------------------------------------------------------------ SpMM-like row operator
 // Op provides:
-//   V gather(int j, int c0) const             operand of node j, this lane's columns
-//   void epi(int i, int c0, V s, double acc[NR][VW])   row i given s = sum_j w_ij x_j
+//   V gather(int j, int c0) const              operand of node j, this lane's columns
+//   void epi(int i, int c0, V s, RAcc &acc)    row i given s = sum_j w_ij x_j
 //   void fin(int c, const double *sums)        per-column finalisation (NR > 0)
-template <typename T, int KT, int NR, class Op>
-__global__ void __launch_bounds__(kBlock) k_rowop(LevelView A, Op op, int nvb_short, int nvb_total,
+// With NR > 0 the per-column sums must not depend on which block finishes a
+// long row, so long rows take their chunk sums from k_chunk_sums (launched
+// just before) and are finished by the group that owns the row, like short
+// rows (PRE = true).  Without reductions the last chunk to arrive finishes
+// the row in the same launch (PRE = false).
+template <typename T, int KT, class Op>
+__global__ void __launch_bounds__(kBlock, 4) k_chunk_sums(LevelView A, Op op, T *chunk_part, int ld_part) {
+    constexpr int VW = Vec<T>::W;
+    constexpr int G = KT / VW;
+    constexpr int RPB = kBlock / G;
+    const int lane = threadIdx.x % G, grp = threadIdx.x / G;
+    const int c0 = blockIdx.y * KT + lane * VW;
+    const int ch = blockIdx.x * RPB + grp;
+    if (ch >= A.n_chunks) return;
+    const int i = __ldg(A.chunk_row + ch);
+    const int e0 = __ldg(A.chunk_begin + ch);
+    const int e1 = min(e0 + kChunk, __ldg(A.rowptr + i + 1));
+    vst<T>(chunk_part + (size_t)ch * ld_part + c0, row_sum<T>(A, op, e0, e1, c0));
+}
+
+template <typename T, int KT, int NR, class Op, bool PRE = false>
+__global__ void __launch_bounds__(kBlock, 4) k_rowop(LevelView A, Op op, int nvb_short, int nvb_total,
                                                   T *chunk_part, int ld_part, RedBuf rb) {
     using V = typename Vec<T>::V;
     constexpr int VW = Vec<T>::W;
@@ -253,19 +337,27 @@ __global__ void __launch_bounds__(kBlock) k_rowop(LevelView A, Op op, int nvb_sh
     const int lane = threadIdx.x % G, grp = threadIdx.x / G;
     const int tile = blockIdx.y;
     const int c0 = tile * KT + lane * VW;
-    T acc[NRA][VW];
+    RAcc<T, NR, VW> acc;
 #pragma unroll
     for (int r = 0; r < NRA; ++r)
 #pragma unroll
-        for (int v = 0; v < VW; ++v) acc[r][v] = T(0);
+        for (int v = 0; v < VW; ++v) acc.a[r][v] = T(0);
 
-    for (int vb = blockIdx.x; vb < nvb_total; vb += gridDim.x) {
+    const int nvb_long = nvb_total - nvb_short;  // chunk blocks come first: they start early
+    for (int vb0 = blockIdx.x; vb0 < nvb_total; vb0 += gridDim.x) {
+        const int vb = PRE ? vb0 : (vb0 < nvb_long ? nvb_short + vb0 : vb0 - nvb_long);
         if (vb < nvb_short) {
             const int i = vb * RPB + grp;
             if (i < A.n) {
                 const int e0 = __ldg(A.rowptr + i), e1 = __ldg(A.rowptr + i + 1);
                 if (e1 - e0 <= kLongRow) {
                     const V s = row_sum<T>(A, op, e0, e1, c0);
+                    op.epi(i, c0, s, acc);
+                } else if (PRE) {
+                    const int li = __ldg(A.long_of_row + i);
+                    const int f0 = __ldg(A.long_first + li), f1 = __ldg(A.long_first + li + 1);
+                    V s = vzero<V>();
+                    for (int f = f0; f < f1; ++f) s = vadd(s, vld<T>(chunk_part + (size_t)f * ld_part + c0));
                     op.epi(i, c0, s, acc);
                 }
             }
@@ -276,7 +368,7 @@ __global__ void __launch_bounds__(kBlock) k_rowop(LevelView A, Op op, int nvb_sh
             if (has) {
                 i = __ldg(A.chunk_row + ch);
                 const int e0 = __ldg(A.chunk_begin + ch);
-                const int e1 = min(e0 + kLongRow, __ldg(A.rowptr + i + 1));
+                const int e1 = min(e0 + kChunk, __ldg(A.rowptr + i + 1));
                 const V s = row_sum<T>(A, op, e0, e1, c0);
                 vst<T>(chunk_part + (size_t)ch * ld_part + c0, s);
                 __threadfence();
@@ -301,26 +393,26 @@ __global__ void __launch_bounds__(kBlock) k_rowop(LevelView A, Op op, int nvb_sh
             __syncwarp();
         }
     }
-    if constexpr (NR > 0) block_reduce_finalize<KT, NR, VW, RPB, T>(acc, lane, grp, rb, op);
+    if constexpr (NR > 0) block_reduce_finalize<KT, NR, VW, G, T>(acc, rb, op);
 }
 
 // ------------------------------------------------------------------ row-local kernels (no gathers)
-// Op provides: void row(int i, int c0, double acc[NR][VW]) and fin (NR > 0).
+// Op provides: void row(int i, int c0, RAcc &acc) and fin (NR > 0).
 template <typename T, int KT, int NR, class Op>
-__global__ void __launch_bounds__(kBlock) k_rows(int n, Op op, RedBuf rb) {
+__global__ void __launch_bounds__(kBlock, 4) k_rows(int n, Op op, RedBuf rb) {
     constexpr int VW = Vec<T>::W;
     constexpr int G = KT / VW;
     constexpr int RPB = kBlock / G;
     constexpr int NRA = NR > 0 ? NR : 1;
     const int lane = threadIdx.x % G, grp = threadIdx.x / G;
     const int c0 = blockIdx.y * KT + lane * VW;
-    T acc[NRA][VW];
+    RAcc<T, NR, VW> acc;
 #pragma unroll
     for (int r = 0; r < NRA; ++r)
 #pragma unroll
-        for (int v = 0; v < VW; ++v) acc[r][v] = T(0);
+        for (int v = 0; v < VW; ++v) acc.a[r][v] = T(0);
     for (int i = blockIdx.x * RPB + grp; i < n; i += gridDim.x * RPB) op.row(i, c0, acc);
-    if constexpr (NR > 0) block_reduce_finalize<KT, NR, VW, RPB, T>(acc, lane, grp, rb, op);
+    if constexpr (NR > 0) block_reduce_finalize<KT, NR, VW, G, T>(acc, rb, op);
 }
 
 }  // namespace cfc

@@ -17,6 +17,11 @@
 // result is returned with zero mean.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "internal.h"
@@ -49,7 +54,7 @@ struct OpSpmvDot {
 #pragma unroll
         for (int v = 0; v < VW; ++v) {
             vel(y, v) = d * vel(x, v) - vel(s, v);
-            acc[0][v] += vel(x, v) * vel(y, v);
+            acc.add(0, v, vel(x, v) * vel(y, v));
         }
         vst<T>(q + (size_t)i * ld + c0, y);
     }
@@ -64,8 +69,8 @@ struct OpSpmvDot {
 // relres_j = ||r_j|| / ||b_j|| ; active_j = relres_j > tol
 template <typename Tin>
 struct OpResid64 {
-    using V = double2;
-    static constexpr int VW = 2;
+    using V = typename Vec<double>::V;
+    static constexpr int VW = Vec<double>::W;
     LevelView A;
     const double *x;
     const double *b;
@@ -84,7 +89,7 @@ struct OpResid64 {
 #pragma unroll
         for (int v = 0; v < VW; ++v) {
             const double rv = vel(bi, v) - (d * vel(xi, v) - vel(s, v));
-            acc[0][v] += rv * rv;
+            acc.add(0, v, rv * rv);
             r[(size_t)i * ld + c0 + v] = (Tin)rv;
         }
     }
@@ -161,10 +166,10 @@ struct OpSmooth {
         if constexpr (NR > 0) {
 #pragma unroll
             for (int v = 0; v < VW; ++v) {
-                acc[0][v] += vel(bi, v) * vel(out, v);
-                acc[1][v] += vel(out, v);
-                acc[2][v] += vel(bi, v);
-                if constexpr (Init) acc[NR - 1][v] += vel(bi, v) * vel(bi, v);
+                acc.add(0, v, vel(bi, v) * vel(out, v));
+                acc.add(1, v, vel(out, v));
+                acc.add(2, v, vel(bi, v));
+                if constexpr (Init) acc.add(NR - 1, v, vel(bi, v) * vel(bi, v));
             }
         }
     }
@@ -285,7 +290,7 @@ struct OpUpdateXR {
         for (int v = 0; v < VW; ++v) {
             vel(xi, v) += vel(a, v) * vel(pi, v);
             vel(ri, v) -= vel(a, v) * vel(qi, v);
-            acc[0][v] += vel(ri, v) * vel(ri, v);
+            acc.add(0, v, vel(ri, v) * vel(ri, v));
         }
         vst<T>(x + o, xi);
         vst<T>(r + o, ri);
@@ -317,10 +322,10 @@ struct OpDotRZ {
 #pragma unroll
         for (int v = 0; v < VW; ++v) {
             const T a = vel(ri, v), b = vel(zi, v);
-            acc[0][v] += a * b;
-            acc[1][v] += b;
-            acc[2][v] += a;
-            if constexpr (Init) acc[3][v] += a * a;
+            acc.add(0, v, a * b);
+            acc.add(1, v, b);
+            acc.add(2, v, a);
+            if constexpr (Init) acc.add(3, v, a * a);
         }
     }
     __device__ void fin(int c, const double *s) const { ds.template fin<Init>(c, s); }
@@ -358,7 +363,8 @@ struct OpUpdateP {
 // first outer step (x = 0): r = b in the inner type
 template <typename Tin>
 struct OpCastB {
-    using V = double2;
+    using V = typename Vec<double>::V;
+    static constexpr int VW = Vec<double>::W;
     const double *b;
     Tin *r;
     int ld;
@@ -366,8 +372,8 @@ struct OpCastB {
     __device__ void row(int i, int c0, Acc &) const {
         const size_t o = (size_t)i * ld + c0;
         const V bi = vld<double>(b + o);
-        r[o] = (Tin)bi.x;
-        r[o + 1] = (Tin)bi.y;
+#pragma unroll
+        for (int v = 0; v < VW; ++v) r[o + v] = (Tin)vel(bi, v);
     }
     __device__ void fin(int, const double *) const {}
 };
@@ -383,8 +389,8 @@ __global__ void k_init_cols(const double *__restrict__ bnorm, double *__restrict
 // x64 += d (active columns only)
 template <typename Tin>
 struct OpAddCorr {
-    using V = double2;
-    static constexpr int VW = 2;
+    using V = typename Vec<double>::V;
+    static constexpr int VW = Vec<double>::W;
     double *x;
     const Tin *d;
     int ld;
@@ -403,7 +409,8 @@ struct OpAddCorr {
 
 // column sums of an FP64 block -> mean
 struct OpColMean64 {
-    using V = double2;
+    using V = typename Vec<double>::V;
+    static constexpr int VW = Vec<double>::W;
     const double *a;
     int ld;
     double inv_n;
@@ -411,15 +418,16 @@ struct OpColMean64 {
     template <class Acc>
     __device__ void row(int i, int c0, Acc &acc) const {
         const V ai = vld<double>(a + (size_t)i * ld + c0);
-        acc[0][0] += ai.x;
-        acc[0][1] += ai.y;
+#pragma unroll
+        for (int v = 0; v < VW; ++v) acc.add(0, v, vel(ai, v));
     }
     __device__ void fin(int c, const double *s) const { mean[c] = s[0] * inv_n; }
 };
 
 // out = a - mean (in place allowed), sum out^2 -> norm
 struct OpSubMean64 {
-    using V = double2;
+    using V = typename Vec<double>::V;
+    static constexpr int VW = Vec<double>::W;
     const double *a;
     double *out;
     int ld;
@@ -429,10 +437,11 @@ struct OpSubMean64 {
     __device__ void row(int i, int c0, Acc &acc) const {
         const size_t o = (size_t)i * ld + c0;
         V ai = vld<double>(a + o);
-        ai.x -= mean[c0];
-        ai.y -= mean[c0 + 1];
-        acc[0][0] += ai.x * ai.x;
-        acc[0][1] += ai.y * ai.y;
+#pragma unroll
+        for (int v = 0; v < VW; ++v) {
+            vel(ai, v) -= mean[c0 + v];
+            acc.add(0, v, vel(ai, v) * vel(ai, v));
+        }
         vst<double>(out + o, ai);
     }
     __device__ void fin(int c, const double *s) const {
@@ -470,6 +479,8 @@ __global__ void k_coarse_dense(const double *__restrict__ Minv, int nc, const T 
     }
 }
 
+constexpr int kRedMaxBlocks = 32768;  // = kTeam * kMaxTeams
+
 int g_num_sms = 0;
 int num_sms() {
     if (!g_num_sms) {
@@ -490,8 +501,8 @@ struct ColState {
 
 template <typename Tin, int KT>
 struct Solver {
-    static constexpr int K64 = KT > 64 ? 64 : KT;  // FP64 tile: at most 32 lanes of double2
-    static constexpr int G64 = K64 / 2;
+    static constexpr int K64 = KT > 64 ? 64 : KT;  // FP64 tile: at most 16 lanes of 4 doubles
+    static constexpr int G64 = K64 / Vec<double>::W;
     static constexpr int RPB64 = kBlock / G64;
 
     lap_hierarchy *h;
@@ -542,8 +553,10 @@ struct Solver {
         }
     }
 
-    int red_grid(int nvb) const { return std::max(1, std::min(nvb, 16 * num_sms())); }
-    int plain_grid(int nvb) const { return std::max(1, std::min(nvb, 32 * num_sms())); }
+    // one block per row block (no serial grid-stride chains of gathers), up to
+    // the size the reduction buffers hold
+    int red_grid(int nvb) const { return std::max(1, std::min(nvb, kRedMaxBlocks)); }
+    int plain_grid(int nvb) const { return std::max(1, std::min(nvb, kRedMaxBlocks)); }
 
     static double vec_bytes(int64_t n, int ld, int nvec, int elem) { return (double)n * ld * elem * nvec; }
     static double mat_bytes(const Level &L, int wb) {
@@ -557,6 +570,15 @@ struct Solver {
         constexpr int RPB = kBlock / G;
         const int nvb_short = (L.n + RPB - 1) / RPB;
         const int nvb_long = (L.n_chunks + RPB - 1) / RPB;
+        if (NR > 0 && L.n_chunks > 0) {
+            // deterministic reductions: chunk sums first, rows finished by their own group
+            CFC_LAUNCH(fam, s, 0.0, (k_chunk_sums<T, KT, Op>), dim3(nvb_long, ntiles), kBlock, 0, view(L), op, cpart,
+                       ld);
+            dim3 grid(red_grid(nvb_short), ntiles);
+            CFC_LAUNCH(fam, s, bytes, (k_rowop<T, KT, NR, Op, true>), grid, kBlock, 0, view(L), op, nvb_short,
+                       nvb_short, cpart, ld, rb);
+            return;
+        }
         const int nvb = nvb_short + nvb_long;
         const int gx = NR > 0 ? red_grid(nvb) : plain_grid(nvb);
         dim3 grid(gx, ntiles);
@@ -741,9 +763,17 @@ struct Solver {
                 dim3 grid(red_grid(nvb), ntiles64);
                 using Op = OpResid64<Tin>;
                 Op op{view(L0), x64, b64, r, ld, cs.bnorm, cs.relres, cs.active_out, o.tol};
-                CFC_LAUNCH(LAP_KF_RESID64, s, mat_bytes(L0, 8) + 2 * v64 + vec_bytes(n, ld, 1, sizeof(Tin)),
-                           (k_rowop<double, K64, 1, Op>), grid, kBlock, 0, view(L0), op, nvb_short, nvb, chunk_part64,
-                           ld, rb);
+                const double bytes = mat_bytes(L0, 8) + 2 * v64 + vec_bytes(n, ld, 1, sizeof(Tin));
+                if (L0.n_chunks > 0) {
+                    CFC_LAUNCH(LAP_KF_RESID64, s, 0.0, (k_chunk_sums<double, K64, Op>), dim3(nvb_long, ntiles64),
+                               kBlock, 0, view(L0), op, chunk_part64, ld);
+                    CFC_LAUNCH(LAP_KF_RESID64, s, bytes, (k_rowop<double, K64, 1, Op, true>),
+                               dim3(red_grid(nvb_short), ntiles64), kBlock, 0, view(L0), op, nvb_short, nvb_short,
+                               chunk_part64, ld, rb);
+                } else {
+                    CFC_LAUNCH(LAP_KF_RESID64, s, bytes, (k_rowop<double, K64, 1, Op>), grid, kBlock, 0, view(L0), op,
+                               nvb_short, nvb, chunk_part64, ld, rb);
+                }
             }
             CFC_CUDA(cudaMemcpyAsync(h_active, cs.active_out, ld * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
             CFC_CUDA(cudaMemcpyAsync(hrel.data(), cs.relres, ld * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -819,7 +849,9 @@ lap_status_t run_solver(lap_hierarchy *h, int32_t k, const double *B, double *X,
     for (int l = 1; l < nlev; ++l)
         for (int v = 0; v < 3; ++v) sizes.push_back(align_up((size_t)h->lv[l].n * ld * sizeof(Tin)));
     sizes.push_back(align_up(std::max<int64_t>(max_chunks, 1) * ld * 8));  // chunk partials (FP64 size)
-    const int P = 16 * num_sms();
+    int64_t max_rows = 0;
+    for (int l = 0; l < nlev; ++l) max_rows = std::max<int64_t>(max_rows, h->lv[l].n + h->lv[l].n_chunks);
+    const int P = (int)std::min<int64_t>(kRedMaxBlocks, (max_rows + 3) / 4 + 1);  // >= blocks of any launch
     sizes.push_back(align_up((size_t)ntiles * 4 * KT * P * 8));          // reduction partials
     sizes.push_back(align_up((size_t)ntiles * 4 * KT * kMaxTeams * 8));  // team partials
     sizes.push_back(align_up(ld * 8) * 10);                       // column scalars
@@ -903,18 +935,11 @@ int32_t *pinned_scratch() {
     return buf;
 }
 
-lap_status_t solve_multi(lap_hierarchy *h, int32_t k, const double *B, double *X, const lap_solve_opts_t &o,
-                         cudaStream_t s, lap_solve_info_t *info) {
-    CFC_REQUIRE(k >= 1 && k <= 4096, LAP_EINVAL, "need 1 <= k <= 4096");
-    CFC_REQUIRE(B && X && B != X, LAP_EINVAL, "B and X must be distinct device buffers");
-    CFC_REQUIRE(is_device_pointer(B) && is_device_pointer(X), LAP_EINVAL, "B and X must be device pointers");
-    CFC_REQUIRE(o.tol > 0 && o.max_outer >= 0 && o.max_inner >= 1, LAP_EINVAL, "bad solve options");
-    int kt = o.k_tile;
+namespace {
+
+lap_status_t dispatch(lap_hierarchy *h, int32_t k, const double *B, double *X, const lap_solve_opts_t &o,
+                      cudaStream_t s, lap_solve_info_t *info, int kt) {
     const bool fp64 = (o.precision == LAP_FP64);
-    if (kt == 0) kt = (k >= 64) ? 64 : (k > 16 ? 32 : 16);
-    if (fp64 && kt > 64) kt = 64;
-    while ((k + kt - 1) / kt > kMaxTiles) kt *= 2;
-    CFC_REQUIRE(kt == 16 || kt == 32 || kt == 64 || (kt == 128 && !fp64), LAP_EINVAL, "k_tile must be 16/32/64/128");
     if (fp64) {
         switch (kt) {
             case 16: return run_solver<double, 16>(h, k, B, X, o, s, info);
@@ -928,6 +953,105 @@ lap_status_t solve_multi(lap_hierarchy *h, int32_t k, const double *B, double *X
         case 64: return run_solver<float, 64>(h, k, B, X, o, s, info);
         default: return run_solver<float, 128>(h, k, B, X, o, s, info);
     }
+}
+
+// Autotuned multigrid depth, per graph size and solve configuration: the
+// first solve with a new key times complete solves with 1, 2, ... levels and
+// keeps the fastest that converged (a one-time cost, like a library picking
+// kernels by timing them).
+struct TuneKey {
+    int64_t n, nnz;
+    int precision, kt, smoother, nu_pre, nu_post;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(n, nnz, precision, kt, smoother, nu_pre, nu_post) <
+               std::tie(o.n, o.nnz, o.precision, o.kt, o.smoother, o.nu_pre, o.nu_post);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;
+
+}  // namespace
+
+lap_status_t solve_multi(lap_hierarchy *h, int32_t k, const double *B, double *X, const lap_solve_opts_t &o_in,
+                         cudaStream_t s, lap_solve_info_t *info) {
+    CFC_REQUIRE(k >= 1 && k <= 4096, LAP_EINVAL, "need 1 <= k <= 4096");
+    CFC_REQUIRE(B && X && B != X, LAP_EINVAL, "B and X must be distinct device buffers");
+    CFC_REQUIRE(is_device_pointer(B) && is_device_pointer(X), LAP_EINVAL, "B and X must be device pointers");
+    CFC_REQUIRE(o_in.tol > 0 && o_in.max_outer >= 0 && o_in.max_inner >= 1, LAP_EINVAL, "bad solve options");
+    lap_solve_opts_t o = o_in;
+    int kt = o.k_tile;
+    const bool fp64 = (o.precision == LAP_FP64);
+    if (kt == 0) kt = (k >= 64) ? 64 : (k > 16 ? 32 : 16);
+    if (fp64 && kt > 64) kt = 64;
+    while ((k + kt - 1) / kt > kMaxTiles) kt *= 2;
+    CFC_REQUIRE(kt == 16 || kt == 32 || kt == 64 || (kt == 128 && !fp64), LAP_EINVAL, "k_tile must be 16/32/64/128");
+    if (o.levels_used > 0) {
+        grow_levels(*h, o.levels_used, s);
+        return dispatch(h, k, B, X, o, s, info, kt);
+    }
+    if (o.levels_used < 0) {  // every level
+        grow_levels(*h, 0, s);
+        o.levels_used = 0;
+        return dispatch(h, k, B, X, o, s, info, kt);
+    }
+    const TuneKey key{h->lv[0].n, h->lv[0].nnz, o.precision, kt, o.smoother, o.nu_pre, o.nu_post};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            o.levels_used = it->second;
+            grow_levels(*h, o.levels_used, s);
+            return dispatch(h, k, B, X, o, s, info, kt);
+        }
+    }
+    grow_levels(*h, 0, s);
+    const int L = (int)h->lv.size();
+    std::vector<int> cand;
+    for (int l = 1; l <= L && l <= 4; ++l) cand.push_back(l);
+    if (L > 4) cand.push_back(L);
+    cudaEvent_t e0, e1;
+    CFC_CUDA(cudaEventCreate(&e0));
+    CFC_CUDA(cudaEventCreate(&e1));
+    // a candidate's cost: its solve plus building its coarse levels (every new
+    // hierarchy of this graph pays that again)
+    float best_ms = 0.f;
+    int best = -1;
+    lap_status_t last = LAP_OK;
+    const bool verbose = std::getenv("LAP_TUNE_VERBOSE") != nullptr;
+    // untimed warm-up: first launches load kernels and size the workspace
+    o.levels_used = cand[0];
+    dispatch(h, k, B, X, o, s, info, kt);
+    for (size_t t = 0; t < cand.size(); ++t) {
+        o.levels_used = cand[t];
+        CFC_CUDA(cudaEventRecord(e0, s));
+        last = dispatch(h, k, B, X, o, s, info, kt);
+        CFC_CUDA(cudaEventRecord(e1, s));
+        CFC_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CFC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        double build = 0.0;
+        for (int l = 1; l < cand[t] && l < (int)h->level_ms.size(); ++l) build += h->level_ms[l];
+        const float cost = ms + (float)build;
+        if (verbose)
+            std::fprintf(stderr, "lap autotune n=%lld kt=%d levels=%d solve=%.3f ms build=%.3f ms status=%d\n",
+                         (long long)h->lv[0].n, kt, cand[t], ms, build, (int)last);
+        if (last == LAP_OK && (best < 0 || cost < best_ms)) {
+            best_ms = cost;
+            best = cand[t];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best < 0) return last;  // nothing converged: report the last attempt
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = best;
+    }
+    if (best != cand.back() || last != LAP_OK) {
+        o.levels_used = best;
+        return dispatch(h, k, B, X, o, s, info, kt);
+    }
+    return last;
 }
 
 }  // namespace cfc

@@ -43,7 +43,7 @@ def _rel(a, b):
 # ------------------------------------------------------------------ ingest / hierarchy
 def test_hierarchy_sizes(P):
     n, s, d, w = _graph(synth.grid2d(48))
-    h = P.lap_build_hierarchy(n, s, d, w)
+    h = P.lap_build_hierarchy(n, s, d, w, P.lap_default_hier_opts(eager=1))
     info = P.lap_hierarchy_info(h)
     assert info["n"] == 2304 and info["m"] == 4512
     assert info["level_nnz"][0] == 2 * 4512
@@ -141,7 +141,7 @@ def test_solve_is_deterministic_and_column_independent(P):
     h = P.lap_build_hierarchy(n, s, d, w)
     B = torch.randn((n, 48), dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
     X1, X2 = torch.empty_like(B), torch.empty_like(B)
-    o = P.lap_default_solve_opts(k_tile=16)
+    o = P.lap_default_solve_opts(k_tile=16, levels_used=-1)
     P.lap_solve_multi(h, B, X1, o)
     P.lap_solve_multi(h, B, X2, o)
     assert torch.equal(X1, X2)
@@ -149,6 +149,27 @@ def test_solve_is_deterministic_and_column_independent(P):
     Xs = torch.empty((n, 16), dtype=torch.float64, device="cuda")
     P.lap_solve_multi(h, B[:, :16].contiguous(), Xs, o)
     assert torch.equal(Xs, X1[:, :16])
+
+
+def test_lazy_levels_and_depth_choices(P):
+    import torch
+    n, s, d, w = _graph(synth.grid2d(64))
+    h = P.lap_build_hierarchy(n, s, d, w)
+    assert P.lap_hierarchy_info(h)["levels"] == 1  # coarse levels are built on demand
+    B = torch.randn((n, 16), dtype=torch.float64, device="cuda")
+    X = torch.empty_like(B)
+    P.lap_solve_multi(h, B, X, P.lap_default_solve_opts(levels_used=2))
+    assert P.lap_hierarchy_info(h)["levels"] == 2
+    ref = None
+    for lv in (1, 3, -1, 0):
+        info = P.lap_solve_multi(h, B, X, P.lap_default_solve_opts(levels_used=lv))
+        assert info["max_rel_residual"] <= 1e-8
+        if ref is None:
+            ref = X.clone()
+        else:
+            err = (X - ref).norm(dim=0) / ref.norm(dim=0)
+            assert float(err.max()) <= 1e-5
+    assert P.lap_hierarchy_info(h)["levels"] >= 4
 
 
 def test_solve_noconv_reports(P):
