@@ -189,6 +189,23 @@ lap_status_t cfc_farness_jl(lap_hierarchy_t *h, int32_t k, double eps, uint64_t 
                             void *stream);
 
 /*
+ * cfc_farness_from_solution -- Algorithm 1, step 4 and the closing formula of
+ * Sec. 5.2 on a solution block the caller already has: for each query node v,
+ * f~(v) = sum_{w != v} ||Z_{.,v} - Z_{.,w}||^2, evaluated in O(nk) as
+ * sum_i [n Z_vi^2 - 2 Z_vi S_i + T_i] with S_i = sum_w Z_wi, T_i = sum_w Z_wi^2,
+ * all sums in FP64 in a fixed order (bitwise reproducible).
+ *   n        number of nodes, n >= 2
+ *   k        columns of Z, 1 <= k <= 4096
+ *   Z        device double[n * k] row-major: Z[u * k + i] = z_i(u), the i-th
+ *            solution of Algorithm 1 evaluated at node u
+ *   q, nodes, farness as cfc_farness_jl (host or device)
+ * Errors: LAP_EINVAL (sizes, NULL, Z not on the device, node out of range),
+ * LAP_ENOMEM, LAP_ECUDA.  Synchronises `stream`.
+ */
+lap_status_t cfc_farness_from_solution(int64_t n, int32_t k, const double *Z, int32_t q,
+                                       const int32_t *nodes, double *farness, void *stream);
+
+/*
  * cfc_sample_pivots -- the pivot set S of Sec. 5.1: a uniform n_pivots-subset
  * of V without replacement (all of V: a query node may be a pivot), drawn on
  * the device by Floyd's algorithm; Floyd step s (s = 0..n_pivots-1, range

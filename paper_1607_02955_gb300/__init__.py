@@ -40,6 +40,7 @@ from ._binding import (  # noqa: F401
     lap_solve_multi,
     cfc_jl_rhs,
     cfc_farness_jl,
+    cfc_farness_from_solution,
     cfc_sample_pivots,
     cfc_farness_sampled,
     cfc_exact_small,

@@ -17,7 +17,8 @@ KERNEL_FAMILIES = ["spmv_fine", "smooth_fine", "restrict_fine", "blas1", "coarse
 
 SYMBOLS = [
     "lap_default_hier_opts", "lap_default_solve_opts", "lap_build_hierarchy", "lap_hierarchy_destroy",
-    "lap_hierarchy_info", "lap_solve_multi", "cfc_jl_rhs", "cfc_farness_jl", "cfc_sample_pivots",
+    "lap_hierarchy_info", "lap_solve_multi", "cfc_jl_rhs", "cfc_farness_jl", "cfc_farness_from_solution",
+    "cfc_sample_pivots",
     "cfc_farness_sampled", "cfc_exact_small", "lap_status_string", "lap_last_error", "lap_stats_reset",
     "lap_stats_set_timing", "lap_stats_read",
 ]
@@ -85,6 +86,8 @@ def lib():
     L.cfc_jl_rhs.restype = C.c_int
     L.cfc_farness_jl.argtypes = [vp, i32, dbl, u64, i32, vp, vp, C.POINTER(SolveOpts), vp]
     L.cfc_farness_jl.restype = C.c_int
+    L.cfc_farness_from_solution.argtypes = [i64, i32, vp, i32, vp, vp, vp]
+    L.cfc_farness_from_solution.restype = C.c_int
     L.cfc_sample_pivots.argtypes = [vp, i32, u64, vp, vp]
     L.cfc_sample_pivots.restype = C.c_int
     L.cfc_farness_sampled.argtypes = [vp, i32, u64, i32, vp, vp, C.POINTER(SolveOpts), vp]
@@ -247,6 +250,19 @@ def cfc_farness_jl(h: Hierarchy, k: int, seed: int, nodes, eps: float = 0.0, opt
     st = lib().cfc_farness_jl(h.handle, int(k), float(eps), int(seed), int(q), pn, po,
                               C.byref(opts) if opts is not None else None, _stream(stream))
     _check(st, "cfc_farness_jl")
+    return out
+
+
+def cfc_farness_from_solution(Z, nodes, out=None, stream=None):
+    """Z: contiguous FP64 CUDA tensor (n, k); returns the farness of each node."""
+    n, k = Z.shape
+    q = len(nodes)
+    pz, kz = _ptr(Z, np.float64)
+    pn, kn = _ptr(nodes, np.int32)
+    out = _out_f64(out, q)
+    po, ko = _ptr(out, np.float64)
+    _check(lib().cfc_farness_from_solution(int(n), int(k), pz, int(q), pn, po, _stream(stream)),
+           "cfc_farness_from_solution")
     return out
 
 

@@ -312,6 +312,13 @@ lap_status_t cfc_farness_jl(lap_hierarchy_t *h, int32_t k, double eps, uint64_t 
     });
 }
 
+lap_status_t cfc_farness_from_solution(int64_t n, int32_t k, const double *Z, int32_t q, const int32_t *nodes,
+                                       double *farness, void *stream) {
+    return guard([&]() -> lap_status_t {
+        return farness_from_solution(n, k, Z, q, nodes, farness, (cudaStream_t)stream);
+    });
+}
+
 lap_status_t cfc_sample_pivots(lap_hierarchy_t *h, int32_t n_pivots, uint64_t seed, int32_t *pivots,
                                void *stream) {
     return guard([&]() -> lap_status_t {

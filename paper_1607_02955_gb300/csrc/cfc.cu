@@ -358,6 +358,27 @@ lap_status_t farness_jl(lap_hierarchy *h, int32_t k, double eps, uint64_t seed, 
     return st;
 }
 
+// Algorithm 1 step 4 on a given block Z (n x k, row-major, device)
+lap_status_t farness_from_solution(int64_t n, int32_t k, const double *Z, int32_t q, const int32_t *nodes,
+                                   double *farness, cudaStream_t s) {
+    CFC_REQUIRE(n >= 2 && n < (int64_t(1) << 31), LAP_EINVAL, "need 2 <= n < 2^31");
+    CFC_REQUIRE(k >= 1 && k <= 4096, LAP_EINVAL, "need 1 <= k <= 4096");
+    CFC_REQUIRE(q >= 1 && q <= n, LAP_EINVAL, "need 1 <= q <= n");
+    CFC_REQUIRE(Z && farness, LAP_EINVAL, "Z and farness must not be NULL");
+    CFC_REQUIRE(is_device_pointer(Z), LAP_EINVAL, "Z must be a device pointer");
+    DBuf<int32_t> ntmp;
+    const int32_t *dn = nodes_to_device(nodes, q, (int32_t)n, ntmp, s);
+    const int P = (int)std::min<int64_t>(2 * num_sms_public(), (n + kRedRows - 1) / kRedRows);
+    DBuf<double> part((size_t)k * P * 2, s), S(k, s), T(k, s), f(q, s);
+    dim3 g1(P, (k + 31) / 32), b1(32, kRedRows);
+    CFC_LAUNCH(LAP_KF_CFC, s, (double)n * k * 8, k_colsum2_part, g1, b1, 0, Z, n, k, k, part.get());
+    CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_colsum2_final, (k + 7) / 8, 256, 0, part.get(), P, k, S.get(), T.get());
+    CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_jl_farness, (q + 7) / 8, 256, 0, Z, n, k, k, S.get(), T.get(), dn, q, f.get());
+    copy_out(farness, f.get(), q, s);
+    CFC_CUDA(cudaStreamSynchronize(s));
+    return LAP_OK;
+}
+
 void sample_pivots(int64_t n, int32_t kk, uint64_t seed, int32_t *dpiv, cudaStream_t s) {
     CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_floyd, 1, 32, (size_t)kk * sizeof(int32_t), n, kk, seed, dpiv);
 }

@@ -978,6 +978,8 @@ lap_status_t solve_multi(lap_hierarchy *h, int32_t k, const double *B, double *X
     CFC_REQUIRE(B && X && B != X, LAP_EINVAL, "B and X must be distinct device buffers");
     CFC_REQUIRE(is_device_pointer(B) && is_device_pointer(X), LAP_EINVAL, "B and X must be device pointers");
     CFC_REQUIRE(o_in.tol > 0 && o_in.max_outer >= 0 && o_in.max_inner >= 1, LAP_EINVAL, "bad solve options");
+    CFC_REQUIRE(o_in.precision == LAP_FP64 || o_in.precision == LAP_FP32_REFINED, LAP_ENOTIMPL,
+                "precision mode not implemented (LAP_FP64 and LAP_FP32_REFINED are)");
     lap_solve_opts_t o = o_in;
     int kt = o.k_tile;
     const bool fp64 = (o.precision == LAP_FP64);

@@ -197,6 +197,18 @@ def test_farness_jl_matches_oracle(P, gen, k):
     assert _rel(f, fo) <= FARNESS_RTOL
 
 
+@pytest.mark.parametrize("n,k", [(3000, 64), (517, 5), (2, 1), (1000, 300)])
+def test_farness_from_solution_matches_literal_sum(P, n, k):
+    import torch
+    rng = np.random.default_rng(n + k)
+    Z = rng.standard_normal((n, k))
+    nodes = np.unique(rng.integers(0, n, size=min(n, 9))).astype(np.int32)
+    f = P.cfc_farness_from_solution(torch.tensor(Z, device="cuda"), nodes)
+    # literal sum over w of ||Z_v - Z_w||^2 (Algorithm 1, step 4)
+    fo = np.array([((Z - Z[v]) ** 2).sum() for v in nodes])
+    assert _rel(f, fo) <= 1e-12
+
+
 def test_farness_jl_eps_rule(P):
     n, s, d, w = _graph(synth.grid2d(20))
     g = canonical_graph(n, s, d, w)
