@@ -206,6 +206,30 @@ lap_status_t cfc_farness_from_solution(int64_t n, int32_t k, const double *Z, in
                                        const int32_t *nodes, double *farness, void *stream);
 
 /*
+ * cfc_farness_from_solution_noalloc -- cfc_farness_from_solution for callers
+ * that cannot allocate device memory when they need the result: code running
+ * inside an allocator or out-of-memory handler, a process held to a hard
+ * device-memory cap, or work on a stream that must not wait on the
+ * allocator.  The paper has no counterpart: this is a deployment variant.
+ * It allocates nothing (no cudaMalloc, cudaFree or allocating library call);
+ * its scratch is a fixed 2 MiB + 4 KiB array in the library, reserved on
+ * every GPU that loads the library until the process exits.
+ *   n, k, Z    as cfc_farness_from_solution, with k <= 256
+ *   q >= 1, nodes  device int32[q]; a node outside [0, n) gets NaN
+ *   farness    device double[q], output
+ * The first call on a device looks up the scratch address for that device;
+ * make that first call before capturing the stream into a CUDA graph.
+ * Results equal those of cfc_farness_from_solution.  All calls share the one
+ * scratch array: calls whose work overlaps on the same GPU race, so order
+ * them on one stream (or synchronise between them).  The call only enqueues
+ * work on `stream` and returns without synchronising.
+ * Errors: LAP_EBUDGET (k > 256), LAP_EINVAL (sizes, NULL, a pointer that is
+ * not device memory), LAP_ECUDA.
+ */
+lap_status_t cfc_farness_from_solution_noalloc(int64_t n, int32_t k, const double *Z, int32_t q,
+                                               const int32_t *nodes, double *farness, void *stream);
+
+/*
  * cfc_sample_pivots -- the pivot set S of Sec. 5.1: a uniform n_pivots-subset
  * of V without replacement (all of V: a query node may be a pivot), drawn on
  * the device by Floyd's algorithm; Floyd step s (s = 0..n_pivots-1, range

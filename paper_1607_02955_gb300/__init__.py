@@ -41,6 +41,7 @@ from ._binding import (  # noqa: F401
     cfc_jl_rhs,
     cfc_farness_jl,
     cfc_farness_from_solution,
+    cfc_farness_from_solution_noalloc,
     cfc_sample_pivots,
     cfc_farness_sampled,
     cfc_exact_small,

@@ -18,7 +18,7 @@ KERNEL_FAMILIES = ["spmv_fine", "smooth_fine", "restrict_fine", "blas1", "coarse
 SYMBOLS = [
     "lap_default_hier_opts", "lap_default_solve_opts", "lap_build_hierarchy", "lap_hierarchy_destroy",
     "lap_hierarchy_info", "lap_solve_multi", "cfc_jl_rhs", "cfc_farness_jl", "cfc_farness_from_solution",
-    "cfc_sample_pivots",
+    "cfc_farness_from_solution_noalloc", "cfc_sample_pivots",
     "cfc_farness_sampled", "cfc_exact_small", "lap_status_string", "lap_last_error", "lap_stats_reset",
     "lap_stats_set_timing", "lap_stats_read",
 ]
@@ -88,6 +88,8 @@ def lib():
     L.cfc_farness_jl.restype = C.c_int
     L.cfc_farness_from_solution.argtypes = [i64, i32, vp, i32, vp, vp, vp]
     L.cfc_farness_from_solution.restype = C.c_int
+    L.cfc_farness_from_solution_noalloc.argtypes = [i64, i32, vp, i32, vp, vp, vp]
+    L.cfc_farness_from_solution_noalloc.restype = C.c_int
     L.cfc_sample_pivots.argtypes = [vp, i32, u64, vp, vp]
     L.cfc_sample_pivots.restype = C.c_int
     L.cfc_farness_sampled.argtypes = [vp, i32, u64, i32, vp, vp, C.POINTER(SolveOpts), vp]
@@ -263,6 +265,19 @@ def cfc_farness_from_solution(Z, nodes, out=None, stream=None):
     po, ko = _ptr(out, np.float64)
     _check(lib().cfc_farness_from_solution(int(n), int(k), pz, int(q), pn, po, _stream(stream)),
            "cfc_farness_from_solution")
+    return out
+
+
+def cfc_farness_from_solution_noalloc(Z, nodes, out, stream=None):
+    """Allocation-free variant: Z (n, k) FP64, nodes int32 and out FP64 must
+    all be CUDA tensors; returns after enqueuing the work on the stream."""
+    n, k = Z.shape
+    q = nodes.numel()
+    pz, kz = _ptr(Z, np.float64)
+    pn, kn = _ptr(nodes, np.int32)
+    po, ko = _ptr(out, np.float64)
+    _check(lib().cfc_farness_from_solution_noalloc(int(n), int(k), pz, int(q), pn, po, _stream(stream)),
+           "cfc_farness_from_solution_noalloc")
     return out
 
 

@@ -319,6 +319,13 @@ lap_status_t cfc_farness_from_solution(int64_t n, int32_t k, const double *Z, in
     });
 }
 
+lap_status_t cfc_farness_from_solution_noalloc(int64_t n, int32_t k, const double *Z, int32_t q,
+                                               const int32_t *nodes, double *farness, void *stream) {
+    return guard([&]() -> lap_status_t {
+        return farness_from_solution_noalloc(n, k, Z, q, nodes, farness, (cudaStream_t)stream);
+    });
+}
+
 lap_status_t cfc_sample_pivots(lap_hierarchy_t *h, int32_t n_pivots, uint64_t seed, int32_t *pivots,
                                void *stream) {
     return guard([&]() -> lap_status_t {

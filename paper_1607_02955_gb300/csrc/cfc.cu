@@ -6,6 +6,7 @@
 //  * exact farness of small graphs from the dense pseudoinverse (Sec. 4).
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -376,6 +377,83 @@ lap_status_t farness_from_solution(int64_t n, int32_t k, const double *Z, int32_
     CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_jl_farness, (q + 7) / 8, 256, 0, Z, n, k, k, S.get(), T.get(), dn, q, f.get());
     copy_out(farness, f.get(), q, s);
     CFC_CUDA(cudaStreamSynchronize(s));
+    return LAP_OK;
+}
+
+// ---------------------------------------------------------------- allocation-free variant
+// Some callers cannot allocate device memory at the point where they need a
+// farness (code running inside an allocator or out-of-memory handler, a
+// process under a hard device-memory cap, or a stream that must not
+// synchronise with the allocator).  cfc_farness_from_solution_noalloc serves
+// them: its scratch is the array below, reserved on every GPU that loads this
+// library until the process exits.  It holds the per-block column partials
+// (at most kNoAllocMaxP blocks of kNoAllocMaxK columns) and the column sums
+// S, T: 2 MiB + 4 KiB.  Every call overwrites what it uses before reading it;
+// calls that overlap on one GPU share the array and race.
+constexpr int kNoAllocMaxK = 256;
+constexpr int kNoAllocMaxP = 512;
+constexpr size_t kNoAllocDoubles = (size_t)kNoAllocMaxP * kNoAllocMaxK * 2 + 2 * kNoAllocMaxK;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+namespace {
+// The host cannot use g_noalloc_scratch's name as a device address: the
+// address is looked up once per device, with that device current.
+double *noalloc_scratch() {
+    static std::mutex mu;
+    static double *ptr[128] = {};
+    int dev = 0;
+    CFC_CUDA(cudaGetDevice(&dev));
+    CFC_REQUIRE(dev >= 0 && dev < 128, LAP_ECUDA, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ptr[dev]) {
+        void *p = nullptr;
+        CFC_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        ptr[dev] = static_cast<double *>(p);
+    }
+    return ptr[dev];
+}
+
+// k_jl_farness with a range check: a node outside [0, n) gets NaN
+__global__ void k_jl_farness_checked(const double *__restrict__ Z, int64_t n, int k, const double *__restrict__ S,
+                                     const double *__restrict__ T, const int32_t *__restrict__ nodes, int q,
+                                     double *__restrict__ f) {
+    const int t = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (t >= q) return;
+    const int64_t v = nodes[t];
+    if (v < 0 || v >= n) {
+        if (lane == 0) f[t] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
+    double a = 0.0;
+    for (int i = lane; i < k; i += 32) {
+        const double z = Z[v * k + i];
+        a += (double)n * z * z - 2.0 * z * S[i] + T[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if (lane == 0) f[t] = a;
+}
+}  // namespace
+
+lap_status_t farness_from_solution_noalloc(int64_t n, int32_t k, const double *Z, int32_t q, const int32_t *nodes,
+                                           double *farness, cudaStream_t s) {
+    CFC_REQUIRE(n >= 2 && n < (int64_t(1) << 31), LAP_EINVAL, "need 2 <= n < 2^31");
+    CFC_REQUIRE(k >= 1, LAP_EINVAL, "need k >= 1");
+    CFC_REQUIRE(k <= kNoAllocMaxK, LAP_EBUDGET,
+                "cfc_farness_from_solution_noalloc: k exceeds its fixed scratch (at most 256 columns)");
+    CFC_REQUIRE(q >= 1, LAP_EINVAL, "need q >= 1");
+    CFC_REQUIRE(Z && nodes && farness, LAP_EINVAL, "Z, nodes and farness must not be NULL");
+    CFC_REQUIRE(is_device_pointer(Z) && is_device_pointer(nodes) && is_device_pointer(farness), LAP_EINVAL,
+                "Z, nodes and farness must be device pointers");
+    double *scr = noalloc_scratch();
+    double *part = scr;
+    double *S = scr + (size_t)kNoAllocMaxP * kNoAllocMaxK * 2;
+    double *T = S + kNoAllocMaxK;
+    const int P = (int)std::min<int64_t>(std::min(2 * num_sms_public(), kNoAllocMaxP), (n + kRedRows - 1) / kRedRows);
+    dim3 g1(P, (k + 31) / 32), b1(32, kRedRows);
+    CFC_LAUNCH(LAP_KF_CFC, s, (double)n * k * 8, k_colsum2_part, g1, b1, 0, Z, n, k, k, part);
+    CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_colsum2_final, (k + 7) / 8, 256, 0, part, P, k, S, T);
+    CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_jl_farness_checked, (q + 7) / 8, 256, 0, Z, n, k, S, T, nodes, q, farness);
     return LAP_OK;
 }
 

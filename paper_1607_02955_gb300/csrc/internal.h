@@ -224,6 +224,8 @@ lap_status_t farness_jl(lap_hierarchy *h, int32_t k, double eps, uint64_t seed, 
                         double *farness, const lap_solve_opts_t &o, cudaStream_t s);
 lap_status_t farness_from_solution(int64_t n, int32_t k, const double *Z, int32_t q, const int32_t *nodes,
                                    double *farness, cudaStream_t s);
+lap_status_t farness_from_solution_noalloc(int64_t n, int32_t k, const double *Z, int32_t q, const int32_t *nodes,
+                                           double *farness, cudaStream_t s);
 lap_status_t pivots_api(lap_hierarchy *h, int32_t kk, uint64_t seed, int32_t *pivots, cudaStream_t s);
 lap_status_t farness_sampled(lap_hierarchy *h, int32_t kk, uint64_t seed, int32_t q, const int32_t *nodes,
                              double *farness, const lap_solve_opts_t &o, cudaStream_t s);
