@@ -87,6 +87,10 @@ typedef struct {
                              first solve for a graph size and configuration times
                              complete solves with 1, 2, 3, 4 and all levels and the
                              fastest converged depth is kept for the process */
+    int32_t nu_coarse;    /* smoothing steps (Chebyshev degree) at a coarsest level that has
+                             no dense solve, e.g. the one-level smoother-only
+                             preconditioner; 0 (default): max(nu_pre, 4), or autotuned
+                             together with levels_used */
 } lap_solve_opts_t;
 
 typedef struct {

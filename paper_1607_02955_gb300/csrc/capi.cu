@@ -196,6 +196,7 @@ void lap_default_solve_opts(lap_solve_opts_t *o) {
     o->nu_post = 2;
     o->check_every = 4;
     o->levels_used = 0;
+    o->nu_coarse = 0;
 }
 
 const char *lap_status_string(lap_status_t s) {

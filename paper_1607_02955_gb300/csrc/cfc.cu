@@ -62,70 +62,126 @@ __device__ __forceinline__ uint32_t jl_bits32(uint64_t e, int cb, uint64_t seed)
     return (uint32_t)(word >> (i0 % 64));
 }
 
-// sum over entries [e0, e1) of row u of sgn * sqrt(w) * q_{i,e} for 32 rows of Q
-__device__ __forceinline__ void jl_accum(const int32_t *col, const int32_t *eid, const double *w, int u, int e0,
-                                         int e1, int cb, uint64_t seed, double scale, double (&acc)[32]) {
-    for (int e = e0; e < e1; ++e) {
-        const int v = col[e];
-        const double sw = (u < v ? scale : -scale) * sqrt(w[e]);
-        const uint32_t bits = jl_bits32((uint64_t)eid[e], cb, seed);
-#pragma unroll
-        for (int t = 0; t < 32; ++t) acc[t] += ((bits >> t) & 1u) ? -sw : sw;
+// JL right-hand sides in exact fixed point.  Row u's terms
+// sgn * sqrt(w_e) / sqrt(k) (sgn = +1 if u < v else -1, the orientation of B)
+// are held as integers in units of 2^-S_u, with S_u chosen from the
+// Cauchy-Schwarz bound
+//   sum_e sqrt(w_e) / sqrt(k) <= sqrt(len_u * D_uu / k) < 2^(61 - S_u),
+// so every column sum is an exact int64 addition (order-free: split rows
+// combine without ordering concerns) and is rounded to FP64 once, by
+// integer instructions.  Each term is rounded to 2^-(S_u + 1).
+__device__ __forceinline__ int jl_row_shift(const int32_t *rowptr, const double *deg, int u, double inv_k) {
+    const double x = (double)(rowptr[u + 1] - rowptr[u]) * deg[u] * inv_k;
+    int ex = 0;
+    frexp(isfinite(x) ? x : 1e300, &ex);  // x < 2^ex, so sqrt(x) < 2^ceil(ex / 2)
+    const int half = ex >= 0 ? (ex + 1) / 2 : -((-ex) / 2);
+    return 61 - half;
+}
+__device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
+
+// a * 2^e2 rounded to the nearest FP64 (ties to even) with integer
+// instructions only; the result must be a normal number
+__device__ __forceinline__ double i64_scaled_to_double(long long a, int e2) {
+    if (a == 0) return 0.0;
+    const unsigned long long sign = a < 0 ? (1ull << 63) : 0ull;
+    unsigned long long m = a < 0 ? 0ull - (unsigned long long)a : (unsigned long long)a;
+    const int lz = __clzll((long long)m);
+    int ex = 63 - lz + e2;  // exponent of the leading bit
+    m <<= lz;               // leading bit at position 63
+    unsigned long long mant = m >> 11;  // 53 bits
+    const unsigned long long rem = m & 0x7FFull;
+    if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) {
+        mant += 1ull;
+        if (mant >> 53) {
+            mant >>= 1;
+            ex += 1;
+        }
+    }
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(ex + 1023) << 52) |
+                                            (mant & ((1ull << 52) - 1))));
+}
+
+// per CSR entry: sgn * round(sqrt(w_e) * 2^S_u); one thread per entry, its
+// row found by binary search in rowptr
+__global__ void k_jl_terms(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                           const double *__restrict__ w, const double *__restrict__ deg, int32_t n, int64_t nnz,
+                           double inv_k, double inv_sqrt_k, long long *__restrict__ a) {
+    GRID_LOOP(e, nnz) {
+        int lo = 0, hi = n - 1;  // last row with rowptr[row] <= e
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(rowptr + mid) <= (int32_t)e) lo = mid;
+            else hi = mid - 1;
+        }
+        const double sc = pow2(jl_row_shift(rowptr, deg, lo, inv_k)) * inv_sqrt_k;
+        const long long t = llrint(sqrt(w[e]) * sc);
+        a[e] = (lo < col[e]) ? t : -t;
     }
 }
 
-__global__ void k_jl_short(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                           const int32_t *__restrict__ eid, const double *__restrict__ w, int32_t n, int k, int ld,
-                           uint64_t seed, double scale, double *__restrict__ Y) {
+// sum over entries [e0, e1) of a_e * q_{i,e} for the 32 rows i = cb*32 ..
+__device__ __forceinline__ void jl_accum(const int32_t *eid, const long long *a, int e0, int e1, int cb,
+                                         uint64_t seed, long long (&acc)[32]) {
+    for (int e = e0; e < e1; ++e) {
+        const long long t = a[e];
+        const uint32_t bits = jl_bits32((uint64_t)eid[e], cb, seed);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) acc[q] += ((bits >> q) & 1u) ? -t : t;
+    }
+}
+
+__global__ void k_jl_short(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ eid,
+                           const long long *__restrict__ a, const double *__restrict__ deg, int32_t n, int k, int ld,
+                           uint64_t seed, double inv_k, double *__restrict__ Y) {
     const int ncb = (ld + 31) / 32;
     GRID_LOOP(t, (int64_t)n * ncb) {
         const int u = (int)(t / ncb), cb = (int)(t - (int64_t)u * ncb);
         const int e0 = rowptr[u], e1 = rowptr[u + 1];
         if (e1 - e0 > kLongRow) continue;
-        double acc[32];
+        long long acc[32];
 #pragma unroll
-        for (int q = 0; q < 32; ++q) acc[q] = 0.0;
-        jl_accum(col, eid, w, u, e0, e1, cb, seed, scale, acc);
+        for (int q = 0; q < 32; ++q) acc[q] = 0;
+        jl_accum(eid, a, e0, e1, cb, seed, acc);
+        const int sh = -jl_row_shift(rowptr, deg, u, inv_k);
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
             const int c = cb * 32 + q;
-            if (c < ld) Y[(size_t)u * ld + c] = c < k ? acc[q] : 0.0;
+            if (c < ld) Y[(size_t)u * ld + c] = c < k ? i64_scaled_to_double(acc[q], sh) : 0.0;
         }
     }
 }
 
-__global__ void k_jl_chunks(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                            const int32_t *__restrict__ eid, const double *__restrict__ w,
-                            const int32_t *__restrict__ chunk_row, const int32_t *__restrict__ chunk_begin,
-                            int32_t n_chunks, int ld, uint64_t seed, double scale, double *__restrict__ part) {
+__global__ void k_jl_chunks(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ eid,
+                            const long long *__restrict__ a, const int32_t *__restrict__ chunk_row,
+                            const int32_t *__restrict__ chunk_begin, int32_t n_chunks, int ld, uint64_t seed,
+                            long long *__restrict__ part) {
     const int ncb = (ld + 31) / 32;
     GRID_LOOP(t, (int64_t)n_chunks * ncb) {
         const int ch = (int)(t / ncb), cb = (int)(t - (int64_t)ch * ncb);
         const int u = chunk_row[ch];
         const int e0 = chunk_begin[ch], e1 = min(e0 + kChunk, rowptr[u + 1]);
-        double acc[32];
+        long long acc[32];
 #pragma unroll
-        for (int q = 0; q < 32; ++q) acc[q] = 0.0;
-        jl_accum(col, eid, w, u, e0, e1, cb, seed, scale, acc);
+        for (int q = 0; q < 32; ++q) acc[q] = 0;
+        jl_accum(eid, a, e0, e1, cb, seed, acc);
 #pragma unroll
         for (int q = 0; q < 32; ++q) part[((size_t)ch * ncb + cb) * 32 + q] = acc[q];
     }
 }
 
-__global__ void k_jl_long(const int32_t *__restrict__ chunk_row, const int32_t *__restrict__ long_first,
-                          int32_t n_long, int k, int ld, const double *__restrict__ part, double *__restrict__ Y) {
+// one thread per (long row, column): exact sum of the row's chunk partials
+__global__ void k_jl_long(const int32_t *__restrict__ rowptr, const double *__restrict__ deg,
+                          const int32_t *__restrict__ chunk_row, const int32_t *__restrict__ long_first,
+                          int32_t n_long, int k, int ld, double inv_k, const long long *__restrict__ part,
+                          double *__restrict__ Y) {
     const int ncb = (ld + 31) / 32;
-    GRID_LOOP(t, (int64_t)n_long * ncb) {
-        const int li = (int)(t / ncb), cb = (int)(t - (int64_t)li * ncb);
+    GRID_LOOP(t, (int64_t)n_long * ld) {
+        const int li = (int)(t / ld), c = (int)(t - (int64_t)li * ld);
         const int f0 = long_first[li], f1 = long_first[li + 1];
         const int u = chunk_row[f0];
-        for (int q = 0; q < 32; ++q) {
-            const int c = cb * 32 + q;
-            if (c >= ld) break;
-            double s = 0.0;
-            for (int f = f0; f < f1; ++f) s += part[((size_t)f * ncb + cb) * 32 + q];
-            Y[(size_t)u * ld + c] = c < k ? s : 0.0;
-        }
+        long long acc = 0;
+        for (int f = f0; f < f1; ++f) acc += part[((size_t)f * ncb + c / 32) * 32 + (c & 31)];
+        Y[(size_t)u * ld + c] = c < k ? i64_scaled_to_double(acc, -jl_row_shift(rowptr, deg, u, inv_k)) : 0.0;
     }
 }
 
@@ -317,17 +373,20 @@ void jl_rhs(lap_hierarchy *h, int k, int ld, uint64_t seed, double *Y, cudaStrea
     const Level &L = h->lv[0];
     const int n = L.n;
     const int ncb = (ld + 31) / 32;
-    const double scale = 1.0 / std::sqrt((double)k);
-    const double bytes = (double)L.nnz * (4 + 4 + 8) + (double)n * 4 + (double)n * ld * 8;
+    const double inv_sqrt_k = 1.0 / std::sqrt((double)k), inv_k = 1.0 / k;
+    DBuf<long long> a(std::max<int64_t>(L.nnz, 1), s);
+    CFC_LAUNCH(LAP_KF_CFC, s, (double)L.nnz * 20, k_jl_terms, grid_for(L.nnz), kBlock, 0, L.rowptr.get(),
+               L.col.get(), L.w64.get(), L.deg64.get(), n, L.nnz, inv_k, inv_sqrt_k, a.get());
+    const double bytes = (double)L.nnz * (4 + 8) + (double)n * 12 + (double)n * ld * 8;
     CFC_LAUNCH(LAP_KF_CFC, s, bytes, k_jl_short, grid_for((int64_t)n * ncb, 128), 128, 0, L.rowptr.get(),
-               L.col.get(), h->eid.get(), L.w64.get(), n, k, ld, seed, scale, Y);
+               h->eid.get(), a.get(), L.deg64.get(), n, k, ld, seed, inv_k, Y);
     if (L.n_chunks > 0) {
-        DBuf<double> part((size_t)L.n_chunks * ncb * 32, s);
+        DBuf<long long> part((size_t)L.n_chunks * ncb * 32, s);
         CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_jl_chunks, grid_for((int64_t)L.n_chunks * ncb, 128), 128, 0,
-                   L.rowptr.get(), L.col.get(), h->eid.get(), L.w64.get(), L.chunk_row.get(), L.chunk_begin.get(),
-                   L.n_chunks, ld, seed, scale, part.get());
-        CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_jl_long, grid_for((int64_t)L.n_long * ncb, 128), 128, 0,
-                   L.chunk_row.get(), L.long_first.get(), L.n_long, k, ld, part.get(), Y);
+                   L.rowptr.get(), h->eid.get(), a.get(), L.chunk_row.get(), L.chunk_begin.get(), L.n_chunks, ld,
+                   seed, part.get());
+        CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_jl_long, grid_for((int64_t)L.n_long * ld, 128), 128, 0, L.rowptr.get(),
+                   L.deg64.get(), L.chunk_row.get(), L.long_first.get(), L.n_long, k, ld, inv_k, part.get(), Y);
     }
 }
 

@@ -122,9 +122,15 @@ __device__ __forceinline__ int32_t uf_find(int32_t *par, int32_t x) {
     }
 }
 
-__global__ void k_uf_init(int32_t *par, int32_t n) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        par[i] = (int32_t)i;
+// start from a forest: every node points to its smallest neighbour when
+// that is smaller than itself (rows are sorted, so it is the first entry)
+__global__ void k_uf_init(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, int32_t *par,
+                          int32_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e0 = rowptr[i];
+        const int32_t j = (e0 < rowptr[i + 1]) ? col[e0] : (int32_t)i;
+        par[i] = j < (int32_t)i ? j : (int32_t)i;
+    }
 }
 
 __global__ void k_uf_hook(const int32_t *__restrict__ row_of, const int32_t *__restrict__ col, int64_t nnz,
@@ -247,7 +253,8 @@ void ingest(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const 
     // connectivity
     DBuf<int32_t> par(n, s), roots(1, s);
     roots.zero(s);
-    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_uf_init, grid_for(n), kBlock, 0, par.get(), (int32_t)n);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_uf_init, grid_for(n), kBlock, 0, out.rowptr.get(), out.col.get(), par.get(),
+               (int32_t)n);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_uf_hook, grid_for(nnz), kBlock, 0, row_of.get(), out.col.get(), nnz,
                par.get());
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_uf_count_roots, grid_for(n), kBlock, 0, par.get(), (int32_t)n,

@@ -303,7 +303,8 @@ __device__ __forceinline__ typename Vec<T>::V row_sum(const LevelView &A, const 
 // ------------------------------------------------------------------ SpMM-like row operator
 // Op provides:
 //   V gather(int j, int c0) const              operand of node j, this lane's columns
-//   void epi(int i, int c0, V s, RAcc &acc)    row i given s = sum_j w_ij x_j
+//   Pre pre(int i, int c0) const               row i's own operands (loaded before the gathers)
+//   void epi(int i, int c0, V s, Pre, RAcc &acc)  row i given s = sum_j w_ij x_j
 //   void fin(int c, const double *sums)        per-column finalisation (NR > 0)
 // With NR > 0 the per-column sums must not depend on which block finishes a
 // long row, so long rows take their chunk sums from k_chunk_sums (launched
@@ -326,7 +327,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_chunk_sums(LevelView A, Op op, T 
 }
 
 template <typename T, int KT, int NR, class Op, bool PRE = false>
-__global__ void __launch_bounds__(kBlock, 4) k_rowop(LevelView A, Op op, int nvb_short, int nvb_total,
+__global__ void __launch_bounds__(kBlock, (NR >= 3 ? 3 : 4)) k_rowop(LevelView A, Op op, int nvb_short, int nvb_total,
                                                   T *chunk_part, int ld_part, RedBuf rb) {
     using V = typename Vec<T>::V;
     constexpr int VW = Vec<T>::W;
@@ -351,14 +352,16 @@ __global__ void __launch_bounds__(kBlock, 4) k_rowop(LevelView A, Op op, int nvb
             if (i < A.n) {
                 const int e0 = __ldg(A.rowptr + i), e1 = __ldg(A.rowptr + i + 1);
                 if (e1 - e0 <= kLongRow) {
+                    const auto pr = op.pre(i, c0);  // own-row operands, in flight with the gathers
                     const V s = row_sum<T>(A, op, e0, e1, c0);
-                    op.epi(i, c0, s, acc);
+                    op.epi(i, c0, s, pr, acc);
                 } else if (PRE) {
+                    const auto pr = op.pre(i, c0);
                     const int li = __ldg(A.long_of_row + i);
                     const int f0 = __ldg(A.long_first + li), f1 = __ldg(A.long_first + li + 1);
                     V s = vzero<V>();
                     for (int f = f0; f < f1; ++f) s = vadd(s, vld<T>(chunk_part + (size_t)f * ld_part + c0));
-                    op.epi(i, c0, s, acc);
+                    op.epi(i, c0, s, pr, acc);
                 }
             }
         } else {
@@ -387,7 +390,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_rowop(LevelView A, Op op, int nvb
                 const int f0 = __ldg(A.long_first + li), f1 = __ldg(A.long_first + li + 1);
                 V s = vzero<V>();
                 for (int f = f0; f < f1; ++f) s = vadd(s, vldcg<T>(chunk_part + (size_t)f * ld_part + c0));
-                op.epi(i, c0, s, acc);
+                op.epi(i, c0, s, op.pre(i, c0), acc);
                 if (lane == 0) A.long_count[(size_t)li * kMaxTiles + tile] = 0;
             }
             __syncwarp();

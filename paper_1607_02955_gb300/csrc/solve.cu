@@ -46,10 +46,14 @@ struct OpSpmvDot {
     T *alpha_t;
     const int32_t *active;
     __device__ V gather(int j, int c0) const { return vldg<T>(p + (size_t)j * ld + c0); }
+    struct Pre {
+        T d;
+    };
+    __device__ Pre pre(int i, int) const { return Pre{ldeg<T>(A, i)}; }
     template <class Acc>
-    __device__ void epi(int i, int c0, V s, Acc &acc) const {
+    __device__ void epi(int i, int c0, V s, const Pre &pr, Acc &acc) const {
         const V x = gather(i, c0);
-        const T d = ldeg<T>(A, i);
+        const T d = pr.d;
         V y;
 #pragma unroll
         for (int v = 0; v < VW; ++v) {
@@ -81,14 +85,17 @@ struct OpResid64 {
     int32_t *active;
     double tol;
     __device__ V gather(int j, int c0) const { return vldg<double>(x + (size_t)j * ld + c0); }
+    struct Pre {
+        double d;
+    };
+    __device__ Pre pre(int i, int) const { return Pre{ldeg<double>(A, i)}; }
     template <class Acc>
-    __device__ void epi(int i, int c0, V s, Acc &acc) const {
+    __device__ void epi(int i, int c0, V s, const Pre &pr, Acc &acc) const {
         const V xi = gather(i, c0);
         const V bi = vldg<double>(b + (size_t)i * ld + c0);
-        const double d = ldeg<double>(A, i);
 #pragma unroll
         for (int v = 0; v < VW; ++v) {
-            const double rv = vel(bi, v) - (d * vel(xi, v) - vel(s, v));
+            const double rv = (vel(bi, v) + vel(s, v)) - pr.d * vel(xi, v);
             acc.add(0, v, rv * rv);
             r[(size_t)i * ld + c0 + v] = (Tin)rv;
         }
@@ -145,11 +152,15 @@ struct OpSmooth {
     bool xp_zero;  // the previous iterate is the zero initial guess
     DotState<T> ds;
     __device__ V gather(int j, int c0) const { return vldg<T>(x + (size_t)j * ld + c0); }
+    struct Pre {
+        T d, di;
+    };
+    __device__ Pre pre(int i, int) const { return Pre{ldeg<T>(A, i), ldinv<T>(A, i)}; }
     template <class Acc>
-    __device__ void epi(int i, int c0, V s, Acc &acc) const {
+    __device__ void epi(int i, int c0, V s, const Pre &pr, Acc &acc) const {
         const V xi = gather(i, c0);
         const V bi = vld<T>(b + (size_t)i * ld + c0);
-        const T d = ldeg<T>(A, i), di = ldinv<T>(A, i);
+        const T d = pr.d, di = pr.di;
         V out;
         if (c != T(0)) {
             const V pi = xp_zero ? vzero<V>() : vld<T>(xp + (size_t)i * ld + c0);
@@ -189,14 +200,17 @@ struct OpResid {
     T *r;
     int ld;
     __device__ V gather(int j, int c0) const { return vldg<T>(x + (size_t)j * ld + c0); }
+    struct Pre {
+        T d;
+    };
+    __device__ Pre pre(int i, int) const { return Pre{ldeg<T>(A, i)}; }
     template <class Acc>
-    __device__ void epi(int i, int c0, V s, Acc &) const {
+    __device__ void epi(int i, int c0, V s, const Pre &pr, Acc &) const {
         const V xi = gather(i, c0);
         const V bi = vld<T>(b + (size_t)i * ld + c0);
-        const T d = ldeg<T>(A, i);
         V out;
 #pragma unroll
-        for (int v = 0; v < VW; ++v) vel(out, v) = vel(bi, v) - (d * vel(xi, v) - vel(s, v));
+        for (int v = 0; v < VW; ++v) vel(out, v) = vel(bi, v) - (pr.d * vel(xi, v) - vel(s, v));
         vst<T>(r + (size_t)i * ld + c0, out);
     }
     __device__ void fin(int, const double *) const {}
@@ -520,7 +534,7 @@ struct Solver {
     int32_t *h_active;  // pinned
     std::vector<double> cheb_c, cheb_e;
     double gamma = 1.0;
-    int nu_pre, nu_post;
+    int nu_pre, nu_post, nu_coarse;
 
     Solver(lap_hierarchy *h_, cudaStream_t s_, int k_, int ld_, const lap_solve_opts_t &o_)
         : h(h_), s(s_), ld(ld_), ntiles(ld_ / KT), ntiles64(ld_ / K64), k(k_), o(o_) {
@@ -528,12 +542,13 @@ struct Solver {
         if (o.levels_used > 0) nlev = std::min(nlev, o.levels_used);
         nu_pre = std::max(1, o.nu_pre);
         nu_post = std::max(1, o.nu_post);
+        nu_coarse = o.nu_coarse > 0 ? o.nu_coarse : std::max(nu_pre, 4);
         setup_smoother();
     }
 
     void setup_smoother() {
         // D^{-1} L of a Laplacian has its spectrum in [0, 2] (Gershgorin).
-        const int nu = std::max(nu_pre, nu_post);
+        const int nu = std::max(std::max(nu_pre, nu_post), nu_coarse);
         cheb_c.assign(nu, 0.0);
         cheb_e.assign(nu, 0.0);
         if (o.smoother == LAP_SMOOTH_JACOBI) {
@@ -648,7 +663,7 @@ struct Solver {
             rows<Tin, 0>(fam_level(l, LAP_KF_SMOOTH_FINE), L.n,
                          OpJacobiZero<Tin>{view(L), lb[l], cur, ld, (Tin)cheb_e[0]},
                          vec_bytes(L.n, ld, 2, et) + L.n * (double)wb);
-        const int npre = coarsest ? std::max(nu_pre, 4) : nu_pre;
+        const int npre = coarsest ? nu_coarse : nu_pre;
         bool dotted = false;
         for (int t = 1; t < npre; ++t) {
             const int d = (coarsest && t == npre - 1) ? dot : 0;
@@ -967,8 +982,11 @@ struct TuneKey {
                std::tie(o.n, o.nnz, o.precision, o.kt, o.smoother, o.nu_pre, o.nu_post);
     }
 };
+struct TuneChoice {
+    int levels, nu_coarse;
+};
 std::mutex g_tune_mu;
-std::map<TuneKey, int> g_tune;
+std::map<TuneKey, TuneChoice> g_tune;
 
 }  // namespace
 
@@ -1001,16 +1019,26 @@ lap_status_t solve_multi(lap_hierarchy *h, int32_t k, const double *B, double *X
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune.find(key);
         if (it != g_tune.end()) {
-            o.levels_used = it->second;
+            o.levels_used = it->second.levels;
+            if (o.nu_coarse <= 0) o.nu_coarse = it->second.nu_coarse;
             grow_levels(*h, o.levels_used, s);
             return dispatch(h, k, B, X, o, s, info, kt);
         }
     }
     grow_levels(*h, 0, s);
     const int L = (int)h->lv.size();
-    std::vector<int> cand;
-    for (int l = 1; l <= L && l <= 4; ++l) cand.push_back(l);
-    if (L > 4) cand.push_back(L);
+    // candidates: a smoother-only preconditioner (one level, polynomial
+    // degree 1 .. 8; degree 1 is Jacobi-PCG), then V-cycles over 2, 3, 4 and
+    // all levels with the configured smoothing
+    std::vector<TuneChoice> cand;
+    const int nc_default = o.nu_coarse > 0 ? o.nu_coarse : std::max(std::max(1, o.nu_pre), 4);
+    if (o.nu_coarse > 0) {
+        cand.push_back({1, o.nu_coarse});
+    } else {
+        for (int d : {1, 2, 3, 4, 6, 8}) cand.push_back({1, d});
+    }
+    for (int l = 2; l <= L && l <= 4; ++l) cand.push_back({l, nc_default});
+    if (L > 4) cand.push_back({L, nc_default});
     cudaEvent_t e0, e1;
     CFC_CUDA(cudaEventCreate(&e0));
     CFC_CUDA(cudaEventCreate(&e1));
@@ -1021,10 +1049,12 @@ lap_status_t solve_multi(lap_hierarchy *h, int32_t k, const double *B, double *X
     lap_status_t last = LAP_OK;
     const bool verbose = std::getenv("LAP_TUNE_VERBOSE") != nullptr;
     // untimed warm-up: first launches load kernels and size the workspace
-    o.levels_used = cand[0];
+    o.levels_used = cand[0].levels;
+    o.nu_coarse = cand[0].nu_coarse;
     dispatch(h, k, B, X, o, s, info, kt);
     for (size_t t = 0; t < cand.size(); ++t) {
-        o.levels_used = cand[t];
+        o.levels_used = cand[t].levels;
+        o.nu_coarse = cand[t].nu_coarse;
         CFC_CUDA(cudaEventRecord(e0, s));
         last = dispatch(h, k, B, X, o, s, info, kt);
         CFC_CUDA(cudaEventRecord(e1, s));
@@ -1032,14 +1062,15 @@ lap_status_t solve_multi(lap_hierarchy *h, int32_t k, const double *B, double *X
         float ms = 0.f;
         CFC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
         double build = 0.0;
-        for (int l = 1; l < cand[t] && l < (int)h->level_ms.size(); ++l) build += h->level_ms[l];
+        for (int l = 1; l < cand[t].levels && l < (int)h->level_ms.size(); ++l) build += h->level_ms[l];
         const float cost = ms + (float)build;
         if (verbose)
-            std::fprintf(stderr, "lap autotune n=%lld kt=%d levels=%d solve=%.3f ms build=%.3f ms status=%d\n",
-                         (long long)h->lv[0].n, kt, cand[t], ms, build, (int)last);
+            std::fprintf(stderr,
+                         "lap autotune n=%lld kt=%d levels=%d nu_coarse=%d solve=%.3f ms build=%.3f ms status=%d\n",
+                         (long long)h->lv[0].n, kt, cand[t].levels, cand[t].nu_coarse, ms, build, (int)last);
         if (last == LAP_OK && (best < 0 || cost < best_ms)) {
             best_ms = cost;
-            best = cand[t];
+            best = (int)t;
         }
     }
     cudaEventDestroy(e0);
@@ -1047,10 +1078,11 @@ lap_status_t solve_multi(lap_hierarchy *h, int32_t k, const double *B, double *X
     if (best < 0) return last;  // nothing converged: report the last attempt
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune[key] = best;
+        g_tune[key] = cand[best];
     }
-    if (best != cand.back() || last != LAP_OK) {
-        o.levels_used = best;
+    if (best != (int)cand.size() - 1 || last != LAP_OK) {
+        o.levels_used = cand[best].levels;
+        o.nu_coarse = cand[best].nu_coarse;
         return dispatch(h, k, B, X, o, s, info, kt);
     }
     return last;
