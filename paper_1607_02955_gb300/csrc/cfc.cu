@@ -402,16 +402,20 @@ lap_status_t farness_jl(lap_hierarchy *h, int32_t k, double eps, uint64_t seed, 
     CFC_REQUIRE(farness, LAP_EINVAL, "farness must not be NULL");
     DBuf<int32_t> ntmp;
     const int32_t *dn = nodes_to_device(nodes, q, (int32_t)n, ntmp, s);
-    DBuf<double> Y((size_t)n * k, s), Z((size_t)n * k, s);
-    jl_rhs(h, k, k, seed, Y.get(), s);
-    lap_status_t st = solve_multi(h, k, Y.get(), Z.get(), o, s, nullptr);
+    // Y is generated straight into the solver's padded layout; its columns sum
+    // to zero (B 1 = 0), and the farness sums are unchanged by a constant
+    // added to a column of Z, so the solve skips both mean projections
+    const int ld = solve_ld(k, o);
+    DBuf<double> Y((size_t)n * ld, s), Z((size_t)n * ld, s);
+    jl_rhs(h, k, ld, seed, Y.get(), s);
+    lap_status_t st = solve_multi_direct(h, k, Y.get(), Z.get(), o, s, nullptr);
     if (st != LAP_OK && st != LAP_ENOCONV) return st;
     const int P = std::min<int64_t>(2 * num_sms_public(), (n + kRedRows - 1) / kRedRows);
     DBuf<double> part((size_t)k * P * 2, s), S(k, s), T(k, s), f(q, s);
     dim3 g1(P, (k + 31) / 32), b1(32, kRedRows);
-    CFC_LAUNCH(LAP_KF_CFC, s, (double)n * k * 8, k_colsum2_part, g1, b1, 0, Z.get(), n, k, k, part.get());
+    CFC_LAUNCH(LAP_KF_CFC, s, (double)n * k * 8, k_colsum2_part, g1, b1, 0, Z.get(), n, k, ld, part.get());
     CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_colsum2_final, (k + 7) / 8, 256, 0, part.get(), P, k, S.get(), T.get());
-    CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_jl_farness, (q + 7) / 8, 256, 0, Z.get(), n, k, k, S.get(), T.get(), dn, q,
+    CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_jl_farness, (q + 7) / 8, 256, 0, Z.get(), n, k, ld, S.get(), T.get(), dn, q,
                f.get());
     copy_out(farness, f.get(), q, s);
     CFC_CUDA(cudaStreamSynchronize(s));

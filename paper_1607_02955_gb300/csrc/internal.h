@@ -213,6 +213,9 @@ namespace cfc {
 // solve.cu
 lap_status_t solve_multi(lap_hierarchy *h, int32_t k, const double *B, double *X,
                          const lap_solve_opts_t &o, cudaStream_t s, lap_solve_info_t *info);
+lap_status_t solve_multi_direct(lap_hierarchy *h, int32_t k, const double *B, double *X, const lap_solve_opts_t &o,
+                                cudaStream_t s, lap_solve_info_t *info);
+int solve_ld(int32_t k, const lap_solve_opts_t &o);  // padded column count of the solver's blocks
 int num_sms_public();
 int32_t *pinned_scratch();  // per-thread pinned host buffer of 8192 int32
 // amg.cu

@@ -136,6 +136,45 @@ __device__ __forceinline__ d4 vadd(const d4 &x, const d4 &y) {
     return d4{make_double2(x.a.x + y.a.x, x.a.y + y.a.y), make_double2(x.b.x + y.b.x, x.b.y + y.b.y)};
 }
 
+// FP32 <-> FP64 conversions with integer instructions (GB300 runs the
+// hardware conversions on its narrow FP64 pipe).  Widening is exact; narrowing
+// rounds to nearest, ties to even; zeros, subnormals, infinities, NaNs and
+// out-of-range values take the hardware conversion.
+__device__ __forceinline__ double f2d(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;
+    return __longlong_as_double((long long)(((uint64_t)(u >> 31) << 63) | ((uint64_t)(e + 896u) << 52) |
+                                            ((uint64_t)(u & 0x7fffffu) << 29)));
+}
+__device__ __forceinline__ float d2f(double d) {
+    const uint64_t b = (uint64_t)__double_as_longlong(d);
+    const int E = (int)((b >> 52) & 0x7ffu) - 1023;
+    if (E < -126 || E > 127) return (float)d;
+    uint32_t m = (uint32_t)((b >> 29) & 0x7fffffu);
+    const uint32_t rem = (uint32_t)(b & 0x1fffffffu);
+    uint32_t ex = (uint32_t)(E + 127);
+    if (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) {
+        if (++m == 0x800000u) {
+            m = 0u;
+            if (++ex == 255u) return (float)d;
+        }
+    }
+    return __uint_as_float(((uint32_t)(b >> 63) << 31) | (ex << 23) | m);
+}
+template <typename T>
+__device__ __forceinline__ T from_double(double d);
+template <>
+__device__ __forceinline__ float from_double<float>(double d) { return d2f(d); }
+template <>
+__device__ __forceinline__ double from_double<double>(double d) { return d; }
+template <typename T>
+__device__ __forceinline__ double to_double(T x);
+template <>
+__device__ __forceinline__ double to_double<float>(float x) { return f2d(x); }
+template <>
+__device__ __forceinline__ double to_double<double>(double x) { return x; }
+
 template <typename T>
 __device__ __forceinline__ T lw(const LevelView &A, int e);
 template <>
@@ -326,9 +365,18 @@ __global__ void __launch_bounds__(kBlock, 4) k_chunk_sums(LevelView A, Op op, T 
     vst<T>(chunk_part + (size_t)ch * ld_part + c0, row_sum<T>(A, op, e0, e1, c0));
 }
 
-template <typename T, int KT, int NR, class Op, bool PRE = false>
+// How rows longer than kLongRow are handled:
+//   kLongLast  chunks are spread over groups; the group finishing a row's last
+//              chunk (arrival counter) adds the chunk sums and finishes the row
+//   kLongPre   chunk sums come from k_chunk_sums, launched just before, and the
+//              row's own group finishes it, so per-column reductions do not
+//              depend on scheduling
+constexpr int kLongLast = 0, kLongPre = 1;
+
+template <typename T, int KT, int NR, class Op, int MODE = kLongLast>
 __global__ void __launch_bounds__(kBlock, (NR >= 3 ? 3 : 4)) k_rowop(LevelView A, Op op, int nvb_short, int nvb_total,
                                                   T *chunk_part, int ld_part, RedBuf rb) {
+    constexpr bool PRE = (MODE == kLongPre);
     using V = typename Vec<T>::V;
     constexpr int VW = Vec<T>::W;
     constexpr int G = KT / VW;

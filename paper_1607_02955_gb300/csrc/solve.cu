@@ -97,7 +97,7 @@ struct OpResid64 {
         for (int v = 0; v < VW; ++v) {
             const double rv = (vel(bi, v) + vel(s, v)) - pr.d * vel(xi, v);
             acc.add(0, v, rv * rv);
-            r[(size_t)i * ld + c0 + v] = (Tin)rv;
+            r[(size_t)i * ld + c0 + v] = from_double<Tin>(rv);
         }
     }
     __device__ void fin(int c, const double *sums) const {
@@ -387,9 +387,41 @@ struct OpCastB {
         const size_t o = (size_t)i * ld + c0;
         const V bi = vld<double>(b + o);
 #pragma unroll
-        for (int v = 0; v < VW; ++v) r[o + v] = (Tin)vel(bi, v);
+        for (int v = 0; v < VW; ++v) r[o + v] = from_double<Tin>(vel(bi, v));
     }
     __device__ void fin(int, const double *) const {}
+};
+
+// first outer step of a direct solve: r = b in the inner type, ||b|| from
+// the same pass (in the inner type: the norm only scales the stopping test)
+template <typename Tin>
+struct OpCastBNorm {  // runs as a k_rows<Tin> kernel: lanes of Vec<Tin>::W columns
+    static constexpr int VW = Vec<Tin>::W;
+    const double *b;
+    Tin *r;
+    int ld;
+    double *bnorm, *relres;
+    int32_t *active;
+    template <class Acc>
+    __device__ void row(int i, int c0, Acc &acc) const {
+        const size_t o = (size_t)i * ld + c0;
+        constexpr int DW = Vec<double>::W;
+        static_assert(VW == DW || VW == 2 * DW, "lane width");
+        const typename Vec<double>::V b0 = vld<double>(b + o);
+        typename Vec<double>::V b1 = vzero<typename Vec<double>::V>();
+        if constexpr (VW > DW) b1 = vld<double>(b + o + DW);
+#pragma unroll
+        for (int v = 0; v < VW; ++v) {
+            const Tin x = from_double<Tin>(v < DW ? vel(b0, v) : vel(b1, v - DW));
+            r[o + v] = x;
+            acc.add(0, v, x * x);
+        }
+    }
+    __device__ void fin(int c, const double *s) const {
+        bnorm[c] = sqrt(s[0]);
+        relres[c] = s[0] > 0.0 ? 1.0 : 0.0;
+        active[c] = s[0] > 0.0 ? 1 : 0;
+    }
 };
 
 __global__ void k_init_cols(const double *__restrict__ bnorm, double *__restrict__ relres,
@@ -415,7 +447,7 @@ struct OpAddCorr {
         V xi = vld<double>(x + o);
 #pragma unroll
         for (int v = 0; v < VW; ++v)
-            if (active[c0 + v]) vel(xi, v) += (double)d[o + v];
+            if (active[c0 + v]) vel(xi, v) += to_double<Tin>(d[o + v]);
         vst<double>(x + o, xi);
     }
     __device__ void fin(int, const double *) const {}
@@ -590,7 +622,7 @@ struct Solver {
             CFC_LAUNCH(fam, s, 0.0, (k_chunk_sums<T, KT, Op>), dim3(nvb_long, ntiles), kBlock, 0, view(L), op, cpart,
                        ld);
             dim3 grid(red_grid(nvb_short), ntiles);
-            CFC_LAUNCH(fam, s, bytes, (k_rowop<T, KT, NR, Op, true>), grid, kBlock, 0, view(L), op, nvb_short,
+            CFC_LAUNCH(fam, s, bytes, (k_rowop<T, KT, NR, Op, kLongPre>), grid, kBlock, 0, view(L), op, nvb_short,
                        nvb_short, cpart, ld, rb);
             return;
         }
@@ -750,14 +782,15 @@ struct Solver {
         const Level &L0 = h->lv[0];
         const int64_t n = L0.n;
         const double v64 = vec_bytes(n, ld, 1, 8);
-        // b64 = B (padded), projected to zero mean; bnorm
-        {
+        // b64 = B (padded), projected to zero mean; bnorm (direct: B is used in
+        // place and its norm comes with the first cast below)
+        if (!direct) {
             const int64_t tot = n * ld;
             const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 8 * num_sms());
             CFC_LAUNCH(LAP_KF_BLAS1, s, v64 * 2, k_copy_pad, blocks, 256, 0, B, k, b64, ld, n);
+            rowsd<1>(n, OpColMean64{b64, ld, 1.0 / n, cs.mu}, v64);
+            rowsd<1>(n, OpSubMean64{b64, b64, ld, cs.mu, cs.bnorm}, 2 * v64);
         }
-        rowsd<1>(n, OpColMean64{b64, ld, 1.0 / n, cs.mu}, v64);
-        rowsd<1>(n, OpSubMean64{b64, b64, ld, cs.mu, cs.bnorm}, 2 * v64);
         CFC_CUDA(cudaMemsetAsync(x64, 0, (size_t)n * ld * 8, s));
 
         int outer = 0, inner_total = 0;
@@ -766,7 +799,10 @@ struct Solver {
         std::vector<double> hrel(ld);
         for (outer = 0;; ++outer) {
             // FP64 residual, written to r in the inner type (x = 0 at the first step: r = b)
-            if (outer == 0) {
+            if (outer == 0 && direct) {
+                rows<Tin, 1>(LAP_KF_BLAS1, n, OpCastBNorm<Tin>{b64, r, ld, cs.bnorm, cs.relres, cs.active_out},
+                             v64 + vec_bytes(n, ld, 1, sizeof(Tin)));
+            } else if (outer == 0) {
                 rowsd<0>(n, OpCastB<Tin>{b64, r, ld}, v64 + vec_bytes(n, ld, 1, sizeof(Tin)));
                 CFC_LAUNCH(LAP_KF_BLAS1, s, 0.0, k_init_cols, (ld + 255) / 256, 256, 0, cs.bnorm, cs.relres,
                            cs.active_out, ld);
@@ -782,7 +818,7 @@ struct Solver {
                 if (L0.n_chunks > 0) {
                     CFC_LAUNCH(LAP_KF_RESID64, s, 0.0, (k_chunk_sums<double, K64, Op>), dim3(nvb_long, ntiles64),
                                kBlock, 0, view(L0), op, chunk_part64, ld);
-                    CFC_LAUNCH(LAP_KF_RESID64, s, bytes, (k_rowop<double, K64, 1, Op, true>),
+                    CFC_LAUNCH(LAP_KF_RESID64, s, bytes, (k_rowop<double, K64, 1, Op, kLongPre>),
                                dim3(red_grid(nvb_short), ntiles64), kBlock, 0, view(L0), op, nvb_short, nvb_short,
                                chunk_part64, ld, rb);
                 } else {
@@ -809,10 +845,10 @@ struct Solver {
             inner_total += inner_pcg(dbuf, o.max_inner, itol);
             rowsd<0>(n, OpAddCorr<Tin>{x64, dbuf, ld, cs.active_out}, 2 * v64 + vec_bytes(n, ld, 1, sizeof(Tin)));
         }
-        // zero-mean result, copied out unpadded
-        rowsd<1>(n, OpColMean64{x64, ld, 1.0 / n, cs.mu}, v64);
-        rowsd<1>(n, OpSubMean64{x64, x64, ld, cs.mu, nullptr}, 2 * v64);
-        {
+        // zero-mean result, copied out unpadded (direct: left as is)
+        if (!direct) {
+            rowsd<1>(n, OpColMean64{x64, ld, 1.0 / n, cs.mu}, v64);
+            rowsd<1>(n, OpSubMean64{x64, x64, ld, cs.mu, nullptr}, 2 * v64);
             const int64_t tot = n * k;
             const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 8 * num_sms());
             CFC_LAUNCH(LAP_KF_BLAS1, s, v64 * 2, k_copy_unpad, blocks, 256, 0, x64, ld, X, k, n);
@@ -835,13 +871,14 @@ struct Solver {
     }
 
     Tin *dbuf = nullptr;
+    bool direct = false;
 };
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 template <typename Tin, int KT>
 lap_status_t run_solver(lap_hierarchy *h, int32_t k, const double *B, double *X, const lap_solve_opts_t &o,
-                        cudaStream_t s, lap_solve_info_t *info) {
+                        cudaStream_t s, lap_solve_info_t *info, bool direct) {
     const int ld = ((k + KT - 1) / KT) * KT;
     const int ntiles = ld / KT;
     CFC_REQUIRE(ntiles <= kMaxTiles, LAP_EBUDGET, "too many column tiles");
@@ -864,9 +901,15 @@ lap_status_t run_solver(lap_hierarchy *h, int32_t k, const double *B, double *X,
     for (int l = 1; l < nlev; ++l)
         for (int v = 0; v < 3; ++v) sizes.push_back(align_up((size_t)h->lv[l].n * ld * sizeof(Tin)));
     sizes.push_back(align_up(std::max<int64_t>(max_chunks, 1) * ld * 8));  // chunk partials (FP64 size)
-    int64_t max_rows = 0;
-    for (int l = 0; l < nlev; ++l) max_rows = std::max<int64_t>(max_rows, h->lv[l].n + h->lv[l].n_chunks);
-    const int P = (int)std::min<int64_t>(kRedMaxBlocks, (max_rows + 3) / 4 + 1);  // >= blocks of any launch
+    // blocks of any launch: at most ceil(n/8) row blocks (8 = fewest rows per
+    // block) plus one block per long row or one per 8 chunks
+    int64_t max_blocks = 1;
+    for (int l = 0; l < nlev; ++l) {
+        const Level &Ll = h->lv[l];
+        max_blocks = std::max<int64_t>(
+            max_blocks, (Ll.n + 7) / 8 + std::max<int64_t>(Ll.n_long, (Ll.n_chunks + 7) / 8) + 1);
+    }
+    const int P = (int)std::min<int64_t>(kRedMaxBlocks, max_blocks);
     sizes.push_back(align_up((size_t)ntiles * 4 * KT * P * 8));          // reduction partials
     sizes.push_back(align_up((size_t)ntiles * 4 * KT * kMaxTeams * 8));  // team partials
     sizes.push_back(align_up(ld * 8) * 10);                       // column scalars
@@ -891,6 +934,11 @@ lap_status_t run_solver(lap_hierarchy *h, int32_t k, const double *B, double *X,
     S.rb.team_counter = S.rb.counter + kMaxTiles;
     S.b64 = (double *)take(idx++);
     S.x64 = (double *)take(idx++);
+    S.direct = direct;
+    if (direct) {  // caller's padded blocks are used in place
+        S.b64 = const_cast<double *>(B);
+        S.x64 = X;
+    }
     S.r = (Tin *)take(idx++);
     S.z = (Tin *)take(idx++);
     S.p = (Tin *)take(idx++);
@@ -953,20 +1001,20 @@ int32_t *pinned_scratch() {
 namespace {
 
 lap_status_t dispatch(lap_hierarchy *h, int32_t k, const double *B, double *X, const lap_solve_opts_t &o,
-                      cudaStream_t s, lap_solve_info_t *info, int kt) {
+                      cudaStream_t s, lap_solve_info_t *info, int kt, bool direct) {
     const bool fp64 = (o.precision == LAP_FP64);
     if (fp64) {
         switch (kt) {
-            case 16: return run_solver<double, 16>(h, k, B, X, o, s, info);
-            case 32: return run_solver<double, 32>(h, k, B, X, o, s, info);
-            default: return run_solver<double, 64>(h, k, B, X, o, s, info);
+            case 16: return run_solver<double, 16>(h, k, B, X, o, s, info, direct);
+            case 32: return run_solver<double, 32>(h, k, B, X, o, s, info, direct);
+            default: return run_solver<double, 64>(h, k, B, X, o, s, info, direct);
         }
     }
     switch (kt) {
-        case 16: return run_solver<float, 16>(h, k, B, X, o, s, info);
-        case 32: return run_solver<float, 32>(h, k, B, X, o, s, info);
-        case 64: return run_solver<float, 64>(h, k, B, X, o, s, info);
-        default: return run_solver<float, 128>(h, k, B, X, o, s, info);
+        case 16: return run_solver<float, 16>(h, k, B, X, o, s, info, direct);
+        case 32: return run_solver<float, 32>(h, k, B, X, o, s, info, direct);
+        case 64: return run_solver<float, 64>(h, k, B, X, o, s, info, direct);
+        default: return run_solver<float, 128>(h, k, B, X, o, s, info, direct);
     }
 }
 
@@ -990,8 +1038,23 @@ std::map<TuneKey, TuneChoice> g_tune;
 
 }  // namespace
 
-lap_status_t solve_multi(lap_hierarchy *h, int32_t k, const double *B, double *X, const lap_solve_opts_t &o_in,
-                         cudaStream_t s, lap_solve_info_t *info) {
+int solve_tile(int32_t k, const lap_solve_opts_t &o) {
+    int kt = o.k_tile;
+    const bool fp64 = (o.precision == LAP_FP64);
+    if (kt == 0) kt = (k >= 64) ? 64 : (k > 16 ? 32 : 16);
+    if (fp64 && kt > 64) kt = 64;
+    while ((k + kt - 1) / kt > kMaxTiles) kt *= 2;
+    return kt;
+}
+
+int solve_ld(int32_t k, const lap_solve_opts_t &o) {
+    const int kt = solve_tile(k, o);
+    return ((k + kt - 1) / kt) * kt;
+}
+
+namespace {
+lap_status_t solve_impl(lap_hierarchy *h, int32_t k, const double *B, double *X, const lap_solve_opts_t &o_in,
+                        cudaStream_t s, lap_solve_info_t *info, bool direct) {
     CFC_REQUIRE(k >= 1 && k <= 4096, LAP_EINVAL, "need 1 <= k <= 4096");
     CFC_REQUIRE(B && X && B != X, LAP_EINVAL, "B and X must be distinct device buffers");
     CFC_REQUIRE(is_device_pointer(B) && is_device_pointer(X), LAP_EINVAL, "B and X must be device pointers");
@@ -999,20 +1062,17 @@ lap_status_t solve_multi(lap_hierarchy *h, int32_t k, const double *B, double *X
     CFC_REQUIRE(o_in.precision == LAP_FP64 || o_in.precision == LAP_FP32_REFINED, LAP_ENOTIMPL,
                 "precision mode not implemented (LAP_FP64 and LAP_FP32_REFINED are)");
     lap_solve_opts_t o = o_in;
-    int kt = o.k_tile;
     const bool fp64 = (o.precision == LAP_FP64);
-    if (kt == 0) kt = (k >= 64) ? 64 : (k > 16 ? 32 : 16);
-    if (fp64 && kt > 64) kt = 64;
-    while ((k + kt - 1) / kt > kMaxTiles) kt *= 2;
+    const int kt = solve_tile(k, o);
     CFC_REQUIRE(kt == 16 || kt == 32 || kt == 64 || (kt == 128 && !fp64), LAP_EINVAL, "k_tile must be 16/32/64/128");
     if (o.levels_used > 0) {
         grow_levels(*h, o.levels_used, s);
-        return dispatch(h, k, B, X, o, s, info, kt);
+        return dispatch(h, k, B, X, o, s, info, kt, direct);
     }
     if (o.levels_used < 0) {  // every level
         grow_levels(*h, 0, s);
         o.levels_used = 0;
-        return dispatch(h, k, B, X, o, s, info, kt);
+        return dispatch(h, k, B, X, o, s, info, kt, direct);
     }
     const TuneKey key{h->lv[0].n, h->lv[0].nnz, o.precision, kt, o.smoother, o.nu_pre, o.nu_post};
     {
@@ -1022,7 +1082,7 @@ lap_status_t solve_multi(lap_hierarchy *h, int32_t k, const double *B, double *X
             o.levels_used = it->second.levels;
             if (o.nu_coarse <= 0) o.nu_coarse = it->second.nu_coarse;
             grow_levels(*h, o.levels_used, s);
-            return dispatch(h, k, B, X, o, s, info, kt);
+            return dispatch(h, k, B, X, o, s, info, kt, direct);
         }
     }
     grow_levels(*h, 0, s);
@@ -1051,12 +1111,12 @@ lap_status_t solve_multi(lap_hierarchy *h, int32_t k, const double *B, double *X
     // untimed warm-up: first launches load kernels and size the workspace
     o.levels_used = cand[0].levels;
     o.nu_coarse = cand[0].nu_coarse;
-    dispatch(h, k, B, X, o, s, info, kt);
+    dispatch(h, k, B, X, o, s, info, kt, direct);
     for (size_t t = 0; t < cand.size(); ++t) {
         o.levels_used = cand[t].levels;
         o.nu_coarse = cand[t].nu_coarse;
         CFC_CUDA(cudaEventRecord(e0, s));
-        last = dispatch(h, k, B, X, o, s, info, kt);
+        last = dispatch(h, k, B, X, o, s, info, kt, direct);
         CFC_CUDA(cudaEventRecord(e1, s));
         CFC_CUDA(cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -1083,9 +1143,23 @@ lap_status_t solve_multi(lap_hierarchy *h, int32_t k, const double *B, double *X
     if (best != (int)cand.size() - 1 || last != LAP_OK) {
         o.levels_used = cand[best].levels;
         o.nu_coarse = cand[best].nu_coarse;
-        return dispatch(h, k, B, X, o, s, info, kt);
+        return dispatch(h, k, B, X, o, s, info, kt, direct);
     }
     return last;
+}
+
+}  // namespace
+
+lap_status_t solve_multi(lap_hierarchy *h, int32_t k, const double *B, double *X, const lap_solve_opts_t &o,
+                         cudaStream_t s, lap_solve_info_t *info) {
+    return solve_impl(h, k, B, X, o, s, info, false);
+}
+
+// B and X already n x solve_ld(k) with zero padding columns, B's columns
+// summing to zero up to rounding; X is returned without the mean removal
+lap_status_t solve_multi_direct(lap_hierarchy *h, int32_t k, const double *B, double *X, const lap_solve_opts_t &o,
+                                cudaStream_t s, lap_solve_info_t *info) {
+    return solve_impl(h, k, B, X, o, s, info, true);
 }
 
 }  // namespace cfc
