@@ -35,7 +35,12 @@ METRIC = "RHS solved/s to rel. residual 1e-8"
 WORKLOADS = {
     "ba100k_jl64": dict(kind="ba", n=100000, m_per=5, seed=2, k=64, jl_seed=1, nodes=[0]),
     "grid48_jl32": dict(kind="grid", a=48, k=32, jl_seed=1, nodes=[0]),
+    "rmat20_jl16": dict(kind="rmat", scale=20, seed=3, k=16, jl_seed=1, nodes=[0]),
     "rmat20_jl64": dict(kind="rmat", scale=20, seed=3, k=64, jl_seed=1, nodes=[0]),
+    "rmat20_jl128": dict(kind="rmat", scale=20, seed=3, k=128, jl_seed=1, nodes=[0]),
+    "grid1024_jl64": dict(kind="grid", a=1024, k=64, jl_seed=1, nodes=[0]),
+    "grid4096_jl64": dict(kind="grid", a=4096, k=64, jl_seed=1, nodes=[0]),
+    "rmat24_jl64": dict(kind="rmat", scale=24, seed=5, k=64, jl_seed=1, nodes=[0]),
 }
 
 

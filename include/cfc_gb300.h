@@ -91,6 +91,9 @@ typedef struct {
                              no dense solve, e.g. the one-level smoother-only
                              preconditioner; 0 (default): max(nu_pre, 4), or autotuned
                              together with levels_used */
+    int32_t cycle;        /* 1: V-cycle, 2: W-cycle (two coarse corrections per level);
+                             0 (default): V, or autotuned together with levels_used */
+    double coarse_scale;  /* factor on each coarse correction (> 0; 0 = 1.0, or autotuned) */
 } lap_solve_opts_t;
 
 typedef struct {

@@ -197,6 +197,8 @@ void lap_default_solve_opts(lap_solve_opts_t *o) {
     o->check_every = 4;
     o->levels_used = 0;
     o->nu_coarse = 0;
+    o->cycle = 0;
+    o->coarse_scale = 0.0;
 }
 
 const char *lap_status_string(lap_status_t s) {

@@ -565,7 +565,8 @@ struct Solver {
     ColState cs;
     int32_t *h_active;  // pinned
     std::vector<double> cheb_c, cheb_e;
-    double gamma = 1.0;
+    double gamma = 1.0;  // coarse-correction scale
+    int cycle = 1;       // 1: V-cycle, 2: W-cycle
     int nu_pre, nu_post, nu_coarse;
 
     Solver(lap_hierarchy *h_, cudaStream_t s_, int k_, int ld_, const lap_solve_opts_t &o_)
@@ -575,6 +576,8 @@ struct Solver {
         nu_pre = std::max(1, o.nu_pre);
         nu_post = std::max(1, o.nu_post);
         nu_coarse = o.nu_coarse > 0 ? o.nu_coarse : std::max(nu_pre, 4);
+        cycle = o.cycle == 2 ? 2 : 1;
+        gamma = o.coarse_scale > 0.0 ? o.coarse_scale : 1.0;
         setup_smoother();
     }
 
@@ -707,16 +710,23 @@ struct Solver {
             lt[l] = oth;
             return dotted;
         }
-        // residual into oth, restrict to level l+1
-        rowop<Tin, 0>(fam_level(l, LAP_KF_RESTRICT_FINE), L, OpResid<Tin>{view(L), cur, lb[l], oth, ld}, chunk_part,
-                      mat_bytes(L, wb) + vec_bytes(L.n, ld, 3, et));
+        // coarse corrections: residual into oth, restrict to level l+1, recurse,
+        // prolong; a W-cycle does this twice (the same operator twice keeps
+        // the preconditioner symmetric); the coarse level's dense solve is
+        // exact, so one correction suffices just above it
         const Level &C = h->lv[l + 1];
-        rows<Tin, 0>(fam_level(l, LAP_KF_RESTRICT_FINE), C.n,
-                     OpRestrict<Tin>{L.mem_ptr.get(), L.mem.get(), oth, lb[l + 1], ld},
-                     vec_bytes(L.n, ld, 1, et) + vec_bytes(C.n, ld, 1, et) + 4.0 * (L.n + C.n));
-        vcycle(l + 1);
-        rows<Tin, 0>(LAP_KF_COARSE_LEVELS, L.n, OpProlong<Tin>{L.agg.get(), lx[l + 1], cur, ld, (Tin)gamma},
-                     vec_bytes(L.n, ld, 2, et) + vec_bytes(C.n, ld, 1, et) + 4.0 * L.n);
+        const bool next_dense = (l + 1 == nlev - 1) && h->coarse_n == C.n && l + 1 == (int)h->lv.size() - 1;
+        const int ncorr = (cycle == 2 && !next_dense) ? 2 : 1;
+        for (int cc = 0; cc < ncorr; ++cc) {
+            rowop<Tin, 0>(fam_level(l, LAP_KF_RESTRICT_FINE), L, OpResid<Tin>{view(L), cur, lb[l], oth, ld},
+                          chunk_part, mat_bytes(L, wb) + vec_bytes(L.n, ld, 3, et));
+            rows<Tin, 0>(fam_level(l, LAP_KF_RESTRICT_FINE), C.n,
+                         OpRestrict<Tin>{L.mem_ptr.get(), L.mem.get(), oth, lb[l + 1], ld},
+                         vec_bytes(L.n, ld, 1, et) + vec_bytes(C.n, ld, 1, et) + 4.0 * (L.n + C.n));
+            vcycle(l + 1);
+            rows<Tin, 0>(LAP_KF_COARSE_LEVELS, L.n, OpProlong<Tin>{L.agg.get(), lx[l + 1], cur, ld, (Tin)gamma},
+                         vec_bytes(L.n, ld, 2, et) + vec_bytes(C.n, ld, 1, et) + 4.0 * L.n);
+        }
         // post-smoothing (the same polynomial: symmetric V-cycle)
         for (int t = 0; t < nu_post; ++t) {
             const int d = (t == nu_post - 1) ? dot : 0;
@@ -1024,14 +1034,17 @@ lap_status_t dispatch(lap_hierarchy *h, int32_t k, const double *B, double *X, c
 // kernels by timing them).
 struct TuneKey {
     int64_t n, nnz;
-    int precision, kt, smoother, nu_pre, nu_post;
+    int k, precision, kt, smoother, nu_pre, nu_post, nu_coarse, cycle;
+    double scale;
     bool operator<(const TuneKey &o) const {
-        return std::tie(n, nnz, precision, kt, smoother, nu_pre, nu_post) <
-               std::tie(o.n, o.nnz, o.precision, o.kt, o.smoother, o.nu_pre, o.nu_post);
+        return std::tie(n, nnz, k, precision, kt, smoother, nu_pre, nu_post, nu_coarse, cycle, scale) <
+               std::tie(o.n, o.nnz, o.k, o.precision, o.kt, o.smoother, o.nu_pre, o.nu_post, o.nu_coarse, o.cycle,
+                        o.scale);
     }
 };
 struct TuneChoice {
-    int levels, nu_coarse;
+    int kt, levels, nu_coarse, cycle;
+    double scale;
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneChoice> g_tune;
@@ -1074,78 +1087,121 @@ lap_status_t solve_impl(lap_hierarchy *h, int32_t k, const double *B, double *X,
         o.levels_used = 0;
         return dispatch(h, k, B, X, o, s, info, kt, direct);
     }
-    const TuneKey key{h->lv[0].n, h->lv[0].nnz, o.precision, kt, o.smoother, o.nu_pre, o.nu_post};
+    // autotuned: tile width (when not given), depth, smoother degree, cycle
+    // shape and coarse scale (those not given), chosen by timing complete
+    // solves the first time a graph size and configuration is seen
+    const TuneKey key{h->lv[0].n, h->lv[0].nnz,  k,         o.precision, o.k_tile,
+                      o.smoother, o.nu_pre,      o.nu_post, o.nu_coarse, o.cycle, o.coarse_scale};
+    auto apply = [&](const TuneChoice &c, lap_solve_opts_t &oo) {
+        oo.levels_used = c.levels;
+        oo.nu_coarse = c.nu_coarse;
+        oo.cycle = c.cycle;
+        oo.coarse_scale = c.scale;
+    };
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune.find(key);
         if (it != g_tune.end()) {
-            o.levels_used = it->second.levels;
-            if (o.nu_coarse <= 0) o.nu_coarse = it->second.nu_coarse;
+            apply(it->second, o);
             grow_levels(*h, o.levels_used, s);
-            return dispatch(h, k, B, X, o, s, info, kt, direct);
+            return dispatch(h, k, B, X, o, s, info, it->second.kt, direct);
         }
     }
     grow_levels(*h, 0, s);
     const int L = (int)h->lv.size();
-    // candidates: a smoother-only preconditioner (one level, polynomial
-    // degree 1 .. 8; degree 1 is Jacobi-PCG), then V-cycles over 2, 3, 4 and
-    // all levels with the configured smoothing
-    std::vector<TuneChoice> cand;
     const int nc_default = o.nu_coarse > 0 ? o.nu_coarse : std::max(std::max(1, o.nu_pre), 4);
-    if (o.nu_coarse > 0) {
-        cand.push_back({1, o.nu_coarse});
-    } else {
-        for (int d : {1, 2, 3, 4, 6, 8}) cand.push_back({1, d});
-    }
-    for (int l = 2; l <= L && l <= 4; ++l) cand.push_back({l, nc_default});
-    if (L > 4) cand.push_back({L, nc_default});
+    const int cyc_default = o.cycle > 0 ? o.cycle : 1;
+    const double sc_default = o.coarse_scale > 0.0 ? o.coarse_scale : 1.0;
     cudaEvent_t e0, e1;
     CFC_CUDA(cudaEventCreate(&e0));
     CFC_CUDA(cudaEventCreate(&e1));
+    const bool verbose = std::getenv("LAP_TUNE_VERBOSE") != nullptr;
+    lap_solve_opts_t trial_o = o;
+    trial_o.max_outer = std::min(o.max_outer, 4);  // a failing candidate should not run long
+    float best_cost = 0.f;
+    int best = -1;
+    std::vector<TuneChoice> tried;
     // a candidate's cost: its solve plus building its coarse levels (every new
     // hierarchy of this graph pays that again)
-    float best_ms = 0.f;
-    int best = -1;
-    lap_status_t last = LAP_OK;
-    const bool verbose = std::getenv("LAP_TUNE_VERBOSE") != nullptr;
-    // untimed warm-up: first launches load kernels and size the workspace
-    o.levels_used = cand[0].levels;
-    o.nu_coarse = cand[0].nu_coarse;
-    dispatch(h, k, B, X, o, s, info, kt, direct);
-    for (size_t t = 0; t < cand.size(); ++t) {
-        o.levels_used = cand[t].levels;
-        o.nu_coarse = cand[t].nu_coarse;
+    auto trial = [&](const TuneChoice &c) -> lap_status_t {
+        lap_solve_opts_t oo = trial_o;
+        apply(c, oo);
         CFC_CUDA(cudaEventRecord(e0, s));
-        last = dispatch(h, k, B, X, o, s, info, kt, direct);
+        const lap_status_t st = dispatch(h, k, B, X, oo, s, info, c.kt, direct);
         CFC_CUDA(cudaEventRecord(e1, s));
         CFC_CUDA(cudaEventSynchronize(e1));
         float ms = 0.f;
         CFC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
         double build = 0.0;
-        for (int l = 1; l < cand[t].levels && l < (int)h->level_ms.size(); ++l) build += h->level_ms[l];
+        for (int l = 1; l < c.levels && l < (int)h->level_ms.size(); ++l) build += h->level_ms[l];
         const float cost = ms + (float)build;
         if (verbose)
             std::fprintf(stderr,
-                         "lap autotune n=%lld kt=%d levels=%d nu_coarse=%d solve=%.3f ms build=%.3f ms status=%d\n",
-                         (long long)h->lv[0].n, kt, cand[t].levels, cand[t].nu_coarse, ms, build, (int)last);
-        if (last == LAP_OK && (best < 0 || cost < best_ms)) {
-            best_ms = cost;
-            best = (int)t;
+                         "lap autotune n=%lld k=%d kt=%d levels=%d nu_coarse=%d cycle=%d scale=%.2f solve=%.3f ms "
+                         "build=%.3f ms status=%d\n",
+                         (long long)h->lv[0].n, k, c.kt, c.levels, c.nu_coarse, c.cycle, c.scale, ms, build, (int)st);
+        tried.push_back(c);
+        if (st == LAP_OK && (best < 0 || cost < best_cost)) {
+            best_cost = cost;
+            best = (int)tried.size() - 1;
+        }
+        return st;
+    };
+    // untimed warm-up: first launches load kernels and size the workspace
+    {
+        lap_solve_opts_t oo = trial_o;
+        apply({kt, 1, 1, 1, 1.0}, oo);
+        dispatch(h, k, B, X, oo, s, info, kt, direct);
+    }
+    // stage 1: preconditioner, at the default tile width
+    if (o.nu_coarse > 0) {
+        trial({kt, 1, o.nu_coarse, cyc_default, sc_default});
+    } else {
+        for (int d : {1, 2, 3, 4, 6, 8}) {
+            const lap_status_t st = trial({kt, 1, d, cyc_default, sc_default});
+            if (st != LAP_OK && d >= 2) break;  // smoothing alone does not reach the tolerance
+        }
+    }
+    std::vector<int> depths;
+    for (int l = 2; l <= L && l <= 4; ++l) depths.push_back(l);
+    if (L > 4) depths.push_back(L);
+    for (int l : depths) trial({kt, l, nc_default, cyc_default, sc_default});
+    if (L >= 3) {
+        if (o.cycle == 0)
+            for (int l : {3, L})
+                if (l <= L) trial({kt, l, nc_default, 2, sc_default});
+        if (o.coarse_scale <= 0.0) {
+            // unsmoothed aggregation under-corrects; scaling the coarse correction helps
+            for (double sc : {1.5, 1.8, 2.0}) trial({kt, L, nc_default, cyc_default, sc});
+            if (o.cycle == 0) trial({kt, L, nc_default, 2, 1.5});
+        }
+    }
+    // stage 2: the tile width, with the best preconditioner
+    if (best >= 0 && o.k_tile == 0) {
+        const TuneChoice b0 = tried[best];
+        const bool fp64 = (o.precision == LAP_FP64);
+        const int ld0 = ((k + kt - 1) / kt) * kt;
+        for (int t : {16, 32, 64, 128}) {
+            if (t == kt || (fp64 && t > 64) || (k + t - 1) / t > kMaxTiles) continue;
+            if (((k + t - 1) / t) * t > ld0) continue;  // no more padding than the default
+            TuneChoice c = b0;
+            c.kt = t;
+            trial(c);
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (best < 0) return last;  // nothing converged: report the last attempt
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune[key] = cand[best];
-    }
-    if (best != (int)cand.size() - 1 || last != LAP_OK) {
-        o.levels_used = cand[best].levels;
-        o.nu_coarse = cand[best].nu_coarse;
+    if (best < 0) {  // nothing converged within the trial cap: one full-length attempt
+        apply({kt, L, nc_default, cyc_default, sc_default}, o);
         return dispatch(h, k, B, X, o, s, info, kt, direct);
     }
-    return last;
+    const TuneChoice choice = tried[best];
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = choice;
+    }
+    apply(choice, o);
+    return dispatch(h, k, B, X, o, s, info, choice.kt, direct);
 }
 
 }  // namespace
