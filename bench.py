@@ -44,6 +44,14 @@ WORKLOADS = {
 }
 
 
+# precision mode of lap_solve_opts_t, dtype of the JSON line, description
+PRECISIONS = {
+    "fp32": (1, "f32+f64", "fp32 V-cycle/PCG in fp64 refinement"),
+    "bf16coarse": (2, "f32+bf16+f64", "fp32 V-cycle/PCG with bf16 weights below the finest level, fp64 refinement"),
+    "fp64": (0, "f64", "fp64 PCG + V-cycle"),
+}
+
+
 def make_graph(wl):
     if wl["kind"] == "ba":
         n, s, d, _ = synth.barabasi_albert(wl["n"], wl["m_per"], seed=wl["seed"])
@@ -78,6 +86,73 @@ def read_traffic(workload, family):
     return e["dram_bytes_per_launch"], e["kernel"]
 
 
+def write_traffic(csv_path, log_path):
+    """Pairs the library's launches in an ncu per-launch CSV (metrics
+    dram__bytes_read.sum, dram__bytes_write.sum, gpu__time_duration.sum) of
+    the timed steps with the launch log of the same command, then stores the
+    DRAM bytes per launch of every kernel family in profiles/traffic.json and
+    prints a per-family and per-kernel summary."""
+    import csv
+    import collections
+    with open(log_path) as fh:
+        log = json.load(fh)
+    launches = collections.OrderedDict()
+    hdr = None
+    with open(csv_path) as fh:
+        for r in csv.reader(fh):
+            if r and r[0] == "ID":
+                hdr = r
+                continue
+            if not hdr or len(r) != len(hdr):
+                continue
+            d = dict(zip(hdr, r))
+            if "cfc::" not in d["Kernel Name"]:
+                continue  # the L2 flush between steps is torch's
+            e = launches.setdefault(d["ID"], {"kernel": d["Kernel Name"]})
+            e[d["Metric Name"]] = float(d["Metric Value"].replace(",", ""))
+    L = list(launches.values())
+    fams = log["families"]
+    if len(L) != len(fams):
+        raise SystemExit(f"ncu lists {len(L)} library launches, the log {len(fams)}")
+    if log["source_digest"] != kernel_source_digest():
+        raise SystemExit("the launch log was taken on other kernel sources")
+    per_fam = collections.OrderedDict()
+    per_kernel = collections.OrderedDict()
+    for f, e in zip(fams, L):
+        b = e.get("dram__bytes_read.sum", 0.0) + e.get("dram__bytes_write.sum", 0.0)
+        t = e.get("gpu__time_duration.sum", 0.0)
+        a = per_fam.setdefault(f, {"launches": 0, "dram_bytes": 0.0, "ns": 0.0, "kernels": collections.Counter()})
+        a["launches"] += 1
+        a["dram_bytes"] += b
+        a["ns"] += t
+        name = e["kernel"].replace("cfc::", "").replace("<unnamed>::", "").replace("void ", "")
+        name = name[:name.index(">(") + 1] if ">(" in name else name.split("(")[0]
+        a["kernels"][name] += t  # device time per kernel within the family
+        k = per_kernel.setdefault((f, name), [0, 0.0, 0.0])
+        k[0] += 1
+        k[1] += b
+        k[2] += t
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    j = json.load(open(path)) if os.path.exists(path) else {}
+    wl = j.setdefault(log["workload"], {})
+    tot_ns = sum(a["ns"] for a in per_fam.values())
+    print(f"workload {log['workload']}, {log['steps']} timed step(s), {len(L)} library launches, "
+          f"source digest {log['source_digest']}")
+    print(f"{'family':14s} {'launches':>8s} {'MB/launch':>10s} {'us/launch':>10s} {'share':>7s}  kernel with most time")
+    for f, a in sorted(per_fam.items(), key=lambda x: -x[1]["ns"]):
+        top = a["kernels"].most_common(1)[0][0]
+        wl[f] = {"source_digest": log["source_digest"], "launches": a["launches"],
+                 "dram_bytes_per_launch": a["dram_bytes"] / a["launches"], "kernel": top}
+        print(f"{f:14s} {a['launches']:8d} {a['dram_bytes'] / a['launches'] / 1e6:10.3f} "
+              f"{a['ns'] / a['launches'] / 1e3:10.2f} {100 * a['ns'] / tot_ns:6.2f}%  {top}")
+    print()
+    print(f"{'kernel':72s} {'launches':>8s} {'MB/launch':>10s} {'us/launch':>10s} {'share':>7s}")
+    for (f, name), (c, b, t) in sorted(per_kernel.items(), key=lambda x: -x[1][2]):
+        print(f"{name[:72]:72s} {c:8d} {b / c / 1e6:10.3f} {t / c / 1e3:10.2f} {100 * t / tot_ns:6.2f}%")
+    with open(path, "w") as fh:
+        json.dump(j, fh, indent=1, sort_keys=True)
+
+
 def read_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -88,11 +163,14 @@ def read_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle samples during the timed region."""
+    """nvidia-smi clock / throttle samples (every 100 ms).  Started before the
+    warm-up so that nvidia-smi's own start-up does not fall in the timed
+    region; mark() / stop() bound the window whose samples are kept."""
 
     def __init__(self, gpu_index=0):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        self.t0 = self.t1 = None
+        q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
@@ -102,9 +180,14 @@ class ClockSampler:
         except Exception:
             self.p = None
 
+    def mark(self):
+        self.t0 = time.time()
+
     def stop(self):
+        self.t1 = time.time()
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)  # let the sample that covers the end of the window arrive
         self.p.terminate()
         try:
             self.p.wait(timeout=5)
@@ -112,22 +195,28 @@ class ClockSampler:
             self.p.kill()
         self.f.flush()
         self.f.seek(0)
-        sm, mx, reasons = [], [], set()
+        import datetime
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.f.read().splitlines():
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[2]), float(parts[3]),
+                             {nm for nm, v in zip(names, parts[6:10]) if v.lower() == "active"}))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
         os.unlink(self.f.name)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+        t0 = self.t0 if self.t0 is not None else -1e30
+        inside = [r for r in rows if t0 - 0.1 <= r[0] <= self.t1 + 0.1]
+        if not inside and rows:  # a window shorter than the sampling period
+            inside = [min(rows, key=lambda r: abs(r[0] - 0.5 * (t0 + self.t1)))]
+        sm = [r[1] for r in inside]
+        reasons = set().union(*[r[3] for r in inside]) if inside else set()
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(r[2] for r in inside) if inside else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
@@ -213,12 +302,24 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ba100k_jl64", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the solve-only FP64 batched / one-RHS comparison")
     ap.add_argument("--print-digest", action="store_true", help="print the kernel source digest and exit")
     ap.add_argument("--levels", type=int, default=None,
                     help="levels_used of the V-cycle (default: autotuned; -1: every level)")
+    ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS),
+                    help="arithmetic of the solve (fp32: FP32 PCG + V-cycle in FP64 refinement)")
+    ap.add_argument("--launch-log", default=None,
+                    help="write the kernel family of every launch in the timed steps to this JSON file")
+    ap.add_argument("--write-traffic", nargs=2, metavar=("NCU_CSV", "LAUNCH_LOG"), default=None,
+                    help="no GPU: attribute the DRAM bytes of an ncu launch list of the timed steps "
+                         "to kernel families and record them in profiles/traffic.json")
     args = ap.parse_args()
     if args.print_digest:
         print(kernel_source_digest())
+        return
+    if args.write_traffic:
+        write_traffic(*args.write_traffic)
         return
     wl = WORKLOADS[args.workload]
     rank, world, local = dist_setup(args.gpus)
@@ -244,7 +345,8 @@ def main():
     far_d = torch.empty(len(nodes), dtype=torch.float64, device=dev)
     stream = torch.cuda.Stream(device=dev)
     sp = stream.cuda_stream
-    sopts = P.lap_default_solve_opts()
+    prec_mode, dtype, prec_text = PRECISIONS[args.precision]
+    sopts = P.lap_default_solve_opts(precision=prec_mode)
     if args.levels is not None:
         sopts.levels_used = args.levels
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
@@ -280,18 +382,25 @@ def main():
                 total += a.elapsed_time(b)
         return total
 
+    clk = ClockSampler(local)
     for _ in range(args.warmup):
         step_device()
         step_host()
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
-    clk = ClockSampler(local)
     P.lap_stats_reset()
+    P.lap_stats_set_log(args.launch_log is not None)
+    clk.mark()
     torch.cuda.profiler.start()  # ncu --profile-from-start off captures exactly the timed steps
     ms_total = timed(step_device, args.steps)
     torch.cuda.profiler.stop()
+    P.lap_stats_set_log(False)
     stats = P.lap_stats_read()
+    if args.launch_log and rank == 0:
+        with open(args.launch_log, "w") as fh:
+            json.dump({"workload": args.workload, "steps": args.steps, "source_digest": kernel_source_digest(),
+                       "families": P.lap_stats_read_log()}, fh)
     clocks = clk.stop()
     torch.cuda.synchronize()
     barrier(world)
@@ -328,15 +437,43 @@ def main():
     P.cfc_jl_rhs(h, k, wl["jl_seed"], Y, stream=sp)
     sinfo = P.lap_solve_multi(h, Y, X, sopts, stream=sp)
     hinfo = P.lap_hierarchy_info(h)
+
+    # solve-only rates on the built hierarchy: the batched mixed-precision form
+    # against FP64 batched and FP64 one right-hand side at a time (same 1e-8
+    # FP64 residual test); hierarchy setup excluded from all three
+    def solve_rate(precision, kk, reps):
+        Yk = torch.empty((n, kk), dtype=torch.float64, device=dev)
+        Xk = torch.empty_like(Yk)
+        P.cfc_jl_rhs(h, kk, wl["jl_seed"], Yk, stream=sp)
+        o = P.lap_default_solve_opts(precision=precision)
+        P.lap_solve_multi(h, Yk, Xk, o, stream=sp)  # autotunes once for this configuration
+        with torch.cuda.stream(stream):
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                inf = P.lap_solve_multi(h, Yk, Xk, o, stream=sp)
+            b.record(stream)
+            b.synchronize()
+        return {"rhs_per_s": kk * reps / (a.elapsed_time(b) / 1e3), "k": kk, "solves": reps,
+                "inner_iters": inf["inner_iters"], "max_rel_residual": inf["max_rel_residual"]}
+
+    compare = None
+    if not args.no_compare:
+        compare = {"solve_only": True,
+                   args.precision + "_batched": solve_rate(prec_mode, k, 3),
+                   "fp64_batched": solve_rate(0, k, 1),
+                   "fp64_one_rhs": solve_rate(0, 1, 4)}
     h.destroy()
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "m": int(s.size), "k": k,
-                       "query_nodes": wl["nodes"], "tol": 1e-8, "precision": "fp32 V-cycle/PCG in fp64 refinement",
+                       "query_nodes": wl["nodes"], "tol": 1e-8, "precision": prec_text,
                        "setup_included": True, "l2": "flushed between steps (256 MiB write, untimed)",
                        "levels_built": hinfo["levels"], "level_n": hinfo["level_n"], "setup_ms": hinfo["setup_ms"],
                        "outer_iters": sinfo["outer_iters"], "inner_iters": sinfo["inner_iters"],
@@ -350,6 +487,7 @@ def main():
                          "algorithmic_bytes_per_launch": dm["bytes"] / max(dm["launches"], 1),
                          "launches": dm["launches"], "ms": dm["ms"]},
             "family_ms_per_step": {kf: v["ms"] / args.steps for kf, v in fam.items()},
+            "precision_comparison": compare,
             "clocks": clocks,
         }
         if world == 1 and not args.no_cpu_baseline:

@@ -56,7 +56,13 @@ typedef enum {
 enum {
     LAP_FP64 = 0,                     /* FP64 PCG + FP64 V-cycle */
     LAP_FP32_REFINED = 1,             /* FP32 PCG + V-cycle inside FP64 iterative refinement */
-    LAP_FP32_BF16COARSE_REFINED = 2   /* as 1, with BF16 edge weights on levels >= 1 */
+    LAP_FP32_BF16COARSE_REFINED = 2   /* as 1, with BF16 edge weights on levels >= 1 (Sec. 3.1
+                                         solver, reduced-precision coarse operators): each
+                                         coarse weight rounded to BF16, the coarse degrees
+                                         recomputed from the rounded weights so every coarse
+                                         operator is still a Laplacian; FP32 accumulation.
+                                         Changes the preconditioner only: the FP64 outer
+                                         residual and stopping test are those of mode 1. */
 };
 
 /* Smoother of the V-cycle. */
@@ -313,6 +319,18 @@ void lap_stats_reset(void);
 void lap_stats_set_timing(int32_t on);
 /* Synchronises the pending timing events, then copies the counters. */
 lap_status_t lap_stats_read(lap_stats_t *out);
+
+/*
+ * Launch log (no counterpart in the paper): while on, the family (LAP_KF_*)
+ * of every kernel launch is appended, in launch order, to a host-side log
+ * that lap_stats_reset clears.  A profiler's per-launch list of the same
+ * region lines up with it one to one, which attributes per-launch hardware
+ * counters to families.  lap_stats_read_log copies min(count, capacity)
+ * entries to the host array `families` and stores the full count in *count;
+ * LAP_EINVAL if `count` is NULL or `families` is NULL with capacity > 0.
+ */
+void lap_stats_set_log(int32_t on);
+lap_status_t lap_stats_read_log(int32_t *families, int64_t capacity, int64_t *count);
 
 #ifdef __cplusplus
 }

@@ -50,4 +50,6 @@ from ._binding import (  # noqa: F401
     lap_stats_reset,
     lap_stats_set_timing,
     lap_stats_read,
+    lap_stats_set_log,
+    lap_stats_read_log,
 )

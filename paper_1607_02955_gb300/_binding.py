@@ -20,7 +20,7 @@ SYMBOLS = [
     "lap_hierarchy_info", "lap_solve_multi", "cfc_jl_rhs", "cfc_farness_jl", "cfc_farness_from_solution",
     "cfc_farness_from_solution_noalloc", "cfc_sample_pivots",
     "cfc_farness_sampled", "cfc_exact_small", "lap_status_string", "lap_last_error", "lap_stats_reset",
-    "lap_stats_set_timing", "lap_stats_read",
+    "lap_stats_set_timing", "lap_stats_read", "lap_stats_set_log", "lap_stats_read_log",
 ]
 
 
@@ -107,6 +107,10 @@ def lib():
     L.lap_stats_set_timing.restype = None
     L.lap_stats_read.argtypes = [C.POINTER(Stats)]
     L.lap_stats_read.restype = C.c_int
+    L.lap_stats_set_log.argtypes = [i32]
+    L.lap_stats_set_log.restype = None
+    L.lap_stats_read_log.argtypes = [vp, i64, C.POINTER(C.c_int64)]
+    L.lap_stats_read_log.restype = C.c_int
     _lib = L
     return L
 
@@ -329,3 +333,16 @@ def lap_stats_read() -> dict:
     return {"launches_total": int(s.launches_total),
             "families": {name: {"launches": int(s.launches[i]), "ms": s.ms[i], "bytes": s.bytes[i]}
                          for i, name in enumerate(KERNEL_FAMILIES)}}
+
+
+def lap_stats_set_log(on: bool):
+    lib().lap_stats_set_log(1 if on else 0)
+
+
+def lap_stats_read_log() -> list:
+    """Families (names of KERNEL_FAMILIES) of the logged launches, in launch order."""
+    cnt = C.c_int64(0)
+    _check(lib().lap_stats_read_log(None, 0, C.byref(cnt)), "lap_stats_read_log")
+    buf = (C.c_int32 * max(cnt.value, 1))()
+    _check(lib().lap_stats_read_log(C.cast(buf, C.c_void_p), cnt.value, C.byref(cnt)), "lap_stats_read_log")
+    return [KERNEL_FAMILIES[buf[i]] for i in range(cnt.value)]

@@ -17,6 +17,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <cuda_bf16.h>
+
 #include "internal.h"
 
 struct lap_hierarchy;
@@ -239,6 +241,23 @@ __global__ void k_finish(const int32_t *__restrict__ rowptr, const double *__res
     }
 }
 
+// thread per row: round the row's weights to BF16 (via FP32) and sum the
+// rounded values in FP64, in CSR order
+__global__ void k_bf16_level(const int32_t *__restrict__ rowptr, const double *__restrict__ w64, int32_t n,
+                             uint16_t *__restrict__ wbf, float *__restrict__ degbf, float *__restrict__ dinvbf) {
+    GRID_LOOP(i, n) {
+        double d = 0.0;
+        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            const uint16_t b = __bfloat16_as_ushort(__float2bfloat16_rn((float)w64[e]));
+            wbf[e] = b;
+            d += (double)__uint_as_float((uint32_t)b << 16);
+        }
+        const float df = (float)d;
+        degbf[i] = df;
+        dinvbf[i] = 1.0f / df;
+    }
+}
+
 __global__ void k_long_index(const int32_t *__restrict__ nchunk, int32_t n, int32_t *__restrict__ is_long) {
     GRID_LOOP(i, n) is_long[i] = nchunk[i] > 0 ? 1 : 0;
 }
@@ -432,6 +451,15 @@ void finish_level(Level &L, cudaStream_t s) {
                cfirst.get(), lidx.get(), n, L.chunk_row.get(), L.chunk_begin.get(), L.chunk_long.get(),
                L.long_first.get(), L.long_of_row.get());
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_set_last, 1, 1, 0, L.long_first.get(), L.n_long, L.n_chunks);
+}
+
+void ensure_bf16(Level &L, cudaStream_t s) {
+    if (L.wbf.get()) return;
+    L.wbf.alloc_persistent(std::max<int64_t>(L.nnz, 1));
+    L.degbf.alloc_persistent(L.n);
+    L.dinvbf.alloc_persistent(L.n);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_bf16_level, grid_for(L.n), kBlock, 0, L.rowptr.get(), L.w64.get(), L.n,
+               L.wbf.get(), L.degbf.get(), L.dinvbf.get());
 }
 
 void dense_spd_inverse_small(double *A, int n, int *d_flag, cudaStream_t s) {

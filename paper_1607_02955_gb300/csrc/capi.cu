@@ -18,6 +18,9 @@ thread_local std::string t_last_error;
 std::atomic<uint64_t> g_launches_total{0};
 std::atomic<uint64_t> g_launches[LAP_KF_COUNT];
 std::atomic<int> g_timing{0};
+std::atomic<int> g_log_on{0};
+std::mutex g_log_mu;
+std::vector<int32_t> g_log;
 
 struct Pending {
     int family;
@@ -64,6 +67,10 @@ LaunchScope::LaunchScope(int fam, cudaStream_t s, double algorithmic_bytes)
     : family(fam), stream(s), bytes(algorithmic_bytes) {
     g_launches_total.fetch_add(1, std::memory_order_relaxed);
     g_launches[fam].fetch_add(1, std::memory_order_relaxed);
+    if (g_log_on.load(std::memory_order_relaxed)) {
+        std::lock_guard<std::mutex> lk(g_log_mu);
+        g_log.push_back(fam);
+    }
     if (g_timing.load(std::memory_order_relaxed)) {
         std::lock_guard<std::mutex> lk(g_mu);
         if (g_pending.size() > 65536) drain_locked();
@@ -137,6 +144,7 @@ LevelView view(const Level &L) {
     v.w32 = L.w32.get();
     v.deg32 = L.deg32.get();
     v.dinv32 = L.dinv32.get();
+    v.wbf = nullptr;
     v.w64 = L.w64.get();
     v.deg64 = L.deg64.get();
     v.dinv64 = L.dinv64.get();
@@ -148,6 +156,14 @@ LevelView view(const Level &L) {
     v.long_first = L.long_first.get();
     v.long_of_row = L.long_of_row.get();
     v.long_count = L.long_count.get();
+    return v;
+}
+
+LevelView view_bf16(const Level &L) {
+    LevelView v = view(L);
+    v.wbf = L.wbf.get();
+    v.deg32 = L.degbf.get();
+    v.dinv32 = L.dinvbf.get();
     return v;
 }
 
@@ -359,6 +375,10 @@ void lap_stats_reset(void) {
     } catch (...) {
     }
     g_launches_total.store(0);
+    {
+        std::lock_guard<std::mutex> lk2(g_log_mu);
+        g_log.clear();
+    }
     for (int f = 0; f < LAP_KF_COUNT; ++f) {
         g_launches[f].store(0);
         g_ms[f] = 0;
@@ -367,6 +387,19 @@ void lap_stats_reset(void) {
 }
 
 void lap_stats_set_timing(int32_t on) { g_timing.store(on ? 1 : 0); }
+
+void lap_stats_set_log(int32_t on) { g_log_on.store(on ? 1 : 0); }
+
+lap_status_t lap_stats_read_log(int32_t *families, int64_t capacity, int64_t *count) {
+    return guard([&]() -> lap_status_t {
+        CFC_REQUIRE(count && (families || capacity <= 0), LAP_EINVAL, "NULL argument");
+        std::lock_guard<std::mutex> lk(g_log_mu);
+        *count = (int64_t)g_log.size();
+        const int64_t c = std::min<int64_t>(capacity, (int64_t)g_log.size());
+        for (int64_t i = 0; i < c; ++i) families[i] = g_log[i];
+        return LAP_OK;
+    });
+}
 
 lap_status_t lap_stats_read(lap_stats_t *out) {
     return guard([&]() -> lap_status_t {

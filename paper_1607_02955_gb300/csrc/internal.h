@@ -128,6 +128,10 @@ struct Level {
     DBuf<int32_t> rowptr, col;
     DBuf<double> w64, deg64, dinv64;
     DBuf<float> w32, deg32, dinv32;
+    // BF16 copy of the weights (bit patterns) and the FP32 degrees of the
+    // rounded weights, made on first use by a solve in the BF16-coarse mode
+    DBuf<uint16_t> wbf;
+    DBuf<float> degbf, dinvbf;
     // rows longer than kLongRow nonzeros are split into chunks of kChunk
     int32_t n_long = 0, n_chunks = 0;
     DBuf<int32_t> chunk_row;     // [n_chunks] row of each chunk
@@ -151,12 +155,16 @@ struct LevelView {
     int32_t n;
     const int32_t *rowptr, *col;
     const float *w32, *deg32, *dinv32;
+    const uint16_t *wbf;  // BF16 weights, read by the kernels instantiated for them
     const double *w64, *deg64, *dinv64;
     int32_t n_chunks, n_long;
     const int32_t *chunk_row, *chunk_begin, *chunk_long, *long_first, *long_of_row;
     uint32_t *long_count;
 };
 LevelView view(const Level &L);
+// The same level with BF16 weights (and the degrees of the rounded weights)
+// in place of the FP32 ones; ensure_bf16 must have run on it.
+LevelView view_bf16(const Level &L);
 
 // ------------------------------------------------------------------ primitives (prims.cu)
 // Exclusive prefix sum of n int32 or int64 values; returns the total.
@@ -182,6 +190,11 @@ void ingest(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const 
 // ------------------------------------------------------------------ hierarchy (amg.cu)
 void init_levels(lap_hierarchy &h, Csr64 &fine, const lap_hier_opts_t &o, cudaStream_t s);
 void grow_levels(lap_hierarchy &h, int target, cudaStream_t s);  // target 0: all
+// Makes L.wbf / degbf / dinvbf (no-op when present): each weight rounded to
+// FP32 and then to BF16 (nearest, ties to even); the degrees are the FP64
+// row sums of the rounded weights, rounded to FP32, so the level stays an
+// exact Laplacian (null space = constants) of the rounded weights.
+void ensure_bf16(Level &L, cudaStream_t s);
 void finish_level(Level &L, cudaStream_t s);  // FP32 copies, inverse degrees, long-row split
 
 // dense SPD inverse (in place, FP64, row-major n x n) -- used for the

@@ -16,6 +16,8 @@
 // every reduction is bitwise reproducible.
 #pragma once
 
+#include <type_traits>
+
 #include "internal.h"
 
 namespace cfc {
@@ -312,30 +314,44 @@ __device__ __forceinline__ void block_reduce_finalize(RAcc<TA, NR, VW> &acc, Red
     if (threadIdx.x == 0) rb.counter[tile] = 0;
 }
 
-// sum_{e in [e0, e1)} w_e x_{col(e)} for this lane's columns; four
-// neighbours (eight 16-byte gathers) in flight per lane
-template <typename T, class Op>
+// edge weight in the kernel's arithmetic type; BF = true reads the BF16 copy
+// (FP32 kernels only), which widens exactly (its 16 bits are the top half of
+// the FP32 pattern)
+template <typename T, bool BF>
+__device__ __forceinline__ T lwk(const LevelView &A, int e) {
+    if constexpr (BF) {
+        static_assert(std::is_same<T, float>::value, "BF16 weights feed FP32 kernels");
+        return __uint_as_float((uint32_t)__ldg(A.wbf + e) << 16);
+    } else {
+        return lw<T>(A, e);
+    }
+}
+
+// sum_{e in [e0, e1)} w_e x_{col(e)} for this lane's columns.  Every round
+// puts four neighbours (eight 16-byte gathers) in flight per lane; the last
+// round of a row is masked rather than finished one neighbour at a time, so
+// a row of length d costs ceil(d / 4) gather latencies.
+template <typename T, bool BF, class Op>
 __device__ __forceinline__ typename Vec<T>::V row_sum(const LevelView &A, const Op &op, int e0, int e1, int c0) {
     using V = typename Vec<T>::V;
     V s0 = vzero<V>(), s1 = vzero<V>();
-    int e = e0;
-    for (; e + 3 < e1; e += 4) {
+    for (int e = e0; e < e1; e += 4) {
         int j[4];
         T w[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            j[u] = __ldg(A.col + e + u);
-            w[u] = lw<T>(A, e + u);
+            const bool ok = e + u < e1;
+            j[u] = ok ? __ldg(A.col + e + u) : -1;
+            w[u] = ok ? lwk<T, BF>(A, e + u) : T(0);
         }
         V x[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) x[u] = op.gather(j[u], c0);
+        for (int u = 0; u < 4; ++u) x[u] = j[u] >= 0 ? op.gather(j[u], c0) : vzero<V>();
         vfma(s0, w[0], x[0]);
         vfma(s1, w[1], x[1]);
         vfma(s0, w[2], x[2]);
         vfma(s1, w[3], x[3]);
     }
-    for (; e < e1; ++e) vfma(s0, lw<T>(A, e), op.gather(__ldg(A.col + e), c0));
     return vadd(s0, s1);
 }
 
@@ -350,7 +366,7 @@ __device__ __forceinline__ typename Vec<T>::V row_sum(const LevelView &A, const 
 // just before) and are finished by the group that owns the row, like short
 // rows (PRE = true).  Without reductions the last chunk to arrive finishes
 // the row in the same launch (PRE = false).
-template <typename T, int KT, class Op>
+template <typename T, int KT, class Op, bool BF = false>
 __global__ void __launch_bounds__(kBlock, 4) k_chunk_sums(LevelView A, Op op, T *chunk_part, int ld_part) {
     constexpr int VW = Vec<T>::W;
     constexpr int G = KT / VW;
@@ -362,7 +378,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_chunk_sums(LevelView A, Op op, T 
     const int i = __ldg(A.chunk_row + ch);
     const int e0 = __ldg(A.chunk_begin + ch);
     const int e1 = min(e0 + kChunk, __ldg(A.rowptr + i + 1));
-    vst<T>(chunk_part + (size_t)ch * ld_part + c0, row_sum<T>(A, op, e0, e1, c0));
+    vst<T>(chunk_part + (size_t)ch * ld_part + c0, row_sum<T, BF>(A, op, e0, e1, c0));
 }
 
 // How rows longer than kLongRow are handled:
@@ -373,7 +389,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_chunk_sums(LevelView A, Op op, T 
 //              depend on scheduling
 constexpr int kLongLast = 0, kLongPre = 1;
 
-template <typename T, int KT, int NR, class Op, int MODE = kLongLast>
+template <typename T, int KT, int NR, class Op, int MODE = kLongLast, bool BF = false>
 __global__ void __launch_bounds__(kBlock, (NR >= 3 ? 3 : 4)) k_rowop(LevelView A, Op op, int nvb_short, int nvb_total,
                                                   T *chunk_part, int ld_part, RedBuf rb) {
     constexpr bool PRE = (MODE == kLongPre);
@@ -401,7 +417,7 @@ __global__ void __launch_bounds__(kBlock, (NR >= 3 ? 3 : 4)) k_rowop(LevelView A
                 const int e0 = __ldg(A.rowptr + i), e1 = __ldg(A.rowptr + i + 1);
                 if (e1 - e0 <= kLongRow) {
                     const auto pr = op.pre(i, c0);  // own-row operands, in flight with the gathers
-                    const V s = row_sum<T>(A, op, e0, e1, c0);
+                    const V s = row_sum<T, BF>(A, op, e0, e1, c0);
                     op.epi(i, c0, s, pr, acc);
                 } else if (PRE) {
                     const auto pr = op.pre(i, c0);
@@ -420,7 +436,7 @@ __global__ void __launch_bounds__(kBlock, (NR >= 3 ? 3 : 4)) k_rowop(LevelView A
                 i = __ldg(A.chunk_row + ch);
                 const int e0 = __ldg(A.chunk_begin + ch);
                 const int e1 = min(e0 + kChunk, __ldg(A.rowptr + i + 1));
-                const V s = row_sum<T>(A, op, e0, e1, c0);
+                const V s = row_sum<T, BF>(A, op, e0, e1, c0);
                 vst<T>(chunk_part + (size_t)ch * ld_part + c0, s);
                 __threadfence();
             }

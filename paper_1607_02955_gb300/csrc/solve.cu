@@ -22,6 +22,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -568,6 +569,10 @@ struct Solver {
     double gamma = 1.0;  // coarse-correction scale
     int cycle = 1;       // 1: V-cycle, 2: W-cycle
     int nu_pre, nu_post, nu_coarse;
+    bool bf16 = false;  // BF16 weights below the finest level
+
+    // the finest level always runs on FP32 weights; coarser ones on BF16 in that mode
+    LevelView lv_view(const Level &L) const { return (bf16 && &L != &h->lv[0]) ? view_bf16(L) : view(L); }
 
     Solver(lap_hierarchy *h_, cudaStream_t s_, int k_, int ld_, const lap_solve_opts_t &o_)
         : h(h_), s(s_), ld(ld_), ntiles(ld_ / KT), ntiles64(ld_ / K64), k(k_), o(o_) {
@@ -578,6 +583,9 @@ struct Solver {
         nu_coarse = o.nu_coarse > 0 ? o.nu_coarse : std::max(nu_pre, 4);
         cycle = o.cycle == 2 ? 2 : 1;
         gamma = o.coarse_scale > 0.0 ? o.coarse_scale : 1.0;
+        bf16 = std::is_same<Tin, float>::value && o.precision == LAP_FP32_BF16COARSE_REFINED;
+        if (bf16)
+            for (int l = 1; l < nlev; ++l) ensure_bf16(h->lv[l], s);
         setup_smoother();
     }
 
@@ -603,11 +611,15 @@ struct Solver {
         }
     }
 
-    // one block per row block (no serial grid-stride chains of gathers), up to
-    // the size the reduction buffers hold
-    int red_grid(int nvb) const { return std::max(1, std::min(nvb, kRedMaxBlocks)); }
-    int plain_grid(int nvb) const { return std::max(1, std::min(nvb, kRedMaxBlocks)); }
+    // about one and a half waves of resident blocks, each walking its row
+    // blocks grid-stride: measured faster than one block per row block (fewer
+    // block launches and block-level reductions), while the half wave of spare
+    // blocks evens out the blocks that drew long rows
+    int red_grid(int nvb) const { return std::max(1, std::min({nvb, 6 * num_sms(), kRedMaxBlocks})); }
+    int plain_grid(int nvb) const { return red_grid(nvb); }
 
+    // bytes of one edge weight as the sweeps of level L read it
+    int wbytes(const Level &L) const { return (bf16 && &L != &h->lv[0]) ? 2 : (int)sizeof(Tin); }
     static double vec_bytes(int64_t n, int ld, int nvec, int elem) { return (double)n * ld * elem * nvec; }
     static double mat_bytes(const Level &L, int wb) {
         return (double)L.nnz * (4.0 + wb) + (double)L.n * (4.0 + 2.0 * wb);
@@ -620,19 +632,30 @@ struct Solver {
         constexpr int RPB = kBlock / G;
         const int nvb_short = (L.n + RPB - 1) / RPB;
         const int nvb_long = (L.n_chunks + RPB - 1) / RPB;
+        if (bf16 && &L != &h->lv[0]) {
+            // below the finest level only reduction-free sweeps run (smoothing, residual)
+            CFC_REQUIRE(NR == 0, LAP_ECUDA, "internal: reduction sweep on a BF16 level");
+            if constexpr (NR == 0 && std::is_same<T, float>::value) {
+                const int nvb = nvb_short + nvb_long;
+                dim3 grid(plain_grid(nvb), ntiles);
+                CFC_LAUNCH(fam, s, bytes, (k_rowop<T, KT, 0, Op, kLongLast, true>), grid, kBlock, 0, lv_view(L), op,
+                           nvb_short, nvb, cpart, ld, rb);
+            }
+            return;
+        }
         if (NR > 0 && L.n_chunks > 0) {
             // deterministic reductions: chunk sums first, rows finished by their own group
-            CFC_LAUNCH(fam, s, 0.0, (k_chunk_sums<T, KT, Op>), dim3(nvb_long, ntiles), kBlock, 0, view(L), op, cpart,
+            CFC_LAUNCH(fam, s, 0.0, (k_chunk_sums<T, KT, Op>), dim3(nvb_long, ntiles), kBlock, 0, lv_view(L), op, cpart,
                        ld);
             dim3 grid(red_grid(nvb_short), ntiles);
-            CFC_LAUNCH(fam, s, bytes, (k_rowop<T, KT, NR, Op, kLongPre>), grid, kBlock, 0, view(L), op, nvb_short,
+            CFC_LAUNCH(fam, s, bytes, (k_rowop<T, KT, NR, Op, kLongPre>), grid, kBlock, 0, lv_view(L), op, nvb_short,
                        nvb_short, cpart, ld, rb);
             return;
         }
         const int nvb = nvb_short + nvb_long;
         const int gx = NR > 0 ? red_grid(nvb) : plain_grid(nvb);
         dim3 grid(gx, ntiles);
-        CFC_LAUNCH(fam, s, bytes, (k_rowop<T, KT, NR, Op>), grid, kBlock, 0, view(L), op, nvb_short, nvb, cpart, ld,
+        CFC_LAUNCH(fam, s, bytes, (k_rowop<T, KT, NR, Op>), grid, kBlock, 0, lv_view(L), op, nvb_short, nvb, cpart, ld,
                    rb);
     }
     template <typename T, int NR, class Op>
@@ -653,16 +676,16 @@ struct Solver {
         const Level &L = h->lv[l];
         const int et = (int)sizeof(Tin);
         const int ti = std::min(t, (int)cheb_c.size() - 1);
-        const double bytes = mat_bytes(L, et) + vec_bytes(L.n, ld, xp_zero || cheb_c[ti] == 0.0 ? 3 : 4, et);
+        const double bytes = mat_bytes(L, wbytes(L)) + vec_bytes(L.n, ld, xp_zero || cheb_c[ti] == 0.0 ? 3 : 4, et);
         const Tin c = (Tin)cheb_c[ti], e = (Tin)cheb_e[ti];
         const int fam = fam_level(l, LAP_KF_SMOOTH_FINE);
         if (dot == 0) {
-            rowop<Tin, 0>(fam, L, OpSmooth<Tin>{view(L), cur, oth, lb[l], ld, c, e, xp_zero, {}}, chunk_part, bytes);
+            rowop<Tin, 0>(fam, L, OpSmooth<Tin>{lv_view(L), cur, oth, lb[l], ld, c, e, xp_zero, {}}, chunk_part, bytes);
         } else if (dot == 1) {
-            rowop<Tin, 3>(fam, L, OpSmooth<Tin, 3, false>{view(L), cur, oth, lb[l], ld, c, e, xp_zero, dstate()},
+            rowop<Tin, 3>(fam, L, OpSmooth<Tin, 3, false>{lv_view(L), cur, oth, lb[l], ld, c, e, xp_zero, dstate()},
                           chunk_part, bytes);
         } else {
-            rowop<Tin, 4>(fam, L, OpSmooth<Tin, 4, true>{view(L), cur, oth, lb[l], ld, c, e, xp_zero, dstate()},
+            rowop<Tin, 4>(fam, L, OpSmooth<Tin, 4, true>{lv_view(L), cur, oth, lb[l], ld, c, e, xp_zero, dstate()},
                           chunk_part, bytes);
         }
         std::swap(cur, oth);
@@ -682,7 +705,7 @@ struct Solver {
     bool vcycle(int l, bool first_done = false, int dot = 0) {
         const Level &L = h->lv[l];
         const int et = (int)sizeof(Tin);
-        const int wb = et;
+        const int wb = wbytes(L);
         const bool coarsest = (l == nlev - 1);
         if (coarsest && h->coarse_n == L.n && l == (int)h->lv.size() - 1) {
             const int nc = L.n;
@@ -696,7 +719,7 @@ struct Solver {
         Tin *cur = lx[l], *oth = lt[l];
         if (!first_done)
             rows<Tin, 0>(fam_level(l, LAP_KF_SMOOTH_FINE), L.n,
-                         OpJacobiZero<Tin>{view(L), lb[l], cur, ld, (Tin)cheb_e[0]},
+                         OpJacobiZero<Tin>{lv_view(L), lb[l], cur, ld, (Tin)cheb_e[0]},
                          vec_bytes(L.n, ld, 2, et) + L.n * (double)wb);
         const int npre = coarsest ? nu_coarse : nu_pre;
         bool dotted = false;
@@ -718,7 +741,7 @@ struct Solver {
         const bool next_dense = (l + 1 == nlev - 1) && h->coarse_n == C.n && l + 1 == (int)h->lv.size() - 1;
         const int ncorr = (cycle == 2 && !next_dense) ? 2 : 1;
         for (int cc = 0; cc < ncorr; ++cc) {
-            rowop<Tin, 0>(fam_level(l, LAP_KF_RESTRICT_FINE), L, OpResid<Tin>{view(L), cur, lb[l], oth, ld},
+            rowop<Tin, 0>(fam_level(l, LAP_KF_RESTRICT_FINE), L, OpResid<Tin>{lv_view(L), cur, lb[l], oth, ld},
                           chunk_part, mat_bytes(L, wb) + vec_bytes(L.n, ld, 3, et));
             rows<Tin, 0>(fam_level(l, LAP_KF_RESTRICT_FINE), C.n,
                          OpRestrict<Tin>{L.mem_ptr.get(), L.mem.get(), oth, lb[l + 1], ld},
@@ -767,10 +790,10 @@ struct Solver {
         int it = 0;
         for (it = 1; it <= max_inner; ++it) {
             rowop<Tin, 1>(LAP_KF_SPMV_FINE, L0,
-                          OpSpmvDot<Tin>{view(L0), p, q, ld, cs.rz, cs.alpha, alpha_t, cs.active_in}, chunk_part,
+                          OpSpmvDot<Tin>{lv_view(L0), p, q, ld, cs.rz, cs.alpha, alpha_t, cs.active_in}, chunk_part,
                           mat_bytes(L0, et) + 2 * vb1);
             rows<Tin, 1>(LAP_KF_BLAS1, n,
-                         OpUpdateXR<Tin>{d, r, p, q, fuse_first ? z : nullptr, view(L0), (Tin)cheb_e[0], ld, alpha_t,
+                         OpUpdateXR<Tin>{d, r, p, q, fuse_first ? z : nullptr, lv_view(L0), (Tin)cheb_e[0], ld, alpha_t,
                                          cs.active_in, cs.rr0, inner_tol * inner_tol},
                          (fuse_first ? 7 : 6) * vb1);
             if (it % check == 0 || it == max_inner) {
@@ -823,16 +846,16 @@ struct Solver {
                 const int nvb = nvb_short + nvb_long;
                 dim3 grid(red_grid(nvb), ntiles64);
                 using Op = OpResid64<Tin>;
-                Op op{view(L0), x64, b64, r, ld, cs.bnorm, cs.relres, cs.active_out, o.tol};
+                Op op{lv_view(L0), x64, b64, r, ld, cs.bnorm, cs.relres, cs.active_out, o.tol};
                 const double bytes = mat_bytes(L0, 8) + 2 * v64 + vec_bytes(n, ld, 1, sizeof(Tin));
                 if (L0.n_chunks > 0) {
                     CFC_LAUNCH(LAP_KF_RESID64, s, 0.0, (k_chunk_sums<double, K64, Op>), dim3(nvb_long, ntiles64),
-                               kBlock, 0, view(L0), op, chunk_part64, ld);
+                               kBlock, 0, lv_view(L0), op, chunk_part64, ld);
                     CFC_LAUNCH(LAP_KF_RESID64, s, bytes, (k_rowop<double, K64, 1, Op, kLongPre>),
-                               dim3(red_grid(nvb_short), ntiles64), kBlock, 0, view(L0), op, nvb_short, nvb_short,
+                               dim3(red_grid(nvb_short), ntiles64), kBlock, 0, lv_view(L0), op, nvb_short, nvb_short,
                                chunk_part64, ld, rb);
                 } else {
-                    CFC_LAUNCH(LAP_KF_RESID64, s, bytes, (k_rowop<double, K64, 1, Op>), grid, kBlock, 0, view(L0), op,
+                    CFC_LAUNCH(LAP_KF_RESID64, s, bytes, (k_rowop<double, K64, 1, Op>), grid, kBlock, 0, lv_view(L0), op,
                                nvb_short, nvb, chunk_part64, ld, rb);
                 }
             }
@@ -1072,8 +1095,9 @@ lap_status_t solve_impl(lap_hierarchy *h, int32_t k, const double *B, double *X,
     CFC_REQUIRE(B && X && B != X, LAP_EINVAL, "B and X must be distinct device buffers");
     CFC_REQUIRE(is_device_pointer(B) && is_device_pointer(X), LAP_EINVAL, "B and X must be device pointers");
     CFC_REQUIRE(o_in.tol > 0 && o_in.max_outer >= 0 && o_in.max_inner >= 1, LAP_EINVAL, "bad solve options");
-    CFC_REQUIRE(o_in.precision == LAP_FP64 || o_in.precision == LAP_FP32_REFINED, LAP_ENOTIMPL,
-                "precision mode not implemented (LAP_FP64 and LAP_FP32_REFINED are)");
+    CFC_REQUIRE(o_in.precision == LAP_FP64 || o_in.precision == LAP_FP32_REFINED ||
+                    o_in.precision == LAP_FP32_BF16COARSE_REFINED,
+                LAP_EINVAL, "unknown precision mode");
     lap_solve_opts_t o = o_in;
     const bool fp64 = (o.precision == LAP_FP64);
     const int kt = solve_tile(k, o);

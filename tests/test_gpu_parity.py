@@ -107,8 +107,13 @@ SOLVE_CASES = [
 ]
 
 
+PRECISIONS = {"fp32": dict(precision=1), "fp64": dict(precision=0),
+              # BF16 coarse weights only matter below the finest level: use every level
+              "bf16coarse": dict(precision=2, levels_used=-1)}
+
+
 @pytest.mark.parametrize("name,gen,k", SOLVE_CASES)
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("precision", sorted(PRECISIONS))
 def test_solve_matches_dense_pinv(P, name, gen, k, precision):
     import torch
     n, s, d, w = _graph(gen())
@@ -118,7 +123,7 @@ def test_solve_matches_dense_pinv(P, name, gen, k, precision):
     B = rng.standard_normal((n, k))
     Bt = torch.tensor(B, device="cuda")
     Xt = torch.empty_like(Bt)
-    opts = P.lap_default_solve_opts(precision=P.LAP_FP64 if precision == "fp64" else P.LAP_FP32_REFINED)
+    opts = P.lap_default_solve_opts(**PRECISIONS[precision])
     info = P.lap_solve_multi(h, Bt, Xt, opts)
     assert info["max_rel_residual"] <= 1e-8
     X = Xt.cpu().numpy()
@@ -187,14 +192,34 @@ def test_solve_noconv_reports(P):
 # ------------------------------------------------------------------ estimators
 @pytest.mark.parametrize("gen,k", [(lambda: synth.grid2d(48), 32), (lambda: synth.barabasi_albert(2000, 5, 4), 64),
                                    (lambda: synth.star_graph(300), 24)])
-def test_farness_jl_matches_oracle(P, gen, k):
+@pytest.mark.parametrize("precision", sorted(PRECISIONS))
+def test_farness_jl_matches_oracle(P, gen, k, precision):
     n, s, d, w = _graph(gen())
     g = canonical_graph(n, s, d, w)
     h = P.lap_build_hierarchy(n, s, d, w)
     nodes = np.array([0, 1, n // 2, n - 1], np.int32)
-    f = P.cfc_farness_jl(h, k, 1, nodes)
+    f = P.cfc_farness_jl(h, k, 1, nodes, opts=P.lap_default_solve_opts(**PRECISIONS[precision]))
     fo = jl.jl_farness(g, k, 1, nodes.tolist(), solver="dense")
     assert _rel(f, fo) <= FARNESS_RTOL
+
+
+def test_bf16_coarse_changes_only_the_preconditioner(P):
+    # same FP64 stopping test: both modes reach 1e-8 and agree to the solve
+    # tolerance; the coarse operators differ, so the inner iterations may differ
+    import torch
+    n, s, d, w = _graph(synth.grid2d(64))
+    h = P.lap_build_hierarchy(n, s, d, w, P.lap_default_hier_opts(eager=1))
+    assert P.lap_hierarchy_info(h)["levels"] >= 3
+    rng = np.random.default_rng(3)
+    B = torch.tensor(rng.standard_normal((n, 16)), device="cuda")
+    X1, X2 = torch.empty_like(B), torch.empty_like(B)
+    i1 = P.lap_solve_multi(h, B, X1, P.lap_default_solve_opts(precision=1, levels_used=-1))
+    i2 = P.lap_solve_multi(h, B, X2, P.lap_default_solve_opts(precision=2, levels_used=-1))
+    assert i1["max_rel_residual"] <= 1e-8 and i2["max_rel_residual"] <= 1e-8
+    g = canonical_graph(n, s, d, w)
+    lam = np.linalg.eigvalsh(laplacian(g).toarray())
+    diff = (X1 - X2).norm(dim=0) / X1.norm(dim=0)
+    assert float(diff.max()) <= 2 * lam[-1] / lam[1] * 1.01e-8
 
 
 @pytest.mark.parametrize("n,k", [(3000, 64), (517, 5), (2, 1), (1000, 300)])
