@@ -49,7 +49,8 @@ typedef enum {
     LAP_ENOCONV = 4,   /* a solve hit its iteration cap; outputs hold the best iterate */
     LAP_ECUDA = 5,     /* a CUDA runtime error (the text is kept, see lap_last_error) */
     LAP_EBUDGET = 6,   /* request exceeds a documented maximum */
-    LAP_ENOTIMPL = 7
+    LAP_ENOTIMPL = 7,
+    LAP_EPENDING = 8   /* a served request has not finished yet (cfc_server_poll) */
 } lap_status_t;
 
 /* Arithmetic of a solve. */
@@ -106,6 +107,11 @@ typedef struct {
     int32_t outer_iters;
     int32_t inner_iters;        /* total over all refinement steps */
     double max_rel_residual;    /* max over columns of the final FP64 ||b - Lx|| / ||b|| */
+    /* the configuration the solve ran with (the autotuner's choice where the
+       options left it open); passing these back as options repeats the solve
+       bit for bit without tuning */
+    int32_t k_tile, levels_used, nu_coarse, cycle;
+    double coarse_scale;
 } lap_solve_info_t;
 
 typedef struct {
@@ -200,6 +206,23 @@ lap_status_t cfc_jl_rhs(lap_hierarchy_t *h, int32_t k, uint64_t seed, double *Y,
 lap_status_t cfc_farness_jl(lap_hierarchy_t *h, int32_t k, double eps, uint64_t seed, int32_t q,
                             const int32_t *nodes, double *farness, const lap_solve_opts_t *o,
                             void *stream);
+
+/*
+ * cfc_farness_jl_rows -- the terms of cfc_farness_jl contributed by rows
+ * row_begin .. row_begin + row_count - 1 of the k_total-row Q (Algorithm 1:
+ * the rows are independent solves, and f~(v) is a sum over rows), scaled by
+ * 1/sqrt(k_total).  Summing the outputs over a partition of [0, k_total)
+ * gives cfc_farness_jl(h, k_total, ...) up to the order of the FP64 sums:
+ * the unit of work that several GPUs split, each summing its own rows, with
+ * one reduction of q doubles at the end (no counterpart in the paper, which
+ * runs on one machine).
+ *   row_begin  multiple of 32, 0 <= row_begin;  row_count >= 1, <= 4096,
+ *              row_begin + row_count <= k_total
+ *   q, nodes, farness as cfc_farness_jl (farness receives the partial sums)
+ */
+lap_status_t cfc_farness_jl_rows(lap_hierarchy_t *h, int32_t k_total, int32_t row_begin, int32_t row_count,
+                                 uint64_t seed, int32_t q, const int32_t *nodes, double *farness,
+                                 const lap_solve_opts_t *o, void *stream);
 
 /*
  * cfc_farness_from_solution -- Algorithm 1, step 4 and the closing formula of
@@ -331,6 +354,79 @@ lap_status_t lap_stats_read(lap_stats_t *out);
  */
 void lap_stats_set_log(int32_t on);
 lap_status_t lap_stats_read_log(int32_t *families, int64_t capacity, int64_t *count);
+
+/*
+ * Serving (no counterpart in the paper, which times one query at a time):
+ * a request loop over resident graphs for the sampling estimator of Sec. 5.1
+ * (cfc_farness_sampled), with continuous batching.  Each request is the
+ * farness of q query nodes from one pivot set of n_pivots nodes (n_pivots + q
+ * column solves).  `slots` worker threads, each with its own CUDA stream,
+ * take requests in arrival order as soon as a slot is free and the request's
+ * device memory fits the HBM budget next to the resident graphs and the
+ * requests in flight, so requests that arrive while others run are admitted
+ * while those are still on the GPU and their solves overlap on the device.
+ *
+ * A graph's hierarchy is built completely when it is added, and the solver
+ * configuration for its requests is autotuned once then and pinned, so a
+ * request's result does not depend on what else is in flight (the kernels'
+ * reductions have a fixed order): the same bits alone and in a mix.
+ *
+ * Ownership: the server owns the hierarchies it builds and the request
+ * results until they are polled.  Inputs are copied.  Calls are thread-safe.
+ */
+typedef struct cfc_server cfc_server_t;
+
+typedef struct {
+    int32_t slots;          /* concurrent requests on the device, 1..64 (default 4) */
+    int64_t hbm_budget;     /* bytes for resident graphs + requests in flight; 0 (default):
+                               80% of the device memory free at creation */
+    lap_solve_opts_t solve; /* solve options (precision, tol, ...); tuned fields left 0 are
+                               autotuned per graph when it is added */
+} cfc_server_opts_t;
+
+typedef struct {
+    int32_t status;         /* the request's lap_status_t */
+    int32_t graph_id, q, n_pivots;
+    int64_t device_bytes;   /* the memory it was admitted with (estimate, charged to the budget) */
+    double queue_ms;        /* submit -> admitted to a slot */
+    double run_ms;          /* admitted -> result on the host */
+    double latency_ms;      /* submit -> result on the host */
+} cfc_request_info_t;
+
+typedef struct {
+    int64_t submitted, completed, pending, in_flight;
+    int32_t max_in_flight;  /* most requests seen on the device at once */
+    double p50_ms, p99_ms, mean_ms, max_ms;  /* latency of the completed requests (nearest rank) */
+    double queries_per_s;   /* completed requests / (last completion - first submission) */
+    double rhs_per_s;       /* their column solves per second over the same span */
+    int64_t graph_bytes, budget_bytes, peak_in_flight_bytes;
+} cfc_server_stats_t;
+
+void cfc_server_default_opts(cfc_server_opts_t *o);
+/* LAP_EINVAL on bad options; LAP_ECUDA if the streams cannot be made. */
+lap_status_t cfc_server_create(const cfc_server_opts_t *o, cfc_server_t **out);
+/* Builds the graph's hierarchy (as lap_build_hierarchy, every level) and
+ * tunes its solves; *graph_id receives its index.  LAP_EBUDGET if it does not
+ * fit the budget next to the graphs already resident. */
+lap_status_t cfc_server_add_graph(cfc_server_t *sv, int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                                  const double *w, int32_t *graph_id);
+/* Queues a request (host `nodes`, copied) and returns at once with its id.
+ * LAP_EINVAL for a bad graph id, node or count; LAP_EBUDGET if the request
+ * alone exceeds what the budget leaves beside the resident graphs. */
+lap_status_t cfc_server_submit(cfc_server_t *sv, int32_t graph_id, int32_t q, const int32_t *nodes,
+                               int32_t n_pivots, uint64_t seed, int64_t *request_id);
+/* Waits up to wait_ms (0: no wait, < 0: until done) for the request.  Done:
+ * copies its q farness values to the host array `farness` (may be NULL),
+ * fills *info (may be NULL), forgets the request and returns its status.
+ * Not done: LAP_EPENDING.  Unknown (or already polled) id: LAP_EINVAL. */
+lap_status_t cfc_server_poll(cfc_server_t *sv, int64_t request_id, int32_t wait_ms, double *farness,
+                             cfc_request_info_t *info);
+lap_status_t cfc_server_stats(cfc_server_t *sv, cfc_server_stats_t *out);
+/* Drops the latency record (the counters of completed requests) and the
+ * throughput span, e.g. after a warm-up. */
+void cfc_server_reset_stats(cfc_server_t *sv);
+/* Finishes the requests in flight, drops the queued ones, frees everything. */
+void cfc_server_destroy(cfc_server_t *sv);
 
 #ifdef __cplusplus
 }

@@ -23,6 +23,7 @@ from ._binding import (  # noqa: F401
     LAP_ECUDA,
     LAP_EBUDGET,
     LAP_ENOTIMPL,
+    LAP_EPENDING,
     LAP_FP64,
     LAP_FP32_REFINED,
     LAP_FP32_BF16COARSE_REFINED,
@@ -40,6 +41,7 @@ from ._binding import (  # noqa: F401
     lap_solve_multi,
     cfc_jl_rhs,
     cfc_farness_jl,
+    cfc_farness_jl_rows,
     cfc_farness_from_solution,
     cfc_farness_from_solution_noalloc,
     cfc_sample_pivots,
@@ -52,4 +54,14 @@ from ._binding import (  # noqa: F401
     lap_stats_read,
     lap_stats_set_log,
     lap_stats_read_log,
+    Server,
+    ServerOpts,
+    cfc_server_default_opts,
+    cfc_server_create,
+    cfc_server_add_graph,
+    cfc_server_submit,
+    cfc_server_poll,
+    cfc_server_stats,
+    cfc_server_reset_stats,
+    cfc_server_destroy,
 )

@@ -9,7 +9,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 lib_path = os.path.join(_HERE, "lib", "libcfc_gb300.so")
 
-LAP_OK, LAP_EINVAL, LAP_ENOTCONN, LAP_ENOMEM, LAP_ENOCONV, LAP_ECUDA, LAP_EBUDGET, LAP_ENOTIMPL = range(8)
+(LAP_OK, LAP_EINVAL, LAP_ENOTCONN, LAP_ENOMEM, LAP_ENOCONV, LAP_ECUDA, LAP_EBUDGET, LAP_ENOTIMPL,
+ LAP_EPENDING) = range(9)
 LAP_FP64, LAP_FP32_REFINED, LAP_FP32_BF16COARSE_REFINED = 0, 1, 2
 LAP_SMOOTH_JACOBI, LAP_SMOOTH_CHEBYSHEV = 0, 1
 KERNEL_FAMILIES = ["spmv_fine", "smooth_fine", "restrict_fine", "blas1", "coarse_levels", "resid64", "setup",
@@ -17,10 +18,13 @@ KERNEL_FAMILIES = ["spmv_fine", "smooth_fine", "restrict_fine", "blas1", "coarse
 
 SYMBOLS = [
     "lap_default_hier_opts", "lap_default_solve_opts", "lap_build_hierarchy", "lap_hierarchy_destroy",
-    "lap_hierarchy_info", "lap_solve_multi", "cfc_jl_rhs", "cfc_farness_jl", "cfc_farness_from_solution",
+    "lap_hierarchy_info", "lap_solve_multi", "cfc_jl_rhs", "cfc_farness_jl", "cfc_farness_jl_rows",
+    "cfc_farness_from_solution",
     "cfc_farness_from_solution_noalloc", "cfc_sample_pivots",
     "cfc_farness_sampled", "cfc_exact_small", "lap_status_string", "lap_last_error", "lap_stats_reset",
     "lap_stats_set_timing", "lap_stats_read", "lap_stats_set_log", "lap_stats_read_log",
+    "cfc_server_default_opts", "cfc_server_create", "cfc_server_add_graph", "cfc_server_submit",
+    "cfc_server_poll", "cfc_server_stats", "cfc_server_reset_stats", "cfc_server_destroy",
 ]
 
 
@@ -38,7 +42,9 @@ class SolveOpts(C.Structure):
 
 
 class SolveInfo(C.Structure):
-    _fields_ = [("outer_iters", C.c_int32), ("inner_iters", C.c_int32), ("max_rel_residual", C.c_double)]
+    _fields_ = [("outer_iters", C.c_int32), ("inner_iters", C.c_int32), ("max_rel_residual", C.c_double),
+                ("k_tile", C.c_int32), ("levels_used", C.c_int32), ("nu_coarse", C.c_int32), ("cycle", C.c_int32),
+                ("coarse_scale", C.c_double)]
 
 
 class HierInfo(C.Structure):
@@ -49,6 +55,24 @@ class HierInfo(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("launches_total", C.c_uint64), ("launches", C.c_uint64 * 8), ("ms", C.c_double * 8),
                 ("bytes", C.c_double * 8)]
+
+
+class ServerOpts(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("hbm_budget", C.c_int64), ("solve", SolveOpts)]
+
+
+class RequestInfo(C.Structure):
+    _fields_ = [("status", C.c_int32), ("graph_id", C.c_int32), ("q", C.c_int32), ("n_pivots", C.c_int32),
+                ("device_bytes", C.c_int64), ("queue_ms", C.c_double), ("run_ms", C.c_double),
+                ("latency_ms", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("pending", C.c_int64),
+                ("in_flight", C.c_int64), ("max_in_flight", C.c_int32), ("p50_ms", C.c_double),
+                ("p99_ms", C.c_double), ("mean_ms", C.c_double), ("max_ms", C.c_double),
+                ("queries_per_s", C.c_double), ("rhs_per_s", C.c_double), ("graph_bytes", C.c_int64),
+                ("budget_bytes", C.c_int64), ("peak_in_flight_bytes", C.c_int64)]
 
 
 class LapError(RuntimeError):
@@ -87,6 +111,8 @@ def lib():
     L.cfc_jl_rhs.restype = C.c_int
     L.cfc_farness_jl.argtypes = [vp, i32, dbl, u64, i32, vp, vp, C.POINTER(SolveOpts), vp]
     L.cfc_farness_jl.restype = C.c_int
+    L.cfc_farness_jl_rows.argtypes = [vp, i32, i32, i32, u64, i32, vp, vp, C.POINTER(SolveOpts), vp]
+    L.cfc_farness_jl_rows.restype = C.c_int
     L.cfc_farness_from_solution.argtypes = [i64, i32, vp, i32, vp, vp, vp]
     L.cfc_farness_from_solution.restype = C.c_int
     L.cfc_farness_from_solution_noalloc.argtypes = [i64, i32, vp, i32, vp, vp, vp]
@@ -107,6 +133,22 @@ def lib():
     L.lap_stats_set_timing.restype = None
     L.lap_stats_read.argtypes = [C.POINTER(Stats)]
     L.lap_stats_read.restype = C.c_int
+    L.cfc_server_default_opts.argtypes = [C.POINTER(ServerOpts)]
+    L.cfc_server_default_opts.restype = None
+    L.cfc_server_create.argtypes = [C.POINTER(ServerOpts), C.POINTER(vp)]
+    L.cfc_server_create.restype = C.c_int
+    L.cfc_server_add_graph.argtypes = [vp, i64, i64, vp, vp, vp, C.POINTER(i32)]
+    L.cfc_server_add_graph.restype = C.c_int
+    L.cfc_server_submit.argtypes = [vp, i32, i32, vp, i32, u64, C.POINTER(i64)]
+    L.cfc_server_submit.restype = C.c_int
+    L.cfc_server_poll.argtypes = [vp, i64, i32, vp, C.POINTER(RequestInfo)]
+    L.cfc_server_poll.restype = C.c_int
+    L.cfc_server_stats.argtypes = [vp, C.POINTER(ServerStats)]
+    L.cfc_server_stats.restype = C.c_int
+    L.cfc_server_reset_stats.argtypes = [vp]
+    L.cfc_server_reset_stats.restype = None
+    L.cfc_server_destroy.argtypes = [vp]
+    L.cfc_server_destroy.restype = None
     L.lap_stats_set_log.argtypes = [i32]
     L.lap_stats_set_log.restype = None
     L.lap_stats_read_log.argtypes = [vp, i64, C.POINTER(C.c_int64)]
@@ -235,7 +277,8 @@ def lap_solve_multi(h: Hierarchy, B, X, opts: SolveOpts | None = None, stream=No
                                _stream(stream), C.byref(info))
     _check(st, "lap_solve_multi", allow=(LAP_ENOCONV,) if allow_noconv else ())
     return {"status": st, "outer_iters": info.outer_iters, "inner_iters": info.inner_iters,
-            "max_rel_residual": info.max_rel_residual}
+            "max_rel_residual": info.max_rel_residual, "k_tile": info.k_tile, "levels_used": info.levels_used,
+            "nu_coarse": info.nu_coarse, "cycle": info.cycle, "coarse_scale": info.coarse_scale}
 
 
 def cfc_jl_rhs(h: Hierarchy, k: int, seed: int, Y, stream=None):
@@ -257,6 +300,18 @@ def cfc_farness_jl(h: Hierarchy, k: int, seed: int, nodes, eps: float = 0.0, opt
     st = lib().cfc_farness_jl(h.handle, int(k), float(eps), int(seed), int(q), pn, po,
                               C.byref(opts) if opts is not None else None, _stream(stream))
     _check(st, "cfc_farness_jl")
+    return out
+
+
+def cfc_farness_jl_rows(h: Hierarchy, k_total: int, row_begin: int, row_count: int, seed: int, nodes,
+                        opts: SolveOpts | None = None, out=None, stream=None):
+    q = len(nodes)
+    pn, kn = _ptr(nodes, np.int32)
+    out = _out_f64(out, q)
+    po, ko = _ptr(out, np.float64)
+    st = lib().cfc_farness_jl_rows(h.handle, int(k_total), int(row_begin), int(row_count), int(seed), int(q), pn,
+                                   po, C.byref(opts) if opts is not None else None, _stream(stream))
+    _check(st, "cfc_farness_jl_rows")
     return out
 
 
@@ -346,3 +401,86 @@ def lap_stats_read_log() -> list:
     buf = (C.c_int32 * max(cnt.value, 1))()
     _check(lib().lap_stats_read_log(C.cast(buf, C.c_void_p), cnt.value, C.byref(cnt)), "lap_stats_read_log")
     return [KERNEL_FAMILIES[buf[i]] for i in range(cnt.value)]
+
+
+# ------------------------------------------------------------------ serving
+def cfc_server_default_opts(**kw) -> ServerOpts:
+    o = ServerOpts()
+    lib().cfc_server_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if k == "solve":
+            o.solve = v
+        else:
+            setattr(o, k, v)
+    return o
+
+
+class Server:
+    """Owner of a cfc_server_t handle (freed by destroy() or on collection)."""
+
+    def __init__(self, handle: int):
+        self.handle = C.c_void_p(handle)
+
+    def destroy(self):
+        if self.handle:
+            lib().cfc_server_destroy(self.handle)
+            self.handle = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def cfc_server_create(opts: ServerOpts | None = None) -> Server:
+    out = C.c_void_p(0)
+    _check(lib().cfc_server_create(C.byref(opts if opts is not None else cfc_server_default_opts()),
+                                   C.byref(out)), "cfc_server_create")
+    return Server(out.value)
+
+
+def cfc_server_add_graph(sv: Server, n, src, dst, w=None) -> int:
+    """Host numpy edge arrays (copied); returns the graph id."""
+    ps, ks = _ptr(np.ascontiguousarray(src, np.int32), np.int32)
+    pd, kd = _ptr(np.ascontiguousarray(dst, np.int32), np.int32)
+    pw, kw = _ptr(None if w is None else np.ascontiguousarray(w, np.float64), np.float64)
+    gid = C.c_int32(-1)
+    _check(lib().cfc_server_add_graph(sv.handle, int(n), int(len(src)), ps, pd, pw, C.byref(gid)),
+           "cfc_server_add_graph")
+    return gid.value
+
+
+def cfc_server_submit(sv: Server, graph_id: int, nodes, n_pivots: int, seed: int) -> int:
+    nd = np.ascontiguousarray(nodes, np.int32)
+    rid = C.c_int64(0)
+    _check(lib().cfc_server_submit(sv.handle, int(graph_id), int(nd.size), nd.ctypes.data_as(C.c_void_p),
+                                   int(n_pivots), C.c_uint64(seed), C.byref(rid)), "cfc_server_submit")
+    return rid.value
+
+
+def cfc_server_poll(sv: Server, request_id: int, wait_ms: int = -1, q: int | None = None):
+    """Returns (farness numpy array, info dict) when done, None while pending."""
+    info = RequestInfo()
+    buf = np.zeros(4096, np.float64) if q is None else np.zeros(q, np.float64)
+    st = lib().cfc_server_poll(sv.handle, int(request_id), int(wait_ms), buf.ctypes.data_as(C.c_void_p),
+                               C.byref(info))
+    if st == LAP_EPENDING:
+        return None
+    _check(st, "cfc_server_poll")
+    d = {f: getattr(info, f) for f, _ in RequestInfo._fields_}
+    return buf[:info.q].copy(), d
+
+
+def cfc_server_stats(sv: Server) -> dict:
+    st = ServerStats()
+    _check(lib().cfc_server_stats(sv.handle, C.byref(st)), "cfc_server_stats")
+    return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+
+def cfc_server_reset_stats(sv: Server):
+    lib().cfc_server_reset_stats(sv.handle)
+
+
+def cfc_server_destroy(sv: Server):
+    sv.destroy()

@@ -444,8 +444,6 @@ void finish_level(Level &L, cudaStream_t s) {
     L.chunk_begin.alloc_persistent(L.n_chunks);
     L.chunk_long.alloc_persistent(L.n_chunks);
     L.long_first.alloc_persistent(L.n_long + 1);
-    L.long_count.alloc_persistent((size_t)L.n_long * kMaxTiles);
-    L.long_count.zero(s);
     L.long_of_row.alloc_persistent(n);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_fill_chunks, grid_for(n), kBlock, 0, L.rowptr.get(), nchunk.get(),
                cfirst.get(), lidx.get(), n, L.chunk_row.get(), L.chunk_begin.get(), L.chunk_long.get(),

@@ -60,6 +60,7 @@ void drain_locked() {
 }  // namespace
 
 void set_last_error(const std::string &s) { t_last_error = s; }
+void clear_last_error() { t_last_error.clear(); }
 
 void count_launch() { g_launches_total.fetch_add(1, std::memory_order_relaxed); }
 
@@ -155,7 +156,7 @@ LevelView view(const Level &L) {
     v.chunk_long = L.chunk_long.get();
     v.long_first = L.long_first.get();
     v.long_of_row = L.long_of_row.get();
-    v.long_count = L.long_count.get();
+    v.long_count = nullptr;  // set by the solve that launches on the level
     return v;
 }
 
@@ -167,22 +168,21 @@ LevelView view_bf16(const Level &L) {
     return v;
 }
 
-template <class F>
-lap_status_t guard(F &&f) {
-    try {
-        t_last_error.clear();
-        return f();
-    } catch (const Error &e) {
-        t_last_error = e.what;
-        return e.status;
-    } catch (const std::bad_alloc &) {
-        t_last_error = "host allocation failed";
-        return LAP_ENOMEM;
-    } catch (...) {
-        t_last_error = "unknown error";
-        return LAP_ECUDA;
-    }
+void release_workspace(lap_hierarchy *h, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(h->ws_mu);
+    h->ws.erase(s);  // DBuf frees on the stream it was taken on
 }
+
+int64_t hierarchy_bytes(const lap_hierarchy *h) {
+    auto b = [](const auto &d) { return (int64_t)(d.n * sizeof(*d.p)); };
+    int64_t t = b(h->eid) + b(h->coarse_inv);
+    for (const Level &L : h->lv)
+        t += b(L.rowptr) + b(L.col) + b(L.w64) + b(L.deg64) + b(L.dinv64) + b(L.w32) + b(L.deg32) + b(L.dinv32) +
+             b(L.wbf) + b(L.degbf) + b(L.dinvbf) + b(L.chunk_row) + b(L.chunk_begin) + b(L.chunk_long) +
+             b(L.long_first) + b(L.long_of_row) + b(L.agg) + b(L.mem_ptr) + b(L.mem);
+    return t;
+}
+
 
 }  // namespace cfc
 
@@ -227,6 +227,7 @@ const char *lap_status_string(lap_status_t s) {
         case LAP_ECUDA: return "LAP_ECUDA: CUDA error";
         case LAP_EBUDGET: return "LAP_EBUDGET: request exceeds a documented maximum";
         case LAP_ENOTIMPL: return "LAP_ENOTIMPL: not implemented";
+        case LAP_EPENDING: return "LAP_EPENDING: request not finished";
     }
     return "unknown status";
 }
@@ -284,6 +285,7 @@ void lap_hierarchy_destroy(lap_hierarchy_t *h) {
 lap_status_t lap_hierarchy_info(const lap_hierarchy_t *h, lap_hier_info_t *info) {
     return guard([&]() -> lap_status_t {
         CFC_REQUIRE(h && info, LAP_EINVAL, "NULL argument");
+        std::shared_lock<std::shared_mutex> lk(h->mu);
         std::memset(info, 0, sizeof(*info));
         info->n = h->n;
         info->m = h->m;
@@ -318,8 +320,18 @@ lap_status_t cfc_jl_rhs(lap_hierarchy_t *h, int32_t k, uint64_t seed, double *Y,
         CFC_REQUIRE(h && Y, LAP_EINVAL, "NULL argument");
         CFC_REQUIRE(k >= 1 && k <= 4096, LAP_EINVAL, "need 1 <= k <= 4096");
         CFC_REQUIRE(is_device_pointer(Y), LAP_EINVAL, "Y must be a device pointer");
-        jl_rhs(h, k, k, seed, Y, (cudaStream_t)stream);
+        jl_rhs(h, k, 0, k, k, seed, Y, (cudaStream_t)stream);
         return LAP_OK;
+    });
+}
+
+lap_status_t cfc_farness_jl_rows(lap_hierarchy_t *h, int32_t k_total, int32_t row_begin, int32_t row_count,
+                                 uint64_t seed, int32_t q, const int32_t *nodes, double *farness,
+                                 const lap_solve_opts_t *o, void *stream) {
+    return guard([&]() -> lap_status_t {
+        CFC_REQUIRE(h, LAP_EINVAL, "NULL hierarchy");
+        return farness_jl_rows(h, k_total, row_begin, row_count, seed, q, nodes, farness, resolve_opts(o),
+                               (cudaStream_t)stream);
     });
 }
 

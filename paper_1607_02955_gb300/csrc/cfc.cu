@@ -132,7 +132,7 @@ __device__ __forceinline__ void jl_accum(const int32_t *eid, const long long *a,
 
 __global__ void k_jl_short(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ eid,
                            const long long *__restrict__ a, const double *__restrict__ deg, int32_t n, int k, int ld,
-                           uint64_t seed, double inv_k, double *__restrict__ Y) {
+                           int cb_off, uint64_t seed, double inv_k, double *__restrict__ Y) {
     const int ncb = (ld + 31) / 32;
     GRID_LOOP(t, (int64_t)n * ncb) {
         const int u = (int)(t / ncb), cb = (int)(t - (int64_t)u * ncb);
@@ -141,7 +141,7 @@ __global__ void k_jl_short(const int32_t *__restrict__ rowptr, const int32_t *__
         long long acc[32];
 #pragma unroll
         for (int q = 0; q < 32; ++q) acc[q] = 0;
-        jl_accum(eid, a, e0, e1, cb, seed, acc);
+        jl_accum(eid, a, e0, e1, cb_off + cb, seed, acc);
         const int sh = -jl_row_shift(rowptr, deg, u, inv_k);
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
@@ -153,8 +153,8 @@ __global__ void k_jl_short(const int32_t *__restrict__ rowptr, const int32_t *__
 
 __global__ void k_jl_chunks(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ eid,
                             const long long *__restrict__ a, const int32_t *__restrict__ chunk_row,
-                            const int32_t *__restrict__ chunk_begin, int32_t n_chunks, int ld, uint64_t seed,
-                            long long *__restrict__ part) {
+                            const int32_t *__restrict__ chunk_begin, int32_t n_chunks, int ld, int cb_off,
+                            uint64_t seed, long long *__restrict__ part) {
     const int ncb = (ld + 31) / 32;
     GRID_LOOP(t, (int64_t)n_chunks * ncb) {
         const int ch = (int)(t / ncb), cb = (int)(t - (int64_t)ch * ncb);
@@ -163,7 +163,7 @@ __global__ void k_jl_chunks(const int32_t *__restrict__ rowptr, const int32_t *_
         long long acc[32];
 #pragma unroll
         for (int q = 0; q < 32; ++q) acc[q] = 0;
-        jl_accum(eid, a, e0, e1, cb, seed, acc);
+        jl_accum(eid, a, e0, e1, cb_off + cb, seed, acc);
 #pragma unroll
         for (int q = 0; q < 32; ++q) part[((size_t)ch * ncb + cb) * 32 + q] = acc[q];
     }
@@ -369,22 +369,24 @@ const int32_t *nodes_to_device(const int32_t *nodes, int q, int32_t n, DBuf<int3
 
 }  // namespace
 
-void jl_rhs(lap_hierarchy *h, int k, int ld, uint64_t seed, double *Y, cudaStream_t s) {
+void jl_rhs(lap_hierarchy *h, int k_total, int row0, int k, int ld, uint64_t seed, double *Y, cudaStream_t s) {
     const Level &L = h->lv[0];
     const int n = L.n;
     const int ncb = (ld + 31) / 32;
-    const double inv_sqrt_k = 1.0 / std::sqrt((double)k), inv_k = 1.0 / k;
+    // the scale (and the fixed-point bound) are those of the full k_total-row Q
+    const double inv_sqrt_k = 1.0 / std::sqrt((double)k_total), inv_k = 1.0 / k_total;
+    const int cb_off = row0 / 32;
     DBuf<long long> a(std::max<int64_t>(L.nnz, 1), s);
     CFC_LAUNCH(LAP_KF_CFC, s, (double)L.nnz * 20, k_jl_terms, grid_for(L.nnz), kBlock, 0, L.rowptr.get(),
                L.col.get(), L.w64.get(), L.deg64.get(), n, L.nnz, inv_k, inv_sqrt_k, a.get());
     const double bytes = (double)L.nnz * (4 + 8) + (double)n * 12 + (double)n * ld * 8;
     CFC_LAUNCH(LAP_KF_CFC, s, bytes, k_jl_short, grid_for((int64_t)n * ncb, 128), 128, 0, L.rowptr.get(),
-               h->eid.get(), a.get(), L.deg64.get(), n, k, ld, seed, inv_k, Y);
+               h->eid.get(), a.get(), L.deg64.get(), n, k, ld, cb_off, seed, inv_k, Y);
     if (L.n_chunks > 0) {
         DBuf<long long> part((size_t)L.n_chunks * ncb * 32, s);
         CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_jl_chunks, grid_for((int64_t)L.n_chunks * ncb, 128), 128, 0,
                    L.rowptr.get(), h->eid.get(), a.get(), L.chunk_row.get(), L.chunk_begin.get(), L.n_chunks, ld,
-                   seed, part.get());
+                   cb_off, seed, part.get());
         CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_jl_long, grid_for((int64_t)L.n_long * ld, 128), 128, 0, L.rowptr.get(),
                    L.deg64.get(), L.chunk_row.get(), L.long_first.get(), L.n_long, k, ld, inv_k, part.get(), Y);
     }
@@ -398,6 +400,16 @@ lap_status_t farness_jl(lap_hierarchy *h, int32_t k, double eps, uint64_t seed, 
         k = (int32_t)std::ceil(std::log((double)n) / (eps * eps));
     }
     CFC_REQUIRE(k >= 1 && k <= 4096, LAP_EINVAL, "need 1 <= k <= 4096");
+    return farness_jl_rows(h, k, 0, k, seed, q, nodes, farness, o, s);
+}
+
+lap_status_t farness_jl_rows(lap_hierarchy *h, int32_t k_total, int32_t row0, int32_t k, uint64_t seed, int32_t q,
+                             const int32_t *nodes, double *farness, const lap_solve_opts_t &o, cudaStream_t s) {
+    const int64_t n = h->lv[0].n;
+    CFC_REQUIRE(k_total >= 1, LAP_EINVAL, "need k_total >= 1");
+    CFC_REQUIRE(row0 >= 0 && row0 % 32 == 0, LAP_EINVAL, "row_begin must be a multiple of 32");
+    CFC_REQUIRE(k >= 1 && k <= 4096 && (int64_t)row0 + k <= k_total, LAP_EINVAL,
+                "need 1 <= row_count <= 4096 and row_begin + row_count <= k_total");
     CFC_REQUIRE(q >= 1 && q <= n, LAP_EINVAL, "need 1 <= q <= n");
     CFC_REQUIRE(farness, LAP_EINVAL, "farness must not be NULL");
     DBuf<int32_t> ntmp;
@@ -407,7 +419,7 @@ lap_status_t farness_jl(lap_hierarchy *h, int32_t k, double eps, uint64_t seed, 
     // added to a column of Z, so the solve skips both mean projections
     const int ld = solve_ld(k, o);
     DBuf<double> Y((size_t)n * ld, s), Z((size_t)n * ld, s);
-    jl_rhs(h, k, ld, seed, Y.get(), s);
+    jl_rhs(h, k_total, row0, k, ld, seed, Y.get(), s);
     lap_status_t st = solve_multi_direct(h, k, Y.get(), Z.get(), o, s, nullptr);
     if (st != LAP_OK && st != LAP_ENOCONV) return st;
     const int P = std::min<int64_t>(2 * num_sms_public(), (n + kRedRows - 1) / kRedRows);
@@ -536,7 +548,7 @@ lap_status_t pivots_api(lap_hierarchy *h, int32_t kk, uint64_t seed, int32_t *pi
 }
 
 lap_status_t farness_sampled(lap_hierarchy *h, int32_t kk, uint64_t seed, int32_t q, const int32_t *nodes,
-                             double *farness, const lap_solve_opts_t &o, cudaStream_t s) {
+                             double *farness, const lap_solve_opts_t &o, cudaStream_t s, lap_solve_info_t *info) {
     const int64_t n = h->lv[0].n;
     CFC_REQUIRE(kk >= 1 && kk <= n, LAP_EINVAL, "need 1 <= n_pivots <= n");
     CFC_REQUIRE(q >= 1 && q <= n, LAP_EINVAL, "need 1 <= q <= n");
@@ -550,7 +562,7 @@ lap_status_t farness_sampled(lap_hierarchy *h, int32_t kk, uint64_t seed, int32_
     DBuf<double> B((size_t)n * kc, s), X((size_t)n * kc, s), f(q, s);
     B.zero(s);
     CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_unit_columns, grid_for(kc), kBlock, 0, piv.get(), kk, dn, q, kc, B.get());
-    lap_status_t st = solve_multi(h, kc, B.get(), X.get(), o, s, nullptr);
+    lap_status_t st = solve_multi(h, kc, B.get(), X.get(), o, s, info);
     if (st != LAP_OK && st != LAP_ENOCONV) return st;
     CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_sample_farness, (q + 7) / 8, 256, 0, X.get(), n, kc, piv.get(), kk, dn, q,
                f.get());

@@ -5,7 +5,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <new>
 #include <string>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <shared_mutex>
 #include <vector>
 
 #include "../../include/cfc_gb300.h"
@@ -21,6 +26,26 @@ struct Error {
 };
 
 void set_last_error(const std::string &s);
+void clear_last_error();
+
+// Runs f and turns what it throws into a status (the text kept for
+// lap_last_error): no C entry point lets an exception through.
+template <class F>
+lap_status_t guard(F &&f) {
+    try {
+        clear_last_error();
+        return f();
+    } catch (const Error &e) {
+        set_last_error(e.what);
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        set_last_error("host allocation failed");
+        return LAP_ENOMEM;
+    } catch (...) {
+        set_last_error("unknown error");
+        return LAP_ECUDA;
+    }
+}
 
 #define CFC_CUDA(call)                                                                         \
     do {                                                                                       \
@@ -139,7 +164,6 @@ struct Level {
     DBuf<int32_t> chunk_long;    // [n_chunks] index of the chunk's long row
     DBuf<int32_t> long_first;    // [n_long + 1] first chunk of each long row
     DBuf<int32_t> long_of_row;   // [n] index of the row among the long rows, -1 if short
-    DBuf<uint32_t> long_count;   // [n_long * max_tiles] arrival counters (zero between launches)
     // map to the next coarser level (empty at the coarsest)
     DBuf<int32_t> agg;           // [n] aggregate (coarse node) of each node
     DBuf<int32_t> mem_ptr, mem;  // members of each coarse node, ascending
@@ -159,7 +183,7 @@ struct LevelView {
     const double *w64, *deg64, *dinv64;
     int32_t n_chunks, n_long;
     const int32_t *chunk_row, *chunk_begin, *chunk_long, *long_first, *long_of_row;
-    uint32_t *long_count;
+    uint32_t *long_count;  // [n_long * kMaxTiles] arrival counters of the launching solve
 };
 LevelView view(const Level &L);
 // The same level with BF16 weights (and the degrees of the rounded weights)
@@ -208,7 +232,7 @@ void dense_spd_inverse_large(double *A, int n, int *d_flag, cudaStream_t s);
 struct lap_hierarchy {
     int device = 0;
     int64_t n = 0, m = 0;
-    std::vector<cfc::Level> lv;
+    std::deque<cfc::Level> lv;        // appending a level leaves the others in place
     cfc::DBuf<int32_t> eid;           // level-0 undirected edge id of each CSR entry
     lap_hier_opts_t hopts{};
     bool complete = false;            // coarsening finished (no further levels)
@@ -216,10 +240,23 @@ struct lap_hierarchy {
     int32_t coarse_n = 0;             // dense coarsest size (0: none)
     cfc::DBuf<double> coarse_inv;     // (L_c + J/n_c)^{-1}, row-major
     double setup_ms = 0;
-    // solve workspace, grown on demand
-    cfc::DBuf<char> ws;
-    size_t ws_bytes = 0;
-    cudaStream_t ws_stream = nullptr;
+    // One solve workspace per stream, grown on demand and reused (stream
+    // order keeps consecutive solves on one stream apart), so solves on
+    // different streams can run on one hierarchy at the same time.
+    struct Workspace {
+        cfc::DBuf<char> buf;
+        size_t bytes = 0;
+        size_t zero_bytes = 0;  // leading bytes known to be zero (arrival counters)
+    };
+    std::mutex ws_mu;
+    std::map<cudaStream_t, Workspace> ws;
+    // exclusive while a call grows the hierarchy (lazy levels, BF16 copies) or
+    // autotunes on it; shared while a solve runs on it
+    mutable std::shared_mutex mu;
+    cudaEvent_t grown = nullptr;  // recorded after the latest growth, on the stream that grew it
+    ~lap_hierarchy() {
+        if (grown) cudaEventDestroy(grown);
+    }
 };
 
 namespace cfc {
@@ -231,20 +268,27 @@ lap_status_t solve_multi_direct(lap_hierarchy *h, int32_t k, const double *B, do
 int solve_ld(int32_t k, const lap_solve_opts_t &o);  // padded column count of the solver's blocks
 int num_sms_public();
 int32_t *pinned_scratch();  // per-thread pinned host buffer of 8192 int32
+// Frees the solve workspace a hierarchy keeps for stream s (stream-ordered).
+void release_workspace(lap_hierarchy *h, cudaStream_t s);
+// Device bytes held by a hierarchy (levels, dense coarsest inverse), workspaces excluded.
+int64_t hierarchy_bytes(const lap_hierarchy *h);
 // amg.cu
 void build_dense(const int32_t *rowptr, const int32_t *col, const double *w, const double *deg, int32_t n,
                  double *M, cudaStream_t s);
 // cfc.cu
-void jl_rhs(lap_hierarchy *h, int k, int ld, uint64_t seed, double *Y, cudaStream_t s);
+// rows row0 .. row0 + k - 1 of the k_total-row Q (row0 a multiple of 32)
+void jl_rhs(lap_hierarchy *h, int k_total, int row0, int k, int ld, uint64_t seed, double *Y, cudaStream_t s);
 lap_status_t farness_jl(lap_hierarchy *h, int32_t k, double eps, uint64_t seed, int32_t q, const int32_t *nodes,
                         double *farness, const lap_solve_opts_t &o, cudaStream_t s);
+lap_status_t farness_jl_rows(lap_hierarchy *h, int32_t k_total, int32_t row0, int32_t k, uint64_t seed, int32_t q,
+                             const int32_t *nodes, double *farness, const lap_solve_opts_t &o, cudaStream_t s);
 lap_status_t farness_from_solution(int64_t n, int32_t k, const double *Z, int32_t q, const int32_t *nodes,
                                    double *farness, cudaStream_t s);
 lap_status_t farness_from_solution_noalloc(int64_t n, int32_t k, const double *Z, int32_t q, const int32_t *nodes,
                                            double *farness, cudaStream_t s);
 lap_status_t pivots_api(lap_hierarchy *h, int32_t kk, uint64_t seed, int32_t *pivots, cudaStream_t s);
 lap_status_t farness_sampled(lap_hierarchy *h, int32_t kk, uint64_t seed, int32_t q, const int32_t *nodes,
-                             double *farness, const lap_solve_opts_t &o, cudaStream_t s);
+                             double *farness, const lap_solve_opts_t &o, cudaStream_t s, lap_solve_info_t *info = nullptr);
 lap_status_t exact_small(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const double *w,
                          double *farness, double *closeness, cudaStream_t s);
 }  // namespace cfc

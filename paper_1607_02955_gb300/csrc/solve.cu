@@ -570,9 +570,19 @@ struct Solver {
     int cycle = 1;       // 1: V-cycle, 2: W-cycle
     int nu_pre, nu_post, nu_coarse;
     bool bf16 = false;  // BF16 weights below the finest level
+    int hsize = 0;      // levels of the hierarchy and its dense coarsest size, as the solve began
+    int32_t coarse_n = 0;
 
     // the finest level always runs on FP32 weights; coarser ones on BF16 in that mode
-    LevelView lv_view(const Level &L) const { return (bf16 && &L != &h->lv[0]) ? view_bf16(L) : view(L); }
+    std::vector<uint32_t *> long_cnt;  // per level: this solve's long-row arrival counters
+
+    LevelView lv_view(const Level &L) const {
+        LevelView v = (bf16 && &L != &h->lv[0]) ? view_bf16(L) : view(L);
+        v.long_count = nullptr;
+        for (size_t l = 0; l < long_cnt.size(); ++l)
+            if (&h->lv[l] == &L) v.long_count = long_cnt[l];
+        return v;
+    }
 
     Solver(lap_hierarchy *h_, cudaStream_t s_, int k_, int ld_, const lap_solve_opts_t &o_)
         : h(h_), s(s_), ld(ld_), ntiles(ld_ / KT), ntiles64(ld_ / K64), k(k_), o(o_) {
@@ -584,8 +594,8 @@ struct Solver {
         cycle = o.cycle == 2 ? 2 : 1;
         gamma = o.coarse_scale > 0.0 ? o.coarse_scale : 1.0;
         bf16 = std::is_same<Tin, float>::value && o.precision == LAP_FP32_BF16COARSE_REFINED;
-        if (bf16)
-            for (int l = 1; l < nlev; ++l) ensure_bf16(h->lv[l], s);
+        hsize = (int)h->lv.size();
+        coarse_n = h->coarse_n;
         setup_smoother();
     }
 
@@ -696,7 +706,7 @@ struct Solver {
                              cs.active_in, cs.active_out};
     }
 
-    bool level0_is_dense() const { return nlev == 1 && h->coarse_n == h->lv[0].n && h->lv.size() == 1; }
+    bool level0_is_dense() const { return nlev == 1 && coarse_n == h->lv[0].n && hsize == 1; }
 
     // ---------------- V-cycle on level l: b = lb[l] -> x = lx[l].
     // first_done: x already holds the first smoothing step e D^{-1} b (fused
@@ -707,7 +717,7 @@ struct Solver {
         const int et = (int)sizeof(Tin);
         const int wb = wbytes(L);
         const bool coarsest = (l == nlev - 1);
-        if (coarsest && h->coarse_n == L.n && l == (int)h->lv.size() - 1) {
+        if (coarsest && coarse_n == L.n && l == hsize - 1) {
             const int nc = L.n;
             const int threads = 128;
             const int blocks = std::max(1, std::min((nc * ld + threads - 1) / threads, 8 * num_sms()));
@@ -738,7 +748,7 @@ struct Solver {
         // the preconditioner symmetric); the coarse level's dense solve is
         // exact, so one correction suffices just above it
         const Level &C = h->lv[l + 1];
-        const bool next_dense = (l + 1 == nlev - 1) && h->coarse_n == C.n && l + 1 == (int)h->lv.size() - 1;
+        const bool next_dense = (l + 1 == nlev - 1) && coarse_n == C.n && l + 1 == hsize - 1;
         const int ncorr = (cycle == 2 && !next_dense) ? 2 : 1;
         for (int cc = 0; cc < ncorr; ++cc) {
             rowop<Tin, 0>(fam_level(l, LAP_KF_RESTRICT_FINE), L, OpResid<Tin>{lv_view(L), cur, lb[l], oth, ld},
@@ -891,6 +901,11 @@ struct Solver {
             info->outer_iters = outer;
             info->inner_iters = inner_total;
             info->max_rel_residual = maxrel;
+            info->k_tile = KT;
+            info->levels_used = nlev;
+            info->nu_coarse = nu_coarse;
+            info->cycle = cycle;
+            info->coarse_scale = gamma;
         }
         return converged ? LAP_OK : LAP_ENOCONV;
     }
@@ -922,7 +937,12 @@ lap_status_t run_solver(lap_hierarchy *h, int32_t k, const double *B, double *X,
     int64_t max_chunks = 0;
     for (int l = 0; l < nlev; ++l) max_chunks = std::max<int64_t>(max_chunks, h->lv[l].n_chunks);
     std::vector<size_t> sizes;
-    sizes.push_back(align_up(kMaxTiles * 4 + kMaxTiles * kMaxTeams * 4));  // arrival counters (first)
+    int64_t n_long_total = 0;
+    for (int l = 0; l < nlev; ++l) n_long_total += h->lv[l].n_long;
+    // arrival counters first: reduction tickets, then the long-row counters
+    // of every level; zero at allocation, and every launch leaves them zero
+    const size_t counter_bytes = align_up(kMaxTiles * 4 + kMaxTiles * kMaxTeams * 4 + n_long_total * kMaxTiles * 4);
+    sizes.push_back(counter_bytes);
     sizes.push_back(align_up(n0 * ld * 8));  // b64
     sizes.push_back(align_up(n0 * ld * 8));  // x64
     sizes.push_back(align_up(n0 * ld * sizeof(Tin)));  // r
@@ -949,12 +969,23 @@ lap_status_t run_solver(lap_hierarchy *h, int32_t k, const double *B, double *X,
     sizes.push_back(align_up(ld * 4) * 2);                        // column flags
     size_t total = 0;
     for (size_t z : sizes) total += z;
-    if (h->ws_bytes < total) {
-        h->ws.release();
-        h->ws.alloc_persistent(total);
-        h->ws_bytes = total;
+    char *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(h->ws_mu);
+        lap_hierarchy::Workspace &w = h->ws[s];
+        if (w.bytes < total) {
+            w.buf.release();  // stream-ordered: after this stream's earlier solves
+            w.buf.alloc(total, s);
+            w.bytes = total;
+            w.zero_bytes = 0;
+        }
+        // after a solve exactly its counter region is known to be zero; a
+        // larger region (more levels) also covers former data
+        if (counter_bytes > w.zero_bytes)
+            CFC_CUDA(cudaMemsetAsync(w.buf.get() + w.zero_bytes, 0, counter_bytes - w.zero_bytes, s));
+        w.zero_bytes = counter_bytes;
+        base = w.buf.get();
     }
-    char *base = h->ws.get();
     size_t off = 0;
     auto take = [&](size_t i) {
         char *p = base + off;
@@ -965,6 +996,14 @@ lap_status_t run_solver(lap_hierarchy *h, int32_t k, const double *B, double *X,
     size_t idx = 0;
     S.rb.counter = (uint32_t *)take(idx++);
     S.rb.team_counter = S.rb.counter + kMaxTiles;
+    {
+        uint32_t *c = S.rb.team_counter + (size_t)kMaxTiles * kMaxTeams;
+        S.long_cnt.assign(nlev, nullptr);
+        for (int l = 0; l < nlev; ++l) {
+            S.long_cnt[l] = c;
+            c += (size_t)h->lv[l].n_long * kMaxTiles;
+        }
+    }
     S.b64 = (double *)take(idx++);
     S.x64 = (double *)take(idx++);
     S.direct = direct;
@@ -1089,31 +1128,14 @@ int solve_ld(int32_t k, const lap_solve_opts_t &o) {
 }
 
 namespace {
-lap_status_t solve_impl(lap_hierarchy *h, int32_t k, const double *B, double *X, const lap_solve_opts_t &o_in,
-                        cudaStream_t s, lap_solve_info_t *info, bool direct) {
-    CFC_REQUIRE(k >= 1 && k <= 4096, LAP_EINVAL, "need 1 <= k <= 4096");
-    CFC_REQUIRE(B && X && B != X, LAP_EINVAL, "B and X must be distinct device buffers");
-    CFC_REQUIRE(is_device_pointer(B) && is_device_pointer(X), LAP_EINVAL, "B and X must be device pointers");
-    CFC_REQUIRE(o_in.tol > 0 && o_in.max_outer >= 0 && o_in.max_inner >= 1, LAP_EINVAL, "bad solve options");
-    CFC_REQUIRE(o_in.precision == LAP_FP64 || o_in.precision == LAP_FP32_REFINED ||
-                    o_in.precision == LAP_FP32_BF16COARSE_REFINED,
-                LAP_EINVAL, "unknown precision mode");
-    lap_solve_opts_t o = o_in;
-    const bool fp64 = (o.precision == LAP_FP64);
-    const int kt = solve_tile(k, o);
-    CFC_REQUIRE(kt == 16 || kt == 32 || kt == 64 || (kt == 128 && !fp64), LAP_EINVAL, "k_tile must be 16/32/64/128");
-    if (o.levels_used > 0) {
-        grow_levels(*h, o.levels_used, s);
-        return dispatch(h, k, B, X, o, s, info, kt, direct);
-    }
-    if (o.levels_used < 0) {  // every level
-        grow_levels(*h, 0, s);
-        o.levels_used = 0;
-        return dispatch(h, k, B, X, o, s, info, kt, direct);
-    }
-    // autotuned: tile width (when not given), depth, smoother degree, cycle
-    // shape and coarse scale (those not given), chosen by timing complete
-    // solves the first time a graph size and configuration is seen
+// Autotuned configuration (caller holds the hierarchy exclusively): tile
+// width (when not given), depth, smoother degree, cycle shape and coarse
+// scale (those not given), chosen by timing complete solves the first time a
+// graph size and configuration is seen.  Leaves the choice in o and returns
+// its tile width.
+template <class PrepareBf16>
+int tune(lap_hierarchy *h, int32_t k, const double *B, double *X, lap_solve_opts_t &o, cudaStream_t s,
+         lap_solve_info_t *info, int kt, bool direct, PrepareBf16 &&prepare_bf16) {
     const TuneKey key{h->lv[0].n, h->lv[0].nnz,  k,         o.precision, o.k_tile,
                       o.smoother, o.nu_pre,      o.nu_post, o.nu_coarse, o.cycle, o.coarse_scale};
     auto apply = [&](const TuneChoice &c, lap_solve_opts_t &oo) {
@@ -1128,17 +1150,25 @@ lap_status_t solve_impl(lap_hierarchy *h, int32_t k, const double *B, double *X,
         if (it != g_tune.end()) {
             apply(it->second, o);
             grow_levels(*h, o.levels_used, s);
-            return dispatch(h, k, B, X, o, s, info, it->second.kt, direct);
+            return it->second.kt;
         }
     }
     grow_levels(*h, 0, s);
     const int L = (int)h->lv.size();
+    prepare_bf16(L);
     const int nc_default = o.nu_coarse > 0 ? o.nu_coarse : std::max(std::max(1, o.nu_pre), 4);
     const int cyc_default = o.cycle > 0 ? o.cycle : 1;
     const double sc_default = o.coarse_scale > 0.0 ? o.coarse_scale : 1.0;
     cudaEvent_t e0, e1;
     CFC_CUDA(cudaEventCreate(&e0));
     CFC_CUDA(cudaEventCreate(&e1));
+    struct EvGuard {
+        cudaEvent_t a, b;
+        ~EvGuard() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } evg{e0, e1};
     const bool verbose = std::getenv("LAP_TUNE_VERBOSE") != nullptr;
     lap_solve_opts_t trial_o = o;
     trial_o.max_outer = std::min(o.max_outer, 4);  // a failing candidate should not run long
@@ -1213,11 +1243,9 @@ lap_status_t solve_impl(lap_hierarchy *h, int32_t k, const double *B, double *X,
             trial(c);
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (best < 0) {  // nothing converged within the trial cap: one full-length attempt
+    if (best < 0) {  // nothing converged within the trial cap: one full-length attempt at full depth
         apply({kt, L, nc_default, cyc_default, sc_default}, o);
-        return dispatch(h, k, B, X, o, s, info, kt, direct);
+        return kt;
     }
     const TuneChoice choice = tried[best];
     {
@@ -1225,7 +1253,56 @@ lap_status_t solve_impl(lap_hierarchy *h, int32_t k, const double *B, double *X,
         g_tune[key] = choice;
     }
     apply(choice, o);
-    return dispatch(h, k, B, X, o, s, info, choice.kt, direct);
+    return choice.kt;
+}
+
+lap_status_t solve_impl(lap_hierarchy *h, int32_t k, const double *B, double *X, const lap_solve_opts_t &o_in,
+                        cudaStream_t s, lap_solve_info_t *info, bool direct) {
+    CFC_REQUIRE(k >= 1 && k <= 4096, LAP_EINVAL, "need 1 <= k <= 4096");
+    CFC_REQUIRE(B && X && B != X, LAP_EINVAL, "B and X must be distinct device buffers");
+    CFC_REQUIRE(is_device_pointer(B) && is_device_pointer(X), LAP_EINVAL, "B and X must be device pointers");
+    CFC_REQUIRE(o_in.tol > 0 && o_in.max_outer >= 0 && o_in.max_inner >= 1, LAP_EINVAL, "bad solve options");
+    CFC_REQUIRE(o_in.precision == LAP_FP64 || o_in.precision == LAP_FP32_REFINED ||
+                    o_in.precision == LAP_FP32_BF16COARSE_REFINED,
+                LAP_EINVAL, "unknown precision mode");
+    lap_solve_opts_t o = o_in;
+    const bool fp64 = (o.precision == LAP_FP64);
+    const int kt = solve_tile(k, o);
+    CFC_REQUIRE(kt == 16 || kt == 32 || kt == 64 || (kt == 128 && !fp64), LAP_EINVAL, "k_tile must be 16/32/64/128");
+    int kt_run = kt;
+    {
+        // phase 1, exclusive: settle the configuration and build what it needs
+        // (lazy levels, BF16 copies, autotuning trials), all on this stream
+        std::unique_lock<std::shared_mutex> ex(h->mu);
+        const size_t levels_before = h->lv.size();
+        int bf16_made = 0;
+        auto prepare_bf16 = [&](int upto) {
+            if (o.precision != LAP_FP32_BF16COARSE_REFINED) return;
+            for (int l = 1; l < upto && l < (int)h->lv.size(); ++l)
+                if (!h->lv[l].wbf.get()) {
+                    ensure_bf16(h->lv[l], s);
+                    ++bf16_made;
+                }
+        };
+        if (o.levels_used > 0) {
+            grow_levels(*h, o.levels_used, s);
+        } else if (o.levels_used < 0) {  // every level
+            grow_levels(*h, 0, s);
+            o.levels_used = 0;
+        } else {
+            kt_run = tune(h, k, B, X, o, s, info, kt, direct, prepare_bf16);
+        }
+        prepare_bf16(o.levels_used > 0 ? o.levels_used : (int)h->lv.size());
+        if (h->lv.size() != levels_before || bf16_made > 0) {
+            // solves on other streams wait for what this call built
+            if (!h->grown) CFC_CUDA(cudaEventCreateWithFlags(&h->grown, cudaEventDisableTiming));
+            CFC_CUDA(cudaEventRecord(h->grown, s));
+        }
+    }
+    // phase 2, shared: the solve itself (solves on other streams may run alongside)
+    std::shared_lock<std::shared_mutex> sh(h->mu);
+    if (h->grown) CFC_CUDA(cudaStreamWaitEvent(s, h->grown, 0));
+    return dispatch(h, k, B, X, o, s, info, kt_run, direct);
 }
 
 }  // namespace

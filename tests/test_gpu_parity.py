@@ -203,6 +203,32 @@ def test_farness_jl_matches_oracle(P, gen, k, precision):
     assert _rel(f, fo) <= FARNESS_RTOL
 
 
+@pytest.mark.parametrize("k,world", [(64, 2), (100, 3), (40, 4)])
+def test_farness_jl_row_shards_sum_to_the_full_query(P, k, world):
+    from paper_1607_02955_gb300.sharding import shard_rows
+    n, s, d, w = _graph(synth.barabasi_albert(2500, 5, seed=8))
+    g = canonical_graph(n, s, d, w)
+    h = P.lap_build_hierarchy(n, s, d, w)
+    nodes = np.array([0, 5, n - 1], np.int32)
+    full = P.cfc_farness_jl(h, k, 3, nodes)
+    Z = jl.jl_solve(g, jl.jl_rhs(g, k, 3))  # k x n, oracle
+    total = np.zeros(len(nodes))
+    for r in range(world):
+        r0, c = shard_rows(k, world, r)
+        if c == 0:
+            continue
+        part = P.cfc_farness_jl_rows(h, k, r0, c, 3, nodes)
+        rows = Z[r0:r0 + c]
+        want = np.array([((rows - rows[:, [v]]) ** 2).sum() for v in nodes])
+        assert _rel(part, want) <= FARNESS_RTOL
+        total += part
+    # separate solves stop at different iterations (all columns of a block
+    # iterate until the slowest converges): equal to the solve tolerance
+    assert _rel(total, full) <= FARNESS_RTOL
+    with pytest.raises(P.LapError):  # shards start on a multiple of 32 rows
+        P.cfc_farness_jl_rows(h, k, 16, 8, 3, nodes)
+
+
 def test_bf16_coarse_changes_only_the_preconditioner(P):
     # same FP64 stopping test: both modes reach 1e-8 and agree to the solve
     # tolerance; the coarse operators differ, so the inner iterations may differ
