@@ -63,6 +63,78 @@ def make_graph(wl):
     return n, s, d, w
 
 
+# resident graphs of the serving mix: grids 256^2 .. 1024^2, BA n = 10k .. 500k,
+# R-MAT scales 14 .. 21 (LCC); unit weights on grids and R-MAT, U[1, 2) on BA
+SERVE_GRAPHS = ([dict(kind="grid", a=a) for a in (256, 384, 512, 768, 1024)] +
+                [dict(kind="ba", n=n, m_per=5, seed=4) for n in (10000, 30000, 100000, 200000, 500000)] +
+                [dict(kind="rmat", scale=sc, seed=4) for sc in (14, 16, 18, 19, 20, 21)])
+# the small mix reported beside every default line
+SERVE_SMALL = [dict(kind="grid", a=256), dict(kind="ba", n=100000, m_per=5, seed=2), dict(kind="rmat", scale=16, seed=4)]
+
+
+def run_serving(P, specs, n_queries, loads, seed=4, n_pivots=200, slots=4):
+    """Continuous-batching request loop on resident graphs (cfc_server_*):
+    a burst of requests measures the saturation rate, then for each load
+    factor Poisson arrivals at that fraction of it; latencies (submit ->
+    result) come from the server.  Query: 1..32 nodes of a uniformly chosen
+    graph, the sampling estimator with n_pivots pivots."""
+    rng = np.random.default_rng(seed)
+    sv = P.cfc_server_create(P.cfc_server_default_opts(slots=slots))
+    t0 = time.time()
+    sizes = []
+    for spec in specs:
+        n, s, d, w = make_graph(spec)
+        P.cfc_server_add_graph(sv, n, s, d, w)
+        sizes.append(n)
+    add_s = time.time() - t0
+
+    def queries(count):
+        out = []
+        for _ in range(count):
+            g = int(rng.integers(len(sizes)))
+            q = int(rng.integers(1, 33))
+            nodes = rng.choice(sizes[g], size=q, replace=False).astype(np.int32)
+            out.append((g, nodes, int(rng.integers(1 << 40))))
+        return out
+
+    def burst(qs):
+        P.cfc_server_reset_stats(sv)
+        ids = [P.cfc_server_submit(sv, g, nodes, n_pivots, sd) for g, nodes, sd in qs]
+        for r in ids:
+            P.cfc_server_poll(sv, r, -1, q=32)
+        return P.cfc_server_stats(sv)
+
+    burst(queries(2 * slots))  # warm-up
+    sat = burst(queries(n_queries))
+    result = {"graphs": len(specs), "nodes_max": max(sizes), "slots": slots, "n_pivots": n_pivots,
+              "queries_per_load": n_queries, "add_graphs_s": add_s,
+              "saturation": {"queries_per_s": sat["queries_per_s"], "rhs_per_s": sat["rhs_per_s"],
+                             "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"],
+                             "max_in_flight": sat["max_in_flight"]},
+              "loads": []}
+    for f in loads:
+        rate = f * sat["queries_per_s"]
+        qs = queries(n_queries)
+        gaps = rng.exponential(1.0 / rate, size=len(qs))
+        P.cfc_server_reset_stats(sv)
+        ids = []
+        t_next = time.perf_counter()
+        for (g, nodes, sd), gap in zip(qs, gaps):
+            t_next += gap
+            dt = t_next - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            ids.append(P.cfc_server_submit(sv, g, nodes, n_pivots, sd))
+        for r in ids:
+            P.cfc_server_poll(sv, r, -1, q=32)
+        st = P.cfc_server_stats(sv)
+        result["loads"].append({"load": f, "offered_qps": rate, "queries_per_s": st["queries_per_s"],
+                                "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+                                "max_in_flight": st["max_in_flight"]})
+    sv.destroy()
+    return result
+
+
 def kernel_source_digest():
     import hashlib
     h = hashlib.sha256()
@@ -294,13 +366,32 @@ def cpu_baseline(wl):
             "sample": f"{ks} of the {wl['k']} JL right-hand sides (canonical graph + RHS + FP64 Jacobi-CG to 1e-8)"}
 
 
+def serve_main(args):
+    """The serving mix: 16 resident graphs, Poisson arrivals at 0.25, 0.5 and
+    0.8 of the measured saturation rate, p50/p99 latency."""
+    import torch
+    torch.cuda.init()
+    import paper_1607_02955_gb300 as P
+    from paper_1607_02955_gb300 import build_ext
+    build_ext.build()
+    r = run_serving(P, SERVE_GRAPHS, n_queries=max(64, 16 * args.steps), loads=(0.25, 0.5, 0.8))
+    mid = r["loads"][1]
+    print(json.dumps({"metric": "query p99 latency at 0.5x saturation", "value": mid["p99_ms"], "unit": "ms",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+                      "scaling": "none", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                      "config": {"workload": "serve_mix", "estimator": "sampling, 200 pivots per query",
+                                 "query_nodes": "1..32 uniform", "arrivals": "Poisson"},
+                      "serving": r}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ba100k_jl64", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="ba100k_jl64", choices=sorted(WORKLOADS) + ["serve_mix"])
+    ap.add_argument("--no-serving", action="store_true", help="skip the small serving mix of the default line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the solve-only FP64 batched / one-RHS comparison")
@@ -320,6 +411,9 @@ def main():
         return
     if args.write_traffic:
         write_traffic(*args.write_traffic)
+        return
+    if args.workload == "serve_mix":
+        serve_main(args)
         return
     wl = WORKLOADS[args.workload]
     rank, world, local = dist_setup(args.gpus)
@@ -490,6 +584,8 @@ def main():
             "precision_comparison": compare,
             "clocks": clocks,
         }
+        if world == 1 and not args.no_serving:
+            line["serving"] = run_serving(P, SERVE_SMALL, n_queries=48, loads=(0.5,))
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl)
         print(json.dumps(line), flush=True)
