@@ -433,13 +433,16 @@ void finish_level(Level &L, cudaStream_t s) {
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_finish, grid_for(std::max<int64_t>(nnz, n)), kBlock, 0, L.rowptr.get(),
                L.w64.get(), L.deg64.get(), n, nnz, L.w32.get(), L.deg32.get(), L.dinv32.get(), L.dinv64.get(),
                nchunk.get());
-    L.n_chunks = (int32_t)scan_exclusive_i32(nchunk.get(), cfirst.get(), n, s);
-    if (L.n_chunks == 0) {
-        L.n_long = 0;
-        return;
-    }
+    // both counts come back with one synchronisation
+    DBuf<int64_t> tot(2, s);
+    scan_exclusive_i32_total(nchunk.get(), cfirst.get(), n, tot.get(), s);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_long_index, grid_for(n), kBlock, 0, nchunk.get(), n, isl.get());
-    L.n_long = (int32_t)scan_exclusive_i32(isl.get(), lidx.get(), n, s);
+    scan_exclusive_i32_total(isl.get(), lidx.get(), n, tot.get() + 1, s);
+    int64_t h[2];
+    read_totals(tot.get(), 2, h, s);
+    L.n_chunks = (int32_t)h[0];
+    L.n_long = (int32_t)h[1];
+    if (L.n_chunks == 0) return;
     L.chunk_row.alloc_persistent(L.n_chunks);
     L.chunk_begin.alloc_persistent(L.n_chunks);
     L.chunk_long.alloc_persistent(L.n_chunks);

@@ -195,17 +195,20 @@ void ingest(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const 
     const int32_t *dd = to_device(dst, m, td, s);
     const double *dw = to_device(w, m, tw, s);
 
-    DBuf<int32_t> flag(1, s), keep(m, s), pos(m, s);
-    flag.zero(s);
+    // device scalars read back in batches: [0] invalid-edge flag, [1] kept
+    // edges, [2] merged entries, [3] union-find roots
+    DBuf<int64_t> tot(4, s);
+    tot.zero(s);
+    DBuf<int32_t> keep(m, s), pos(m, s);
     const double eb = (double)m * (8.0 + (w ? 8.0 : 0.0));
-    CFC_LAUNCH(LAP_KF_SETUP, s, eb, k_validate, grid_for(m), kBlock, 0, ds, dd, dw, m, (int32_t)n, flag.get(),
-               keep.get());
-    int32_t hflag = 0;
-    CFC_CUDA(cudaMemcpyAsync(&hflag, flag.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    CFC_CUDA(cudaStreamSynchronize(s));
-    CFC_REQUIRE(hflag == 0, LAP_EINVAL, "edge endpoint out of range or weight not finite and > 0");
-
-    const int64_t kept = scan_exclusive_i32(keep.get(), pos.get(), m, s);
+    // invalid edges get keep = 0, so nothing downstream reads them before the flag is checked
+    CFC_LAUNCH(LAP_KF_SETUP, s, eb, k_validate, grid_for(m), kBlock, 0, ds, dd, dw, m, (int32_t)n,
+               reinterpret_cast<int32_t *>(tot.get()), keep.get());
+    scan_exclusive_i32_total(keep.get(), pos.get(), m, tot.get() + 1, s);
+    int64_t h[4];
+    read_totals(tot.get(), 2, h, s);
+    CFC_REQUIRE(h[0] == 0, LAP_EINVAL, "edge endpoint out of range or weight not finite and > 0");
+    const int64_t kept = h[1];
     CFC_REQUIRE(kept > 0, LAP_ENOTCONN, "graph has no edges besides self-loops");
     const int64_t len = 2 * kept;
     const int b = bits_for(n);
@@ -219,7 +222,9 @@ void ingest(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const 
 
     DBuf<int32_t> head(len, s), hpos(len, s);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_heads, grid_for(len), kBlock, 0, keys.get(), len, head.get());
-    const int64_t nnz = scan_exclusive_i32(head.get(), hpos.get(), len, s);
+    scan_exclusive_i32_total(head.get(), hpos.get(), len, tot.get() + 2, s);
+    read_totals(tot.get() + 2, 1, h + 2, s);
+    const int64_t nnz = h[2];
 
     out.n = (int32_t)n;
     out.nnz = nnz;
@@ -237,7 +242,7 @@ void ingest(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const 
     vals.release();
     head.release();
     hpos.release();
-    scan_exclusive_i32(rowcnt.get(), out.rowptr.get(), n, s);
+    scan_exclusive_i32_async(rowcnt.get(), out.rowptr.get(), n, s);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_finish_rowptr, 1, 1, 0, out.rowptr.get(), (int32_t)n, (int32_t)nnz);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_row_sums, grid_for(32 * n), kBlock, 0, out.rowptr.get(), out.w.get(),
                (int32_t)n, out.deg.get());
@@ -246,23 +251,20 @@ void ingest(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const 
     DBuf<int32_t> up(nnz, s);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_upper_flags, grid_for(nnz), kBlock, 0, row_of.get(), out.col.get(), nnz,
                up.get());
-    scan_exclusive_i32(up.get(), out.eid.get(), nnz, s);
+    scan_exclusive_i32_async(up.get(), out.eid.get(), nnz, s);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_mirror_eid, grid_for(nnz), kBlock, 0, out.rowptr.get(), row_of.get(),
                out.col.get(), nnz, out.eid.get());
 
     // connectivity
-    DBuf<int32_t> par(n, s), roots(1, s);
-    roots.zero(s);
+    DBuf<int32_t> par(n, s);
+    int32_t *roots = reinterpret_cast<int32_t *>(tot.get() + 3);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_uf_init, grid_for(n), kBlock, 0, out.rowptr.get(), out.col.get(), par.get(),
                (int32_t)n);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_uf_hook, grid_for(nnz), kBlock, 0, row_of.get(), out.col.get(), nnz,
                par.get());
-    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_uf_count_roots, grid_for(n), kBlock, 0, par.get(), (int32_t)n,
-               roots.get());
-    int32_t hroots = 0;
-    CFC_CUDA(cudaMemcpyAsync(&hroots, roots.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    CFC_CUDA(cudaStreamSynchronize(s));
-    CFC_REQUIRE(hroots == 1, LAP_ENOTCONN, "graph is not connected");
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_uf_count_roots, grid_for(n), kBlock, 0, par.get(), (int32_t)n, roots);
+    read_totals(tot.get() + 3, 1, h + 3, s);
+    CFC_REQUIRE(h[3] == 1, LAP_ENOTCONN, "graph is not connected");
 }
 
 }  // namespace cfc

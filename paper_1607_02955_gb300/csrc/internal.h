@@ -194,6 +194,13 @@ LevelView view_bf16(const Level &L);
 // Exclusive prefix sum of n int32 or int64 values; returns the total.
 int64_t scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
 int64_t scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
+// The same scan without the total: nothing waits for the device.
+void scan_exclusive_i32_async(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
+// The same scan with its total written to *d_total (device); nothing waits.
+void scan_exclusive_i32_total(const int32_t *in, int32_t *out, int64_t n, int64_t *d_total, cudaStream_t s);
+// Copies `count` int64 device values to the host with one synchronisation.
+void read_totals(const int64_t *d_totals, int count, int64_t *host, cudaStream_t s);
+int64_t *pinned_small();  // per-thread pinned host buffer of 64 int64
 // Stable LSD radix sort of (key, value) pairs on the low `bits` key bits.
 // keys/vals are sorted in place (scratch is allocated internally).
 void radix_sort_pairs(uint64_t *keys, uint32_t *vals, int64_t n, int bits, cudaStream_t s);

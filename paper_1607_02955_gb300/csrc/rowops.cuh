@@ -328,29 +328,60 @@ __device__ __forceinline__ T lwk(const LevelView &A, int e) {
 }
 
 // sum_{e in [e0, e1)} w_e x_{col(e)} for this lane's columns.  Every round
-// puts four neighbours (eight 16-byte gathers) in flight per lane; the last
-// round of a row is masked rather than finished one neighbour at a time, so
-// a row of length d costs ceil(d / 4) gather latencies.
-template <typename T, bool BF, class Op>
-__device__ __forceinline__ typename Vec<T>::V row_sum(const LevelView &A, const Op &op, int e0, int e1, int c0) {
+// puts four neighbours (eight 16-byte gathers) in flight per lane, the last
+// round of a row masked, so a row of length d costs ceil(d / 4) gather
+// latencies.  In the FP64 kernels (16-lane groups at 64 columns) the G lanes
+// of a row group first load up to G column indices and weights of the row in
+// one coalesced access (lane l takes entry e + l) and hand them out by
+// shuffles: measured 4-10 % faster there, and slower for the FP32 kernels,
+// whose index loads are not what limits them.
+template <typename T, bool BF, int G, class Op>
+__device__ __forceinline__ typename Vec<T>::V row_sum(const LevelView &A, const Op &op, int e0, int e1, int c0,
+                                                     int lane) {
     using V = typename Vec<T>::V;
     V s0 = vzero<V>(), s1 = vzero<V>();
-    for (int e = e0; e < e1; e += 4) {
-        int j[4];
-        T w[4];
+    if constexpr (G >= 4 && std::is_same<T, double>::value) {
+        // the group's lanes within the warp (G divides 32)
+        const unsigned gmask = (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) << ((threadIdx.x & 31) & ~(G - 1));
+        for (int eb = e0; eb < e1; eb += G) {
+            const int my = eb + lane;
+            const int jj = my < e1 ? __ldg(A.col + my) : -1;
+            const T ww = my < e1 ? lwk<T, BF>(A, my) : T(0);
+            const int cnt = min(G, e1 - eb);
+            for (int u = 0; u < cnt; u += 4) {
+                int j[4];
+                T w[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const bool ok = e + u < e1;
-            j[u] = ok ? __ldg(A.col + e + u) : -1;
-            w[u] = ok ? lwk<T, BF>(A, e + u) : T(0);
+                for (int q = 0; q < 4; ++q) {
+                    j[q] = __shfl_sync(gmask, jj, u + q, G);  // u + q < G: cnt <= G and G % 4 == 0
+                    w[q] = __shfl_sync(gmask, ww, u + q, G);
+                }
+                V x[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) x[q] = j[q] >= 0 ? op.gather(j[q], c0) : vzero<V>();
+#pragma unroll
+                for (int q = 0; q < 4; ++q) vfma(s0, w[q], x[q]);  // one accumulator: registers are the limit
+            }
         }
-        V x[4];
+        return s0;
+    } else {
+        for (int e = e0; e < e1; e += 4) {
+            int j[4];
+            T w[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) x[u] = j[u] >= 0 ? op.gather(j[u], c0) : vzero<V>();
-        vfma(s0, w[0], x[0]);
-        vfma(s1, w[1], x[1]);
-        vfma(s0, w[2], x[2]);
-        vfma(s1, w[3], x[3]);
+            for (int u = 0; u < 4; ++u) {
+                const bool ok = e + u < e1;
+                j[u] = ok ? __ldg(A.col + e + u) : -1;
+                w[u] = ok ? lwk<T, BF>(A, e + u) : T(0);
+            }
+            V x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = j[u] >= 0 ? op.gather(j[u], c0) : vzero<V>();
+            vfma(s0, w[0], x[0]);
+            vfma(s1, w[1], x[1]);
+            vfma(s0, w[2], x[2]);
+            vfma(s1, w[3], x[3]);
+        }
     }
     return vadd(s0, s1);
 }
@@ -378,7 +409,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_chunk_sums(LevelView A, Op op, T 
     const int i = __ldg(A.chunk_row + ch);
     const int e0 = __ldg(A.chunk_begin + ch);
     const int e1 = min(e0 + kChunk, __ldg(A.rowptr + i + 1));
-    vst<T>(chunk_part + (size_t)ch * ld_part + c0, row_sum<T, BF>(A, op, e0, e1, c0));
+    vst<T>(chunk_part + (size_t)ch * ld_part + c0, row_sum<T, BF, G>(A, op, e0, e1, c0, lane));
 }
 
 // How rows longer than kLongRow are handled:
@@ -417,7 +448,7 @@ __global__ void __launch_bounds__(kBlock, (NR >= 3 ? 3 : 4)) k_rowop(LevelView A
                 const int e0 = __ldg(A.rowptr + i), e1 = __ldg(A.rowptr + i + 1);
                 if (e1 - e0 <= kLongRow) {
                     const auto pr = op.pre(i, c0);  // own-row operands, in flight with the gathers
-                    const V s = row_sum<T, BF>(A, op, e0, e1, c0);
+                    const V s = row_sum<T, BF, G>(A, op, e0, e1, c0, lane);
                     op.epi(i, c0, s, pr, acc);
                 } else if (PRE) {
                     const auto pr = op.pre(i, c0);
@@ -436,7 +467,7 @@ __global__ void __launch_bounds__(kBlock, (NR >= 3 ? 3 : 4)) k_rowop(LevelView A
                 i = __ldg(A.chunk_row + ch);
                 const int e0 = __ldg(A.chunk_begin + ch);
                 const int e1 = min(e0 + kChunk, __ldg(A.rowptr + i + 1));
-                const V s = row_sum<T, BF>(A, op, e0, e1, c0);
+                const V s = row_sum<T, BF, G>(A, op, e0, e1, c0, lane);
                 vst<T>(chunk_part + (size_t)ch * ld_part + c0, s);
                 __threadfence();
             }
