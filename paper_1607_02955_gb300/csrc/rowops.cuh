@@ -22,9 +22,12 @@
 
 namespace cfc {
 
-// A lane owns VW consecutive columns held as two native 16-byte vectors
-// (8 floats or 4 doubles): two gathers of 16 bytes per neighbour per lane,
-// twice the rows in flight per thread of one-vector lanes.
+// A lane owns VW consecutive columns: 8 floats or 4 doubles, 32 bytes, moved
+// by one 256-bit load or store (sm_100 and later).  A row group of KT/VW
+// lanes thus reads a neighbour's tile row as one contiguous run with one
+// instruction per lane: two 16-byte accesses per lane would touch every
+// 32-byte sector of the run twice, in two instructions.  Every block of
+// vectors is 32-byte aligned (checked on the host before a solve).
 struct f8 {
     float4 a, b;
 };
@@ -56,51 +59,64 @@ __device__ __forceinline__ d4 vzero<d4>() {
     return d4{make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
 }
 
+#define CFC_V8F_OUT(v) "=f"(v.a.x), "=f"(v.a.y), "=f"(v.a.z), "=f"(v.a.w), "=f"(v.b.x), "=f"(v.b.y), "=f"(v.b.z), "=f"(v.b.w)
+#define CFC_V4D_OUT(v) "=d"(v.a.x), "=d"(v.a.y), "=d"(v.b.x), "=d"(v.b.y)
+
+// plain load (data this kernel may also write)
 template <typename T>
 __device__ __forceinline__ typename Vec<T>::V vld(const T *p);
 template <>
 __device__ __forceinline__ f8 vld<float>(const float *p) {
-    const float4 *q = reinterpret_cast<const float4 *>(p);
-    return f8{q[0], q[1]};
+    f8 v;
+    asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];" : CFC_V8F_OUT(v) : "l"(p) : "memory");
+    return v;
 }
 template <>
 __device__ __forceinline__ d4 vld<double>(const double *p) {
-    const double2 *q = reinterpret_cast<const double2 *>(p);
-    return d4{q[0], q[1]};
+    d4 v;
+    asm volatile("ld.global.v4.f64 {%0, %1, %2, %3}, [%4];" : CFC_V4D_OUT(v) : "l"(p) : "memory");
+    return v;
 }
+// read-only path (data no thread of the kernel writes)
 template <typename T>
-__device__ __forceinline__ typename Vec<T>::V vldg(const T *p);  // read-only path
+__device__ __forceinline__ typename Vec<T>::V vldg(const T *p);
 template <>
 __device__ __forceinline__ f8 vldg<float>(const float *p) {
-    const float4 *q = reinterpret_cast<const float4 *>(p);
-    return f8{__ldg(q), __ldg(q + 1)};
+    f8 v;
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];" : CFC_V8F_OUT(v) : "l"(p));
+    return v;
 }
 template <>
 __device__ __forceinline__ d4 vldg<double>(const double *p) {
-    const double2 *q = reinterpret_cast<const double2 *>(p);
-    return d4{__ldg(q), __ldg(q + 1)};
+    d4 v;
+    asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];" : CFC_V4D_OUT(v) : "l"(p));
+    return v;
 }
+// L2 only, coherent across blocks (data other blocks of this kernel wrote)
 template <typename T>
-__device__ __forceinline__ typename Vec<T>::V vldcg(const T *p);  // L2, coherent across blocks
+__device__ __forceinline__ typename Vec<T>::V vldcg(const T *p);
 template <>
 __device__ __forceinline__ f8 vldcg<float>(const float *p) {
-    const float4 *q = reinterpret_cast<const float4 *>(p);
-    return f8{__ldcg(q), __ldcg(q + 1)};
+    f8 v;
+    asm volatile("ld.global.cg.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];" : CFC_V8F_OUT(v) : "l"(p) : "memory");
+    return v;
 }
 template <>
 __device__ __forceinline__ d4 vldcg<double>(const double *p) {
-    const double2 *q = reinterpret_cast<const double2 *>(p);
-    return d4{__ldcg(q), __ldcg(q + 1)};
+    d4 v;
+    asm volatile("ld.global.cg.v4.f64 {%0, %1, %2, %3}, [%4];" : CFC_V4D_OUT(v) : "l"(p) : "memory");
+    return v;
 }
+#undef CFC_V8F_OUT
+#undef CFC_V4D_OUT
 __device__ __forceinline__ void vst_(float *p, const f8 &v) {
-    float4 *q = reinterpret_cast<float4 *>(p);
-    q[0] = v.a;
-    q[1] = v.b;
+    asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(v.a.x), "f"(v.a.y),
+                 "f"(v.a.z), "f"(v.a.w), "f"(v.b.x), "f"(v.b.y), "f"(v.b.z), "f"(v.b.w)
+                 : "memory");
 }
 __device__ __forceinline__ void vst_(double *p, const d4 &v) {
-    double2 *q = reinterpret_cast<double2 *>(p);
-    q[0] = v.a;
-    q[1] = v.b;
+    asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(p), "d"(v.a.x), "d"(v.a.y), "d"(v.b.x), "d"(v.b.y)
+                 : "memory");
 }
 template <typename T>
 __device__ __forceinline__ void vst(T *p, const typename Vec<T>::V &v) {

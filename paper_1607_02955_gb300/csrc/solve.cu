@@ -986,6 +986,11 @@ lap_status_t run_solver(lap_hierarchy *h, int32_t k, const double *B, double *X,
         w.zero_bytes = counter_bytes;
         base = w.buf.get();
     }
+    // the row kernels move 32-byte vectors: every block must start 32-byte
+    // aligned (pool blocks are; the workspace is carved in 256-byte steps)
+    CFC_REQUIRE(((uintptr_t)base & 255) == 0, LAP_ECUDA, "internal: solve workspace not 256-byte aligned");
+    CFC_REQUIRE(!direct || (((uintptr_t)B & 31) == 0 && ((uintptr_t)X & 31) == 0), LAP_ECUDA,
+                "internal: padded blocks not 32-byte aligned");
     size_t off = 0;
     auto take = [&](size_t i) {
         char *p = base + off;
