@@ -101,6 +101,9 @@ typedef struct {
     int32_t cycle;        /* 1: V-cycle, 2: W-cycle (two coarse corrections per level);
                              0 (default): V, or autotuned together with levels_used */
     double coarse_scale;  /* factor on each coarse correction (> 0; 0 = 1.0, or autotuned) */
+    int32_t w_levels;     /* with cycle 2: the levels, from the finest, that take two coarse
+                             corrections (V below them); 0 (default): every level, or
+                             autotuned together with the cycle */
 } lap_solve_opts_t;
 
 typedef struct {
@@ -112,6 +115,7 @@ typedef struct {
        bit for bit without tuning */
     int32_t k_tile, levels_used, nu_coarse, cycle;
     double coarse_scale;
+    int32_t w_levels;
 } lap_solve_info_t;
 
 typedef struct {

@@ -214,6 +214,7 @@ void lap_default_solve_opts(lap_solve_opts_t *o) {
     o->levels_used = 0;
     o->nu_coarse = 0;
     o->cycle = 0;
+    o->w_levels = 0;
     o->coarse_scale = 0.0;
 }
 

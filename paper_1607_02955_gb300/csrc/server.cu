@@ -202,6 +202,7 @@ lap_status_t cfc_server_add_graph(cfc_server_t *sv, int64_t n, int64_t m, const 
         g.opts.nu_coarse = info.nu_coarse;
         g.opts.cycle = info.cycle;
         g.opts.coarse_scale = info.coarse_scale;
+        g.opts.w_levels = info.w_levels;
         g.bytes = cfc::hierarchy_bytes(g.h);  // with any BF16 copies the tuning made
         std::lock_guard<std::mutex> lk(sv->mu);
         CFC_REQUIRE(sv->graph_bytes + sv->inflight_bytes + g.bytes <= sv->budget, LAP_EBUDGET,

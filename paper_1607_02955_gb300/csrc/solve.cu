@@ -568,6 +568,7 @@ struct Solver {
     std::vector<double> cheb_c, cheb_e;
     double gamma = 1.0;  // coarse-correction scale
     int cycle = 1;       // 1: V-cycle, 2: W-cycle
+    int w_levels = 0;    // W-cycle: levels 0 .. w_levels-1 correct twice (0: all)
     int nu_pre, nu_post, nu_coarse;
     bool bf16 = false;  // BF16 weights below the finest level
     int hsize = 0;      // levels of the hierarchy and its dense coarsest size, as the solve began
@@ -592,6 +593,7 @@ struct Solver {
         nu_post = std::max(1, o.nu_post);
         nu_coarse = o.nu_coarse > 0 ? o.nu_coarse : std::max(nu_pre, 4);
         cycle = o.cycle == 2 ? 2 : 1;
+        w_levels = std::max(0, o.w_levels);
         gamma = o.coarse_scale > 0.0 ? o.coarse_scale : 1.0;
         bf16 = std::is_same<Tin, float>::value && o.precision == LAP_FP32_BF16COARSE_REFINED;
         hsize = (int)h->lv.size();
@@ -749,7 +751,7 @@ struct Solver {
         // exact, so one correction suffices just above it
         const Level &C = h->lv[l + 1];
         const bool next_dense = (l + 1 == nlev - 1) && coarse_n == C.n && l + 1 == hsize - 1;
-        const int ncorr = (cycle == 2 && !next_dense) ? 2 : 1;
+        const int ncorr = (cycle == 2 && !next_dense && (w_levels == 0 || l < w_levels)) ? 2 : 1;
         for (int cc = 0; cc < ncorr; ++cc) {
             rowop<Tin, 0>(fam_level(l, LAP_KF_RESTRICT_FINE), L, OpResid<Tin>{lv_view(L), cur, lb[l], oth, ld},
                           chunk_part, mat_bytes(L, wb) + vec_bytes(L.n, ld, 3, et));
@@ -906,6 +908,7 @@ struct Solver {
             info->nu_coarse = nu_coarse;
             info->cycle = cycle;
             info->coarse_scale = gamma;
+            info->w_levels = cycle == 2 ? w_levels : 0;
         }
         return converged ? LAP_OK : LAP_ENOCONV;
     }
@@ -943,8 +946,8 @@ lap_status_t run_solver(lap_hierarchy *h, int32_t k, const double *B, double *X,
     // of every level; zero at allocation, and every launch leaves them zero
     const size_t counter_bytes = align_up(kMaxTiles * 4 + kMaxTiles * kMaxTeams * 4 + n_long_total * kMaxTiles * 4);
     sizes.push_back(counter_bytes);
-    sizes.push_back(align_up(n0 * ld * 8));  // b64
-    sizes.push_back(align_up(n0 * ld * 8));  // x64
+    sizes.push_back(direct ? 0 : align_up(n0 * ld * 8));  // b64 (direct: the caller's block)
+    sizes.push_back(direct ? 0 : align_up(n0 * ld * 8));  // x64 (direct: the caller's block)
     sizes.push_back(align_up(n0 * ld * sizeof(Tin)));  // r
     sizes.push_back(align_up(n0 * ld * sizeof(Tin)));  // z
     sizes.push_back(align_up(n0 * ld * sizeof(Tin)));  // p
@@ -1103,15 +1106,17 @@ struct TuneKey {
     int64_t n, nnz;
     int k, precision, kt, smoother, nu_pre, nu_post, nu_coarse, cycle;
     double scale;
+    int w_levels;
     bool operator<(const TuneKey &o) const {
-        return std::tie(n, nnz, k, precision, kt, smoother, nu_pre, nu_post, nu_coarse, cycle, scale) <
+        return std::tie(n, nnz, k, precision, kt, smoother, nu_pre, nu_post, nu_coarse, cycle, scale, w_levels) <
                std::tie(o.n, o.nnz, o.k, o.precision, o.kt, o.smoother, o.nu_pre, o.nu_post, o.nu_coarse, o.cycle,
-                        o.scale);
+                        o.scale, o.w_levels);
     }
 };
 struct TuneChoice {
     int kt, levels, nu_coarse, cycle;
     double scale;
+    int w_levels = 0;
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneChoice> g_tune;
@@ -1142,12 +1147,13 @@ template <class PrepareBf16>
 int tune(lap_hierarchy *h, int32_t k, const double *B, double *X, lap_solve_opts_t &o, cudaStream_t s,
          lap_solve_info_t *info, int kt, bool direct, PrepareBf16 &&prepare_bf16) {
     const TuneKey key{h->lv[0].n, h->lv[0].nnz,  k,         o.precision, o.k_tile,
-                      o.smoother, o.nu_pre,      o.nu_post, o.nu_coarse, o.cycle, o.coarse_scale};
+                      o.smoother, o.nu_pre,      o.nu_post, o.nu_coarse, o.cycle, o.coarse_scale, o.w_levels};
     auto apply = [&](const TuneChoice &c, lap_solve_opts_t &oo) {
         oo.levels_used = c.levels;
         oo.nu_coarse = c.nu_coarse;
         oo.cycle = c.cycle;
         oo.coarse_scale = c.scale;
+        oo.w_levels = c.w_levels;
     };
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1182,7 +1188,8 @@ int tune(lap_hierarchy *h, int32_t k, const double *B, double *X, lap_solve_opts
     std::vector<TuneChoice> tried;
     // a candidate's cost: its solve plus building its coarse levels (every new
     // hierarchy of this graph pays that again)
-    auto trial = [&](const TuneChoice &c) -> lap_status_t {
+    // returns the candidate's cost, or -1 when it did not converge within the trial cap
+    auto trial = [&](const TuneChoice &c) -> float {
         lap_solve_opts_t oo = trial_o;
         apply(c, oo);
         CFC_CUDA(cudaEventRecord(e0, s));
@@ -1196,15 +1203,16 @@ int tune(lap_hierarchy *h, int32_t k, const double *B, double *X, lap_solve_opts
         const float cost = ms + (float)build;
         if (verbose)
             std::fprintf(stderr,
-                         "lap autotune n=%lld k=%d kt=%d levels=%d nu_coarse=%d cycle=%d scale=%.2f solve=%.3f ms "
-                         "build=%.3f ms status=%d\n",
-                         (long long)h->lv[0].n, k, c.kt, c.levels, c.nu_coarse, c.cycle, c.scale, ms, build, (int)st);
+                         "lap autotune n=%lld k=%d kt=%d levels=%d nu_coarse=%d cycle=%d w_levels=%d scale=%.2f "
+                         "solve=%.3f ms build=%.3f ms status=%d\n",
+                         (long long)h->lv[0].n, k, c.kt, c.levels, c.nu_coarse, c.cycle, c.w_levels, c.scale, ms,
+                         build, (int)st);
         tried.push_back(c);
         if (st == LAP_OK && (best < 0 || cost < best_cost)) {
             best_cost = cost;
             best = (int)tried.size() - 1;
         }
-        return st;
+        return st == LAP_OK ? cost : -1.f;
     };
     // untimed warm-up: first launches load kernels and size the workspace
     {
@@ -1217,8 +1225,8 @@ int tune(lap_hierarchy *h, int32_t k, const double *B, double *X, lap_solve_opts
         trial({kt, 1, o.nu_coarse, cyc_default, sc_default});
     } else {
         for (int d : {1, 2, 3, 4, 6, 8}) {
-            const lap_status_t st = trial({kt, 1, d, cyc_default, sc_default});
-            if (st != LAP_OK && d >= 2) break;  // smoothing alone does not reach the tolerance
+            const float cost = trial({kt, 1, d, cyc_default, sc_default});
+            if (cost < 0 && d >= 2) break;  // smoothing alone does not reach the tolerance
         }
     }
     std::vector<int> depths;
@@ -1226,14 +1234,23 @@ int tune(lap_hierarchy *h, int32_t k, const double *B, double *X, lap_solve_opts
     if (L > 4) depths.push_back(L);
     for (int l : depths) trial({kt, l, nc_default, cyc_default, sc_default});
     if (L >= 3) {
-        if (o.cycle == 0)
-            for (int l : {3, L})
-                if (l <= L) trial({kt, l, nc_default, 2, sc_default});
+        // unsmoothed aggregation under-corrects; scaling the coarse correction helps
+        double sc_best = sc_default;
         if (o.coarse_scale <= 0.0) {
-            // unsmoothed aggregation under-corrects; scaling the coarse correction helps
-            for (double sc : {1.5, 1.8, 2.0}) trial({kt, L, nc_default, cyc_default, sc});
-            if (o.cycle == 0) trial({kt, L, nc_default, 2, 1.5});
+            float sc_cost = -1.f;
+            for (double sc : {1.5, 1.8, 2.0}) {
+                const float cost = trial({kt, L, nc_default, cyc_default, sc});
+                if (cost >= 0 && (sc_cost < 0 || cost < sc_cost)) {
+                    sc_best = sc;
+                    sc_cost = cost;
+                }
+            }
         }
+        // W-cycles: two coarse corrections on the top 1, 2, 3 levels or on all
+        // of them (each extra level doubles the visits below it)
+        if (o.cycle == 0)
+            for (int w : {1, 2, 3, 0})
+                if (w < L - 1) trial({kt, L, nc_default, 2, sc_best, w});
     }
     // stage 2: the tile width, with the best preconditioner
     if (best >= 0 && o.k_tile == 0) {
