@@ -16,6 +16,7 @@
 // mean once, the search directions are projected every iteration, and the
 // result is returned with zero mean.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -540,6 +541,15 @@ int num_sms() {
 }
 
 // ====================================================================== solver
+// Deadline of an autotuning trial on this thread (steady clock, seconds; 0 =
+// none), checked at the solve's host synchronisations, so that a slow
+// candidate is abandoned early.
+thread_local double t_trial_deadline = 0.0;
+double steady_seconds() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+bool past_trial_deadline() { return t_trial_deadline > 0.0 && steady_seconds() > t_trial_deadline; }
+
 struct ColState {
     double *bnorm, *relres, *alpha, *beta, *rz, *rr0, *mu;
     void *alpha_t, *beta_t, *mu_t;  // the same scalars in the inner arithmetic type
@@ -814,7 +824,7 @@ struct Solver {
                 int na = 0;
                 for (int c = 0; c < ld; ++c) na += h_active[c] ? 1 : 0;
                 if (na == 0) break;
-                if (it == max_inner) break;
+                if (it == max_inner || past_trial_deadline()) break;
             }
             if (!precond(fuse_first, 1))
                 rows<Tin, 3>(LAP_KF_BLAS1, n, OpDotRZ<Tin, false>{r, z, ld, dstate()}, 2 * vb1);
@@ -884,7 +894,7 @@ struct Solver {
                 converged = true;
                 break;
             }
-            if (outer >= o.max_outer) break;
+            if (outer >= o.max_outer || past_trial_deadline()) break;
             // inner solve of L d = r; d lives in lt-independent buffer `dbuf`
             const double itol = (o.precision == LAP_FP64) ? std::max(o.tol * 0.5, 1e-15) : o.inner_tol;
             inner_total += inner_pcg(dbuf, o.max_inner, itol);
@@ -1189,11 +1199,20 @@ int tune(lap_hierarchy *h, int32_t k, const double *B, double *X, lap_solve_opts
     // a candidate's cost: its solve plus building its coarse levels (every new
     // hierarchy of this graph pays that again)
     // returns the candidate's cost, or -1 when it did not converge within the trial cap
+    // A candidate is abandoned once it has run twice as long as the best one
+    // so far (checked at the solve's host synchronisations).
+    struct TrialLimits {
+        ~TrialLimits() { t_trial_deadline = 0.0; }
+    } limits_guard;
     auto trial = [&](const TuneChoice &c) -> float {
         lap_solve_opts_t oo = trial_o;
         apply(c, oo);
+        // the solve's own check interval: checking more often would add host
+        // synchronisations to every candidate's cost and favour fewer, dearer iterations
+        t_trial_deadline = best >= 0 ? steady_seconds() + 2.0 * best_cost * 1e-3 : 0.0;
         CFC_CUDA(cudaEventRecord(e0, s));
         const lap_status_t st = dispatch(h, k, B, X, oo, s, info, c.kt, direct);
+        t_trial_deadline = 0.0;
         CFC_CUDA(cudaEventRecord(e1, s));
         CFC_CUDA(cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -1218,9 +1237,15 @@ int tune(lap_hierarchy *h, int32_t k, const double *B, double *X, lap_solve_opts
     {
         lap_solve_opts_t oo = trial_o;
         apply({kt, 1, 1, 1, 1.0}, oo);
+        oo.max_outer = 1;  // a couple of iterations is all this needs
+        oo.max_inner = 2;
         dispatch(h, k, B, X, oo, s, info, kt, direct);
     }
-    // stage 1: preconditioner, at the default tile width
+    // stage 1: preconditioner, at the default tile width.  First a baseline
+    // that converges on every graph family seen (the full-depth V-cycle), so
+    // that every later candidate runs under a deadline.
+    const double sc_base = o.coarse_scale > 0.0 ? o.coarse_scale : 1.5;
+    const float base_cost = L >= 3 ? trial({kt, L, nc_default, cyc_default, sc_base}) : -1.f;
     if (o.nu_coarse > 0) {
         trial({kt, 1, o.nu_coarse, cyc_default, sc_default});
     } else {
@@ -1235,10 +1260,10 @@ int tune(lap_hierarchy *h, int32_t k, const double *B, double *X, lap_solve_opts
     for (int l : depths) trial({kt, l, nc_default, cyc_default, sc_default});
     if (L >= 3) {
         // unsmoothed aggregation under-corrects; scaling the coarse correction helps
-        double sc_best = sc_default;
+        double sc_best = sc_base;
         if (o.coarse_scale <= 0.0) {
-            float sc_cost = -1.f;
-            for (double sc : {1.5, 1.8, 2.0}) {
+            float sc_cost = base_cost;
+            for (double sc : {1.8, 2.0}) {
                 const float cost = trial({kt, L, nc_default, cyc_default, sc});
                 if (cost >= 0 && (sc_cost < 0 || cost < sc_cost)) {
                     sc_best = sc;
@@ -1246,11 +1271,13 @@ int tune(lap_hierarchy *h, int32_t k, const double *B, double *X, lap_solve_opts
                 }
             }
         }
-        // W-cycles: two coarse corrections on the top 1, 2, 3 levels or on all
-        // of them (each extra level doubles the visits below it)
-        if (o.cycle == 0)
+        // W-cycles, when the hierarchy pays at all: two coarse corrections on
+        // the top 1, 2 or 3 levels or on all of them (each extra level doubles
+        // the visits below it); two corrections at scale 2 overshoot, so at
+        // most 1.5
+        if (o.cycle == 0 && best >= 0 && tried[best].levels > 1)
             for (int w : {1, 2, 3, 0})
-                if (w < L - 1) trial({kt, L, nc_default, 2, sc_best, w});
+                if (w < L - 1) trial({kt, L, nc_default, 2, std::min(sc_best, 1.5), w});
     }
     // stage 2: the tile width, with the best preconditioner
     if (best >= 0 && o.k_tile == 0) {
