@@ -104,6 +104,11 @@ typedef struct {
     int32_t w_levels;     /* with cycle 2: the levels, from the finest, that take two coarse
                              corrections (V below them); 0 (default): every level, or
                              autotuned together with the cycle */
+    int32_t graphs;       /* 1 (default): a multilevel cycle is captured once per solve as
+                             a CUDA graph and replayed at every preconditioner application
+                             (one launch instead of one per kernel); 0: plain launches.
+                             Plain launches are also used while lap_stats timing or the
+                             launch log is on, so that those see every kernel */
 } lap_solve_opts_t;
 
 typedef struct {

@@ -38,7 +38,8 @@ class SolveOpts(C.Structure):
                 ("max_inner", C.c_int32), ("inner_tol", C.c_double), ("k_tile", C.c_int32),
                 ("smoother", C.c_int32), ("nu_pre", C.c_int32), ("nu_post", C.c_int32),
                 ("check_every", C.c_int32), ("levels_used", C.c_int32), ("nu_coarse", C.c_int32),
-                ("cycle", C.c_int32), ("coarse_scale", C.c_double), ("w_levels", C.c_int32)]
+                ("cycle", C.c_int32), ("coarse_scale", C.c_double), ("w_levels", C.c_int32),
+                ("graphs", C.c_int32)]
 
 
 class SolveInfo(C.Structure):

@@ -64,6 +64,20 @@ void clear_last_error() { t_last_error.clear(); }
 
 void count_launch() { g_launches_total.fetch_add(1, std::memory_order_relaxed); }
 
+bool stats_detailed() {
+    return g_timing.load(std::memory_order_relaxed) != 0 || g_log_on.load(std::memory_order_relaxed) != 0;
+}
+void stats_launches(int64_t out[LAP_KF_COUNT]) {
+    for (int f = 0; f < LAP_KF_COUNT; ++f) out[f] = (int64_t)g_launches[f].load(std::memory_order_relaxed);
+}
+void stats_add_launches(const int64_t delta[LAP_KF_COUNT], int64_t times) {
+    for (int f = 0; f < LAP_KF_COUNT; ++f) {
+        const int64_t d = delta[f] * times;
+        g_launches[f].fetch_add((uint64_t)d, std::memory_order_relaxed);
+        g_launches_total.fetch_add((uint64_t)d, std::memory_order_relaxed);
+    }
+}
+
 LaunchScope::LaunchScope(int fam, cudaStream_t s, double algorithmic_bytes)
     : family(fam), stream(s), bytes(algorithmic_bytes) {
     g_launches_total.fetch_add(1, std::memory_order_relaxed);
@@ -215,6 +229,7 @@ void lap_default_solve_opts(lap_solve_opts_t *o) {
     o->nu_coarse = 0;
     o->cycle = 0;
     o->w_levels = 0;
+    o->graphs = 1;
     o->coarse_scale = 0.0;
 }
 

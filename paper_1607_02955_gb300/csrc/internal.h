@@ -77,6 +77,11 @@ struct LaunchScope {
     ~LaunchScope();
 };
 void count_launch();
+// for graph replays: whether timing or the launch log is on (graphs are then
+// not used), the per-family launch counters, and adding a graph's launches
+bool stats_detailed();
+void stats_launches(int64_t out[LAP_KF_COUNT]);
+void stats_add_launches(const int64_t delta[LAP_KF_COUNT], int64_t times);
 
 #define CFC_LAUNCH(family, stream, bytes, kernel, grid, block, smem, ...)       \
     do {                                                                       \

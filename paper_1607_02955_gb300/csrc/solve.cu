@@ -608,6 +608,8 @@ struct Solver {
         bf16 = std::is_same<Tin, float>::value && o.precision == LAP_FP32_BF16COARSE_REFINED;
         hsize = (int)h->lv.size();
         coarse_n = h->coarse_n;
+        // a one-level preconditioner is two or three kernels: nothing to gain
+        use_graphs = o.graphs != 0 && nlev >= 2 && !stats_detailed();
         setup_smoother();
     }
 
@@ -786,7 +788,7 @@ struct Solver {
     // z = M^{-1} r  (the result may land in either of the two finest-level
     // buffers; z and t0 are swapped accordingly).  Returns true when the PCG
     // dot products were computed on the way.
-    bool precond(bool first_done, int dot) {
+    bool precond_eager(bool first_done, int dot) {
         lb[0] = r;
         lx[0] = z;
         lt[0] = t0;
@@ -794,6 +796,70 @@ struct Solver {
         z = lx[0];
         t0 = lt[0];
         return dotted;
+    }
+
+    // A multilevel cycle is a fixed sequence of kernels for a given entry
+    // state (variant, and which of the two level-0 buffers holds z): the
+    // first application in each state is captured as a CUDA graph (on a
+    // private stream: capture cannot run on the legacy stream) and every
+    // application replays it with one launch on the solve's stream.  The
+    // smoothing ping-pongs buffers, so the state after the cycle is recorded
+    // with the graph and restored on replay.  Coarse-level buffers are
+    // scratch within a cycle, so their assignment at capture is kept.
+    struct CycleGraph {
+        cudaGraphExec_t exec = nullptr;
+        bool dotted = false;
+        Tin *z_after = nullptr, *t0_after = nullptr;
+        int64_t launches[LAP_KF_COUNT] = {};
+    };
+    std::map<std::tuple<bool, int, Tin *, Tin *>, CycleGraph> graphs;
+    cudaStream_t cap_stream = nullptr;
+    bool use_graphs = false;
+
+    ~Solver() {
+        for (auto &g : graphs)
+            if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
+
+    bool precond(bool first_done, int dot) {
+        if (!use_graphs) return precond_eager(first_done, dot);
+        const auto key = std::make_tuple(first_done, dot, z, t0);
+        auto it = graphs.find(key);
+        if (it == graphs.end()) {
+            CycleGraph g;
+            if (!cap_stream) CFC_CUDA(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+            int64_t before[LAP_KF_COUNT], after[LAP_KF_COUNT];
+            stats_launches(before);
+            const cudaStream_t run_stream = s;
+            s = cap_stream;
+            cudaGraph_t graph = nullptr;
+            CFC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            try {
+                g.dotted = precond_eager(first_done, dot);
+            } catch (...) {
+                cudaStreamEndCapture(s, &graph);
+                if (graph) cudaGraphDestroy(graph);
+                s = run_stream;
+                throw;
+            }
+            CFC_CUDA(cudaStreamEndCapture(s, &graph));
+            s = run_stream;
+            const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            CFC_CUDA(ie);
+            stats_launches(after);
+            for (int f = 0; f < LAP_KF_COUNT; ++f) g.launches[f] = after[f] - before[f];
+            stats_add_launches(g.launches, -1);  // captured, not run: counted per replay below
+            g.z_after = z;
+            g.t0_after = t0;
+            it = graphs.emplace(key, g).first;
+        }
+        CFC_CUDA(cudaGraphLaunch(it->second.exec, s));
+        stats_add_launches(it->second.launches, 1);
+        z = it->second.z_after;
+        t0 = it->second.t0_after;
+        return it->second.dotted;
     }
 
     // inner PCG on the finest level: solves L d = r; returns iterations

@@ -229,6 +229,26 @@ def test_farness_jl_row_shards_sum_to_the_full_query(P, k, world):
         P.cfc_farness_jl_rows(h, k, 16, 8, 3, nodes)
 
 
+@pytest.mark.parametrize("cycle,w_levels", [(1, 0), (2, 0), (2, 1)])
+def test_graph_replay_matches_plain_launches(P, cycle, w_levels):
+    # the captured cycle is the same kernels in the same order: identical bits
+    import torch
+    n, s, d, w = _graph(synth.grid2d(64))
+    h = P.lap_build_hierarchy(n, s, d, w, P.lap_default_hier_opts(eager=1))
+    assert P.lap_hierarchy_info(h)["levels"] >= 3
+    rng = np.random.default_rng(4)
+    B = torch.tensor(rng.standard_normal((n, 24)), device="cuda")
+    out = []
+    for graphs in (1, 0):
+        X = torch.empty_like(B)
+        o = P.lap_default_solve_opts(levels_used=-1, cycle=cycle, w_levels=w_levels, coarse_scale=1.5,
+                                     k_tile=32, graphs=graphs)
+        info = P.lap_solve_multi(h, B, X, o)
+        assert info["max_rel_residual"] <= 1e-8
+        out.append(X.cpu().numpy())
+    assert np.array_equal(out[0], out[1])
+
+
 def test_bf16_coarse_changes_only_the_preconditioner(P):
     # same FP64 stopping test: both modes reach 1e-8 and agree to the solve
     # tolerance; the coarse operators differ, so the inner iterations may differ
