@@ -268,6 +268,17 @@ def test_bf16_coarse_changes_only_the_preconditioner(P):
     assert float(diff.max()) <= 2 * lam[-1] / lam[1] * 1.01e-8
 
 
+def test_farness_jl_all_nodes(P):
+    # the estimator for every node at once (q = n): one solve block, O(nk) sums
+    n, s, d, w = _graph(synth.grid2d(48))
+    g = canonical_graph(n, s, d, w)
+    h = P.lap_build_hierarchy(n, s, d, w)
+    nodes = np.arange(n, dtype=np.int32)
+    f = P.cfc_farness_jl(h, 32, 1, nodes)
+    fo = jl.jl_farness(g, 32, 1, nodes.tolist(), solver="dense")
+    assert _rel(f, fo) <= FARNESS_RTOL
+
+
 @pytest.mark.parametrize("n,k", [(3000, 64), (517, 5), (2, 1), (1000, 300)])
 def test_farness_from_solution_matches_literal_sum(P, n, k):
     import torch
