@@ -366,6 +366,61 @@ def cpu_baseline(wl):
             "sample": f"{ks} of the {wl['k']} JL right-hand sides (canonical graph + RHS + FP64 Jacobi-CG to 1e-8)"}
 
 
+def _ranks(x):
+    r = np.empty(len(x))
+    r[np.argsort(x, kind="stable")] = np.arange(len(x))
+    return r
+
+
+def accuracy_main(args):
+    """Accuracy against time of the two estimators on synthetic graphs (the
+    shape of Sec. 6.4): the exact farness of every node (dense, on the device)
+    against the projection estimator at eps = 0.5 .. 0.05 (k = ceil(ln n /
+    eps^2), Sec. 6.4) and the sampling estimator with |S| = 10 .. 1000 pivots,
+    every node queried.  Reports per setting the device time, the largest
+    relative farness error, the Spearman correlation of the closeness ranking
+    with the exact one, and the fraction of node pairs whose order flips."""
+    import torch
+    torch.cuda.init()
+    import paper_1607_02955_gb300 as P
+    from paper_1607_02955_gb300 import build_ext
+    build_ext.build()
+    graphs = {"ba3000": dict(kind="ba", n=3000, m_per=5, seed=2), "grid48": dict(kind="grid", a=48)}
+    out = {}
+    rng = np.random.default_rng(4)
+    for name, spec in graphs.items():
+        n, s, d, w = make_graph(spec)
+        f_exact, _ = P.cfc_exact_small(n, s, d, w)
+        h = P.lap_build_hierarchy(n, s, d, w)
+        nodes = np.arange(n, dtype=np.int32)
+        pairs = rng.integers(0, n, size=(200000, 2))
+        ex_order = np.sign(f_exact[pairs[:, 0]] - f_exact[pairs[:, 1]])
+        rows = []
+
+        def record(kind, param, fn):
+            fn()  # first call: autotuning for this column count
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            f = fn()
+            ms = (time.perf_counter() - t0) * 1e3
+            rel = float(np.max(np.abs(f - f_exact) / f_exact))
+            rho = float(np.corrcoef(_ranks(f), _ranks(f_exact))[0, 1])
+            flips = float(np.mean(np.sign(f[pairs[:, 0]] - f[pairs[:, 1]]) != ex_order))
+            rows.append({"estimator": kind, **param, "ms": ms, "max_rel_err": rel, "spearman": rho,
+                         "pair_flips": flips})
+
+        for eps in (0.5, 0.4, 0.3, 0.2, 0.1, 0.05):
+            k = int(np.ceil(np.log(n) / eps ** 2))
+            record("projection", {"eps": eps, "k": k}, lambda k=k: P.cfc_farness_jl(h, k, 1, nodes))
+        for piv in (10, 30, 100, 300, 1000):
+            # the sampling estimate scales a sum over |S| pivots by n/|S| (Proposition 1)
+            record("sampling", {"pivots": piv}, lambda piv=piv: P.cfc_farness_sampled(h, piv, 1, nodes))
+        h.destroy()
+        out[name] = {"n": n, "m": int(s.size), "rows": rows}
+    print(json.dumps({"metric": "estimator accuracy vs device time", "data": "synthetic", "n_gpus": 1,
+                      "config": {"workload": "accuracy", "queried": "every node"}, "accuracy": out}), flush=True)
+
+
 def serve_main(args):
     """The serving mix: 16 resident graphs, Poisson arrivals at 0.25, 0.5 and
     0.8 of the measured saturation rate, p50/p99 latency."""
@@ -390,7 +445,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ba100k_jl64", choices=sorted(WORKLOADS) + ["serve_mix"])
+    ap.add_argument("--workload", default="ba100k_jl64", choices=sorted(WORKLOADS) + ["serve_mix", "accuracy"])
     ap.add_argument("--no-serving", action="store_true", help="skip the small serving mix of the default line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
@@ -414,6 +469,9 @@ def main():
         return
     if args.workload == "serve_mix":
         serve_main(args)
+        return
+    if args.workload == "accuracy":
+        accuracy_main(args)
         return
     wl = WORKLOADS[args.workload]
     rank, world, local = dist_setup(args.gpus)
