@@ -170,6 +170,7 @@ LevelView view(const Level &L) {
     v.chunk_long = L.chunk_long.get();
     v.long_first = L.long_first.get();
     v.long_of_row = L.long_of_row.get();
+    v.order = L.order.get();
     v.long_count = nullptr;  // set by the solve that launches on the level
     return v;
 }
@@ -193,7 +194,7 @@ int64_t hierarchy_bytes(const lap_hierarchy *h) {
     for (const Level &L : h->lv)
         t += b(L.rowptr) + b(L.col) + b(L.w64) + b(L.deg64) + b(L.dinv64) + b(L.w32) + b(L.deg32) + b(L.dinv32) +
              b(L.wbf) + b(L.degbf) + b(L.dinvbf) + b(L.chunk_row) + b(L.chunk_begin) + b(L.chunk_long) +
-             b(L.long_first) + b(L.long_of_row) + b(L.agg) + b(L.mem_ptr) + b(L.mem);
+             b(L.long_first) + b(L.long_of_row) + b(L.order) + b(L.agg) + b(L.mem_ptr) + b(L.mem);
     return t;
 }
 

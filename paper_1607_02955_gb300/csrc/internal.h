@@ -169,6 +169,7 @@ struct Level {
     DBuf<int32_t> chunk_long;    // [n_chunks] index of the chunk's long row
     DBuf<int32_t> long_first;    // [n_long + 1] first chunk of each long row
     DBuf<int32_t> long_of_row;   // [n] index of the row among the long rows, -1 if short
+    DBuf<int32_t> order;         // [n] processing order of the rows (longest first), or empty: natural
     // map to the next coarser level (empty at the coarsest)
     DBuf<int32_t> agg;           // [n] aggregate (coarse node) of each node
     DBuf<int32_t> mem_ptr, mem;  // members of each coarse node, ascending
@@ -187,7 +188,7 @@ struct LevelView {
     const uint16_t *wbf;  // BF16 weights, read by the kernels instantiated for them
     const double *w64, *deg64, *dinv64;
     int32_t n_chunks, n_long;
-    const int32_t *chunk_row, *chunk_begin, *chunk_long, *long_first, *long_of_row;
+    const int32_t *chunk_row, *chunk_begin, *chunk_long, *long_first, *long_of_row, *order;
     uint32_t *long_count;  // [n_long * kMaxTiles] arrival counters of the launching solve
 };
 LevelView view(const Level &L);

@@ -459,8 +459,9 @@ __global__ void __launch_bounds__(kBlock, (NR >= 3 ? 3 : 4)) k_rowop(LevelView A
     for (int vb0 = blockIdx.x; vb0 < nvb_total; vb0 += gridDim.x) {
         const int vb = PRE ? vb0 : (vb0 < nvb_long ? nvb_short + vb0 : vb0 - nvb_long);
         if (vb < nvb_short) {
-            const int i = vb * RPB + grp;
-            if (i < A.n) {
+            const int slot = vb * RPB + grp;
+            if (slot < A.n) {
+                const int i = A.order ? __ldg(A.order + slot) : slot;
                 const int e0 = __ldg(A.rowptr + i), e1 = __ldg(A.rowptr + i + 1);
                 if (e1 - e0 <= kLongRow) {
                     const auto pr = op.pre(i, c0);  // own-row operands, in flight with the gathers
