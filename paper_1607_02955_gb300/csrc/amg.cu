@@ -1,6 +1,6 @@
 // Multigrid hierarchy of aggregation type (Sec. 3.1, Sec. 6.1: the paper's
 // LAMG coarsens by elimination of low-degree nodes and by aggregation driven
-// by an affinity measure; this build aggregates by parallel pairwise
+// by an affinity measure; this file aggregates by parallel pairwise
 // matching on the edge strength s_ij = w_ij / max(D_ii, D_jj)).
 //
 // Per level: a few handshake rounds of locally-dominant-edge matching (each

@@ -62,8 +62,6 @@ void drain_locked() {
 void set_last_error(const std::string &s) { t_last_error = s; }
 void clear_last_error() { t_last_error.clear(); }
 
-void count_launch() { g_launches_total.fetch_add(1, std::memory_order_relaxed); }
-
 bool stats_detailed() {
     return g_timing.load(std::memory_order_relaxed) != 0 || g_log_on.load(std::memory_order_relaxed) != 0;
 }

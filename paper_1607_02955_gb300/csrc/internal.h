@@ -76,7 +76,6 @@ struct LaunchScope {
     LaunchScope(int family, cudaStream_t s, double algorithmic_bytes);
     ~LaunchScope();
 };
-void count_launch();
 // for graph replays: whether timing or the launch log is on (graphs are then
 // not used), the per-family launch counters, and adding a graph's launches
 bool stats_detailed();
