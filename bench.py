@@ -267,29 +267,38 @@ class ClockSampler:
             self.p.kill()
         self.f.flush()
         self.f.seek(0)
-        import datetime
-        rows = []
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.f.read().splitlines():
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 10:
-                continue
-            try:
-                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
-                rows.append((ts, float(parts[2]), float(parts[3]),
-                             {nm for nm, v in zip(names, parts[6:10]) if v.lower() == "active"}))
-            except ValueError:
-                continue
+        text = self.f.read()
         os.unlink(self.f.name)
-        t0 = self.t0 if self.t0 is not None else -1e30
-        inside = [r for r in rows if t0 - 0.1 <= r[0] <= self.t1 + 0.1]
-        if not inside and rows:  # a window shorter than the sampling period
-            inside = [min(rows, key=lambda r: abs(r[0] - 0.5 * (t0 + self.t1)))]
-        sm = [r[1] for r in inside]
-        reasons = set().union(*[r[3] for r in inside]) if inside else set()
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(r[2] for r in inside) if inside else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return summarize_clocks(text, self.t0, self.t1)
+
+
+def summarize_clocks(text, t0, t1):
+    """Median SM clock, the maximum clock and the active throttle reasons of
+    the nvidia-smi samples (timestamp first) taken in [t0, t1] (host time,
+    seconds; 100 ms of slack each side); a window shorter than the sampling
+    period takes the sample nearest its middle."""
+    import datetime
+    rows = []
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in text.splitlines():
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 10:
+            continue
+        try:
+            ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            rows.append((ts, float(parts[2]), float(parts[3]),
+                         {nm for nm, v in zip(names, parts[6:10]) if v.lower() == "active"}))
+        except ValueError:
+            continue
+    t0 = t0 if t0 is not None else -1e30
+    inside = [r for r in rows if t0 - 0.1 <= r[0] <= t1 + 0.1]
+    if not inside and rows:  # a window shorter than the sampling period
+        inside = [min(rows, key=lambda r: abs(r[0] - 0.5 * (t0 + t1)))]
+    sm = [r[1] for r in inside]
+    reasons = set().union(*[r[3] for r in inside]) if inside else set()
+    return {"sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(r[2] for r in inside) if inside else None,
+            "reasons": sorted(reasons), "samples": len(sm)}
 
 
 def dist_setup(n_gpus):
