@@ -2,18 +2,25 @@
 // KT right-hand-side columns of row-major n x ld blocks.
 //
 // Layout: a group of G = KT / VW lanes owns one row; each lane owns VW
-// consecutive columns (float4 for FP32, double2 for FP64), so a gathered
-// neighbour row of the tile is one coalesced KT*sizeof(T)-byte load.
-// Rows with more than kLongRow nonzeros are split into chunks processed by
-// separate groups; the chunk sums go to a scratch buffer and the group that
-// finishes a row's last chunk (arrival counter) adds them up in chunk order
-// and runs the row's epilogue, so results are independent of scheduling.
+// consecutive columns (8 floats or 4 doubles, 32 bytes, one 256-bit access),
+// so a gathered neighbour row of the tile is one contiguous KT*sizeof(T)-byte
+// run read with one instruction per lane.  Blocks walk row blocks
+// grid-stride; on levels with very uneven row lengths the rows are taken in a
+// fixed longest-first order (LevelView::order).
 //
-// Per-column reductions (dot products, norms, sums) are accumulated in FP64:
-// per thread over its rows, per block over its groups in a fixed order,
-// then across blocks by the last block to arrive, again in a fixed order.
-// The grid size depends only on the problem and the device's SM count, so
-// every reduction is bitwise reproducible.
+// Rows with more than kLongRow nonzeros are split into chunks of kChunk.
+// Without reductions the group that finishes a row's last chunk (arrival
+// counter) adds the chunk sums in chunk order and runs the row's epilogue;
+// with reductions the chunk sums come from a k_chunk_sums launch just before
+// and the row's own group finishes it.  Either way results do not depend on
+// scheduling.
+//
+// Per-column reductions (dot products, norms, sums) keep thread partials in
+// the kernel's arithmetic type over the rows a thread handles, add them
+// across a warp by a fixed shuffle tree and across warps in order, and then
+// in FP64 across blocks, by teams of blocks and by the last team to arrive,
+// each in a fixed order.  The grid size depends only on the problem and the
+// device's SM count, so every reduction is bitwise reproducible.
 #pragma once
 
 #include <type_traits>

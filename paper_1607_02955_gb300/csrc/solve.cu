@@ -1,20 +1,27 @@
 // Block solve of L X = B (Eq. system) for k right-hand sides: FP64 iterative
 // refinement around a column-independent preconditioned CG (Sec. 3.1: CG,
-// relative-residual stopping rule) whose preconditioner is one V-cycle of
-// the aggregation hierarchy built in amg.cu.
+// relative-residual stopping rule) whose preconditioner is one multigrid
+// cycle of the aggregation hierarchy built in amg.cu.
 //
 //   outer (FP64):  r = b - L x ;  stop when ||r_j|| <= tol ||b_j|| for all j
 //                  d = PCG(L, r) in Tin (FP32, or FP64 in LAP_FP64 mode)
 //                  x += d
 //   inner PCG:     per column j its own alpha_j, beta_j (columns never mix)
-//   V-cycle:       Chebyshev (or damped Jacobi) smoothing with D^{-1},
+//   cycle:         Chebyshev (or damped Jacobi) smoothing with D^{-1},
 //                  residual, restriction (sum over each aggregate),
-//                  recursion, dense FP64 coarsest solve, prolongation,
-//                  the same smoothing again (a symmetric preconditioner).
+//                  recursion (once: V-cycle, twice on the top levels:
+//                  W-cycle), dense FP64 coarsest solve, prolongation scaled
+//                  by the coarse-correction factor, the same smoothing again
+//                  (a symmetric preconditioner).  Levels below the finest may
+//                  run on BF16 weights (LAP_FP32_BF16COARSE_REFINED).  A
+//                  multilevel cycle is captured once per solve as a CUDA graph
+//                  and replayed at every application.
 //
 // L is singular with null space span{1} (Sec. 2): b is projected to zero
 // mean once, the search directions are projected every iteration, and the
-// result is returned with zero mean.
+// result is returned with zero mean.  The first solve of a graph size and
+// configuration autotunes what the options leave open (depth, smoother
+// degree, cycle, coarse scale, column tile).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
