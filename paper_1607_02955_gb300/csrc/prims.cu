@@ -114,6 +114,31 @@ __global__ void __launch_bounds__(kSingleThreads) k_scan_single(const T *in, T *
     }
 }
 
+// Second pass of a two-launch scan: block b adds the sum of the tile totals
+// before it (read and reduced by the block itself, in a fixed order: at most
+// kPrefixMaxTiles of them) to its tile's local scan.
+constexpr int64_t kPrefixMaxTiles = 4096;
+template <typename T>
+__global__ void k_scan_add_prefix(T *out, const T *sums, int64_t n) {
+    __shared__ T warp_tot[kScanThreads / 32];
+    const int b = blockIdx.x;
+    T part = 0;
+    for (int j = threadIdx.x; j < b; j += kScanThreads) part += sums[j];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) warp_tot[wid] = part;
+    __syncthreads();
+    T off = 0;
+#pragma unroll
+    for (int w = 0; w < kScanThreads / 32; ++w) off += warp_tot[w];
+    const int64_t base = (int64_t)b * kScanTile;
+    for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
+        const int64_t j = base + i;
+        if (j < n) out[j] += off;
+    }
+}
+
 // in-place capable recursive scan; returns nothing (total computed by caller)
 template <typename T>
 void scan_rec(const T *in, T *out, int64_t n, cudaStream_t s) {
@@ -128,6 +153,10 @@ void scan_rec(const T *in, T *out, int64_t n, cudaStream_t s) {
     }
     DBuf<T> sums(nb, s);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_scan_tile<T>, (unsigned)nb, kScanThreads, 0, in, out, sums.get(), n);
+    if (nb <= kPrefixMaxTiles) {  // two launches: each tile sums the totals before it
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_scan_add_prefix<T>, (unsigned)nb, kScanThreads, 0, out, sums.get(), n);
+        return;
+    }
     scan_rec<T>(sums.get(), sums.get(), nb, s);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_scan_add<T>, (unsigned)nb, kScanThreads, 0, out, sums.get(), n);
 }
