@@ -49,9 +49,21 @@ def _digest() -> str:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link the library; returns its path."""
+    """Compile and link the library; returns its path.  Processes that build
+    at the same time (one per rank) take turns on a file lock; the later
+    ones find the stamp current and return."""
+    import fcntl
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
+    with open(os.path.join(BUILD, "lock"), "w") as lk:
+        fcntl.flock(lk, fcntl.LOCK_EX)
+        try:
+            return _build_locked(force, verbose)
+        finally:
+            fcntl.flock(lk, fcntl.LOCK_UN)
+
+
+def _build_locked(force: bool, verbose: bool) -> str:
     stamp = os.path.join(BUILD, "stamp")
     dg = _digest()
     if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == dg:
