@@ -320,8 +320,9 @@ def dist_setup(n_gpus):
 
 def barrier(world):
     if world > 1:
+        import torch
         import torch.distributed as dist
-        dist.barrier()
+        dist.barrier(device_ids=[torch.cuda.current_device()])
 
 
 def max_over_ranks(x, world):
