@@ -72,14 +72,18 @@ SERVE_GRAPHS = ([dict(kind="grid", a=a) for a in (256, 384, 512, 768, 1024)] +
 SERVE_SMALL = [dict(kind="grid", a=256), dict(kind="ba", n=100000, m_per=5, seed=2), dict(kind="rmat", scale=16, seed=4)]
 
 
-def run_serving(P, specs, n_queries, loads, seed=4, n_pivots=200, slots=4):
+def run_serving(P, specs, n_queries, loads, seed=4, n_pivots=200, slots=4, resident=False):
     """Continuous-batching request loop on resident graphs (cfc_server_*):
     a burst of requests measures the saturation rate, then for each load
     factor Poisson arrivals at that fraction of it; latencies (submit ->
     result) come from the server.  Query: 1..32 nodes of a uniformly chosen
-    graph, the sampling estimator with n_pivots pivots."""
+    graph, the sampling estimator with n_pivots pivots: drawn per request, or
+    (resident=True) one pivot set per graph whose solutions stay on the
+    device, so a request solves only its nodes' columns."""
     rng = np.random.default_rng(seed)
-    sv = P.cfc_server_create(P.cfc_server_default_opts(slots=slots))
+    sv = P.cfc_server_create(P.cfc_server_default_opts(slots=slots, resident_pivots=n_pivots if resident else 0,
+                                                       pivot_seed=seed))
+    req_pivots = 0 if resident else n_pivots
     t0 = time.time()
     sizes = []
     for spec in specs:
@@ -99,7 +103,7 @@ def run_serving(P, specs, n_queries, loads, seed=4, n_pivots=200, slots=4):
 
     def burst(qs):
         P.cfc_server_reset_stats(sv)
-        ids = [P.cfc_server_submit(sv, g, nodes, n_pivots, sd) for g, nodes, sd in qs]
+        ids = [P.cfc_server_submit(sv, g, nodes, req_pivots, sd) for g, nodes, sd in qs]
         for r in ids:
             P.cfc_server_poll(sv, r, -1, q=32)
         return P.cfc_server_stats(sv)
@@ -107,6 +111,7 @@ def run_serving(P, specs, n_queries, loads, seed=4, n_pivots=200, slots=4):
     burst(queries(2 * slots))  # warm-up
     sat = burst(queries(n_queries))
     result = {"graphs": len(specs), "nodes_max": max(sizes), "slots": slots, "n_pivots": n_pivots,
+              "pivots": "one resident set per graph" if resident else "drawn per request",
               "queries_per_load": n_queries, "add_graphs_s": add_s,
               "saturation": {"queries_per_s": sat["queries_per_s"], "rhs_per_s": sat["rhs_per_s"],
                              "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"],
@@ -124,7 +129,7 @@ def run_serving(P, specs, n_queries, loads, seed=4, n_pivots=200, slots=4):
             dt = t_next - time.perf_counter()
             if dt > 0:
                 time.sleep(dt)
-            ids.append(P.cfc_server_submit(sv, g, nodes, n_pivots, sd))
+            ids.append(P.cfc_server_submit(sv, g, nodes, req_pivots, sd))
         for r in ids:
             P.cfc_server_poll(sv, r, -1, q=32)
         st = P.cfc_server_stats(sv)
@@ -661,6 +666,8 @@ def main():
         }
         if world == 1 and not args.no_serving:
             line["serving"] = run_serving(P, SERVE_SMALL, n_queries=48, loads=(0.5,))
+            line["serving_resident_pivots"] = run_serving(P, SERVE_SMALL, n_queries=48, loads=(0.5,),
+                                                          resident=True)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl)
         print(json.dumps(line), flush=True)

@@ -391,6 +391,12 @@ typedef struct {
                                80% of the device memory free at creation */
     lap_solve_opts_t solve; /* solve options (precision, tol, ...); tuned fields left 0 are
                                autotuned per graph when it is added */
+    int32_t resident_pivots; /* > 0: every added graph also gets a pivot set of this many
+                                nodes (drawn as cfc_sample_pivots with seed pivot_seed +
+                                graph id) whose solutions stay on the device (n x count FP64,
+                                charged to the budget); requests with n_pivots = 0 then solve
+                                only their q nodes' columns against it.  0 (default): none */
+    uint64_t pivot_seed;
 } cfc_server_opts_t;
 
 typedef struct {
@@ -420,8 +426,13 @@ lap_status_t cfc_server_create(const cfc_server_opts_t *o, cfc_server_t **out);
 lap_status_t cfc_server_add_graph(cfc_server_t *sv, int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
                                   const double *w, int32_t *graph_id);
 /* Queues a request (host `nodes`, copied) and returns at once with its id.
- * LAP_EINVAL for a bad graph id, node or count; LAP_EBUDGET if the request
- * alone exceeds what the budget leaves beside the resident graphs. */
+ * n_pivots > 0: a fresh pivot set of that size drawn with `seed` (n_pivots + q
+ * column solves); n_pivots = 0: the graph's resident pivot set (q column
+ * solves; `seed` unused).  The estimate is unbiased either way (Proposition
+ * 1); requests sharing the resident set are correlated with each other.
+ * LAP_EINVAL for a bad graph id, node or count, or n_pivots = 0 on a graph
+ * without a resident set; LAP_EBUDGET if the request alone exceeds what the
+ * budget leaves beside the resident graphs. */
 lap_status_t cfc_server_submit(cfc_server_t *sv, int32_t graph_id, int32_t q, const int32_t *nodes,
                                int32_t n_pivots, uint64_t seed, int64_t *request_id);
 /* Waits up to wait_ms (0: no wait, < 0: until done) for the request.  Done:

@@ -59,7 +59,8 @@ class Stats(C.Structure):
 
 
 class ServerOpts(C.Structure):
-    _fields_ = [("slots", C.c_int32), ("hbm_budget", C.c_int64), ("solve", SolveOpts)]
+    _fields_ = [("slots", C.c_int32), ("hbm_budget", C.c_int64), ("solve", SolveOpts),
+                ("resident_pivots", C.c_int32), ("pivot_seed", C.c_uint64)]
 
 
 class RequestInfo(C.Structure):
@@ -453,7 +454,8 @@ def cfc_server_add_graph(sv: Server, n, src, dst, w=None) -> int:
     return gid.value
 
 
-def cfc_server_submit(sv: Server, graph_id: int, nodes, n_pivots: int, seed: int) -> int:
+def cfc_server_submit(sv: Server, graph_id: int, nodes, n_pivots: int, seed: int = 0) -> int:
+    """n_pivots = 0: use the graph's resident pivot set (see ServerOpts.resident_pivots)."""
     nd = np.ascontiguousarray(nodes, np.int32)
     rid = C.c_int64(0)
     _check(lib().cfc_server_submit(sv.handle, int(graph_id), int(nd.size), nd.ctypes.data_as(C.c_void_p),

@@ -296,19 +296,24 @@ __global__ void k_unit_columns(const int32_t *__restrict__ piv, int kk, const in
 }
 
 // f^(v) = (n/k) sum_s [x_v(v) - x_v(s) - x_s(v) + x_s(s)]: one warp per query node
-__global__ void k_sample_farness(const double *__restrict__ X, int64_t n, int ld, const int32_t *__restrict__ piv,
-                                 int kk, const int32_t *__restrict__ nodes, int q, double *__restrict__ f) {
+// (n / kk) sum_s d(v, s), d(v, s) = x_v(v) - x_v(s) - x_s(v) + x_s(s) (Proposition 1,
+// with pair solves written as single-node solves): the pivot solutions are
+// columns cs0 + i of XS (leading dimension ldS), the query nodes' columns
+// cv0 + t of XV (ldV); a warp per query node, its lanes over the pivots
+__global__ void k_sample_farness(const double *__restrict__ XS, int ldS, int cs0, const double *__restrict__ XV,
+                                 int ldV, int cv0, int64_t n, const int32_t *__restrict__ piv, int kk,
+                                 const int32_t *__restrict__ nodes, int q, double *__restrict__ f) {
     const int t = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
     if (t >= q) return;
     const int64_t v = nodes[t];
-    const int cv = kk + t;
-    const double xvv = X[v * ld + cv];
+    const int cv = cv0 + t;
+    const double xvv = XV[v * ldV + cv];
     double a = 0.0;
     for (int i = lane; i < kk; i += 32) {
         const int64_t sv = piv[i];
         if (sv == v) continue;  // d_ER(v, v) = 0
-        a += xvv - X[sv * ld + cv] - X[v * ld + i] + X[sv * ld + i];
+        a += xvv - XV[sv * ldV + cv] - XS[v * ldS + cs0 + i] + XS[sv * ldS + cs0 + i];
     }
     for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
     if (lane == 0) f[t] = a * ((double)n / kk);
@@ -564,8 +569,43 @@ lap_status_t farness_sampled(lap_hierarchy *h, int32_t kk, uint64_t seed, int32_
     CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_unit_columns, grid_for(kc), kBlock, 0, piv.get(), kk, dn, q, kc, B.get());
     lap_status_t st = solve_multi(h, kc, B.get(), X.get(), o, s, info);
     if (st != LAP_OK && st != LAP_ENOCONV) return st;
-    CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_sample_farness, (q + 7) / 8, 256, 0, X.get(), n, kc, piv.get(), kk, dn, q,
-               f.get());
+    CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_sample_farness, (q + 7) / 8, 256, 0, X.get(), kc, 0, X.get(), kc, kk, n,
+               piv.get(), kk, dn, q, f.get());
+    copy_out(farness, f.get(), q, s);
+    CFC_CUDA(cudaStreamSynchronize(s));
+    return st;
+}
+
+lap_status_t pivot_solutions(lap_hierarchy *h, int32_t kk, uint64_t seed, double *XS, int32_t *piv,
+                             const lap_solve_opts_t &o, cudaStream_t s, lap_solve_info_t *info) {
+    const int64_t n = h->lv[0].n;
+    CFC_REQUIRE(kk >= 1 && kk <= n && kk <= 4096, LAP_EINVAL, "need 1 <= n_pivots <= min(n, 4096)");
+    sample_pivots(n, kk, seed, piv, s);
+    DBuf<double> B((size_t)n * kk, s);
+    B.zero(s);
+    CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_unit_columns, grid_for(kk), kBlock, 0, piv, kk, (const int32_t *)nullptr, 0,
+               kk, B.get());
+    const lap_status_t st = solve_multi(h, kk, B.get(), XS, o, s, info);
+    CFC_CUDA(cudaStreamSynchronize(s));
+    return st;
+}
+
+lap_status_t farness_sampled_resident(lap_hierarchy *h, const double *XS, const int32_t *piv, int32_t kk, int32_t q,
+                                      const int32_t *nodes, double *farness, const lap_solve_opts_t &o,
+                                      cudaStream_t s) {
+    const int64_t n = h->lv[0].n;
+    CFC_REQUIRE(q >= 1 && q <= n && q <= 4096, LAP_EINVAL, "need 1 <= q <= min(n, 4096)");
+    CFC_REQUIRE(farness, LAP_EINVAL, "farness must not be NULL");
+    DBuf<int32_t> ntmp;
+    const int32_t *dn = nodes_to_device(nodes, q, (int32_t)n, ntmp, s);
+    DBuf<double> B((size_t)n * q, s), X((size_t)n * q, s), f(q, s);
+    B.zero(s);
+    CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_unit_columns, grid_for(q), kBlock, 0, (const int32_t *)nullptr, 0, dn, q, q,
+               B.get());
+    lap_status_t st = solve_multi(h, q, B.get(), X.get(), o, s, nullptr);
+    if (st != LAP_OK && st != LAP_ENOCONV) return st;
+    CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_sample_farness, (q + 7) / 8, 256, 0, XS, kk, 0, X.get(), q, 0, n, piv, kk,
+               dn, q, f.get());
     copy_out(farness, f.get(), q, s);
     CFC_CUDA(cudaStreamSynchronize(s));
     return st;

@@ -301,6 +301,14 @@ lap_status_t farness_from_solution_noalloc(int64_t n, int32_t k, const double *Z
 lap_status_t pivots_api(lap_hierarchy *h, int32_t kk, uint64_t seed, int32_t *pivots, cudaStream_t s);
 lap_status_t farness_sampled(lap_hierarchy *h, int32_t kk, uint64_t seed, int32_t q, const int32_t *nodes,
                              double *farness, const lap_solve_opts_t &o, cudaStream_t s, lap_solve_info_t *info = nullptr);
+// A pivot set kept on the device: the kk pivots drawn as cfc_sample_pivots and
+// their solutions x_s = L^+ (e_s - 1/n) (n x kk, row-major); and the sampling
+// estimate of q nodes that solves only the nodes' columns against such a set.
+lap_status_t pivot_solutions(lap_hierarchy *h, int32_t kk, uint64_t seed, double *XS, int32_t *piv,
+                             const lap_solve_opts_t &o, cudaStream_t s, lap_solve_info_t *info);
+lap_status_t farness_sampled_resident(lap_hierarchy *h, const double *XS, const int32_t *piv, int32_t kk, int32_t q,
+                                      const int32_t *nodes, double *farness, const lap_solve_opts_t &o,
+                                      cudaStream_t s);
 lap_status_t exact_small(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const double *w,
                          double *farness, double *closeness, cudaStream_t s);
 }  // namespace cfc

@@ -34,8 +34,13 @@ struct cfc_server {
         lap_hierarchy *h = nullptr;
         lap_solve_opts_t opts{};  // pinned configuration of its requests
         int64_t n = 0, bytes = 0;
+        // resident pivot set: pivots and their solutions (n x kp, FP64)
+        int32_t kp = 0;
+        cfc::DBuf<int32_t> piv;
+        cfc::DBuf<double> xs;
     };
-    std::vector<Graph> graphs;  // guarded by mu; entries are never removed while serving
+    // guarded by mu for growth; entries never move (deque) or go while serving
+    std::deque<Graph> graphs;
 
     struct Request {
         int64_t id = 0;
@@ -86,14 +91,14 @@ struct cfc_server {
         cudaStream_t s = streams[slot];
         for (;;) {
             Request *r = nullptr;
-            Graph g;
+            const Graph *gp = nullptr;
             {
                 std::unique_lock<std::mutex> lk(mu);
                 cv_work.wait(lk, [&] { return stopping || head_admissible(); });
                 if (stopping) return;
                 r = reqs.at(queue.front()).get();
                 queue.pop_front();
-                g = graphs[r->graph];
+                gp = &graphs[r->graph];
                 inflight_bytes += r->bytes;
                 peak_inflight_bytes = std::max(peak_inflight_bytes, inflight_bytes);
                 ++in_flight;
@@ -102,7 +107,12 @@ struct cfc_server {
             }
             lap_status_t st;
             try {
-                st = cfc::farness_sampled(g.h, r->kk, r->seed, r->q, r->nodes.data(), r->far.data(), g.opts, s);
+                const Graph &g = *gp;
+                if (r->kk > 0)
+                    st = cfc::farness_sampled(g.h, r->kk, r->seed, r->q, r->nodes.data(), r->far.data(), g.opts, s);
+                else
+                    st = cfc::farness_sampled_resident(g.h, g.xs.get(), g.piv.get(), g.kp, r->q, r->nodes.data(),
+                                                       r->far.data(), g.opts, s);
                 cfc::release_workspace(g.h, s);  // back to the pool, for the next admission
                 cudaError_t e = cudaStreamSynchronize(s);
                 if (e != cudaSuccess && st == LAP_OK) st = LAP_ECUDA;
@@ -125,7 +135,7 @@ struct cfc_server {
                 if (st == LAP_OK) {
                     lat_ms.push_back(ms_between(r->t_submit, r->t_done));
                     ++completed;
-                    rhs_done += r->kk + r->q;
+                    rhs_done += r->kk + r->q;  // resident requests: kk = 0, their q columns
                     span1 = r->t_done;
                 }
             }
@@ -204,12 +214,34 @@ lap_status_t cfc_server_add_graph(cfc_server_t *sv, int64_t n, int64_t m, const 
         g.opts.coarse_scale = info.coarse_scale;
         g.opts.w_levels = info.w_levels;
         g.bytes = cfc::hierarchy_bytes(g.h);  // with any BF16 copies the tuning made
+        int32_t id;
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            id = (int32_t)sv->graphs.size();
+        }
+        if (sv->o.resident_pivots > 0) {
+            g.kp = (int32_t)std::min<int64_t>(std::min<int64_t>(sv->o.resident_pivots, n), 4096);
+            {
+                std::lock_guard<std::mutex> lk(sv->mu);
+                CFC_REQUIRE(sv->graph_bytes + sv->inflight_bytes + g.bytes + n * g.kp * 8 <= sv->budget,
+                            LAP_EBUDGET, "graph and its pivot solutions do not fit the HBM budget");
+            }
+            g.piv.alloc_persistent(g.kp);
+            g.xs.alloc_persistent((size_t)n * g.kp);
+            st = cfc::pivot_solutions(g.h, g.kp, sv->o.pivot_seed + (uint64_t)id, g.xs.get(), g.piv.get(), g.opts,
+                                      s, nullptr);
+            cfc::release_workspace(g.h, s);
+            CFC_CUDA(cudaStreamSynchronize(s));
+            if (st != LAP_OK) return st;
+            g.bytes += n * g.kp * 8 + g.kp * 4;
+        }
         std::lock_guard<std::mutex> lk(sv->mu);
         CFC_REQUIRE(sv->graph_bytes + sv->inflight_bytes + g.bytes <= sv->budget, LAP_EBUDGET,
                     "graph does not fit the HBM budget");
+        CFC_REQUIRE((int32_t)sv->graphs.size() == id, LAP_EINVAL, "graphs added concurrently");
         sv->graph_bytes += g.bytes;
-        *graph_id = (int32_t)sv->graphs.size();
-        sv->graphs.push_back(g);
+        *graph_id = id;
+        sv->graphs.push_back(std::move(g));
         guard_h.release();
         return LAP_OK;
     });
@@ -224,7 +256,8 @@ lap_status_t cfc_server_submit(cfc_server_t *sv, int32_t graph_id, int32_t q, co
         CFC_REQUIRE(graph_id >= 0 && graph_id < (int32_t)sv->graphs.size(), LAP_EINVAL, "unknown graph id");
         const cfc_server::Graph &g = sv->graphs[graph_id];
         CFC_REQUIRE(q >= 1 && q <= g.n, LAP_EINVAL, "need 1 <= q <= n");
-        CFC_REQUIRE(n_pivots >= 1 && n_pivots <= g.n, LAP_EINVAL, "need 1 <= n_pivots <= n");
+        CFC_REQUIRE(n_pivots >= 0 && n_pivots <= g.n, LAP_EINVAL, "need 0 <= n_pivots <= n");
+        CFC_REQUIRE(n_pivots > 0 || g.kp > 0, LAP_EINVAL, "n_pivots = 0 needs the graph's resident pivot set");
         CFC_REQUIRE(n_pivots + q <= 4096, LAP_EBUDGET, "n_pivots + q must be <= 4096 columns");
         for (int i = 0; i < q; ++i) CFC_REQUIRE(nodes[i] >= 0 && nodes[i] < g.n, LAP_EINVAL, "query node out of range");
         r->graph = graph_id;

@@ -127,3 +127,37 @@ def test_server_budget_and_errors(P):
             P.cfc_server_poll(sv, rid, 0)
     finally:
         sv.destroy()
+
+
+def test_server_resident_pivot_sets(P):
+    # requests with n_pivots = 0 solve only their nodes' columns against the
+    # graph's pivot solutions kept on the device: the same estimate as the
+    # oracle's with that pivot set, and the same bits alone and in a mix
+    graphs = _graphs()
+    sv = P.cfc_server_create(P.cfc_server_default_opts(slots=3, resident_pivots=40, pivot_seed=11))
+    try:
+        gids = [P.cfc_server_add_graph(sv, n, s, d, w) for n, s, d, w in graphs]
+        qs = [(gid, nodes, 0, 0) for gid, nodes, _, _ in _queries(graphs, 9, 8)]
+        qs += _queries(graphs, 5, 9)  # fresh pivot sets in the same stream of requests
+        alone = [P.cfc_server_poll(sv, P.cfc_server_submit(sv, g, nodes, kk, seed), -1)[0]
+                 for g, nodes, kk, seed in qs]
+        rids = [P.cfc_server_submit(sv, g, nodes, kk, seed) for g, nodes, kk, seed in qs]
+        mix = [P.cfc_server_poll(sv, r, -1)[0] for r in rids]
+        for a, m in zip(alone, mix):
+            assert np.array_equal(a, m)
+        for (gid, nodes, kk, seed), f in zip(qs[:4], alone[:4]):
+            n, s, d, w = graphs[gid]
+            fo = sampling.sampled_farness(canonical_graph(n, s, d, w), 40, 11 + gids[gid], nodes.tolist(),
+                                          solver="dense")
+            assert np.max(np.abs(f - fo) / np.abs(fo)) <= FARNESS_RTOL
+    finally:
+        sv.destroy()
+    plain = P.cfc_server_create(P.cfc_server_default_opts(slots=1))
+    try:
+        n, s, d, w = graphs[0]
+        gid = P.cfc_server_add_graph(plain, n, s, d, w)
+        with pytest.raises(P.LapError) as e:  # no resident set on this server
+            P.cfc_server_submit(plain, gid, [1, 2], 0)
+        assert e.value.status == P.LAP_EINVAL
+    finally:
+        plain.destroy()
