@@ -372,21 +372,26 @@ def run_reference(args, wl, rank, world):
     print(json.dumps(line), flush=True)
 
 
+CPU_SAMPLE_ROWS = 8
+
+
 def cpu_baseline(wl):
-    """Oracle on a bounded sample of the workload: 8 of the k JL columns."""
+    """Oracle on a bounded sample of the workload: the first 8 of the k JL
+    rows.  Returns the timing and the oracle's solutions Z (8 x n)."""
     from oracle import jl
     from oracle.cg import cg_solve
     from oracle.graph import canonical_graph, laplacian
     n, s, d, w = make_graph(wl)
-    ks = 8
+    ks = CPU_SAMPLE_ROWS
     t0 = time.perf_counter()
     g = canonical_graph(n, s, d, w)
     Y = jl.jl_rhs(g, wl["k"], wl["jl_seed"])[:ks]
-    cg_solve(laplacian(g), Y.T, tol=1e-8)
+    Z, _, _ = cg_solve(laplacian(g), Y.T, tol=1e-8)
     sec = time.perf_counter() - t0
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": ks / sec, "unit": "RHS/s", "cores": cores, "kind": "oracle",
+    info = {"value": ks / sec, "unit": "RHS/s", "cores": cores, "kind": "oracle",
             "sample": f"{ks} of the {wl['k']} JL right-hand sides (canonical graph + RHS + FP64 Jacobi-CG to 1e-8)"}
+    return info, np.asarray(Z).T
 
 
 def _ranks(x):
@@ -670,7 +675,18 @@ def main():
             line["serving_resident_pivots"] = run_serving(P, SERVE_SMALL, n_queries=48, loads=(0.5,),
                                                           resident=True)
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(wl)
+            line["cpu_baseline"], Zo = cpu_baseline(wl)
+            # this run's error against the oracle on the same sample: the JL
+            # farness terms of rows 0..7 for the query node (Algorithm 1)
+            v = int(wl["nodes"][0])
+            f_or = float(((Zo - Zo[:, [v]]) ** 2).sum())
+            h = P.lap_build_hierarchy(n, src_d, dst_d, w_d, stream=sp)
+            f_gpu = float(P.cfc_farness_jl_rows(h, k, 0, CPU_SAMPLE_ROWS, wl["jl_seed"], np.array([v], np.int32),
+                                                opts=sopts, stream=sp)[0])
+            h.destroy()
+            line["parity"] = {"quantity": f"JL farness terms of rows 0-{CPU_SAMPLE_ROWS - 1} for node {v}",
+                              "oracle": f_or, "gpu": f_gpu, "rel_err": abs(f_gpu - f_or) / abs(f_or),
+                              "bound": 1e-6}
         print(json.dumps(line), flush=True)
 
 
