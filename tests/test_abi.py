@@ -41,6 +41,13 @@ def test_status_strings_and_defaults(P):
     assert o.tol == 1e-8 and o.precision == P.LAP_FP32_REFINED
     h = P.lap_default_hier_opts()
     assert h.coarse_max == 64 and h.agg_passes == 2
+    # options the autotuner fills in are left open; cycles are replayed as graphs
+    assert (o.levels_used, o.nu_coarse, o.cycle, o.coarse_scale, o.w_levels, o.k_tile) == (0, 0, 0, 0.0, 0, 0)
+    assert o.graphs == 1
+    assert "not finished" in P.lap_status_string(P.LAP_EPENDING)
+    sv = P.cfc_server_default_opts()
+    assert sv.slots == 4 and sv.hbm_budget == 0 and sv.resident_pivots == 0
+    assert sv.solve.tol == 1e-8 and sv.solve.graphs == 1
 
 
 def test_product_does_not_import_oracle():
