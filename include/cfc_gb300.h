@@ -89,11 +89,14 @@ typedef struct {
     int32_t nu_pre;       /* smoothing steps before the coarse correction (default 2) */
     int32_t nu_post;      /* smoothing steps after (default 2) */
     int32_t check_every;  /* inner iterations between host convergence reads (default 4) */
-    int32_t levels_used;  /* levels of the hierarchy the V-cycle uses: > 0 that many
+    int32_t levels_used;  /* levels of the hierarchy the cycle uses: > 0 that many
                              (at most), -1 every level, 0 (default) autotuned: the
                              first solve for a graph size and configuration times
-                             complete solves with 1, 2, 3, 4 and all levels and the
-                             fastest converged depth is kept for the process */
+                             complete solves (smoother alone, 2, 3, 4 and all levels,
+                             coarse scales, W-cycles, column tiles; each candidate
+                             stopped once it runs twice as long as the best) and the
+                             fastest converged one is kept for the process; the choice
+                             is reported in lap_solve_info_t */
     int32_t nu_coarse;    /* smoothing steps (Chebyshev degree) at a coarsest level that has
                              no dense solve, e.g. the one-level smoother-only
                              preconditioner; 0 (default): max(nu_pre, 4), or autotuned
