@@ -608,6 +608,13 @@ def main():
     dm = fam[dom]
     achieved = (dm["bytes"] / 1e9) / (dm["ms"] / 1e3) if dm["ms"] > 0 else 0.0
     traffic, traffic_kernel = read_traffic(args.workload, dom)
+    # the HBM-roofline ideal of the solve: every solver family's algorithmic
+    # bytes moved at the measured copy bandwidth (k / that time, per step)
+    solve_bytes = sum(v["bytes"] for v in solve_fams.values()) / args.steps
+    solve_ms = sum(v["ms"] for v in solve_fams.values()) / args.steps
+    ideal = {"rhs_per_s": k / (solve_bytes / (peak * 1e9)) if solve_bytes > 0 else None,
+             "solve_bytes_per_step": solve_bytes, "measured_solve_ms_per_step": solve_ms,
+             "measured_rhs_per_s_solve_kernels": k / (solve_ms / 1e3) if solve_ms > 0 else None}
 
     # setup alone (ingest + hierarchy) and solver iteration counts, for context
     h = P.lap_build_hierarchy(n, src_d, dst_d, w_d, stream=sp)
@@ -667,6 +674,7 @@ def main():
                          "algorithmic_bytes_per_launch": dm["bytes"] / max(dm["launches"], 1),
                          "launches": dm["launches"], "ms": dm["ms"]},
             "family_ms_per_step": {kf: v["ms"] / args.steps for kf, v in fam.items()},
+            "solve_roofline_ideal": ideal,
             "precision_comparison": compare,
             "clocks": clocks,
         }
