@@ -8,6 +8,18 @@ right-hand sides, the block solve to ||b - Lx|| <= 1e-8 ||b|| per column in
 FP32 PCG + V-cycle inside FP64 refinement, and the farness reduction for
 node 0 (cfc_farness_jl).  value = 64 * N / step time.
 
+The line also carries: the same step through the C ABI with host buffers
+(e2e), the dominant solver family against the measured HBM bandwidth
+(roofline, with ncu DRAM traffic from profiles/traffic.json), the solve's
+HBM-roofline ideal, solve-only rates of FP32 batched against FP64 batched and
+FP64 one right-hand side at a time, a small serving mix (p50/p99 latency),
+the oracle on 8 of the 64 columns (cpu_baseline) and this run's error
+against it (parity), and the SM clocks sampled during the timed steps.
+
+Other workloads: --workload rmat20_jl16/64/128, grid1024_jl64,
+grid4096_jl64, rmat24_jl64 (the same step), serve_mix (16 resident graphs,
+Poisson arrivals) and accuracy (both estimators against the exact farness).
+
 --impl reference times the CPU FP64 oracle on the same workload and metric.
 Run with torchrun for N > 1 GPUs: every rank solves its own independent
 instance (weak scaling, no collective on the data path).
