@@ -26,3 +26,18 @@ def test_rmat_lcc():
     import scipy.sparse.csgraph as cg
     a = sp.coo_matrix((np.ones(s.size), (s, d)), shape=(n, n))
     assert cg.connected_components(a, directed=False)[0] == 1
+
+
+def test_rmat_stream_does_not_depend_on_the_process_count(monkeypatch):
+    # chunks of samples each draw from their own seeded stream, so a spawned
+    # pool of any size yields the same graph as a serial run (small chunks
+    # here, so that scale 15 has 16 of them)
+    import synth.graphs as G
+    monkeypatch.setattr(G, "_RMAT_CHUNK", 1 << 14)
+    a = synth.rmat(15, seed=7, processes=1)
+    b = synth.rmat(15, seed=7, processes=3)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+    c = synth.rmat(15, seed=8, processes=1)
+    assert not (c[0] == a[0] and np.array_equal(c[1], a[1]))
+    key = a[1].astype(np.int64) * a[0] + a[2]
+    assert np.all(np.diff(key) > 0)  # sorted, no duplicate pairs
