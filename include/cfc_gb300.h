@@ -27,9 +27,15 @@
  *  - Dense n x k blocks are row-major with the k columns of a row
  *    contiguous (element (i, j) at [i * k + j]).
  *  - Sizes: 2 <= n < 2^31 and 2 * m < 2^31 (32-bit row pointers).
- *  - A hierarchy may be used by one call at a time (it holds the solve
- *    workspace); distinct hierarchies may run concurrently on distinct
- *    streams.
+ *  - Solves on one hierarchy may run at the same time on different streams
+ *    (and from different host threads): each stream gets its own solve
+ *    workspace, and a call that grows the hierarchy (lazy coarse levels,
+ *    BF16 copies, autotuning) holds it exclusively while it does.  Calls on
+ *    one stream run in stream order.  lap_hierarchy_destroy must not overlap
+ *    any call on the same hierarchy.
+ *  - A device reset (cudaDeviceReset) frees the library's device state
+ *    along with everything else: hierarchies and servers made before it must
+ *    not be used after it.
  */
 #ifndef CFC_GB300_H
 #define CFC_GB300_H
@@ -43,10 +49,14 @@ extern "C" {
 
 typedef enum {
     LAP_OK = 0,
-    LAP_EINVAL = 1,    /* bad argument: size, index range, weight <= 0 or not finite, NULL */
+    LAP_EINVAL = 1,    /* bad argument: size, index range, weight outside [1e-150, 1e150], NULL */
     LAP_ENOTCONN = 2,  /* the graph is not connected (Sec. 2 assumes connected G) */
     LAP_ENOMEM = 3,    /* a device allocation failed; nothing leaked */
-    LAP_ENOCONV = 4,   /* a solve hit its iteration cap; outputs hold the best iterate */
+    LAP_ENOCONV = 4,   /* a solve hit its iteration cap, or its residual became non-finite
+                          (NaN or infinite, e.g. from FP32 overflow); outputs hold the last
+                          iterate and lap_solve_info_t.max_rel_residual the (possibly NaN)
+                          residual.  cfc_exact_small: its dense FP64 factorization lost
+                          positive definiteness (weights too far apart) */
     LAP_ECUDA = 5,     /* a CUDA runtime error (the text is kept, see lap_last_error) */
     LAP_EBUDGET = 6,   /* request exceeds a documented maximum */
     LAP_ENOTIMPL = 7,
@@ -117,7 +127,8 @@ typedef struct {
 typedef struct {
     int32_t outer_iters;
     int32_t inner_iters;        /* total over all refinement steps */
-    double max_rel_residual;    /* max over columns of the final FP64 ||b - Lx|| / ||b|| */
+    double max_rel_residual;    /* max over columns of the final FP64 ||b - Lx|| / ||b||;
+                                   NaN when some column's residual is NaN */
     /* the configuration the solve ran with (the autotuner's choice where the
        options left it open); passing these back as options repeats the solve
        bit for bit without tuning */
@@ -133,6 +144,11 @@ typedef struct {
     int64_t level_n[32];
     int64_t level_nnz[32];      /* off-diagonal entries of each level's CSR */
     double setup_ms;            /* device time of lap_build_hierarchy */
+    int32_t weight_exp;         /* e with 2^e <= largest weight < 2^(e+1): the FP32 and BF16
+                                   sweeps run on the exactly scaled operator 2^-e L, so that
+                                   weights far from 1 stay inside FP32's range */
+    int32_t level_row_order[32];/* 1: the row kernels take the level's rows longest first (the
+                                   level's row lengths are very uneven); 0: natural order */
 } lap_hier_info_t;
 
 typedef struct lap_hierarchy lap_hierarchy_t;
@@ -154,10 +170,12 @@ void lap_default_solve_opts(lap_solve_opts_t *o);
  *               repeated pairs are merged with their weights summed
  *               (parallel conductances) (Sec. 6.3).
  *   w           double[m], host or device, or NULL for unit weights; each
- *               weight finite and > 0 (conductances, Sec. 2).
+ *               weight a conductance (Sec. 2) with 1e-150 <= w <= 1e150, a
+ *               range in which the FP64 sums and products of the solver
+ *               cannot overflow.
  *   opts        NULL = defaults.
  *   out         receives the hierarchy on LAP_OK, NULL otherwise.
- * Errors: LAP_EINVAL (sizes, NULL, endpoint out of range, bad weight);
+ * Errors: LAP_EINVAL (sizes, NULL, endpoint out of range, weight outside the range);
  * LAP_ENOTCONN (G not connected, Sec. 2); LAP_ENOMEM; LAP_ECUDA.
  * Synchronises `stream`.
  */
@@ -182,9 +200,16 @@ lap_status_t lap_hierarchy_info(const lap_hierarchy_t *h, lap_hier_info_t *info)
  *   X    device double[n * k] row-major, output: the zero-mean solution
  *        L^+ B of every column.  May not alias B.
  *   o    NULL = defaults.  info may be NULL.
- * Errors: LAP_EINVAL; LAP_ENOCONV (some column above tol after max_outer
- * refinement steps; X holds the best iterate, info the residual); LAP_ENOMEM;
- * LAP_ECUDA.  Synchronises `stream` (convergence is read on the host).
+ * A column is converged once its FP64 relative residual is <= tol; a NaN or
+ * infinite residual never is.  The FP32 modes scale each column's residual
+ * by a power of two before demoting it to FP32 (and the operator by
+ * 2^-weight_exp), so the inner solves see no overflow or underflow.
+ * Errors: LAP_EINVAL (also when a column of B has a non-finite 2-norm: NaN or
+ * infinite entries, or entries too large to square; X is then not written);
+ * LAP_ENOCONV (some column above tol after max_outer refinement steps, or a
+ * residual that became non-finite; X holds the last iterate, info the
+ * residual); LAP_ENOMEM; LAP_ECUDA.  Synchronises `stream` (convergence is
+ * read on the host).
  */
 lap_status_t lap_solve_multi(lap_hierarchy_t *h, int32_t k, const double *B, double *X,
                              const lap_solve_opts_t *o, void *stream, lap_solve_info_t *info);
@@ -265,8 +290,12 @@ lap_status_t cfc_farness_from_solution(int64_t n, int32_t k, const double *Z, in
  *   n, k, Z    as cfc_farness_from_solution, with k <= 256
  *   q >= 1, nodes  device int32[q]; a node outside [0, n) gets NaN
  *   farness    device double[q], output
- * The first call on a device looks up the scratch address for that device;
- * make that first call before capturing the stream into a CUDA graph.
+ * The scratch address is looked up once per device, by the first call on
+ * that device of this function, cfc_farness_from_solution or
+ * lap_build_hierarchy, with the device current; under CUDA's lazy module
+ * loading that first call also loads the library's device code, which
+ * allocates.  So make one such call on each device before memory runs short
+ * and before capturing the stream into a CUDA graph.
  * Results equal those of cfc_farness_from_solution.  All calls share the one
  * scratch array: calls whose work overlaps on the same GPU race, so order
  * them on one stream (or synchronise between them).  The call only enqueues
@@ -312,8 +341,9 @@ lap_status_t cfc_farness_sampled(lap_hierarchy_t *h, int32_t n_pivots, uint64_t 
  *   src, dst, w as lap_build_hierarchy;
  *   farness   double[n], host or device, output
  *   closeness double[n], host or device, output, or NULL
- * Errors: LAP_EINVAL, LAP_EBUDGET (n too large), LAP_ENOTCONN, LAP_ENOMEM,
- * LAP_ECUDA.  Synchronises `stream`.
+ * Errors: LAP_EINVAL, LAP_EBUDGET (n too large), LAP_ENOTCONN, LAP_ENOCONV
+ * (the FP64 factorization lost definiteness: weights too far apart),
+ * LAP_ENOMEM, LAP_ECUDA.  Synchronises `stream`.
  */
 lap_status_t cfc_exact_small(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
                              const double *w, double *farness, double *closeness, void *stream);

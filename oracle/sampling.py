@@ -66,7 +66,3 @@ def sampled_farness(g: Graph, k: int, seed: int, nodes, solver: str = "dense", t
         d = pair_resistance_solves(g, int(v), S, solver, tol)
         out[t] = (g.n / S.size) * d.sum()
     return out
-
-
-def closeness_from_farness(n: int, f):
-    return (n - 1) / np.asarray(f)

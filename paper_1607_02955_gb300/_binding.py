@@ -50,7 +50,8 @@ class SolveInfo(C.Structure):
 
 class HierInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("m", C.c_int64), ("levels", C.c_int32), ("coarse_n", C.c_int32),
-                ("level_n", C.c_int64 * 32), ("level_nnz", C.c_int64 * 32), ("setup_ms", C.c_double)]
+                ("level_n", C.c_int64 * 32), ("level_nnz", C.c_int64 * 32), ("setup_ms", C.c_double),
+                ("weight_exp", C.c_int32), ("level_row_order", C.c_int32 * 32)]
 
 
 class Stats(C.Structure):
@@ -266,7 +267,8 @@ def lap_hierarchy_info(h: Hierarchy) -> dict:
     _check(lib().lap_hierarchy_info(h.handle, C.byref(info)), "lap_hierarchy_info")
     L = info.levels
     return {"n": info.n, "m": info.m, "levels": L, "coarse_n": info.coarse_n,
-            "level_n": list(info.level_n[:L]), "level_nnz": list(info.level_nnz[:L]), "setup_ms": info.setup_ms}
+            "level_n": list(info.level_n[:L]), "level_nnz": list(info.level_nnz[:L]), "setup_ms": info.setup_ms,
+            "weight_exp": info.weight_exp, "level_row_order": list(info.level_row_order[:L])}
 
 
 def lap_solve_multi(h: Hierarchy, B, X, opts: SolveOpts | None = None, stream=None, allow_noconv=False) -> dict:

@@ -12,10 +12,11 @@
 // quotient graph (edge weights between aggregates summed, edges inside an
 // aggregate dropped), so the Galerkin operator is built by a sort-and-merge
 // of the aggregated edge list.  The coarsest level (n_c <= coarse_max) is
-// solved by the dense FP64 inverse of L_c + J/n_c, which equals L_c^+ on
-// zero-sum vectors.
+// solved by the dense FP64 inverse of L_c + alpha J/n_c (alpha = 2^wexp, of
+// the order of the weights), which equals L_c^+ on zero-sum vectors.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include <cuda_bf16.h>
 
@@ -43,6 +44,8 @@ int bits_for(int64_t n) {
 #define GRID_LOOP(i, count) \
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (count); i += (int64_t)gridDim.x * blockDim.x)
 
+// Tie-break hash of an edge: the 64-bit finaliser of MurmurHash3 (fmix64,
+// Appleby; public domain) applied to the ordered pair.
 __device__ __forceinline__ uint32_t edge_hash(uint32_t a, uint32_t b) {
     // symmetric in (a, b): the same edge gets the same tie-break from both ends
     uint32_t lo = min(a, b), hi = max(a, b);
@@ -225,36 +228,58 @@ __global__ void k_u32_to_i32(const uint32_t *__restrict__ a, int32_t *__restrict
     GRID_LOOP(i, n) b[i] = (int32_t)a[i];
 }
 
-// FP32 copies, inverse degrees, long-row flags
+// FP32 copies of 2^-wexp times the weights and degrees (an exact power-of-two
+// scaling, see lap_hierarchy::wexp), inverse degrees, long-row flags.  An
+// inverse degree beyond FP32's range (a degree that underflows after the
+// scaling) is stored as 0: the smoother then leaves that node alone instead
+// of producing infinities.
 __global__ void k_finish(const int32_t *__restrict__ rowptr, const double *__restrict__ w64,
-                         const double *__restrict__ deg64, int32_t n, int64_t nnz, float *__restrict__ w32,
-                         float *__restrict__ deg32, float *__restrict__ dinv32, double *__restrict__ dinv64,
-                         int32_t *__restrict__ nchunk) {
-    GRID_LOOP(e, nnz) w32[e] = (float)w64[e];
+                         const double *__restrict__ deg64, int32_t n, int64_t nnz, double sc,
+                         float *__restrict__ w32, float *__restrict__ deg32, float *__restrict__ dinv32,
+                         double *__restrict__ dinv64, int32_t *__restrict__ nchunk) {
+    GRID_LOOP(e, nnz) w32[e] = (float)(w64[e] * sc);
     GRID_LOOP(i, n) {
         const double d = deg64[i];
-        deg32[i] = (float)d;
-        dinv32[i] = (float)(1.0 / d);
+        const double ds = d * sc;
+        deg32[i] = (float)ds;
+        const double di = 1.0 / ds;
+        dinv32[i] = (deg32[i] > 0.f && di <= 3.0e38) ? (float)di : 0.f;
         dinv64[i] = 1.0 / d;
         const int len = rowptr[i + 1] - rowptr[i];
         nchunk[i] = len > kLongRow ? (len + kChunk - 1) / kChunk : 0;
     }
 }
 
+// largest of n positive doubles: positive doubles order like their bit
+// patterns read as unsigned integers
+__global__ void k_max_bits(const double *__restrict__ v, int64_t n, unsigned long long *__restrict__ out) {
+    unsigned long long m = 0;
+    GRID_LOOP(i, n) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(v[i]);
+        m = b > m ? b : m;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_down_sync(0xffffffffu, m, o);
+        m = t > m ? t : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
 // thread per row: round the row's weights to BF16 (via FP32) and sum the
 // rounded values in FP64, in CSR order
 __global__ void k_bf16_level(const int32_t *__restrict__ rowptr, const double *__restrict__ w64, int32_t n,
-                             uint16_t *__restrict__ wbf, float *__restrict__ degbf, float *__restrict__ dinvbf) {
+                             double sc, uint16_t *__restrict__ wbf, float *__restrict__ degbf,
+                             float *__restrict__ dinvbf) {
     GRID_LOOP(i, n) {
         double d = 0.0;
         for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
-            const uint16_t b = __bfloat16_as_ushort(__float2bfloat16_rn((float)w64[e]));
+            const uint16_t b = __bfloat16_as_ushort(__float2bfloat16_rn((float)(w64[e] * sc)));
             wbf[e] = b;
             d += (double)__uint_as_float((uint32_t)b << 16);
         }
         const float df = (float)d;
         degbf[i] = df;
-        dinvbf[i] = 1.0f / df;
+        dinvbf[i] = (df > 0.f && 1.0 / d <= 3.0e38) ? 1.0f / df : 0.f;
     }
 }
 
@@ -454,7 +479,19 @@ void contract(const int32_t *rowptr, const int32_t *col, const double *w, int32_
 
 }  // namespace
 
-void finish_level(Level &L, cudaStream_t s) {
+int max_exponent(const double *v, int64_t n, cudaStream_t s) {
+    DBuf<int64_t> m(1, s);
+    m.zero(s);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_max_bits, grid_for(n), kBlock, 0, v, n,
+               reinterpret_cast<unsigned long long *>(m.get()));
+    int64_t h = 0;
+    read_totals(m.get(), 1, &h, s);
+    double mx = 0.0;
+    std::memcpy(&mx, &h, sizeof(mx));
+    return mx > 0.0 ? std::ilogb(mx) : 0;
+}
+
+void finish_level(Level &L, int wexp, cudaStream_t s) {
     const int32_t n = L.n;
     const int64_t nnz = L.nnz;
     L.w32.alloc_persistent(std::max<int64_t>(nnz, 1));
@@ -463,8 +500,8 @@ void finish_level(Level &L, cudaStream_t s) {
     L.dinv64.alloc_persistent(n);
     DBuf<int32_t> nchunk(n, s), cfirst(n, s), isl(n, s), lidx(n, s);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_finish, grid_for(std::max<int64_t>(nnz, n)), kBlock, 0, L.rowptr.get(),
-               L.w64.get(), L.deg64.get(), n, nnz, L.w32.get(), L.deg32.get(), L.dinv32.get(), L.dinv64.get(),
-               nchunk.get());
+               L.w64.get(), L.deg64.get(), n, nnz, std::ldexp(1.0, -wexp), L.w32.get(), L.deg32.get(),
+               L.dinv32.get(), L.dinv64.get(), nchunk.get());
     // the counts and the round statistics come back with one synchronisation
     DBuf<int64_t> tot(4, s);
     tot.zero(s);
@@ -505,13 +542,13 @@ void finish_level(Level &L, cudaStream_t s) {
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_set_last, 1, 1, 0, L.long_first.get(), L.n_long, L.n_chunks);
 }
 
-void ensure_bf16(Level &L, cudaStream_t s) {
+void ensure_bf16(Level &L, int wexp, cudaStream_t s) {
     if (L.wbf.get()) return;
     L.wbf.alloc_persistent(std::max<int64_t>(L.nnz, 1));
     L.degbf.alloc_persistent(L.n);
     L.dinvbf.alloc_persistent(L.n);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_bf16_level, grid_for(L.n), kBlock, 0, L.rowptr.get(), L.w64.get(), L.n,
-               L.wbf.get(), L.degbf.get(), L.dinvbf.get());
+               std::ldexp(1.0, -wexp), L.wbf.get(), L.degbf.get(), L.dinvbf.get());
 }
 
 void dense_spd_inverse_small(double *A, int n, int *d_flag, cudaStream_t s) {
@@ -531,8 +568,8 @@ void dense_spd_inverse_large(double *A, int n, int *d_flag, cudaStream_t s) {
 }
 
 void build_dense(const int32_t *rowptr, const int32_t *col, const double *w, const double *deg, int32_t n,
-                 double *M, cudaStream_t s) {
-    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_fill, grid_for((int64_t)n * n), kBlock, 0, M, (int64_t)n * n, 1.0 / n);
+                 double alpha, double *M, cudaStream_t s) {
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_fill, grid_for((int64_t)n * n), kBlock, 0, M, (int64_t)n * n, alpha / n);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_dense_scatter, grid_for(n), kBlock, 0, rowptr, col, w, deg, n, M);
 }
 
@@ -550,7 +587,8 @@ void init_levels(lap_hierarchy &h, Csr64 &fine, const lap_hier_opts_t &o, cudaSt
     h.hopts = o;
     h.complete = false;
     h.coarse_n = 0;
-    finish_level(L0, s);
+    h.wexp = max_exponent(L0.w64.get(), std::max<int64_t>(L0.nnz, 1), s);
+    finish_level(L0, h.wexp, s);
     if (L0.n <= std::min(256, std::max(2, o.coarse_max)) || o.max_levels <= 1) grow_levels(h, 0, s);
 }
 
@@ -620,7 +658,7 @@ void grow_levels(lap_hierarchy &h, int target, cudaStream_t s) {
         Cl.w64 = std::move(C.w);
         Cl.deg64 = std::move(C.deg);
         h.lv.push_back(std::move(Cl));
-        finish_level(h.lv.back(), s);
+        finish_level(h.lv.back(), h.wexp, s);
         CFC_CUDA(cudaEventRecord(ev1, s));
         CFC_CUDA(cudaEventSynchronize(ev1));
         float ms = 0.f;
@@ -638,7 +676,9 @@ void grow_levels(lap_hierarchy &h, int target, cudaStream_t s) {
     if (Lc.n <= 256) {
         const int nc = Lc.n;
         h.coarse_inv.alloc_persistent((size_t)nc * nc);
-        build_dense(Lc.rowptr.get(), Lc.col.get(), Lc.w64.get(), Lc.deg64.get(), nc, h.coarse_inv.get(), s);
+        // the constant mode gets eigenvalue 2^wexp, of the order of the weights
+        build_dense(Lc.rowptr.get(), Lc.col.get(), Lc.w64.get(), Lc.deg64.get(), nc, std::ldexp(1.0, h.wexp),
+                    h.coarse_inv.get(), s);
         DBuf<int> flag(1, s);
         flag.zero(s);
         if (nc <= 160) dense_spd_inverse_small(h.coarse_inv.get(), nc, flag.get(), s);
@@ -646,8 +686,12 @@ void grow_levels(lap_hierarchy &h, int target, cudaStream_t s) {
         int hf = 0;
         CFC_CUDA(cudaMemcpyAsync(&hf, flag.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
         CFC_CUDA(cudaStreamSynchronize(s));
-        CFC_REQUIRE(hf == 0, LAP_ENOTCONN, "coarsest operator singular: graph not connected");
-        h.coarse_n = nc;
+        // The graph is connected (checked at ingest), so a non-positive pivot
+        // means FP64 lost the matrix's definiteness (weights many orders of
+        // magnitude apart): the coarsest level is then smoothed instead of
+        // solved densely, which keeps the cycle a valid preconditioner.
+        if (hf == 0) h.coarse_n = nc;
+        else h.coarse_inv.release();
         CFC_CUDA(cudaEventRecord(ev1, s));
         CFC_CUDA(cudaEventSynchronize(ev1));
         float ms = 0.f;

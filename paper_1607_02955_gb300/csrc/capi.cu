@@ -273,6 +273,7 @@ lap_status_t lap_build_hierarchy(int64_t n, int64_t m, const int32_t *src, const
             h->eid = std::move(g.eid);
             init_levels(*h, g, o, s);
             if (o.eager) grow_levels(*h, 0, s);
+            noalloc_prepare();  // the allocation-free entry point's scratch, on this device
             CFC_CUDA(cudaEventRecord(e1, s));
             CFC_CUDA(cudaEventSynchronize(e1));
             float ms = 0.f;
@@ -311,6 +312,8 @@ lap_status_t lap_hierarchy_info(const lap_hierarchy_t *h, lap_hier_info_t *info)
             info->level_nnz[l] = h->lv[l].nnz;
         }
         info->setup_ms = h->setup_ms;
+        info->weight_exp = h->wexp;
+        for (size_t l = 0; l < h->lv.size() && l < 32; ++l) info->level_row_order[l] = h->lv[l].order.get() ? 1 : 0;
         return LAP_OK;
     });
 }

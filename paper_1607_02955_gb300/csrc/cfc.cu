@@ -319,7 +319,7 @@ __global__ void k_sample_farness(const double *__restrict__ XS, int ldS, int cs0
     if (lane == 0) f[t] = a * ((double)n / kk);
 }
 
-// exact: f(v) = n L+_vv + tr L+ with L+ = M^{-1} - J/n
+// exact: f(v) = n L+_vv + tr L+ with L+ = M^{-1} - J/(alpha n), M = L + alpha J/n
 __global__ void k_trace(const double *__restrict__ Minv, int n, double *__restrict__ tr) {
     __shared__ double sm[1024];
     double s = 0.0;
@@ -333,11 +333,11 @@ __global__ void k_trace(const double *__restrict__ Minv, int n, double *__restri
     if (threadIdx.x == 0) tr[0] = sm[0];
 }
 
-__global__ void k_exact_farness(const double *__restrict__ Minv, int n, const double *__restrict__ tr,
+__global__ void k_exact_farness(const double *__restrict__ Minv, int n, double alpha, const double *__restrict__ tr,
                                 double *__restrict__ f, double *__restrict__ c) {
     GRID_LOOP(v, n) {
-        const double lpv = Minv[(size_t)v * n + v] - 1.0 / n;
-        const double trl = tr[0] - 1.0;
+        const double lpv = Minv[(size_t)v * n + v] - 1.0 / (alpha * n);
+        const double trl = tr[0] - 1.0 / alpha;
         const double fv = (double)n * lpv + trl;
         f[v] = fv;
         if (c) c[v] = (double)(n - 1) / fv;
@@ -447,6 +447,7 @@ lap_status_t farness_from_solution(int64_t n, int32_t k, const double *Z, int32_
     CFC_REQUIRE(q >= 1 && q <= n, LAP_EINVAL, "need 1 <= q <= n");
     CFC_REQUIRE(Z && farness, LAP_EINVAL, "Z and farness must not be NULL");
     CFC_REQUIRE(is_device_pointer(Z), LAP_EINVAL, "Z must be a device pointer");
+    noalloc_prepare();  // the allocation-free variant's scratch, on this device
     DBuf<int32_t> ntmp;
     const int32_t *dn = nodes_to_device(nodes, q, (int32_t)n, ntmp, s);
     const int P = (int)std::min<int64_t>(2 * num_sms_public(), (n + kRedRows - 1) / kRedRows);
@@ -493,6 +494,11 @@ double *noalloc_scratch() {
     return ptr[dev];
 }
 
+}  // namespace
+
+void noalloc_prepare() { noalloc_scratch(); }
+
+namespace {
 // k_jl_farness with a range check: a node outside [0, n) gets NaN
 __global__ void k_jl_farness_checked(const double *__restrict__ Z, int64_t n, int k, const double *__restrict__ S,
                                      const double *__restrict__ T, const int32_t *__restrict__ nodes, int q,
@@ -619,7 +625,9 @@ lap_status_t exact_small(int64_t n, int64_t m, const int32_t *src, const int32_t
     Csr64 g;
     ingest(n, m, src, dst, w, s, g);
     DBuf<double> M((size_t)n * n, s), tr(1, s), f(n, s), c(n, s);
-    build_dense(g.rowptr.get(), g.col.get(), g.w.get(), g.deg.get(), (int32_t)n, M.get(), s);
+    // the constant mode of M gets an eigenvalue of the order of the weights
+    const double alpha = std::ldexp(1.0, max_exponent(g.w.get(), std::max<int64_t>(g.nnz, 1), s));
+    build_dense(g.rowptr.get(), g.col.get(), g.w.get(), g.deg.get(), (int32_t)n, alpha, M.get(), s);
     DBuf<int> flag(1, s);
     flag.zero(s);
     if (n <= 160) dense_spd_inverse_small(M.get(), (int)n, flag.get(), s);
@@ -627,10 +635,12 @@ lap_status_t exact_small(int64_t n, int64_t m, const int32_t *src, const int32_t
     int hf = 0;
     CFC_CUDA(cudaMemcpyAsync(&hf, flag.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
     CFC_CUDA(cudaStreamSynchronize(s));
-    CFC_REQUIRE(hf == 0, LAP_ENOTCONN, "L + J/n is singular: graph not connected");
+    // connectivity was checked at ingest: a non-positive pivot is FP64 losing definiteness
+    CFC_REQUIRE(hf == 0, LAP_ENOCONV,
+                "the dense FP64 factorization of L + alpha J/n lost positive definiteness (weights too far apart)");
     CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_trace, 1, 1024, 0, M.get(), (int)n, tr.get());
-    CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_exact_farness, grid_for(n), kBlock, 0, M.get(), (int)n, tr.get(), f.get(),
-               closeness ? c.get() : nullptr);
+    CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_exact_farness, grid_for(n), kBlock, 0, M.get(), (int)n, alpha, tr.get(),
+               f.get(), closeness ? c.get() : nullptr);
     copy_out(farness, f.get(), n, s);
     if (closeness) copy_out(closeness, c.get(), n, s);
     CFC_CUDA(cudaStreamSynchronize(s));

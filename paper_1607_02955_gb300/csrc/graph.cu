@@ -17,9 +17,9 @@ __global__ void k_validate(const int32_t *__restrict__ src, const int32_t *__res
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
         const int32_t u = src[e], v = dst[e];
         bool ok = u >= 0 && v >= 0 && u < n && v < n;
-        if (w) {
+        if (w) {  // conductances (Sec. 2), in a range whose sums and products FP64 holds
             const double x = w[e];
-            ok = ok && isfinite(x) && x > 0.0;
+            ok = ok && x >= 1e-150 && x <= 1e150;
         }
         if (!ok) atomicOr(flag, 1);
         keep[e] = (ok && u != v) ? 1 : 0;
@@ -207,7 +207,7 @@ void ingest(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const 
     scan_exclusive_i32_total(keep.get(), pos.get(), m, tot.get() + 1, s);
     int64_t h[4];
     read_totals(tot.get(), 2, h, s);
-    CFC_REQUIRE(h[0] == 0, LAP_EINVAL, "edge endpoint out of range or weight not finite and > 0");
+    CFC_REQUIRE(h[0] == 0, LAP_EINVAL, "edge endpoint out of range or weight outside [1e-150, 1e150]");
     const int64_t kept = h[1];
     CFC_REQUIRE(kept > 0, LAP_ENOTCONN, "graph has no edges besides self-loops");
     const int64_t len = 2 * kept;

@@ -230,8 +230,13 @@ void grow_levels(lap_hierarchy &h, int target, cudaStream_t s);  // target 0: al
 // FP32 and then to BF16 (nearest, ties to even); the degrees are the FP64
 // row sums of the rounded weights, rounded to FP32, so the level stays an
 // exact Laplacian (null space = constants) of the rounded weights.
-void ensure_bf16(Level &L, cudaStream_t s);
-void finish_level(Level &L, cudaStream_t s);  // FP32 copies, inverse degrees, long-row split
+// wexp: the hierarchy's weight exponent; the FP32 and BF16 copies hold
+// w * 2^-wexp (see lap_hierarchy::wexp)
+void ensure_bf16(Level &L, int wexp, cudaStream_t s);
+void finish_level(Level &L, int wexp, cudaStream_t s);  // FP32 copies, inverse degrees, long-row split
+// Exponent of the largest of n positive FP64 values (device array): the e with
+// 2^e <= max < 2^(e+1).  Synchronises s.
+int max_exponent(const double *v, int64_t n, cudaStream_t s);
 
 // dense SPD inverse (in place, FP64, row-major n x n) -- used for the
 // coarsest level (single CTA, n <= 160) and cfc_exact_small (global memory).
@@ -250,7 +255,13 @@ struct lap_hierarchy {
     bool complete = false;            // coarsening finished (no further levels)
     std::vector<double> level_ms;     // device time to build each level (level 0: ingest)
     int32_t coarse_n = 0;             // dense coarsest size (0: none)
-    cfc::DBuf<double> coarse_inv;     // (L_c + J/n_c)^{-1}, row-major
+    cfc::DBuf<double> coarse_inv;     // (L_c + 2^wexp J/n_c)^{-1}, row-major
+    // Weight exponent: the largest level-0 weight lies in [2^wexp, 2^(wexp+1)).
+    // The FP32 (and BF16) operators of every level are those of 2^-wexp L, an
+    // exact power-of-two scaling, so that weights far from 1 (conductances of
+    // any magnitude, Sec. 2) neither overflow nor fall below FP32's normal
+    // range; the FP64 copies are unscaled.  0 for weights in [1, 2).
+    int32_t wexp = 0;
     double setup_ms = 0;
     // One solve workspace per stream, grown on demand and reused (stream
     // order keeps consecutive solves on one stream apart), so solves on
@@ -285,8 +296,10 @@ void release_workspace(lap_hierarchy *h, cudaStream_t s);
 // Device bytes held by a hierarchy (levels, dense coarsest inverse), workspaces excluded.
 int64_t hierarchy_bytes(const lap_hierarchy *h);
 // amg.cu
+// M = L + alpha J/n (dense, row-major): (L + alpha J/n)^{-1} = L^+ + J/(alpha n)
+// for a connected graph; alpha of the order of the weights keeps M well scaled
 void build_dense(const int32_t *rowptr, const int32_t *col, const double *w, const double *deg, int32_t n,
-                 double *M, cudaStream_t s);
+                 double alpha, double *M, cudaStream_t s);
 // cfc.cu
 // rows row0 .. row0 + k - 1 of the k_total-row Q (row0 a multiple of 32)
 void jl_rhs(lap_hierarchy *h, int k_total, int row0, int k, int ld, uint64_t seed, double *Y, cudaStream_t s);
@@ -296,6 +309,9 @@ lap_status_t farness_jl_rows(lap_hierarchy *h, int32_t k_total, int32_t row0, in
                              const int32_t *nodes, double *farness, const lap_solve_opts_t &o, cudaStream_t s);
 lap_status_t farness_from_solution(int64_t n, int32_t k, const double *Z, int32_t q, const int32_t *nodes,
                                    double *farness, cudaStream_t s);
+// Looks up (once per device, with the device current) the address of the
+// fixed scratch array of farness_from_solution_noalloc.
+void noalloc_prepare();
 lap_status_t farness_from_solution_noalloc(int64_t n, int32_t k, const double *Z, int32_t q, const int32_t *nodes,
                                            double *farness, cudaStream_t s);
 lap_status_t pivots_api(lap_hierarchy *h, int32_t kk, uint64_t seed, int32_t *pivots, cudaStream_t s);

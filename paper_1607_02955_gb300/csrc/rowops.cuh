@@ -187,6 +187,17 @@ __device__ __forceinline__ float d2f(double d) {
     }
     return __uint_as_float(((uint32_t)(b >> 63) << 31) | (ex << 23) | m);
 }
+// x * 2^e by an integer add on the exponent field where the result stays a
+// normal number (exact either way); zeros, subnormals, infinities, NaNs and
+// results outside the normal range take ldexp.
+__device__ __forceinline__ double scale2(double x, int e) {
+    if (e == 0) return x;
+    const long long b = __double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (ex == 0 || ex == 0x7ff || ex + e <= 0 || ex + e >= 0x7ff) return ldexp(x, e);
+    return __longlong_as_double(b + ((long long)e << 52));
+}
+
 template <typename T>
 __device__ __forceinline__ T from_double(double d);
 template <>

@@ -78,8 +78,13 @@ struct OpSpmvDot {
     }
 };
 
-// FP64 outer residual r = b - L x, written in the inner type; sum r^2;
-// relres_j = ||r_j|| / ||b_j|| ; active_j = relres_j > tol
+// FP64 outer residual r = b - L x, written in the inner type scaled by
+// 2^rexp_j (a per-column power of two, so that the FP32 copy and its squares
+// stay inside FP32's normal range whatever the residual's size); sum r^2;
+// relres_j = ||r_j|| / ||b_j||.  A column stays active until relres_j <= tol
+// holds, so a NaN residual never counts as converged.  With scaling on, fin
+// also predicts the exponent of the next refinement step's residual (this
+// one reduced by the inner tolerance), used by the next residual pass.
 template <typename Tin>
 struct OpResid64 {
     using V = typename Vec<double>::V;
@@ -93,6 +98,9 @@ struct OpResid64 {
     double *relres;
     int32_t *active;
     double tol;
+    const int32_t *rexp;      // exponent of this pass's scaling
+    int32_t *rexp_next;       // predicted exponent for the next pass (null: no scaling)
+    double pred;              // inner tolerance / sqrt(n): predicted RMS of the next residual per unit norm
     __device__ V gather(int j, int c0) const { return vldg<double>(x + (size_t)j * ld + c0); }
     struct Pre {
         double d;
@@ -106,14 +114,16 @@ struct OpResid64 {
         for (int v = 0; v < VW; ++v) {
             const double rv = (vel(bi, v) + vel(s, v)) - pr.d * vel(xi, v);
             acc.add(0, v, rv * rv);
-            r[(size_t)i * ld + c0 + v] = from_double<Tin>(rv);
+            r[(size_t)i * ld + c0 + v] = from_double<Tin>(scale2(rv, __ldg(rexp + c0 + v)));
         }
     }
     __device__ void fin(int c, const double *sums) const {
         const double bn = bnorm[c];
-        const double rr = bn > 0.0 ? sqrt(sums[0]) / bn : 0.0;
+        const double rn = sqrt(sums[0]);
+        const double rr = bn > 0.0 ? rn / bn : 0.0;
         relres[c] = rr;
-        active[c] = (bn > 0.0 && rr > tol) ? 1 : 0;
+        active[c] = (bn > 0.0 && !(rr <= tol)) ? 1 : 0;
+        if (rexp_next) rexp_next[c] = (rn * pred > 0.0 && isfinite(rn)) ? -ilogb(rn * pred) : rexp[c];
     }
 };
 
@@ -383,7 +393,7 @@ struct OpUpdateP {
     __device__ void fin(int, const double *) const {}
 };
 
-// first outer step (x = 0): r = b in the inner type
+// first outer step (x = 0): r = b in the inner type, scaled by 2^rexp
 template <typename Tin>
 struct OpCastB {
     using V = typename Vec<double>::V;
@@ -391,57 +401,62 @@ struct OpCastB {
     const double *b;
     Tin *r;
     int ld;
+    const int32_t *rexp;
     template <class Acc>
     __device__ void row(int i, int c0, Acc &) const {
         const size_t o = (size_t)i * ld + c0;
         const V bi = vld<double>(b + o);
 #pragma unroll
-        for (int v = 0; v < VW; ++v) r[o + v] = from_double<Tin>(vel(bi, v));
+        for (int v = 0; v < VW; ++v) r[o + v] = from_double<Tin>(scale2(vel(bi, v), __ldg(rexp + c0 + v)));
     }
     __device__ void fin(int, const double *) const {}
 };
 
-// first outer step of a direct solve: r = b in the inner type, ||b|| from
-// the same pass (in the inner type: the norm only scales the stopping test)
-template <typename Tin>
-struct OpCastBNorm {  // runs as a k_rows<Tin> kernel: lanes of Vec<Tin>::W columns
-    static constexpr int VW = Vec<Tin>::W;
+// Column state of the first outer step from ||b_j|| (FP64): relres = 1 and
+// active for a nonzero column, and (with scaling on) the exponents that
+// scale b to unit RMS and the next residual to its predicted RMS.
+__device__ __forceinline__ void init_column(int c, double bn, double inv_sqrt_n, double pred, double *relres,
+                                            int32_t *active, int32_t *rexp0, int32_t *rexp1) {
+    relres[c] = bn > 0.0 ? 1.0 : 0.0;
+    active[c] = bn > 0.0 ? 1 : 0;
+    if (rexp0) {
+        const bool ok = bn > 0.0 && isfinite(bn);
+        rexp0[c] = ok ? -ilogb(bn * inv_sqrt_n) : 0;
+        rexp1[c] = ok ? -ilogb(bn * pred) : 0;
+    }
+}
+
+// ||b_j|| in FP64 (direct solves: B is the caller's padded block)
+struct OpColNorm64 {
+    using V = typename Vec<double>::V;
+    static constexpr int VW = Vec<double>::W;
     const double *b;
-    Tin *r;
     int ld;
     double *bnorm, *relres;
-    int32_t *active;
+    int32_t *active, *rexp0, *rexp1;
+    double inv_sqrt_n, pred;
     template <class Acc>
     __device__ void row(int i, int c0, Acc &acc) const {
-        const size_t o = (size_t)i * ld + c0;
-        constexpr int DW = Vec<double>::W;
-        static_assert(VW == DW || VW == 2 * DW, "lane width");
-        const typename Vec<double>::V b0 = vld<double>(b + o);
-        typename Vec<double>::V b1 = vzero<typename Vec<double>::V>();
-        if constexpr (VW > DW) b1 = vld<double>(b + o + DW);
+        const V bi = vld<double>(b + (size_t)i * ld + c0);
 #pragma unroll
-        for (int v = 0; v < VW; ++v) {
-            const Tin x = from_double<Tin>(v < DW ? vel(b0, v) : vel(b1, v - DW));
-            r[o + v] = x;
-            acc.add(0, v, x * x);
-        }
+        for (int v = 0; v < VW; ++v) acc.add(0, v, vel(bi, v) * vel(bi, v));
     }
     __device__ void fin(int c, const double *s) const {
-        bnorm[c] = sqrt(s[0]);
-        relres[c] = s[0] > 0.0 ? 1.0 : 0.0;
-        active[c] = s[0] > 0.0 ? 1 : 0;
+        const double bn = sqrt(s[0]);
+        bnorm[c] = bn;
+        init_column(c, bn, inv_sqrt_n, pred, relres, active, rexp0, rexp1);
     }
 };
 
 __global__ void k_init_cols(const double *__restrict__ bnorm, double *__restrict__ relres,
-                            int32_t *__restrict__ active, int ld) {
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ld; c += gridDim.x * blockDim.x) {
-        relres[c] = bnorm[c] > 0.0 ? 1.0 : 0.0;
-        active[c] = bnorm[c] > 0.0 ? 1 : 0;
-    }
+                            int32_t *__restrict__ active, int32_t *__restrict__ rexp0, int32_t *__restrict__ rexp1,
+                            double inv_sqrt_n, double pred, int ld) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ld; c += gridDim.x * blockDim.x)
+        init_column(c, bnorm[c], inv_sqrt_n, pred, relres, active, rexp0, rexp1);
 }
 
-// x64 += d (active columns only)
+// x64 += d 2^-(wexp + rexp_j) (active columns only): the inner solve ran on
+// the operator 2^-wexp L and the right-hand side 2^rexp_j r
 template <typename Tin>
 struct OpAddCorr {
     using V = typename Vec<double>::V;
@@ -450,13 +465,15 @@ struct OpAddCorr {
     const Tin *d;
     int ld;
     const int32_t *active;
+    const int32_t *rexp;
+    int wexp;
     template <class Acc>
     __device__ void row(int i, int c0, Acc &) const {
         const size_t o = (size_t)i * ld + c0;
         V xi = vld<double>(x + o);
 #pragma unroll
         for (int v = 0; v < VW; ++v)
-            if (active[c0 + v]) vel(xi, v) += to_double<Tin>(d[o + v]);
+            if (active[c0 + v]) vel(xi, v) += scale2(to_double<Tin>(d[o + v]), -(wexp + __ldg(rexp + c0 + v)));
         vst<double>(x + o, xi);
     }
     __device__ void fin(int, const double *) const {}
@@ -521,16 +538,17 @@ __global__ void k_copy_unpad(const double *__restrict__ src, int ld, double *__r
     }
 }
 
-// x_c = M^{-1} b_c with the dense FP64 inverse (coarsest level), FP64 sums
+// x_c = 2^e M^{-1} b_c with the dense FP64 inverse (coarsest level), FP64
+// sums; e = wexp when the cycle runs on the operator 2^-wexp L (FP32), else 0
 template <typename T>
 __global__ void k_coarse_dense(const double *__restrict__ Minv, int nc, const T *__restrict__ b, T *__restrict__ x,
-                               int ld, int k) {
+                               int ld, int k, int e) {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nc * k; t += gridDim.x * blockDim.x) {
         const int I = t / k, c = t - (t / k) * k;
         const double *row = Minv + (size_t)I * nc;
         double s = 0.0;
         for (int J = 0; J < nc; ++J) s += row[J] * (double)b[(size_t)J * ld + c];
-        x[(size_t)I * ld + c] = (T)s;
+        x[(size_t)I * ld + c] = (T)scale2(s, e);
     }
 }
 
@@ -561,6 +579,7 @@ struct ColState {
     double *bnorm, *relres, *alpha, *beta, *rz, *rr0, *mu;
     void *alpha_t, *beta_t, *mu_t;  // the same scalars in the inner arithmetic type
     int32_t *active_out, *active_in;
+    int32_t *rexp[2];  // residual exponents of even and odd refinement steps
 };
 
 template <typename Tin, int KT>
@@ -729,6 +748,12 @@ struct Solver {
 
     bool level0_is_dense() const { return nlev == 1 && coarse_n == h->lv[0].n && hsize == 1; }
 
+    // The FP32 sweeps run on 2^-wexp L and on residuals scaled per column by
+    // powers of two (exact: FP32 results are those of the unscaled problem
+    // wherever that stays in range); FP64 sweeps are unscaled.
+    static constexpr bool kScaled = std::is_same<Tin, float>::value;
+    int op_wexp() const { return kScaled ? h->wexp : 0; }
+
     // ---------------- V-cycle on level l: b = lb[l] -> x = lx[l].
     // first_done: x already holds the first smoothing step e D^{-1} b (fused
     // into the PCG update); dot: the level-0 final step also computes the PCG
@@ -743,7 +768,7 @@ struct Solver {
             const int threads = 128;
             const int blocks = std::max(1, std::min((nc * ld + threads - 1) / threads, 8 * num_sms()));
             CFC_LAUNCH(LAP_KF_COARSE_LEVELS, s, (double)nc * nc * 8 + 2.0 * nc * ld * et, k_coarse_dense<Tin>,
-                       blocks, threads, 0, h->coarse_inv.get(), nc, lb[l], lx[l], ld, ld);
+                       blocks, threads, 0, h->coarse_inv.get(), nc, lb[l], lx[l], ld, ld, op_wexp());
             return false;
         }
         // pre-smoothing from zero
@@ -910,8 +935,14 @@ struct Solver {
         const Level &L0 = h->lv[0];
         const int64_t n = L0.n;
         const double v64 = vec_bytes(n, ld, 1, 8);
+        const double inv_sqrt_n = 1.0 / std::sqrt((double)n);
+        // predicted RMS of the next refinement step's residual per unit of this
+        // one's norm: the inner solve reduces it by about its tolerance
+        const double itol = (o.precision == LAP_FP64) ? std::max(o.tol * 0.5, 1e-15) : o.inner_tol;
+        const double pred = std::max(itol, 1e-7) * inv_sqrt_n;
+        int32_t *rx0 = kScaled ? cs.rexp[0] : nullptr, *rx1 = kScaled ? cs.rexp[1] : nullptr;
         // b64 = B (padded), projected to zero mean; bnorm (direct: B is used in
-        // place and its norm comes with the first cast below)
+        // place and its norm comes with the first step below)
         if (!direct) {
             const int64_t tot = n * ld;
             const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 8 * num_sms());
@@ -924,16 +955,19 @@ struct Solver {
         int outer = 0, inner_total = 0;
         bool converged = false;
         double maxrel = 0.0;
-        std::vector<double> hrel(ld);
+        std::vector<double> hrel(ld), hbn(ld);
         for (outer = 0;; ++outer) {
+            // step j's residual is written scaled by 2^rexp[j % 2]; its pass
+            // predicts rexp[(j + 1) % 2] for the next step
+            const int32_t *rx_cur = cs.rexp[outer & 1];
             // FP64 residual, written to r in the inner type (x = 0 at the first step: r = b)
             if (outer == 0 && direct) {
-                rows<Tin, 1>(LAP_KF_BLAS1, n, OpCastBNorm<Tin>{b64, r, ld, cs.bnorm, cs.relres, cs.active_out},
-                             v64 + vec_bytes(n, ld, 1, sizeof(Tin)));
+                rowsd<1>(n, OpColNorm64{b64, ld, cs.bnorm, cs.relres, cs.active_out, rx0, rx1, inv_sqrt_n, pred}, v64);
+                rowsd<0>(n, OpCastB<Tin>{b64, r, ld, rx_cur}, v64 + vec_bytes(n, ld, 1, sizeof(Tin)));
             } else if (outer == 0) {
-                rowsd<0>(n, OpCastB<Tin>{b64, r, ld}, v64 + vec_bytes(n, ld, 1, sizeof(Tin)));
                 CFC_LAUNCH(LAP_KF_BLAS1, s, 0.0, k_init_cols, (ld + 255) / 256, 256, 0, cs.bnorm, cs.relres,
-                           cs.active_out, ld);
+                           cs.active_out, rx0, rx1, inv_sqrt_n, pred, ld);
+                rowsd<0>(n, OpCastB<Tin>{b64, r, ld, rx_cur}, v64 + vec_bytes(n, ld, 1, sizeof(Tin)));
             } else {
                 constexpr int RPB = RPB64;
                 const int nvb_short = (L0.n + RPB - 1) / RPB;
@@ -941,7 +975,8 @@ struct Solver {
                 const int nvb = nvb_short + nvb_long;
                 dim3 grid(red_grid(nvb), ntiles64);
                 using Op = OpResid64<Tin>;
-                Op op{lv_view(L0), x64, b64, r, ld, cs.bnorm, cs.relres, cs.active_out, o.tol};
+                Op op{lv_view(L0), x64,   b64, r, ld, cs.bnorm, cs.relres, cs.active_out, o.tol, rx_cur,
+                      kScaled ? cs.rexp[(outer + 1) & 1] : nullptr, pred};
                 const double bytes = mat_bytes(L0, 8) + 2 * v64 + vec_bytes(n, ld, 1, sizeof(Tin));
                 if (L0.n_chunks > 0) {
                     CFC_LAUNCH(LAP_KF_RESID64, s, 0.0, (k_chunk_sums<double, K64, Op>), dim3(nvb_long, ntiles64),
@@ -956,22 +991,33 @@ struct Solver {
             }
             CFC_CUDA(cudaMemcpyAsync(h_active, cs.active_out, ld * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
             CFC_CUDA(cudaMemcpyAsync(hrel.data(), cs.relres, ld * sizeof(double), cudaMemcpyDeviceToHost, s));
+            if (outer == 0)
+                CFC_CUDA(cudaMemcpyAsync(hbn.data(), cs.bnorm, ld * sizeof(double), cudaMemcpyDeviceToHost, s));
             CFC_CUDA(cudaStreamSynchronize(s));
+            if (outer == 0)
+                for (int c = 0; c < ld; ++c)
+                    CFC_REQUIRE(std::isfinite(hbn[c]), LAP_EINVAL,
+                                "a column of B has a non-finite 2-norm (NaN or infinite entries, or entries too "
+                                "large to square)");
             int na = 0;
+            bool finite = true;
             maxrel = 0.0;
             for (int c = 0; c < ld; ++c) {
                 na += h_active[c] ? 1 : 0;
-                maxrel = std::max(maxrel, hrel[c]);
+                if (!std::isfinite(hrel[c])) finite = false;
+                if (std::isnan(hrel[c]) || hrel[c] > maxrel) maxrel = hrel[c];  // a NaN is kept
+                if (std::isnan(maxrel)) break;
             }
-            if (na == 0) {
+            if (na == 0 && finite) {
                 converged = true;
                 break;
             }
-            if (outer >= o.max_outer || past_trial_deadline()) break;
+            // a non-finite residual cannot recover: stop with LAP_ENOCONV
+            if (!finite || outer >= o.max_outer || past_trial_deadline()) break;
             // inner solve of L d = r; d lives in lt-independent buffer `dbuf`
-            const double itol = (o.precision == LAP_FP64) ? std::max(o.tol * 0.5, 1e-15) : o.inner_tol;
             inner_total += inner_pcg(dbuf, o.max_inner, itol);
-            rowsd<0>(n, OpAddCorr<Tin>{x64, dbuf, ld, cs.active_out}, 2 * v64 + vec_bytes(n, ld, 1, sizeof(Tin)));
+            rowsd<0>(n, OpAddCorr<Tin>{x64, dbuf, ld, cs.active_out, rx_cur, op_wexp()},
+                     2 * v64 + vec_bytes(n, ld, 1, sizeof(Tin)));
         }
         // zero-mean result, copied out unpadded (direct: left as is)
         if (!direct) {
@@ -1052,7 +1098,7 @@ lap_status_t run_solver(lap_hierarchy *h, int32_t k, const double *B, double *X,
     sizes.push_back(align_up((size_t)ntiles * 4 * KT * P * 8));          // reduction partials
     sizes.push_back(align_up((size_t)ntiles * 4 * KT * kMaxTeams * 8));  // team partials
     sizes.push_back(align_up(ld * 8) * 10);                       // column scalars
-    sizes.push_back(align_up(ld * 4) * 2);                        // column flags
+    sizes.push_back(align_up(ld * 4) * 4);                        // column flags, residual exponents
     size_t total = 0;
     for (size_t z : sizes) total += z;
     char *base = nullptr;
@@ -1143,10 +1189,14 @@ lap_status_t run_solver(lap_hierarchy *h, int32_t k, const double *B, double *X,
         char *cf = take(idx++);
         S.cs.active_out = (int32_t *)cf;
         S.cs.active_in = (int32_t *)(cf + align_up(ld * 4));
+        S.cs.rexp[0] = (int32_t *)(cf + 2 * align_up(ld * 4));
+        S.cs.rexp[1] = (int32_t *)(cf + 3 * align_up(ld * 4));
     }
     // arrival counters must start at zero (every kernel leaves them at zero)
     CFC_CUDA(cudaMemsetAsync(S.rb.counter, 0, kMaxTiles * 4 + kMaxTiles * kMaxTeams * 4, s));
     CFC_CUDA(cudaMemsetAsync(S.cs.active_in, 0, ld * 4, s));
+    // residual exponents stay 0 in FP64 solves (no scaling)
+    CFC_CUDA(cudaMemsetAsync(S.cs.rexp[0], 0, 2 * align_up(ld * 4), s));
     S.h_active = pinned_scratch();
     return S.run(B, X, info);
 }
@@ -1402,7 +1452,7 @@ lap_status_t solve_impl(lap_hierarchy *h, int32_t k, const double *B, double *X,
             if (o.precision != LAP_FP32_BF16COARSE_REFINED) return;
             for (int l = 1; l < upto && l < (int)h->lv.size(); ++l)
                 if (!h->lv[l].wbf.get()) {
-                    ensure_bf16(h->lv[l], s);
+                    ensure_bf16(h->lv[l], h->wexp, s);
                     ++bf16_made;
                 }
         };

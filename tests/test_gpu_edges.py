@@ -1,0 +1,181 @@
+"""Parity on the paths the large workloads take, and the method's edge cases
+(through the C ABI, against the CPU oracle).
+
+* R-MAT (skewed degrees, Sec. 6.3's complex networks): scale 14, largest
+  connected component.  Its row lengths are uneven enough that the row
+  kernels take the rows longest first, and its hubs are split into chunks:
+  the paths the R-MAT benchmark runs.
+* Pinned configurations the autotuner may or may not pick: every level of
+  the hierarchy in FP32 and FP64, and the 128-column tile.
+* Inputs at the edge of the arithmetic: a right-hand side with a non-finite
+  entry is rejected; conductances of any magnitude (Sec. 2 allows any
+  positive weight) give the oracle's answer, scaled (L(c w) = c L(w), so the
+  farness of c w is the farness of w over c); weights spanning 80 orders of
+  magnitude either converge or report LAP_ENOCONV, never LAP_OK with a
+  non-finite value.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import dense, jl
+from oracle.graph import canonical_graph, laplacian
+
+pytestmark = pytest.mark.gpu
+
+FARNESS_RTOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def P():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1607_02955_gb300 import build_ext
+    build_ext.build()
+    import paper_1607_02955_gb300 as P
+    torch.cuda.init()
+    return P
+
+
+def _rel(a, b):
+    return np.max(np.abs(np.asarray(a) - np.asarray(b)) / np.maximum(np.abs(np.asarray(b)), 1e-300))
+
+
+PRECISIONS = {"fp32": dict(precision=1), "fp64": dict(precision=0),
+              "bf16coarse": dict(precision=2, levels_used=-1),
+              "fp32_all_levels": dict(precision=1, levels_used=-1),
+              "fp64_all_levels": dict(precision=0, levels_used=-1)}
+
+
+@pytest.fixture(scope="module")
+def rmat14():
+    n, s, d, _ = synth.rmat(14, seed=3)
+    w = synth.uniform_weights(s.size, seed=5)
+    return n, s, d, w, canonical_graph(n, s, d, w)
+
+
+def _certify(g, B, X, tol=1e-8):
+    """Independent FP64 residual check on the CPU: ||Bp - L X|| <= tol ||Bp||
+    per column, Bp the zero-mean projection of B, and X of zero mean."""
+    Bp = B - B.mean(axis=0)
+    R = Bp - laplacian(g) @ X
+    assert np.all(np.linalg.norm(R, axis=0) <= 1.01 * tol * np.linalg.norm(Bp, axis=0))
+    np.testing.assert_allclose(X.mean(axis=0), 0, atol=1e-12 * np.abs(X).max())
+
+
+# ------------------------------------------------------------------ R-MAT: longest-first rows, split hubs
+def test_rmat_takes_the_longest_first_row_order(P, rmat14):
+    n, s, d, w, g = rmat14
+    h = P.lap_build_hierarchy(n, s, d, w)
+    info = P.lap_hierarchy_info(h)
+    assert info["level_row_order"][0] == 1
+    assert np.bincount(np.concatenate([s, d])).max() > 32  # hubs: rows split into chunks
+    grid = P.lap_build_hierarchy(*synth.grid2d(32)[:3])
+    assert P.lap_hierarchy_info(grid)["level_row_order"][0] == 0
+
+
+@pytest.mark.parametrize("precision", sorted(PRECISIONS))
+def test_rmat_solve_is_certified(P, rmat14, precision):
+    import torch
+    n, s, d, w, g = rmat14
+    h = P.lap_build_hierarchy(n, s, d, w)
+    B = np.random.default_rng(2).standard_normal((n, 40))
+    Xt = torch.empty((n, 40), dtype=torch.float64, device="cuda")
+    info = P.lap_solve_multi(h, torch.tensor(B, device="cuda"), Xt, P.lap_default_solve_opts(**PRECISIONS[precision]))
+    assert info["max_rel_residual"] <= 1e-8
+    _certify(g, B, Xt.cpu().numpy())
+
+
+@pytest.mark.parametrize("precision", sorted(PRECISIONS))
+def test_rmat_farness_jl_matches_oracle(P, rmat14, precision):
+    n, s, d, w, g = rmat14
+    h = P.lap_build_hierarchy(n, s, d, w)
+    hub = int(np.argmax(np.bincount(np.concatenate([s, d]))))
+    nodes = np.array([0, hub, n // 2, n - 1], np.int32)
+    f = P.cfc_farness_jl(h, 32, 4, nodes, opts=P.lap_default_solve_opts(**PRECISIONS[precision]))
+    fo = jl.jl_farness(g, 32, 4, nodes.tolist(), solver="cg", tol=1e-12)
+    assert _rel(f, fo) <= FARNESS_RTOL
+
+
+@pytest.mark.parametrize("levels", [0, -1])
+def test_rmat_k128_tile128(P, rmat14, levels):
+    import torch
+    n, s, d, w, g = rmat14
+    h = P.lap_build_hierarchy(n, s, d, w)
+    opts = P.lap_default_solve_opts(k_tile=128, levels_used=levels)
+    B = np.random.default_rng(3).standard_normal((n, 128))
+    Xt = torch.empty((n, 128), dtype=torch.float64, device="cuda")
+    info = P.lap_solve_multi(h, torch.tensor(B, device="cuda"), Xt, opts)
+    assert info["k_tile"] == 128 and info["max_rel_residual"] <= 1e-8
+    _certify(g, B, Xt.cpu().numpy())
+    nodes = np.array([1, n - 2], np.int32)
+    f = P.cfc_farness_jl(h, 128, 6, nodes, opts=opts)
+    fo = jl.jl_farness(g, 128, 6, nodes.tolist(), solver="cg", tol=1e-12)
+    assert _rel(f, fo) <= FARNESS_RTOL
+
+
+# ------------------------------------------------------------------ non-finite right-hand sides
+@pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf, 1e200])
+def test_nonfinite_rhs_is_rejected(P, bad):
+    import torch
+    n, s, d, _ = synth.grid2d(20)
+    h = P.lap_build_hierarchy(n, s, d)
+    B = np.random.default_rng(0).standard_normal((n, 8))
+    B[17, 3] = bad  # 1e200 is finite, but its square is not
+    X = torch.zeros((n, 8), dtype=torch.float64, device="cuda")
+    with pytest.raises(P.LapError) as e:
+        P.lap_solve_multi(h, torch.tensor(B, device="cuda"), X)
+    assert e.value.status == P.LAP_EINVAL
+
+
+# ------------------------------------------------------------------ conductances far from 1
+SCALES = [2.0 ** 133, 2.0 ** -133, 1e40, 1e-40]
+
+
+@pytest.mark.parametrize("c", SCALES)
+@pytest.mark.parametrize("precision", sorted(PRECISIONS))
+def test_weights_far_from_one_scale_the_farness(P, c, precision):
+    n, s, d, _ = synth.grid2d(16)
+    w = synth.uniform_weights(s.size, seed=3)
+    g = canonical_graph(n, s, d, w)
+    h = P.lap_build_hierarchy(n, s, d, w * c)
+    assert P.lap_hierarchy_info(h)["weight_exp"] == int(np.floor(np.log2((w * c).max())))
+    nodes = np.array([0, 37, n - 1], np.int32)
+    f = P.cfc_farness_jl(h, 32, 2, nodes, opts=P.lap_default_solve_opts(**PRECISIONS[precision]))
+    assert np.all(np.isfinite(f))
+    # L(c w) = c L(w): Z scales by c^-1/2 (Y by c^1/2), the farness by 1/c
+    fo = jl.jl_farness(g, 32, 2, nodes.tolist(), solver="dense")
+    assert _rel(f * c, fo) <= FARNESS_RTOL
+
+
+@pytest.mark.parametrize("c", SCALES)
+def test_exact_small_with_weights_far_from_one(P, c):
+    n, s, d, _ = synth.grid2d(12, 9)
+    w = synth.uniform_weights(s.size, seed=4)
+    g = canonical_graph(n, s, d, w)
+    f, cl = P.cfc_exact_small(n, s, d, w * c)
+    assert _rel(f * c, dense.farness(g)) <= 1e-9
+    assert _rel(cl / c, dense.closeness(g)) <= 1e-9
+
+
+@pytest.mark.parametrize("precision", sorted(PRECISIONS))
+def test_weights_spanning_80_orders_never_ok_with_nonfinite(P, precision):
+    import torch
+    n, s, d, _ = synth.grid2d(16)
+    w = np.where(np.random.default_rng(1).random(s.size) < 0.5, 1e40, 1e-40)
+    h = P.lap_build_hierarchy(n, s, d, w)
+    opts = P.lap_default_solve_opts(**PRECISIONS[precision])
+    try:
+        f = P.cfc_farness_jl(h, 32, 2, np.array([0, 100], np.int32), opts=opts)
+        assert np.all(np.isfinite(f)) and np.all(f > 0)
+    except P.LapError as e:
+        assert e.status == P.LAP_ENOCONV
+    B = torch.tensor(np.random.default_rng(5).standard_normal((n, 16)), device="cuda")
+    X = torch.empty_like(B)
+    info = P.lap_solve_multi(h, B, X, opts, allow_noconv=True)
+    if info["status"] == P.LAP_OK:
+        assert info["max_rel_residual"] <= 1e-8 and bool(torch.isfinite(X).all())
+    else:
+        assert info["status"] == P.LAP_ENOCONV
+        assert not (info["max_rel_residual"] <= 1e-8)

@@ -55,3 +55,19 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(P):
     with pytest.raises(P.LapError) as e:
         P.cfc_farness_from_solution_noalloc(Z, nodes, out)
     assert e.value.status == P.LAP_EBUDGET
+
+
+def test_noalloc_out_of_range_nodes_get_nan(P):
+    # a node id outside [0, n) yields NaN at its position and leaves the
+    # other positions equal to the allocating entry point's values
+    import torch
+    Z, _ = _case(torch, 5000, 48, 4)
+    good = np.array([0, 17, 4999], np.int32)
+    ref = P.cfc_farness_from_solution(Z, good)
+    nodes = torch.tensor([0, -1, 17, 5000, 4999], dtype=torch.int32, device="cuda")
+    out = torch.zeros(5, dtype=torch.float64, device="cuda")
+    P.cfc_farness_from_solution_noalloc(Z, nodes, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert np.isnan(got[1]) and np.isnan(got[3])
+    np.testing.assert_allclose(got[[0, 2, 4]], ref, rtol=RTOL, atol=0)
