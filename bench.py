@@ -1,24 +1,29 @@
 """Benchmark: right-hand sides solved per second to relative residual 1e-8.
 
-One step is one pass of the whole hot path on the 100k-node Barabasi-Albert
-workload (5 edges per new node, weights uniform in [1, 2), seed 2): ingest
-of the edge list and construction of the multigrid hierarchy
-(lap_build_hierarchy), generation of the k = 64 Johnson-Lindenstrauss
-right-hand sides, the block solve to ||b - Lx|| <= 1e-8 ||b|| per column in
-FP32 PCG + V-cycle inside FP64 refinement, and the farness reduction for
-node 0 (cfc_farness_jl).  value = 64 * N / step time.
+One step is one pass of the whole hot path on R-MAT scale 24 (a, b, c =
+.57, .19, .19, 8 * 2^24 samples, unit weights, largest connected component:
+n = 7,368,759 nodes, 131.7M edges, seed 5), the largest single-GPU
+configuration and the one where HBM bandwidth binds: ingest of the edge list
+and construction of the hierarchy (lap_build_hierarchy), generation of the
+k = 64 Johnson-Lindenstrauss right-hand sides, the block solve to
+||b - Lx|| <= 1e-8 ||b|| per column in FP32 PCG inside FP64 refinement, and
+the farness reduction for node 0 (cfc_farness_jl).  value = 64 * N / step
+time.
 
 The line also carries: the same step through the C ABI with host buffers
 (e2e), the dominant solver family against the measured HBM bandwidth
-(roofline, with ncu DRAM traffic from profiles/traffic.json), the solve's
-HBM-roofline ideal, solve-only rates of FP32 batched against FP64 batched and
-FP64 one right-hand side at a time, a small serving mix (p50/p99 latency),
-the oracle on 8 of the 64 columns (cpu_baseline) and this run's error
-against it (parity), and the SM clocks sampled during the timed steps.
+(roofline, with ncu DRAM traffic from profiles/traffic.json) and every
+family's achieved bandwidth, the solve's HBM-roofline ideal, the 100k-node
+Barabasi-Albert configuration's rate with the batched mixed-precision solve
+against FP64 batched and FP64 one right-hand side at a time, a small serving
+mix (p50/p99 latency), the oracle on the host cores (cpu_baseline: on R-MAT
+24 capped iterations, extrapolated) and this run's error against it
+(parity: right-hand sides at sampled nodes and the oracle's FP64 residual of
+the device's solutions), and the SM clocks sampled during the timed steps.
 
-Other workloads: --workload rmat20_jl16/64/128, grid1024_jl64,
-grid4096_jl64, rmat24_jl64 (the same step), serve_mix (16 resident graphs,
-Poisson arrivals) and accuracy (both estimators against the exact farness).
+Other workloads: --workload ba100k_jl64, rmat20_jl16/64/128, grid1024_jl64,
+grid4096_jl64 (the same step), serve_mix (16 resident graphs, Poisson
+arrivals) and accuracy (both estimators against the exact farness).
 
 --impl reference times the CPU FP64 oracle on the same workload and metric.
 Run with torchrun for N > 1 GPUs: every rank solves its own independent
@@ -44,6 +49,9 @@ if ROOT not in sys.path:
 import synth  # noqa: E402
 
 METRIC = "RHS solved/s to rel. residual 1e-8"
+# the largest single-GPU configuration, where the HBM roofline binds: R-MAT
+# scale 24 (LCC), JL farness of one node with k = 64
+DEFAULT_WORKLOAD = "rmat24_jl64"
 WORKLOADS = {
     "ba100k_jl64": dict(kind="ba", n=100000, m_per=5, seed=2, k=64, jl_seed=1, nodes=[0]),
     "grid48_jl32": dict(kind="grid", a=48, k=32, jl_seed=1, nodes=[0]),
@@ -174,13 +182,13 @@ def read_traffic(workload, family):
     summary, or None when it was taken on other kernel sources."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
-        return None, None
+        return None, None, None
     with open(p) as fh:
         j = json.load(fh)
     e = j.get(workload, {}).get(family)
     if not e or e.get("source_digest") != kernel_source_digest():
-        return None, None
-    return e["dram_bytes_per_launch"], e["kernel"]
+        return None, None, None
+    return e["dram_bytes_per_launch"], e["kernel"], e.get("note")
 
 
 def write_traffic(csv_path, log_path):
@@ -354,56 +362,164 @@ def max_over_ranks(x, world):
 
 
 def run_reference(args, wl, rank, world):
-    """CPU oracle on the same workload: JL farness with the oracle's FP64 CG
-    to relative residual 1e-8, timed on the host cores."""
+    """The reference arm: the CPU FP64 oracle on the same workload and metric,
+    on all host cores (the oracle's columns solved in threads).  Small
+    graphs: each step is the whole oracle pipeline (canonical graph,
+    Laplacian, the k JL right-hand sides, CG to 1e-8, farness of the query
+    node).  Large graphs: the oracle graph is built once; each step is the
+    oracle's CG capped at one iteration on one column per thread, and the
+    rate is extrapolated to the estimated iteration count (a capped run
+    costs about three iteration-equivalents: projection and first residual,
+    the iteration, the final residual check; a full solve about iters + 2)."""
     if rank != 0:
         return
     from oracle import jl
-    from oracle.graph import canonical_graph
+    threads = oracle_threads()
     n, s, d, w = make_graph(wl)
     k = wl["k"]
     times = []
-    for it in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        g = canonical_graph(n, s, d, w)
-        jl.jl_farness(g, k, wl["jl_seed"], wl["nodes"], solver="cg", tol=1e-8)
-        dt = time.perf_counter() - t0
-        if it >= args.warmup:
-            times.append(dt)
-    sec = sum(times) / len(times)
-    value = k / sec
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    extra = {}
+    if wl_nodes(wl) <= LARGE_N:
+        for it in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            g, L, _ = oracle_graph(wl)
+            Y = jl.jl_rhs(g, k, wl["jl_seed"])
+            Z, _, used = cg_threaded(L, Y.T, 1e-8, 100000, threads)
+            jl.farness_from_Z(Z.T, wl["nodes"])
+            dt = time.perf_counter() - t0
+            if it >= args.warmup:
+                times.append(dt)
+        sec = sum(times) / len(times)
+        value = k / sec
+        sample = (f"full {args.workload} step per step (canonical graph + Laplacian, {k} JL RHS, FP64 Jacobi-CG "
+                  f"to 1e-8 on {used} threads, farness of node {wl['nodes'][0]})")
+    else:
+        g, L, setup_s = oracle_graph(wl)
+        iters, spec = oracle_iterations_estimate(wl, threads)
+        B = np.random.default_rng(0).standard_normal((g.n, threads))
+        for it in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            _, _, used = cg_threaded(L, B, 1e-8, 1, threads)
+            dt = time.perf_counter() - t0
+            if it >= args.warmup:
+                times.append(dt * (iters + 2) / 3.0)
+        sec = sum(times) / len(times)
+        value = threads / sec
+        sample = (f"extrapolated: per step the oracle's FP64 Jacobi-CG capped at 1 iteration on {threads} columns "
+                  f"of this graph (one per thread), scaled by (iters + 2) / 3 to the {iters} iterations estimated "
+                  f"from the same oracle on {spec}; oracle setup ({setup_s:.1f} s) excluded")
+        extra = {"extrapolated": True, "iterations": iters}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "k": k, "n": n, "m": int(s.size)},
-            "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": cores, "kind": "oracle",
-                             "sample": f"full {args.workload} step (canonical graph, {k} JL RHS, FP64 Jacobi-CG "
-                                       f"to 1e-8, farness of node 0) per step"},
+            "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": threads, "kind": "oracle", "sample": sample,
+                             **extra},
             "e2e": {"value": value, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 CPU_SAMPLE_ROWS = 8
+# workloads with more nodes take the extrapolated CPU baseline (capped oracle
+# iterations): a converged oracle solve of them takes far longer than the bench
+LARGE_N = 2_000_000
 
 
-def cpu_baseline(wl):
-    """Oracle on a bounded sample of the workload: the first 8 of the k JL
-    rows.  Returns the timing and the oracle's solutions Z (8 x n)."""
-    from oracle import jl
+def oracle_threads():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+def cg_threaded(L, B, tol, maxiter, threads):
+    """The oracle's CG (oracle.cg.cg_solve, unchanged) on column chunks of B
+    in host threads: its columns are independent systems, and SciPy's sparse
+    products release the GIL, so the chunks run on separate cores.  Returns
+    (X, max iterations over the chunks)."""
+    from concurrent.futures import ThreadPoolExecutor
     from oracle.cg import cg_solve
+    chunks = [c for c in np.array_split(np.arange(B.shape[1]), min(threads, B.shape[1])) if c.size]
+    with ThreadPoolExecutor(len(chunks)) as ex:
+        res = list(ex.map(lambda c: cg_solve(L, np.ascontiguousarray(B[:, c]), tol=tol, maxiter=maxiter), chunks))
+    X = np.empty(B.shape)
+    for c, (x, _, _) in zip(chunks, res):
+        X[:, c] = x
+    return X, max(r[1] for r in res), len(chunks)
+
+
+def oracle_graph(wl):
+    """The oracle's graph and Laplacian of a workload, and the seconds it took."""
     from oracle.graph import canonical_graph, laplacian
     n, s, d, w = make_graph(wl)
-    ks = CPU_SAMPLE_ROWS
     t0 = time.perf_counter()
     g = canonical_graph(n, s, d, w)
-    Y = jl.jl_rhs(g, wl["k"], wl["jl_seed"])[:ks]
-    Z, _, _ = cg_solve(laplacian(g), Y.T, tol=1e-8)
-    sec = time.perf_counter() - t0
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    info = {"value": ks / sec, "unit": "RHS/s", "cores": cores, "kind": "oracle",
-            "sample": f"{ks} of the {wl['k']} JL right-hand sides (canonical graph + RHS + FP64 Jacobi-CG to 1e-8)"}
-    return info, np.asarray(Z).T
+    L = laplacian(g)
+    return g, L, time.perf_counter() - t0
+
+
+def oracle_iterations_estimate(wl, threads):
+    """Iterations of the oracle's CG to 1e-8 (8 JL right-hand sides) on a
+    smaller instance of the workload's family, standing in for the large
+    instance, whose converged solve does not fit the bench.  R-MAT: scale 20,
+    same generator and seed (the count barely grows with the scale: 24, 27,
+    28 iterations at scales 16, 18, 20).  Grid: the 256 x 256 grid, the count
+    multiplied by side / 256 (Jacobi-CG iterations grow with the square root
+    of the condition number, which grows with the square of the side)."""
+    from oracle import jl
+    if wl["kind"] == "rmat":
+        spec, factor = dict(kind="rmat", scale=20, seed=wl.get("seed", 3)), 1.0
+    else:
+        spec, factor = dict(kind="grid", a=256), wl["a"] / 256.0
+    g, L, _ = oracle_graph(spec)
+    Y = jl.jl_rhs(g, 8, wl["jl_seed"])
+    _, it, _ = cg_threaded(L, Y.T, 1e-8, 100000, threads)
+    return int(round(it * factor)), spec
+
+
+def cpu_baseline(wl, threads, gL=None):
+    """The oracle on a bounded sample of the workload, on `threads` host
+    cores.  Small graphs: the first 8 of the k JL rows solved to 1e-8
+    (returns their solutions for the parity check).  Large graphs: the
+    oracle's CG on `threads` columns capped at 1 and 3 iterations gives the
+    time per iteration, extrapolated to the iteration count of the same
+    oracle on R-MAT 20 (oracle_iterations_estimate); setup excluded."""
+    from oracle import jl
+    if wl_nodes(wl) <= LARGE_N:
+        ks = CPU_SAMPLE_ROWS
+        t0 = time.perf_counter()
+        g, L, _ = oracle_graph(wl)
+        Y = jl.jl_rhs(g, wl["k"], wl["jl_seed"])[:ks]
+        Z, _, used = cg_threaded(L, Y.T, 1e-8, 100000, threads)
+        sec = time.perf_counter() - t0
+        info = {"value": ks / sec, "unit": "RHS/s", "cores": used, "kind": "oracle",
+                "sample": f"{ks} of the {wl['k']} JL right-hand sides (canonical graph + Laplacian + RHS + FP64 "
+                          f"Jacobi-CG to 1e-8, one column per thread)"}
+        return info, Z.T
+    g, L, setup_s = gL if gL is not None else oracle_graph(wl)
+    cols = threads
+    B = np.random.default_rng(0).standard_normal((g.n, cols))
+    t0 = time.perf_counter()
+    cg_threaded(L, B, 1e-8, 1, threads)
+    t1 = time.perf_counter()
+    _, _, used = cg_threaded(L, B, 1e-8, 3, threads)
+    t3 = time.perf_counter()
+    per_it = (t3 - t1 - (t1 - t0)) / 2.0
+    fixed = max(t1 - t0 - per_it, 0.0)  # projection, first residual and final residual check
+    iters, spec = oracle_iterations_estimate(wl, threads)
+    sec = fixed + iters * per_it
+    info = {"value": cols / sec, "unit": "RHS/s", "cores": used, "kind": "oracle", "extrapolated": True,
+            "sample": f"the oracle's FP64 Jacobi-CG on {cols} columns of this graph, one per thread, capped at 1 and "
+                      f"3 iterations ({per_it:.2f} s per iteration, {fixed:.2f} s fixed); extrapolated to the "
+                      f"{iters} iterations estimated from the same oracle on {spec} (oracle_iterations_estimate); "
+                      f"oracle setup (canonical graph + Laplacian, {setup_s:.1f} s) excluded",
+            "per_iteration_s": per_it, "iterations": iters}
+    return info, None
+
+
+def wl_nodes(wl):
+    if wl["kind"] == "rmat":
+        return 1 << wl["scale"]
+    if wl["kind"] == "grid":
+        return wl["a"] * wl["a"]
+    return wl["n"]
 
 
 def _ranks(x):
@@ -479,17 +595,224 @@ def serve_main(args):
                       "serving": r}), flush=True)
 
 
+def gpu_workload(P, torch, name, args, steps, warmup, local, world, clk=None, full=True):
+    """Times `steps` steps of a workload on this rank's GPU (after `warmup`
+    untimed ones), device-resident inputs, L2 flushed between steps.  With
+    `full`: also the same steps through the C ABI with host buffers (e2e),
+    the launch count, and an instrumented pass (per-family device time by
+    CUDA events on the launching stream)."""
+    wl = WORKLOADS[name]
+    n, s, d, w = make_graph(wl)
+    k = wl["k"]
+    nodes = np.array(wl["nodes"], np.int32)
+    dev = torch.device("cuda", local)
+    src_d = torch.tensor(s, dtype=torch.int32, device=dev)
+    dst_d = torch.tensor(d, dtype=torch.int32, device=dev)
+    w_d = torch.tensor(w, dtype=torch.float64, device=dev) if w is not None else None
+    nodes_d = torch.tensor(nodes, device=dev)
+    far_d = torch.empty(len(nodes), dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    sp = stream.cuda_stream
+    prec_mode, dtype, prec_text = PRECISIONS[args.precision]
+    sopts = P.lap_default_solve_opts(precision=prec_mode)
+    if args.levels is not None:
+        sopts.levels_used = args.levels
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+
+    def step_device():
+        h = P.lap_build_hierarchy(n, src_d, dst_d, w_d, stream=sp)
+        P.cfc_farness_jl(h, k, wl["jl_seed"], nodes_d, opts=sopts, out=far_d, stream=sp)
+        h.destroy()
+
+    # host-buffer variant: pinned host inputs, result read back to the host
+    src_h = torch.tensor(s, dtype=torch.int32).pin_memory()
+    dst_h = torch.tensor(d, dtype=torch.int32).pin_memory()
+    w_h = torch.tensor(w, dtype=torch.float64).pin_memory() if w is not None else None
+    far_h = torch.empty(len(nodes), dtype=torch.float64).pin_memory()
+
+    def step_host():
+        h = P.lap_build_hierarchy(n, src_h, dst_h, w_h, stream=sp)
+        P.cfc_farness_jl(h, k, wl["jl_seed"], nodes, opts=sopts, out=far_h, stream=sp)
+        h.destroy()
+
+    def timed(step, K):
+        total = 0.0
+        with torch.cuda.stream(stream):
+            for _ in range(K):
+                flush.fill_(1.0)
+                torch.cuda.synchronize()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                step()
+                b.record(stream)
+                b.synchronize()
+                total += a.elapsed_time(b)
+        return total
+
+    for _ in range(warmup):
+        step_device()
+        if full:
+            step_host()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    P.lap_stats_reset()
+    P.lap_stats_set_log(full and args.launch_log is not None)
+    if clk is not None:
+        clk.mark()
+    torch.cuda.profiler.start()  # ncu --profile-from-start off captures exactly the timed steps
+    ms_total = timed(step_device, steps)
+    torch.cuda.profiler.stop()
+    P.lap_stats_set_log(False)
+    stats = P.lap_stats_read()
+    out = {"wl": wl, "wl_name": name, "n": n, "m": int(s.size), "k": k, "dtype": dtype, "prec_text": prec_text, "sopts": sopts,
+           "graph": (n, src_d, dst_d, w_d), "stream": stream, "dev": dev, "launches": stats["launches_total"]}
+    if full and args.launch_log and int(os.environ.get("RANK", "0")) == 0:
+        with open(args.launch_log, "w") as fh:
+            json.dump({"workload": name, "steps": steps, "source_digest": kernel_source_digest(),
+                       "families": P.lap_stats_read_log()}, fh)
+    out["clocks"] = clk.stop() if clk is not None else None
+    torch.cuda.synchronize()
+    barrier(world)
+    ms_total = max_over_ranks(ms_total, world)
+    out["ms_step"] = ms_total / steps
+    out["value"] = k * world / (out["ms_step"] / 1e3)
+    if not full:
+        return out
+    # end to end through the C ABI with host buffers
+    barrier(world)
+    ms_e2e = max_over_ranks(timed(step_host, steps) / steps, world)
+    out["e2e"] = {"value": k * world / (ms_e2e / 1e3), "unit": "RHS/s",
+                  "h2d_bytes_per_step": int(s.size) * (4 + 4 + (8 if w is not None else 0)) + len(nodes) * 4,
+                  "d2h_bytes_per_step": len(nodes) * 8}
+    # instrumented pass: per-kernel-family device time by CUDA events on the launch stream
+    P.lap_stats_reset()
+    P.lap_stats_set_timing(True)
+    timed(step_device, steps)
+    out["families"] = P.lap_stats_read()["families"]
+    P.lap_stats_set_timing(False)
+    return out
+
+
+def solve_rate(P, torch, res, precision, kk, reps):
+    """Solve-only rate on a built hierarchy (setup excluded), the same 1e-8
+    FP64 residual test; the first solve autotunes for its configuration."""
+    n, src_d, dst_d, w_d = res["graph"]
+    stream, dev, wl = res["stream"], res["dev"], res["wl"]
+    sp = stream.cuda_stream
+    h = P.lap_build_hierarchy(n, src_d, dst_d, w_d, stream=sp)
+    Yk = torch.empty((n, kk), dtype=torch.float64, device=dev)
+    Xk = torch.empty_like(Yk)
+    P.cfc_jl_rhs(h, kk, wl["jl_seed"], Yk, stream=sp)
+    o = P.lap_default_solve_opts(precision=precision)
+    P.lap_solve_multi(h, Yk, Xk, o, stream=sp)
+    with torch.cuda.stream(stream):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            inf = P.lap_solve_multi(h, Yk, Xk, o, stream=sp)
+        b.record(stream)
+        b.synchronize()
+    h.destroy()
+    return {"rhs_per_s": kk * reps / (a.elapsed_time(b) / 1e3), "k": kk, "solves": reps,
+            "inner_iters": inf["inner_iters"], "max_rel_residual": inf["max_rel_residual"]}
+
+
+def precision_comparison(P, torch, res, args):
+    """The batched mixed-precision solve against FP64 batched and FP64 one
+    right-hand side at a time (solve only, same 1e-8 test)."""
+    prec_mode = PRECISIONS[args.precision][0]
+    k = res["k"]
+    return {"solve_only": True, "workload": res["wl_name"],
+            args.precision + "_batched": solve_rate(P, torch, res, prec_mode, k, 3),
+            "fp64_batched": solve_rate(P, torch, res, 0, k, 1),
+            "fp64_one_rhs": solve_rate(P, torch, res, 0, 1, 4)}
+
+
+def parity_large(P, torch, res, g, L, threads):
+    """This run's error against the oracle at a size the oracle cannot solve
+    within the bench: the first 8 JL right-hand sides (k = 64 scaling) on the
+    device against the oracle's at sampled nodes (jl_rhs_at), and the
+    oracle's FP64 residual ||Y - L Z|| / ||Y|| of the device's solutions of
+    those columns (a property every solution at 1e-8 has, at any size)."""
+    from concurrent.futures import ThreadPoolExecutor
+    from oracle import jl
+    n, src_d, dst_d, w_d = res["graph"]
+    wl, stream, dev = res["wl"], res["stream"], res["dev"]
+    sp = stream.cuda_stream
+    k, ks = wl["k"], CPU_SAMPLE_ROWS
+    h = P.lap_build_hierarchy(n, src_d, dst_d, w_d, stream=sp)
+    Y = torch.empty((n, k), dtype=torch.float64, device=dev)
+    P.cfc_jl_rhs(h, k, wl["jl_seed"], Y, stream=sp)
+    Y8 = Y[:, :ks].contiguous()
+    del Y
+    Z8 = torch.empty_like(Y8)
+    info = P.lap_solve_multi(h, Y8, Z8, res["sopts"], stream=sp)
+    h.destroy()
+    torch.cuda.synchronize()
+    Yh, Zh = Y8.cpu().numpy(), Z8.cpu().numpy()
+    del Y8, Z8
+    deg = np.diff(L.indptr)
+    nodes = [0, int(np.argmax(deg)), n // 2, n - 1]
+    Yo = jl.jl_rhs_at(g, k, wl["jl_seed"], nodes)[:ks]  # k x len(nodes) -> first ks rows
+    rhs_err = float(np.abs(Yh[nodes, :].T - Yo).max() / np.abs(Yo).max())
+    chunks = [c for c in np.array_split(np.arange(ks), min(threads, ks)) if c.size]
+    with ThreadPoolExecutor(len(chunks)) as ex:
+        LZ = list(ex.map(lambda c: L @ Zh[:, c], chunks))
+    R = np.empty_like(Yh)
+    for c, v in zip(chunks, LZ):
+        R[:, c] = v
+    Yp = Yh - Yh.mean(axis=0)
+    rel = np.linalg.norm(Yp - R, axis=0) / np.linalg.norm(Yp, axis=0)
+    return {"quantity": f"JL right-hand sides 0-{ks - 1} at nodes {nodes} against the oracle, and the oracle's "
+                        f"FP64 residual of the device's solutions of those columns",
+            "rhs_rel_err": rhs_err, "rhs_bound": 1e-13, "max_rel_residual": float(rel.max()), "bound": 1e-8,
+            "device_reported_residual": info["max_rel_residual"]}
+
+
+def roofline_of(res, steps, P):
+    """The dominant solver kernel family's algorithmic bytes over its
+    event-timed duration, against the measured copy bandwidth, and the
+    HBM-roofline ideal of the whole solve."""
+    fam = res["families"]
+    solve_fams = {kf: v for kf, v in fam.items() if v["ms"] > 0 and kf not in ("setup", "cfc")}
+    dom = max(solve_fams, key=lambda kf: solve_fams[kf]["ms"])
+    peak, peak_src = read_peaks()
+    dm = fam[dom]
+    achieved = (dm["bytes"] / 1e9) / (dm["ms"] / 1e3) if dm["ms"] > 0 else 0.0
+    traffic, traffic_kernel, traffic_note = read_traffic(res["wl_name"], dom)
+    per_launch = dm["bytes"] / max(dm["launches"], 1)
+    roof = {"bound": "hbm", "kernel_family": dom, "achieved": achieved, "peak": peak,
+            "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": traffic, "traffic_kernel": traffic_kernel,
+            "traffic_note": traffic_note, "algorithmic_bytes_per_launch": per_launch,
+            "traffic_over_algorithmic": traffic / per_launch if traffic else None,
+            "launches": dm["launches"], "ms": dm["ms"]}
+    k = res["k"]
+    solve_bytes = sum(v["bytes"] for v in solve_fams.values()) / steps
+    solve_ms = sum(v["ms"] for v in solve_fams.values()) / steps
+    ideal = {"rhs_per_s": k / (solve_bytes / (peak * 1e9)) if solve_bytes > 0 else None,
+             "solve_bytes_per_step": solve_bytes, "measured_solve_ms_per_step": solve_ms,
+             "measured_rhs_per_s_solve_kernels": k / (solve_ms / 1e3) if solve_ms > 0 else None}
+    achieved_by_family = {kf: (v["bytes"] / 1e9) / (v["ms"] / 1e3) for kf, v in fam.items()
+                          if v["ms"] > 0 and v["bytes"] > 0}
+    return roof, ideal, achieved_by_family
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ba100k_jl64", choices=sorted(WORKLOADS) + ["serve_mix", "accuracy"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + ["serve_mix", "accuracy"])
     ap.add_argument("--no-serving", action="store_true", help="skip the small serving mix of the default line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
-                    help="skip the solve-only FP64 batched / one-RHS comparison")
+                    help="skip the BA 100k block (its rate and the FP64 batched / one-RHS comparison)")
     ap.add_argument("--print-digest", action="store_true", help="print the kernel source digest and exit")
     ap.add_argument("--levels", type=int, default=None,
                     help="levels_used of the V-cycle (default: autotuned; -1: every level)")
@@ -526,187 +849,85 @@ def main():
     from paper_1607_02955_gb300 import build_ext
     build_ext.build()
 
-    n, s, d, w = make_graph(wl)
-    k = wl["k"]
-    nodes = np.array(wl["nodes"], np.int32)
-    dev = torch.device("cuda", local)
-    src_d = torch.tensor(s, dtype=torch.int32, device=dev)
-    dst_d = torch.tensor(d, dtype=torch.int32, device=dev)
-    w_d = torch.tensor(w, dtype=torch.float64, device=dev) if w is not None else None
-    nodes_d = torch.tensor(nodes, device=dev)
-    far_d = torch.empty(len(nodes), dtype=torch.float64, device=dev)
-    stream = torch.cuda.Stream(device=dev)
-    sp = stream.cuda_stream
-    prec_mode, dtype, prec_text = PRECISIONS[args.precision]
-    sopts = P.lap_default_solve_opts(precision=prec_mode)
-    if args.levels is not None:
-        sopts.levels_used = args.levels
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
-
-    def step_device():
-        h = P.lap_build_hierarchy(n, src_d, dst_d, w_d, stream=sp)
-        P.cfc_farness_jl(h, k, wl["jl_seed"], nodes_d, opts=sopts, out=far_d, stream=sp)
-        h.destroy()
-
-    # host-buffer variant: pinned host inputs, result read back to the host
-    src_h = torch.tensor(s, dtype=torch.int32).pin_memory()
-    dst_h = torch.tensor(d, dtype=torch.int32).pin_memory()
-    w_h = torch.tensor(w, dtype=torch.float64).pin_memory() if w is not None else None
-    far_h = torch.empty(len(nodes), dtype=torch.float64).pin_memory()
-
-    def step_host():
-        h = P.lap_build_hierarchy(n, src_h, dst_h, w_h, stream=sp)
-        P.cfc_farness_jl(h, k, wl["jl_seed"], nodes, opts=sopts, out=far_h, stream=sp)
-        h.destroy()
-
-    def timed(step, K, instrument=False):
-        total = 0.0
-        with torch.cuda.stream(stream):
-            for _ in range(K):
-                flush.fill_(1.0)
-                torch.cuda.synchronize()
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                step()
-                b.record(stream)
-                b.synchronize()
-                total += a.elapsed_time(b)
-        return total
-
     clk = ClockSampler(local)
-    for _ in range(args.warmup):
-        step_device()
-        step_host()
-    torch.cuda.synchronize()
-    barrier(world)
-    torch.cuda.synchronize()
-    P.lap_stats_reset()
-    P.lap_stats_set_log(args.launch_log is not None)
-    clk.mark()
-    torch.cuda.profiler.start()  # ncu --profile-from-start off captures exactly the timed steps
-    ms_total = timed(step_device, args.steps)
-    torch.cuda.profiler.stop()
-    P.lap_stats_set_log(False)
-    stats = P.lap_stats_read()
-    if args.launch_log and rank == 0:
-        with open(args.launch_log, "w") as fh:
-            json.dump({"workload": args.workload, "steps": args.steps, "source_digest": kernel_source_digest(),
-                       "families": P.lap_stats_read_log()}, fh)
-    clocks = clk.stop()
-    torch.cuda.synchronize()
-    barrier(world)
-    ms_total = max_over_ranks(ms_total, world)
-    ms_step = ms_total / args.steps
-    value = k * world / (ms_step / 1e3)
-    launches = stats["launches_total"]
-
-    # end to end through the C ABI with host buffers
-    barrier(world)
-    ms_e2e = max_over_ranks(timed(step_host, args.steps) / args.steps, world)
-    e2e_value = k * world / (ms_e2e / 1e3)
-    h2d = int(s.size) * (4 + 4 + (8 if w is not None else 0)) + len(nodes) * 4
-    d2h = len(nodes) * 8
-
-    # instrumented pass: per-kernel-family device time by CUDA events on the launch stream
-    P.lap_stats_reset()
-    P.lap_stats_set_timing(True)
-    timed(step_device, args.steps)
-    fam = P.lap_stats_read()["families"]
-    P.lap_stats_set_timing(False)
-    solve_fams = {kf: v for kf, v in fam.items() if v["ms"] > 0 and kf not in ("setup", "cfc")}
-    dom = max(solve_fams, key=lambda kf: solve_fams[kf]["ms"])
-    peak, peak_src = read_peaks()
-    dm = fam[dom]
-    achieved = (dm["bytes"] / 1e9) / (dm["ms"] / 1e3) if dm["ms"] > 0 else 0.0
-    traffic, traffic_kernel = read_traffic(args.workload, dom)
-    # the HBM-roofline ideal of the solve: every solver family's algorithmic
-    # bytes moved at the measured copy bandwidth (k / that time, per step)
-    solve_bytes = sum(v["bytes"] for v in solve_fams.values()) / args.steps
-    solve_ms = sum(v["ms"] for v in solve_fams.values()) / args.steps
-    ideal = {"rhs_per_s": k / (solve_bytes / (peak * 1e9)) if solve_bytes > 0 else None,
-             "solve_bytes_per_step": solve_bytes, "measured_solve_ms_per_step": solve_ms,
-             "measured_rhs_per_s_solve_kernels": k / (solve_ms / 1e3) if solve_ms > 0 else None}
+    res = gpu_workload(P, torch, args.workload, args, args.steps, args.warmup, local, world, clk=clk)
+    n, k = res["n"], res["k"]
+    roof, ideal, by_family = roofline_of(res, args.steps, P)
+    fam = res["families"]
 
     # setup alone (ingest + hierarchy) and solver iteration counts, for context
-    h = P.lap_build_hierarchy(n, src_d, dst_d, w_d, stream=sp)
-    hinfo = P.lap_hierarchy_info(h)
-    Y = torch.empty((n, k), dtype=torch.float64, device=dev)
+    gn, src_d, dst_d, w_d = res["graph"]
+    sp = res["stream"].cuda_stream
+    h = P.lap_build_hierarchy(gn, src_d, dst_d, w_d, stream=sp)
+    Y = torch.empty((n, k), dtype=torch.float64, device=res["dev"])
     X = torch.empty_like(Y)
     P.cfc_jl_rhs(h, k, wl["jl_seed"], Y, stream=sp)
-    sinfo = P.lap_solve_multi(h, Y, X, sopts, stream=sp)
+    sinfo = P.lap_solve_multi(h, Y, X, res["sopts"], stream=sp)
     hinfo = P.lap_hierarchy_info(h)
-
-    # solve-only rates on the built hierarchy: the batched mixed-precision form
-    # against FP64 batched and FP64 one right-hand side at a time (same 1e-8
-    # FP64 residual test); hierarchy setup excluded from all three
-    def solve_rate(precision, kk, reps):
-        Yk = torch.empty((n, kk), dtype=torch.float64, device=dev)
-        Xk = torch.empty_like(Yk)
-        P.cfc_jl_rhs(h, kk, wl["jl_seed"], Yk, stream=sp)
-        o = P.lap_default_solve_opts(precision=precision)
-        P.lap_solve_multi(h, Yk, Xk, o, stream=sp)  # autotunes once for this configuration
-        with torch.cuda.stream(stream):
-            torch.cuda.synchronize()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            for _ in range(reps):
-                inf = P.lap_solve_multi(h, Yk, Xk, o, stream=sp)
-            b.record(stream)
-            b.synchronize()
-        return {"rhs_per_s": kk * reps / (a.elapsed_time(b) / 1e3), "k": kk, "solves": reps,
-                "inner_iters": inf["inner_iters"], "max_rel_residual": inf["max_rel_residual"]}
-
-    compare = None
-    if not args.no_compare:
-        compare = {"solve_only": True,
-                   args.precision + "_batched": solve_rate(prec_mode, k, 3),
-                   "fp64_batched": solve_rate(0, k, 1),
-                   "fp64_one_rhs": solve_rate(0, 1, 4)}
     h.destroy()
+    del Y, X
 
+    large = wl_nodes(wl) > LARGE_N
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-            "config": {"workload": args.workload, "n": n, "m": int(s.size), "k": k,
-                       "query_nodes": wl["nodes"], "tol": 1e-8, "precision": prec_text,
-                       "setup_included": True, "l2": "flushed between steps (256 MiB write, untimed)",
+            "metric": METRIC, "value": res["value"], "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["ms_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": res["dtype"], "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "m": res["m"], "k": k,
+                       "query_nodes": wl["nodes"], "tol": 1e-8, "precision": res["prec_text"],
+                       "setup_included": True,
+                       "l2": "flushed between steps (256 MiB write, untimed)" +
+                             ("; every FP32 block (n x 64 x 4 B) is larger than L2" if large else ""),
                        "levels_built": hinfo["levels"], "level_n": hinfo["level_n"], "setup_ms": hinfo["setup_ms"],
-                       "outer_iters": sinfo["outer_iters"], "inner_iters": sinfo["inner_iters"],
-                       "max_rel_residual": sinfo["max_rel_residual"],
-                       "parallelism": f"{world} independent replicas"},
-            "e2e": {"value": e2e_value, "unit": "RHS/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches,
-            "roofline": {"bound": "hbm", "kernel_family": dom, "achieved": achieved, "peak": peak,
-                         "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": traffic, "traffic_kernel": traffic_kernel,
-                         "algorithmic_bytes_per_launch": dm["bytes"] / max(dm["launches"], 1),
-                         "launches": dm["launches"], "ms": dm["ms"]},
+                       "level_row_order": hinfo["level_row_order"],
+                       "solve": {key: sinfo[key] for key in ("outer_iters", "inner_iters", "max_rel_residual",
+                                                              "k_tile", "levels_used", "nu_coarse", "cycle",
+                                                              "coarse_scale", "w_levels")},
+                       "parallelism": f"{world} independent replicas" if world > 1 else "one GPU"},
+            "e2e": res["e2e"],
+            "gpu_launches": res["launches"],
+            "roofline": roof,
+            "achieved_gbs_by_family": by_family,
             "family_ms_per_step": {kf: v["ms"] / args.steps for kf, v in fam.items()},
             "solve_roofline_ideal": ideal,
-            "precision_comparison": compare,
-            "clocks": clocks,
+            "clocks": res["clocks"],
         }
+        if world == 1 and not args.no_compare:
+            if large:
+                # the 100k-node BA configuration: its own rate and the FP64 comparison
+                ba = gpu_workload(P, torch, "ba100k_jl64", args, 10, 3, local, 1, full=False)
+                line["ba100k_jl64"] = {"value": ba["value"], "unit": "RHS/s", "ms_per_step": ba["ms_step"],
+                                       "steps": 10, "precision_comparison": precision_comparison(P, torch, ba, args)}
+                del ba
+            else:
+                res2 = gpu_workload(P, torch, args.workload, args, 1, 1, local, 1, full=False)
+                line["precision_comparison"] = precision_comparison(P, torch, res2, args)
+                del res2
         if world == 1 and not args.no_serving:
             line["serving"] = run_serving(P, SERVE_SMALL, n_queries=48, loads=(0.5,))
             line["serving_resident_pivots"] = run_serving(P, SERVE_SMALL, n_queries=48, loads=(0.5,),
                                                           resident=True)
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"], Zo = cpu_baseline(wl)
-            # this run's error against the oracle on the same sample: the JL
-            # farness terms of rows 0..7 for the query node (Algorithm 1)
-            v = int(wl["nodes"][0])
-            f_or = float(((Zo - Zo[:, [v]]) ** 2).sum())
-            h = P.lap_build_hierarchy(n, src_d, dst_d, w_d, stream=sp)
-            f_gpu = float(P.cfc_farness_jl_rows(h, k, 0, CPU_SAMPLE_ROWS, wl["jl_seed"], np.array([v], np.int32),
-                                                opts=sopts, stream=sp)[0])
-            h.destroy()
-            line["parity"] = {"quantity": f"JL farness terms of rows 0-{CPU_SAMPLE_ROWS - 1} for node {v}",
-                              "oracle": f_or, "gpu": f_gpu, "rel_err": abs(f_gpu - f_or) / abs(f_or),
-                              "bound": 1e-6}
+            threads = oracle_threads()
+            if large:
+                gL = oracle_graph(wl)
+                line["cpu_baseline"], _ = cpu_baseline(wl, threads, gL)
+                line["parity"] = parity_large(P, torch, res, gL[0], gL[1], threads)
+                del gL
+            else:
+                line["cpu_baseline"], Zo = cpu_baseline(wl, threads)
+                # this run's error against the oracle on the same sample: the JL
+                # farness terms of rows 0..7 for the query node (Algorithm 1)
+                v = int(wl["nodes"][0])
+                f_or = float(((Zo - Zo[:, [v]]) ** 2).sum())
+                n0, s0, d0, w0 = make_graph(wl)
+                h = P.lap_build_hierarchy(n0, s0, d0, w0)
+                f_gpu = float(P.cfc_farness_jl_rows(h, k, 0, CPU_SAMPLE_ROWS, wl["jl_seed"],
+                                                    np.array([v], np.int32))[0])
+                h.destroy()
+                line["parity"] = {"quantity": f"JL farness terms of rows 0-{CPU_SAMPLE_ROWS - 1} for node {v}",
+                                  "oracle": f_or, "gpu": f_gpu, "rel_err": abs(f_gpu - f_or) / abs(f_or),
+                                  "bound": 1e-6}
         print(json.dumps(line), flush=True)
 
 

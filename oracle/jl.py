@@ -87,9 +87,35 @@ def jl_farness(g: Graph, k: int, seed: int, nodes, solver: str = "dense", tol: f
     summed literally over w (end of Sec. 5.2)."""
     Y = jl_rhs(g, k, seed)
     Z = jl_solve(g, Y, solver, tol)
+    out = farness_from_Z(Z, nodes)
+    return (out, Z) if return_Z else out
+
+
+def farness_from_Z(Z: np.ndarray, nodes) -> np.ndarray:
+    """sum_{w != v} ||Z_{.,v} - Z_{.,w}||^2 for each query node v, summed
+    literally over w (Algorithm 1, step 4; Z is k x n)."""
     out = np.empty(len(nodes))
     for t, v in enumerate(nodes):
         D = Z - Z[:, [v]]
         col = np.einsum("ij,ij->j", D, D)  # d~(v, w) for every w; w = v gives 0
         out[t] = col.sum()
-    return (out, Z) if return_Z else out
+    return out
+
+
+def jl_rhs_at(g: Graph, k: int, seed: int, nodes) -> np.ndarray:
+    """Columns ``nodes`` of Y = Q W^{1/2} B (a k x len(nodes) array), each
+    summed over the node's incident edges only (Algorithm 1, step 2): for a
+    node u, Y[i, u] = sum over edges e containing u of Q[i, e] sqrt(w_e)
+    B[e, u], with B[e, u] = +1 when u is the smaller endpoint and -1 when it
+    is the larger.  For spot checks of very large graphs, where the whole Y
+    is too costly."""
+    out = np.zeros((k, len(nodes)))
+    for t, u in enumerate(nodes):
+        e_lo = np.nonzero(g.u == u)[0]  # u = min(e): B[e, u] = +1
+        e_hi = np.nonzero(g.v == u)[0]  # u = max(e): B[e, u] = -1
+        for edges, sign in ((e_lo, 1.0), (e_hi, -1.0)):
+            if edges.size == 0:
+                continue
+            q = (1.0 - 2.0 * jl_sign_bits(seed, k, edges).astype(np.float64)) / math.sqrt(k)  # edges x k
+            out[:, t] += sign * (q * np.sqrt(g.w[edges])[:, None]).sum(axis=0)
+    return out

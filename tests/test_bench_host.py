@@ -96,7 +96,7 @@ def test_read_traffic_checks_the_digest(tmp_path, monkeypatch):
     (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(
         {"w": {"smooth_fine": {"source_digest": "d1", "dram_bytes_per_launch": 5.0, "kernel": "k"}}}))
     monkeypatch.setattr(bench, "kernel_source_digest", lambda: "d1")
-    assert bench.read_traffic("w", "smooth_fine") == (5.0, "k")
-    assert bench.read_traffic("w", "spmv_fine") == (None, None)
+    assert bench.read_traffic("w", "smooth_fine") == (5.0, "k", None)
+    assert bench.read_traffic("w", "spmv_fine") == (None, None, None)
     monkeypatch.setattr(bench, "kernel_source_digest", lambda: "d2")
-    assert bench.read_traffic("w", "smooth_fine") == (None, None)
+    assert bench.read_traffic("w", "smooth_fine") == (None, None, None)

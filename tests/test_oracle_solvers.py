@@ -71,6 +71,19 @@ def test_jl_rhs_matches_brute_force_and_sums_to_zero():
     np.testing.assert_allclose(Y.sum(axis=1), 0, atol=1e-12)  # B 1 = 0
 
 
+@pytest.mark.parametrize("k", [5, 64, 300])
+def test_jl_rhs_at_nodes_matches_brute_force(k):
+    # the node-restricted right-hand side against the brute-force edge loop
+    # over the explicit Q (a hub, a leaf of the star and an arbitrary node)
+    g = _weighted(synth.barabasi_albert(60, 3, seed=5))
+    Q = jl.projection_matrix(g, k, seed=13)
+    nodes = [0, 17, g.n - 1]
+    np.testing.assert_allclose(jl.jl_rhs_at(g, k, 13, nodes), _y_brute(g, Q)[:, nodes], atol=1e-13)
+    gs = _weighted(synth.star_graph(12))
+    np.testing.assert_allclose(jl.jl_rhs_at(gs, k, 2, [0, 5]), _y_brute(gs, jl.projection_matrix(gs, k, 2))[:, [0, 5]],
+                               atol=1e-13)
+
+
 def test_identity_projection_gives_exact_resistance():
     # with Q = I_m (no projection) Algorithm 1 returns d_ER exactly:
     # d_ER(u,v) = ||W^{1/2} B L^+ (e_u - e_v)||^2 (Sec. 5.2)
