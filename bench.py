@@ -58,6 +58,9 @@ WORKLOADS = {
     "rmat20_jl16": dict(kind="rmat", scale=20, seed=3, k=16, jl_seed=1, nodes=[0]),
     "rmat20_jl64": dict(kind="rmat", scale=20, seed=3, k=64, jl_seed=1, nodes=[0]),
     "rmat20_jl128": dict(kind="rmat", scale=20, seed=3, k=128, jl_seed=1, nodes=[0]),
+    # between L2 and the headline size: profiling cases whose FP32 blocks exceed L2
+    "rmat21_jl64": dict(kind="rmat", scale=21, seed=5, k=64, jl_seed=1, nodes=[0]),
+    "rmat22_jl64": dict(kind="rmat", scale=22, seed=5, k=64, jl_seed=1, nodes=[0]),
     "grid1024_jl64": dict(kind="grid", a=1024, k=64, jl_seed=1, nodes=[0]),
     "grid4096_jl64": dict(kind="grid", a=4096, k=64, jl_seed=1, nodes=[0]),
     "rmat24_jl64": dict(kind="rmat", scale=24, seed=5, k=64, jl_seed=1, nodes=[0]),

@@ -86,6 +86,16 @@ typedef struct {
     int32_t match_rounds; /* handshake rounds per pass (default 4) */
     int32_t eager;        /* 1: build every level now; 0 (default): build the coarse
                              levels on the first solve that uses them */
+    int32_t eliminate;    /* 1 (default): LAMG's low-degree elimination (Sec. 3.1): an
+                             independent set of the nodes with one or two neighbours is
+                             eliminated exactly before the multigrid levels, when that
+                             removes at least 5% of the nodes; the PCG and the cycle then
+                             run on the Schur complement (a Laplacian), the FP64 residual
+                             of the refinement on G itself.  0: no elimination */
+    int32_t reorder;      /* processing order of each level's rows by the row kernels (the
+                             nodes keep their labels): 0 (default) longest rows first on
+                             levels whose row lengths are very uneven, natural order
+                             elsewhere; 1 natural order; 2 longest first everywhere */
 } lap_hier_opts_t;
 
 typedef struct {
@@ -149,6 +159,10 @@ typedef struct {
                                    weights far from 1 stay inside FP32's range */
     int32_t level_row_order[32];/* 1: the row kernels take the level's rows longest first (the
                                    level's row lengths are very uneven); 0: natural order */
+    uint64_t fingerprint;       /* order-free 64-bit hash of the merged graph (its edges and
+                                   weights): the key of the autotuner's choices */
+    int32_t elim_levels;        /* leading levels made by low-degree elimination (0 or 1): the
+                                   PCG and the multigrid cycle start at level elim_levels */
 } lap_hier_info_t;
 
 typedef struct lap_hierarchy lap_hierarchy_t;
@@ -347,6 +361,29 @@ lap_status_t cfc_farness_sampled(lap_hierarchy_t *h, int32_t n_pivots, uint64_t 
  */
 lap_status_t cfc_exact_small(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
                              const double *w, double *farness, double *closeness, void *stream);
+
+/*
+ * Autotuner table (no counterpart in the paper).  A solve whose options leave
+ * the configuration open (levels_used = 0) is tuned once per graph (keyed by
+ * lap_hier_info_t.fingerprint, so graphs of equal size but different
+ * structure are tuned separately) and per solve configuration (k, precision
+ * and the fields the caller fixed); the choice is kept for the process.  The
+ * choice depends on timings, so two processes may choose differently; a
+ * process that loads the table another one saved repeats its choices, and
+ * with them the bits of every solve, without timing candidates again.
+ *   lap_tune_save   writes the whole table to `path` as JSON (through a
+ *                   temporary file renamed into place)
+ *   lap_tune_load   adds the entries of such a file (keys already present
+ *                   keep their choice); *added (nullable) receives how many
+ *   lap_tune_entries  number of entries in the table
+ * With the environment variable LAP_TUNE_CACHE set to a path, that file is
+ * loaded before the process's first tuning and rewritten after each new
+ * choice.  Errors: LAP_EINVAL (NULL or empty path, a file that cannot be
+ * read or written, a malformed entry).
+ */
+lap_status_t lap_tune_save(const char *path);
+lap_status_t lap_tune_load(const char *path, int64_t *added);
+int64_t lap_tune_entries(void);
 
 /* Human-readable name of a status. */
 const char *lap_status_string(lap_status_t s);

@@ -54,6 +54,9 @@ from ._binding import (  # noqa: F401
     lap_stats_read,
     lap_stats_set_log,
     lap_stats_read_log,
+    lap_tune_entries,
+    lap_tune_load,
+    lap_tune_save,
     Server,
     ServerOpts,
     cfc_server_default_opts,

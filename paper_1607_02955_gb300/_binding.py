@@ -25,12 +25,14 @@ SYMBOLS = [
     "lap_stats_set_timing", "lap_stats_read", "lap_stats_set_log", "lap_stats_read_log",
     "cfc_server_default_opts", "cfc_server_create", "cfc_server_add_graph", "cfc_server_submit",
     "cfc_server_poll", "cfc_server_stats", "cfc_server_reset_stats", "cfc_server_destroy",
+    "lap_tune_save", "lap_tune_load", "lap_tune_entries",
 ]
 
 
 class HierOpts(C.Structure):
     _fields_ = [("coarse_max", C.c_int32), ("max_levels", C.c_int32), ("agg_passes", C.c_int32),
-                ("match_rounds", C.c_int32), ("eager", C.c_int32)]
+                ("match_rounds", C.c_int32), ("eager", C.c_int32), ("eliminate", C.c_int32),
+                ("reorder", C.c_int32)]
 
 
 class SolveOpts(C.Structure):
@@ -51,7 +53,8 @@ class SolveInfo(C.Structure):
 class HierInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("m", C.c_int64), ("levels", C.c_int32), ("coarse_n", C.c_int32),
                 ("level_n", C.c_int64 * 32), ("level_nnz", C.c_int64 * 32), ("setup_ms", C.c_double),
-                ("weight_exp", C.c_int32), ("level_row_order", C.c_int32 * 32)]
+                ("weight_exp", C.c_int32), ("level_row_order", C.c_int32 * 32), ("fingerprint", C.c_uint64),
+                ("elim_levels", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -152,6 +155,12 @@ def lib():
     L.cfc_server_reset_stats.restype = None
     L.cfc_server_destroy.argtypes = [vp]
     L.cfc_server_destroy.restype = None
+    L.lap_tune_save.argtypes = [C.c_char_p]
+    L.lap_tune_save.restype = C.c_int
+    L.lap_tune_load.argtypes = [C.c_char_p, C.POINTER(C.c_int64)]
+    L.lap_tune_load.restype = C.c_int
+    L.lap_tune_entries.argtypes = []
+    L.lap_tune_entries.restype = C.c_int64
     L.lap_stats_set_log.argtypes = [i32]
     L.lap_stats_set_log.restype = None
     L.lap_stats_read_log.argtypes = [vp, i64, C.POINTER(C.c_int64)]
@@ -268,7 +277,8 @@ def lap_hierarchy_info(h: Hierarchy) -> dict:
     L = info.levels
     return {"n": info.n, "m": info.m, "levels": L, "coarse_n": info.coarse_n,
             "level_n": list(info.level_n[:L]), "level_nnz": list(info.level_nnz[:L]), "setup_ms": info.setup_ms,
-            "weight_exp": info.weight_exp, "level_row_order": list(info.level_row_order[:L])}
+            "weight_exp": info.weight_exp, "level_row_order": list(info.level_row_order[:L]),
+            "fingerprint": int(info.fingerprint), "elim_levels": info.elim_levels}
 
 
 def lap_solve_multi(h: Hierarchy, B, X, opts: SolveOpts | None = None, stream=None, allow_noconv=False) -> dict:
@@ -406,6 +416,20 @@ def lap_stats_read_log() -> list:
     buf = (C.c_int32 * max(cnt.value, 1))()
     _check(lib().lap_stats_read_log(C.cast(buf, C.c_void_p), cnt.value, C.byref(cnt)), "lap_stats_read_log")
     return [KERNEL_FAMILIES[buf[i]] for i in range(cnt.value)]
+
+
+def lap_tune_save(path: str):
+    _check(lib().lap_tune_save(os.fsencode(path)), "lap_tune_save")
+
+
+def lap_tune_load(path: str) -> int:
+    added = C.c_int64(0)
+    _check(lib().lap_tune_load(os.fsencode(path), C.byref(added)), "lap_tune_load")
+    return added.value
+
+
+def lap_tune_entries() -> int:
+    return int(lib().lap_tune_entries())
 
 
 # ------------------------------------------------------------------ serving

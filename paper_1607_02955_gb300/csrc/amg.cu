@@ -250,6 +250,32 @@ __global__ void k_finish(const int32_t *__restrict__ rowptr, const double *__res
     }
 }
 
+// Order-free fingerprint of a level's graph: the sum (mod 2^64) over its CSR
+// entries of the MurmurHash3 finaliser (fmix64) of (row, column) mixed with
+// the weight's bit pattern; one warp per row, lanes striding its entries.
+// Integer sums commute, so the value does not depend on scheduling.
+__device__ __forceinline__ unsigned long long fmix64(unsigned long long x) {
+    x ^= x >> 33;
+    x *= 0xff51afd7ed558ccdull;
+    x ^= x >> 33;
+    x *= 0xc4ceb9fe1a85ec53ull;
+    x ^= x >> 33;
+    return x;
+}
+__global__ void k_fingerprint(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                              const double *__restrict__ w, int32_t n, unsigned long long *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long acc = 0;
+    WARP_ROW_LOOP(i, n) {
+        for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) {
+            const unsigned long long rc = ((unsigned long long)(uint32_t)i << 32) | (uint32_t)col[e];
+            acc += fmix64(rc ^ fmix64((unsigned long long)__double_as_longlong(w[e])));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0 && acc) atomicAdd(out, acc);
+}
+
 // largest of n positive doubles: positive doubles order like their bit
 // patterns read as unsigned integers
 __global__ void k_max_bits(const double *__restrict__ v, int64_t n, unsigned long long *__restrict__ out) {
@@ -312,6 +338,15 @@ __global__ void k_order_keys(const int32_t *__restrict__ rowptr, int32_t n, uint
         const int len = rowptr[i + 1] - rowptr[i];
         keys[i] = (uint64_t)(kLongRow + 1 - min(len, kLongRow + 1));
         vals[i] = (uint32_t)i;
+    }
+}
+
+// sort key of a chunk for its processing order: the column of its first entry
+__global__ void k_chunk_keys(const int32_t *__restrict__ col, const int32_t *__restrict__ chunk_begin, int32_t n_chunks,
+                             uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    GRID_LOOP(c, n_chunks) {
+        keys[c] = (uint32_t)col[chunk_begin[c]];
+        vals[c] = (uint32_t)c;
     }
 }
 
@@ -477,7 +512,236 @@ void contract(const int32_t *rowptr, const int32_t *col, const double *w, int32_
                out.w.get(), nc, out.deg.get());
 }
 
+// ---------------------------------------------------------------- low-degree elimination
+// Candidates are the nodes with one or two neighbours; they are picked in an
+// independent set by Luby-style rounds on the key (neighbour count, fmix32 of
+// the id) -- MurmurHash3's 32-bit finaliser, a bijection, so the tie-break
+// is unrelated to the labelling and never ties.  State: 0 undecided
+// candidate, 1 eliminated, 2 kept.  A round eliminates every undecided
+// candidate with no undecided neighbour of smaller key and keeps every
+// undecided candidate next to an eliminated node; nodes still undecided after
+// the last round are kept.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+__device__ __forceinline__ uint64_t elim_key(const int32_t *rowptr, int32_t i) {
+    return ((uint64_t)(rowptr[i + 1] - rowptr[i]) << 32) | fmix32((uint32_t)i);
+}
+
+__global__ void k_elim_init(const int32_t *__restrict__ rowptr, int32_t n, int32_t *__restrict__ state) {
+    GRID_LOOP(i, n) {
+        const int c = rowptr[i + 1] - rowptr[i];
+        state[i] = (c >= 1 && c <= 2) ? 0 : 2;
+    }
+}
+
+__global__ void k_elim_round(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, int32_t n,
+                             const int32_t *__restrict__ st, int32_t *__restrict__ st_next) {
+    GRID_LOOP(i, n) {
+        int v = st[i];
+        if (v == 0) {
+            const uint64_t ki = elim_key(rowptr, (int32_t)i);
+            bool blocked = false, smaller = false;
+            for (int t = rowptr[i]; t < rowptr[i + 1]; ++t) {
+                const int j = col[t];
+                const int sj = st[j];
+                blocked |= (sj == 1);
+                smaller |= (sj == 0 && elim_key(rowptr, j) < ki);
+            }
+            v = blocked ? 2 : (smaller ? 0 : 1);
+        }
+        st_next[i] = v;
+    }
+}
+
+__global__ void k_elim_flags(const int32_t *__restrict__ st, int32_t n, int32_t *__restrict__ elim,
+                             int32_t *__restrict__ keep) {
+    GRID_LOOP(i, n) {
+        const int e = st[i] == 1 ? 1 : 0;
+        elim[i] = e;
+        keep[i] = 1 - e;
+    }
+}
+
+// ids at the next level, the eliminated nodes' neighbours and coefficients,
+// and the series weight w_a w_b / d_u of each eliminated node with two
+// neighbours (its fill edge)
+__global__ void k_elim_tables(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                              const double *__restrict__ w, const double *__restrict__ deg, int32_t n,
+                              const int32_t *__restrict__ elim, const int32_t *__restrict__ eidx,
+                              const int32_t *__restrict__ kidx, double sc, int32_t *__restrict__ keep_id,
+                              int32_t *__restrict__ keep_node, int32_t *__restrict__ e_node,
+                              int32_t *__restrict__ e_nb, double *__restrict__ e_c64, float *__restrict__ e_c32,
+                              double *__restrict__ e_dinv64, float *__restrict__ e_dinv32,
+                              int32_t *__restrict__ fill_cnt, int32_t *__restrict__ pull_cnt,
+                              double *__restrict__ fill_w) {
+    GRID_LOOP(i, n) {
+        if (!elim[i]) {
+            keep_id[i] = kidx[i];
+            keep_node[kidx[i]] = (int32_t)i;
+            continue;
+        }
+        const int j = eidx[i];
+        keep_id[i] = -(j + 1);
+        e_node[j] = (int32_t)i;
+        const double d = deg[i];
+        const int e0 = rowptr[i], cnt = rowptr[i + 1] - e0;
+        for (int m = 0; m < 2; ++m) {
+            const bool has = m < cnt;
+            e_nb[2 * j + m] = has ? kidx[col[e0 + m]] : -1;  // neighbours are kept (independent set)
+            e_c64[2 * j + m] = has ? w[e0 + m] / d : 0.0;
+            e_c32[2 * j + m] = has ? (float)(w[e0 + m] / d) : 0.f;
+        }
+        e_dinv64[j] = 1.0 / d;
+        const double di = 1.0 / (d * sc);
+        e_dinv32[j] = di <= 3.0e38 ? (float)di : 0.f;
+        fill_cnt[j] = cnt == 2 ? 2 : 0;
+        pull_cnt[j] = cnt;
+        fill_w[j] = cnt == 2 ? w[e0] * w[e0 + 1] / d : 0.0;
+    }
+}
+
+// entries of the next level between two kept nodes: flags per entry
+__global__ void k_keep_flags(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, int32_t n,
+                             const int32_t *__restrict__ elim, int32_t *__restrict__ flag) {
+    const int lane = threadIdx.x & 31;
+    WARP_ROW_LOOP(i, n) {
+        const bool ki = !elim[i];
+        for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) flag[e] = (ki && !elim[col[e]]) ? 1 : 0;
+    }
+}
+
+// both directions of each fill edge as (row << b | col) keys at base + fpos[j],
+// their weights in wv
+__global__ void k_elim_emit_fill(const int32_t *__restrict__ e_nb, const int32_t *__restrict__ fill_cnt,
+                                 const int32_t *__restrict__ fpos, const double *__restrict__ fill_w, int32_t n_elim,
+                                 int64_t base, int b, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                                 double *__restrict__ wv) {
+    GRID_LOOP(j, n_elim) {
+        if (!fill_cnt[j]) continue;
+        const uint64_t a = (uint32_t)e_nb[2 * j], c = (uint32_t)e_nb[2 * j + 1];
+        const int64_t p = base + fpos[j];
+        keys[p] = (a << b) | c;
+        keys[p + 1] = (c << b) | a;
+        vals[p] = (uint32_t)p;
+        vals[p + 1] = (uint32_t)(p + 1);
+        wv[p] = fill_w[j];
+        wv[p + 1] = fill_w[j];
+    }
+}
+
+// The next level's rows without a global sort.  Old-to-new ids are
+// monotone, so the entries between two kept nodes, taken in CSR order, are
+// already sorted by (new row, new column): they are compacted (kcol, kw) and
+// each new row's run starts at kstart.  The fill edges (few) are sorted on
+// their own and merged with equal fills summed (ucol, uw, rows at fptr); then
+// each row's fills are merged into its kept run: a fill whose column the row
+// already has adds its weight there, the others are inserted in order.
+__global__ void k_elim_compact(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                               const double *__restrict__ w, int32_t n, const int32_t *__restrict__ elim,
+                               const int32_t *__restrict__ kidx, const int32_t *__restrict__ flag,
+                               const int32_t *__restrict__ pos, int32_t *__restrict__ kcol,
+                               double *__restrict__ kw, int32_t *__restrict__ kstart) {
+    const int lane = threadIdx.x & 31;
+    WARP_ROW_LOOP(i, n) {
+        if (elim[i]) continue;
+        if (lane == 0) kstart[kidx[i]] = pos[rowptr[i]];
+        for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) {
+            if (!flag[e]) continue;
+            kcol[pos[e]] = kidx[col[e]];
+            kw[pos[e]] = w[e];
+        }
+    }
+}
+
+// first index in a[lo, hi) with a[idx] >= x
+__device__ __forceinline__ int lower_bound_i32(const int32_t *a, int lo, int hi, int32_t x) {
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// per fill: 1 when its column is not among the row's kept entries (inserted)
+__global__ void k_elim_fill_new(const int32_t *__restrict__ kcol, const int32_t *__restrict__ kstart,
+                                const int32_t *__restrict__ ucol, const int32_t *__restrict__ fptr, int32_t nk,
+                                int32_t *__restrict__ fnew) {
+    const int lane = threadIdx.x & 31;
+    WARP_ROW_LOOP(I, nk) {
+        const int k0 = kstart[I], k1 = kstart[I + 1];
+        for (int f = fptr[I] + lane; f < fptr[I + 1]; f += 32) {
+            const int p = lower_bound_i32(kcol, k0, k1, ucol[f]);
+            fnew[f] = (p < k1 && kcol[p] == ucol[f]) ? 0 : 1;
+        }
+    }
+}
+
+// row lengths of the next level: kept entries plus inserted fills
+__global__ void k_elim_row_len(const int32_t *__restrict__ kstart, const int32_t *__restrict__ fptr,
+                               const int32_t *__restrict__ fnew_pref, int32_t nk, int32_t *__restrict__ len) {
+    GRID_LOOP(I, nk) len[I] = (kstart[I + 1] - kstart[I]) + (fnew_pref[fptr[I + 1]] - fnew_pref[fptr[I]]);
+}
+
+__global__ void k_elim_write(const int32_t *__restrict__ kcol, const double *__restrict__ kw,
+                             const int32_t *__restrict__ kstart, const int32_t *__restrict__ ucol,
+                             const double *__restrict__ uw, const int32_t *__restrict__ fptr,
+                             const int32_t *__restrict__ fnew, const int32_t *__restrict__ fnew_pref,
+                             const int32_t *__restrict__ rowptr_n, int32_t nk, int32_t *__restrict__ col_n,
+                             double *__restrict__ w_n) {
+    const int lane = threadIdx.x & 31;
+    WARP_ROW_LOOP(I, nk) {
+        const int k0 = kstart[I], k1 = kstart[I + 1], f0 = fptr[I], f1 = fptr[I + 1];
+        const int base = rowptr_n[I];
+        for (int t = k0 + lane; t < k1; t += 32) {
+            const int32_t c = kcol[t];
+            const int p = lower_bound_i32(ucol, f0, f1, c);  // fills with a smaller column
+            double wt = kw[t];
+            if (p < f1 && ucol[p] == c) wt += uw[p];     // the kept weight, then the fills' sum
+            col_n[base + (t - k0) + (fnew_pref[p] - fnew_pref[f0])] = c;
+            w_n[base + (t - k0) + (fnew_pref[p] - fnew_pref[f0])] = wt;
+        }
+        for (int f = f0 + lane; f < f1; f += 32) {
+            if (!fnew[f]) continue;
+            const int q = lower_bound_i32(kcol, k0, k1, ucol[f]) - k0;  // kept entries with a smaller column
+            col_n[base + q + (fnew_pref[f] - fnew_pref[f0])] = ucol[f];
+            w_n[base + q + (fnew_pref[f] - fnew_pref[f0])] = uw[f];
+        }
+    }
+}
+
+// pull lists: (next-level node, slot 2 j + m) pairs, sorted by node (stable:
+// ascending j within a node)
+__global__ void k_elim_emit_pull(const int32_t *__restrict__ e_nb, const int32_t *__restrict__ pull_cnt,
+                                 const int32_t *__restrict__ ppos, int32_t n_elim, uint64_t *__restrict__ keys,
+                                 uint32_t *__restrict__ vals, int32_t *__restrict__ cnt) {
+    GRID_LOOP(j, n_elim) {
+        for (int m = 0; m < pull_cnt[j]; ++m) {
+            const int64_t p = ppos[j] + m;
+            keys[p] = (uint32_t)e_nb[2 * j + m];
+            vals[p] = (uint32_t)(2 * j + m);
+            atomicAdd(&cnt[e_nb[2 * j + m]], 1);
+        }
+    }
+}
+
 }  // namespace
+
+uint64_t graph_fingerprint(const Level &L, cudaStream_t s) {
+    DBuf<int64_t> f(1, s);
+    f.zero(s);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_fingerprint, grid_for(32 * (int64_t)L.n), kBlock, 0, L.rowptr.get(),
+               L.col.get(), L.w64.get(), L.n, reinterpret_cast<unsigned long long *>(f.get()));
+    int64_t h = 0;
+    read_totals(f.get(), 1, &h, s);
+    return (uint64_t)h;
+}
 
 int max_exponent(const double *v, int64_t n, cudaStream_t s) {
     DBuf<int64_t> m(1, s);
@@ -491,7 +755,7 @@ int max_exponent(const double *v, int64_t n, cudaStream_t s) {
     return mx > 0.0 ? std::ilogb(mx) : 0;
 }
 
-void finish_level(Level &L, int wexp, cudaStream_t s) {
+void finish_level(Level &L, int wexp, int reorder, cudaStream_t s) {
     const int32_t n = L.n;
     const int64_t nnz = L.nnz;
     L.w32.alloc_persistent(std::max<int64_t>(nnz, 1));
@@ -523,7 +787,9 @@ void finish_level(Level &L, int wexp, cudaStream_t s) {
     // from the extra indirection (1.0).  Sorting only within 32-row windows
     // lost the gain.
     L.order.release();
-    if ((double)h[2] > 1.5 * (double)h[3] / 4.0) {  // warps spend 50 % more rounds than balanced rows would
+    // reorder 0: when warps spend 50 % more rounds than balanced rows would
+    const bool uneven = (double)h[2] > 1.5 * (double)h[3] / 4.0;
+    if (reorder == 2 || (reorder == 0 && uneven)) {
         DBuf<uint64_t> keys(n, s);
         L.order.alloc_persistent(n);
         CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_order_keys, grid_for(n), kBlock, 0, L.rowptr.get(), n, keys.get(),
@@ -540,6 +806,151 @@ void finish_level(Level &L, int wexp, cudaStream_t s) {
                cfirst.get(), lidx.get(), n, L.chunk_row.get(), L.chunk_begin.get(), L.chunk_long.get(),
                L.long_first.get(), L.long_of_row.get());
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_set_last, 1, 1, 0, L.long_first.get(), L.n_long, L.n_chunks);
+    // chunks in ascending order of their first column (stable: row order among equals)
+    {
+        DBuf<uint64_t> keys(L.n_chunks, s);
+        L.chunk_order.alloc_persistent(L.n_chunks);
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_chunk_keys, grid_for(L.n_chunks), kBlock, 0, L.col.get(),
+                   L.chunk_begin.get(), L.n_chunks, keys.get(), reinterpret_cast<uint32_t *>(L.chunk_order.get()));
+        radix_sort_pairs(keys.get(), reinterpret_cast<uint32_t *>(L.chunk_order.get()), L.n_chunks, bits_for(n), s);
+    }
+}
+
+// LAMG's low-degree elimination (Sec. 3.1) from the last level of h: an
+// independent set of nodes with one or two neighbours is eliminated exactly,
+// and the Schur complement becomes the next level.  Returns false (and builds
+// nothing) when fewer than min_frac of the nodes would go, or fewer than 64
+// would stay.
+bool eliminate_level(lap_hierarchy &h, double min_frac, cudaStream_t s) {
+    Level &F = h.lv.back();
+    const int32_t n = F.n;
+    DBuf<int32_t> elim(n, s), keep(n, s), eidx(n, s), kidx(n, s);
+    {
+        DBuf<int32_t> st0(n, s), st1(n, s);
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_elim_init, grid_for(n), kBlock, 0, F.rowptr.get(), n, st0.get());
+        for (int r = 0; r < 4; ++r) {
+            CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_elim_round, grid_for(n), kBlock, 0, F.rowptr.get(), F.col.get(), n,
+                       st0.get(), st1.get());
+            std::swap(st0, st1);
+        }
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_elim_flags, grid_for(n), kBlock, 0, st0.get(), n, elim.get(), keep.get());
+    }
+    DBuf<int64_t> tot(2, s);
+    tot.zero(s);
+    scan_exclusive_i32_total(elim.get(), eidx.get(), n, tot.get(), s);
+    scan_exclusive_i32_total(keep.get(), kidx.get(), n, tot.get() + 1, s);
+    int64_t ht[2];
+    read_totals(tot.get(), 2, ht, s);
+    const int32_t ne = (int32_t)ht[0], nk = (int32_t)ht[1];
+    if (ne < min_frac * n || nk < 64) return false;
+    F.elim = true;
+    F.n_elim = ne;
+    F.keep_id.alloc_persistent(n);
+    F.keep_node.alloc_persistent(nk);
+    F.e_node.alloc_persistent(ne);
+    F.e_nb.alloc_persistent(2 * (size_t)ne);
+    F.e_c64.alloc_persistent(2 * (size_t)ne);
+    F.e_c32.alloc_persistent(2 * (size_t)ne);
+    F.e_dinv64.alloc_persistent(ne);
+    F.e_dinv32.alloc_persistent(ne);
+    DBuf<int32_t> fill_cnt(ne, s), pull_cnt(ne, s), fpos(ne, s), ppos(ne, s);
+    DBuf<double> fill_w(ne, s);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_elim_tables, grid_for(n), kBlock, 0, F.rowptr.get(), F.col.get(),
+               F.w64.get(), F.deg64.get(), n, elim.get(), eidx.get(), kidx.get(), std::ldexp(1.0, -h.wexp),
+               F.keep_id.get(), F.keep_node.get(), F.e_node.get(), F.e_nb.get(), F.e_c64.get(), F.e_c32.get(),
+               F.e_dinv64.get(), F.e_dinv32.get(), fill_cnt.get(), pull_cnt.get(), fill_w.get());
+    // next-level entries: the kept ones (already in order), merged row by row
+    // with the fill edges (sorted and summed on their own)
+    DBuf<int32_t> flag(F.nnz, s), pos(F.nnz, s);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_keep_flags, grid_for(32 * (int64_t)n), kBlock, 0, F.rowptr.get(), F.col.get(),
+               n, elim.get(), flag.get());
+    DBuf<int64_t> tot2(3, s);
+    tot2.zero(s);
+    scan_exclusive_i32_total(flag.get(), pos.get(), F.nnz, tot2.get(), s);
+    scan_exclusive_i32_total(fill_cnt.get(), fpos.get(), ne, tot2.get() + 1, s);
+    scan_exclusive_i32_total(pull_cnt.get(), ppos.get(), ne, tot2.get() + 2, s);
+    int64_t h3[3];
+    read_totals(tot2.get(), 3, h3, s);
+    const int64_t nkept = h3[0], nfill = h3[1], npull = h3[2];
+    const int b = bits_for(nk);
+    Graph64 C;
+    C.n = nk;
+    C.rowptr.alloc_persistent(nk + 1);
+    C.deg.alloc_persistent(nk);
+    {
+        DBuf<int32_t> kcol(std::max<int64_t>(nkept, 1), s), kstart(nk + 1, s);
+        DBuf<double> kw(std::max<int64_t>(nkept, 1), s);
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_elim_compact, grid_for(32 * (int64_t)n), kBlock, 0, F.rowptr.get(),
+                   F.col.get(), F.w64.get(), n, elim.get(), kidx.get(), flag.get(), pos.get(), kcol.get(), kw.get(),
+                   kstart.get());
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_set_last, 1, 1, 0, kstart.get(), nk, (int32_t)nkept);
+        flag.release();
+        pos.release();
+        // fill edges: sort, sum equal pairs, count per row
+        DBuf<int32_t> ucol(std::max<int64_t>(nfill, 1), s), fptr(nk + 1, s), fcnt(nk + 1, s);
+        DBuf<double> uw(std::max<int64_t>(nfill, 1), s);
+        fcnt.zero(s);
+        int64_t nu = 0;
+        if (nfill > 0) {
+            DBuf<uint64_t> keys(nfill, s);
+            DBuf<uint32_t> vals(nfill, s);
+            DBuf<double> wv(nfill, s);
+            CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_elim_emit_fill, grid_for(ne), kBlock, 0, F.e_nb.get(), fill_cnt.get(),
+                       fpos.get(), fill_w.get(), ne, (int64_t)0, b, keys.get(), vals.get(), wv.get());
+            radix_sort_pairs(keys.get(), vals.get(), nfill, 2 * b, s);
+            DBuf<int32_t> head(nfill, s), hpos(nfill, s);
+            CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_heads, grid_for(nfill), kBlock, 0, keys.get(), nfill, head.get());
+            nu = scan_exclusive_i32(head.get(), hpos.get(), nfill, s);
+            CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_merge, grid_for(nfill), kBlock, 0, keys.get(), vals.get(), head.get(),
+                       hpos.get(), nfill, b, wv.get(), ucol.get(), uw.get(), fcnt.get());
+        }
+        scan_exclusive_i32(fcnt.get(), fptr.get(), nk, s);
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_set_last, 1, 1, 0, fptr.get(), nk, (int32_t)nu);
+        // which fills are new entries, the row lengths, and the merge
+        DBuf<int32_t> fnew(std::max<int64_t>(nu, 1), s), fnew_pref(nu + 1, s), rlen(nk, s);
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_elim_fill_new, grid_for(32 * (int64_t)nk), kBlock, 0, kcol.get(),
+                   kstart.get(), ucol.get(), fptr.get(), nk, fnew.get());
+        const int64_t nnew = nu > 0 ? scan_exclusive_i32(fnew.get(), fnew_pref.get(), nu, s) : 0;
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_set_last, 1, 1, 0, fnew_pref.get(), (int32_t)nu, (int32_t)nnew);
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_elim_row_len, grid_for(nk), kBlock, 0, kstart.get(), fptr.get(),
+                   fnew_pref.get(), nk, rlen.get());
+        const int64_t cnnz = scan_exclusive_i32(rlen.get(), C.rowptr.get(), nk, s);
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_set_last, 1, 1, 0, C.rowptr.get(), nk, (int32_t)cnnz);
+        C.nnz = cnnz;
+        C.col.alloc_persistent(std::max<int64_t>(cnnz, 1));
+        C.w.alloc_persistent(std::max<int64_t>(cnnz, 1));
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_elim_write, grid_for(32 * (int64_t)nk), kBlock, 0, kcol.get(), kw.get(),
+                   kstart.get(), ucol.get(), uw.get(), fptr.get(), fnew.get(), fnew_pref.get(), C.rowptr.get(), nk,
+                   C.col.get(), C.w.get());
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_row_sums, grid_for(32 * (int64_t)nk), kBlock, 0, C.rowptr.get(),
+                   C.w.get(), nk, C.deg.get());
+    }
+    // pull lists of the restriction, in ascending order of the eliminated node
+    {
+        DBuf<uint64_t> keys(std::max<int64_t>(npull, 1), s);
+        DBuf<uint32_t> vals(std::max<int64_t>(npull, 1), s);
+        DBuf<int32_t> cnt(nk + 1, s);
+        cnt.zero(s);
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_elim_emit_pull, grid_for(ne), kBlock, 0, F.e_nb.get(), pull_cnt.get(),
+                   ppos.get(), ne, keys.get(), vals.get(), cnt.get());
+        radix_sort_pairs(keys.get(), vals.get(), npull, bits_for(nk), s);
+        F.pull_ptr.alloc_persistent(nk + 1);
+        F.pull_e.alloc_persistent(std::max<int64_t>(npull, 1));
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_u32_to_i32, grid_for(npull), kBlock, 0, vals.get(), F.pull_e.get(),
+                   (int32_t)npull);
+        scan_exclusive_i32(cnt.get(), F.pull_ptr.get(), nk, s);
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_set_last, 1, 1, 0, F.pull_ptr.get(), nk, (int32_t)npull);
+    }
+    Level Cl;
+    Cl.n = nk;
+    Cl.nnz = C.nnz;
+    Cl.rowptr = std::move(C.rowptr);
+    Cl.col = std::move(C.col);
+    Cl.w64 = std::move(C.w);
+    Cl.deg64 = std::move(C.deg);
+    h.lv.push_back(std::move(Cl));
+    finish_level(h.lv.back(), h.wexp, h.hopts.reorder, s);
+    return true;
 }
 
 void ensure_bf16(Level &L, int wexp, cudaStream_t s) {
@@ -588,8 +999,13 @@ void init_levels(lap_hierarchy &h, Csr64 &fine, const lap_hier_opts_t &o, cudaSt
     h.complete = false;
     h.coarse_n = 0;
     h.wexp = max_exponent(L0.w64.get(), std::max<int64_t>(L0.nnz, 1), s);
-    finish_level(L0, h.wexp, s);
-    if (L0.n <= std::min(256, std::max(2, o.coarse_max)) || o.max_levels <= 1) grow_levels(h, 0, s);
+    h.fingerprint = graph_fingerprint(L0, s);
+    finish_level(L0, h.wexp, o.reorder, s);
+    h.p0 = 0;
+    // low-degree elimination when it removes at least 5 % of the nodes
+    if (o.eliminate && L0.n > 256 && eliminate_level(h, 0.05, s)) h.p0 = 1;
+    const Level &T = h.lv.back();
+    if (T.n <= std::min(256, std::max(2, o.coarse_max)) || o.max_levels <= 1) grow_levels(h, 0, s);
 }
 
 // Coarsen until the hierarchy has `target` levels (0: until coarsening stops:
@@ -611,7 +1027,9 @@ void grow_levels(lap_hierarchy &h, int target, cudaStream_t s) {
             cudaEventDestroy(b);
         }
     } evg{ev0, ev1};
-    while ((int)h.lv.size() < max_levels && h.lv.back().n > coarse_max && (target <= 0 || (int)h.lv.size() < target)) {
+    // levels of the cycle: those from lv[p0] on (the elimination levels in front are not counted)
+    auto cycle_levels = [&]() { return (int)h.lv.size() - h.p0; };
+    while (cycle_levels() < max_levels && h.lv.back().n > coarse_max && (target <= 0 || cycle_levels() < target)) {
         CFC_CUDA(cudaEventRecord(ev0, s));
         Level &F = h.lv.back();
         const int32_t n = F.n;
@@ -658,7 +1076,7 @@ void grow_levels(lap_hierarchy &h, int target, cudaStream_t s) {
         Cl.w64 = std::move(C.w);
         Cl.deg64 = std::move(C.deg);
         h.lv.push_back(std::move(Cl));
-        finish_level(h.lv.back(), h.wexp, s);
+        finish_level(h.lv.back(), h.wexp, o.reorder, s);
         CFC_CUDA(cudaEventRecord(ev1, s));
         CFC_CUDA(cudaEventSynchronize(ev1));
         float ms = 0.f;
@@ -666,7 +1084,7 @@ void grow_levels(lap_hierarchy &h, int target, cudaStream_t s) {
         h.level_ms.resize(h.lv.size(), 0.0);
         h.level_ms[h.lv.size() - 1] = ms;
     }
-    const bool done = stalled || (int)h.lv.size() >= max_levels || h.lv.back().n <= coarse_max;
+    const bool done = stalled || cycle_levels() >= max_levels || h.lv.back().n <= coarse_max;
     if (!done) return;
     h.complete = true;
     // dense coarsest solve

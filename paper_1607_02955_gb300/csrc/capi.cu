@@ -169,6 +169,7 @@ LevelView view(const Level &L) {
     v.long_first = L.long_first.get();
     v.long_of_row = L.long_of_row.get();
     v.order = L.order.get();
+    v.chunk_order = L.chunk_order.get();
     v.long_count = nullptr;  // set by the solve that launches on the level
     return v;
 }
@@ -192,7 +193,10 @@ int64_t hierarchy_bytes(const lap_hierarchy *h) {
     for (const Level &L : h->lv)
         t += b(L.rowptr) + b(L.col) + b(L.w64) + b(L.deg64) + b(L.dinv64) + b(L.w32) + b(L.deg32) + b(L.dinv32) +
              b(L.wbf) + b(L.degbf) + b(L.dinvbf) + b(L.chunk_row) + b(L.chunk_begin) + b(L.chunk_long) +
-             b(L.long_first) + b(L.long_of_row) + b(L.order) + b(L.agg) + b(L.mem_ptr) + b(L.mem);
+             b(L.long_first) + b(L.long_of_row) + b(L.order) + b(L.chunk_order) + b(L.agg) + b(L.mem_ptr) +
+             b(L.mem) +
+             b(L.keep_id) + b(L.keep_node) + b(L.e_node) + b(L.e_nb) + b(L.e_c64) + b(L.e_c32) +
+             b(L.e_dinv64) + b(L.e_dinv32) + b(L.pull_ptr) + b(L.pull_e);
     return t;
 }
 
@@ -210,6 +214,8 @@ void lap_default_hier_opts(lap_hier_opts_t *o) {
     o->agg_passes = 2;
     o->match_rounds = 4;
     o->eager = 0;
+    o->eliminate = 1;
+    o->reorder = 0;
 }
 
 void lap_default_solve_opts(lap_solve_opts_t *o) {
@@ -258,6 +264,8 @@ lap_status_t lap_build_hierarchy(int64_t n, int64_t m, const int32_t *src, const
         lap_default_hier_opts(&o);
         if (opts) o = *opts;
         CFC_REQUIRE(o.agg_passes >= 1 && o.agg_passes <= 4, LAP_EINVAL, "agg_passes must be 1..4");
+        CFC_REQUIRE(o.eliminate == 0 || o.eliminate == 1, LAP_EINVAL, "eliminate must be 0 or 1");
+        CFC_REQUIRE(o.reorder >= 0 && o.reorder <= 2, LAP_EINVAL, "reorder must be 0, 1 or 2");
         cudaStream_t s = (cudaStream_t)stream;
         auto *h = new lap_hierarchy();
         try {
@@ -313,6 +321,8 @@ lap_status_t lap_hierarchy_info(const lap_hierarchy_t *h, lap_hier_info_t *info)
         }
         info->setup_ms = h->setup_ms;
         info->weight_exp = h->wexp;
+        info->fingerprint = h->fingerprint;
+        info->elim_levels = h->p0;
         for (size_t l = 0; l < h->lv.size() && l < 32; ++l) info->level_row_order[l] = h->lv[l].order.get() ? 1 : 0;
         return LAP_OK;
     });
@@ -397,6 +407,16 @@ lap_status_t cfc_exact_small(int64_t n, int64_t m, const int32_t *src, const int
         return exact_small(n, m, src, dst, w, farness, closeness, (cudaStream_t)stream);
     });
 }
+
+lap_status_t lap_tune_save(const char *path) {
+    return guard([&]() -> lap_status_t { return tune_save(path); });
+}
+
+lap_status_t lap_tune_load(const char *path, int64_t *added) {
+    return guard([&]() -> lap_status_t { return tune_load(path, added); });
+}
+
+int64_t lap_tune_entries(void) { return tune_entries(); }
 
 void lap_stats_reset(void) {
     std::lock_guard<std::mutex> lk(g_mu);

@@ -168,10 +168,35 @@ struct Level {
     DBuf<int32_t> chunk_long;    // [n_chunks] index of the chunk's long row
     DBuf<int32_t> long_first;    // [n_long + 1] first chunk of each long row
     DBuf<int32_t> long_of_row;   // [n] index of the row among the long rows, -1 if short
+    // [n_chunks] processing order of the chunks: ascending first column, so
+    // that the chunks in flight together gather from a narrow range of
+    // columns (the long rows' columns are sorted) and the gathered rows are
+    // reused from L2; each chunk's partial sum stays at its own index
+    DBuf<int32_t> chunk_order;
     DBuf<int32_t> order;         // [n] processing order of the rows (longest first), or empty: natural
     // map to the next coarser level (empty at the coarsest)
     DBuf<int32_t> agg;           // [n] aggregate (coarse node) of each node
     DBuf<int32_t> mem_ptr, mem;  // members of each coarse node, ascending
+    // Elimination to the next level (LAMG's low-degree elimination, Sec. 3.1):
+    // an independent set of this level's nodes with one or two neighbours is
+    // eliminated exactly, and the next level is the Schur complement, itself
+    // a Laplacian (a leaf disappears; a node between a and b becomes the
+    // series edge w_a w_b / (w_a + w_b)).  With b on this level:
+    //   restriction   b'(I) = b(keep_node[I]) + sum over the eliminated
+    //                 neighbours u of keep_node[I] of (w_u,I / d_u) b(u)
+    //   back-substitution  x(u) = b(u) / d_u + sum_m (w_um / d_u) x'(nb_m(u))
+    bool elim = false;
+    int32_t n_elim = 0;
+    DBuf<int32_t> keep_id;       // [n] id at the next level, or -(j + 1) for eliminated node j
+    DBuf<int32_t> keep_node;     // [n_next] the node of this level each next-level node is
+    DBuf<int32_t> e_node;        // [n_elim] the eliminated nodes, ascending
+    DBuf<int32_t> e_nb;          // [2 n_elim] their neighbours, as next-level ids (-1: none)
+    DBuf<double> e_c64;          // [2 n_elim] w_um / d_u
+    DBuf<float> e_c32;
+    DBuf<double> e_dinv64;       // [n_elim] 1 / d_u
+    DBuf<float> e_dinv32;        //          2^wexp / d_u (the FP32 operators are 2^-wexp L)
+    DBuf<int32_t> pull_ptr;      // [n_next + 1] eliminated neighbours of each next-level node,
+    DBuf<int32_t> pull_e;        //   as slots 2 j + m of e_nb / e_c (ascending j)
 };
 
 constexpr int kLongRow = 32;     // rows with more nonzeros are split into chunks
@@ -187,7 +212,7 @@ struct LevelView {
     const uint16_t *wbf;  // BF16 weights, read by the kernels instantiated for them
     const double *w64, *deg64, *dinv64;
     int32_t n_chunks, n_long;
-    const int32_t *chunk_row, *chunk_begin, *chunk_long, *long_first, *long_of_row, *order;
+    const int32_t *chunk_row, *chunk_begin, *chunk_long, *long_first, *long_of_row, *order, *chunk_order;
     uint32_t *long_count;  // [n_long * kMaxTiles] arrival counters of the launching solve
 };
 LevelView view(const Level &L);
@@ -233,10 +258,14 @@ void grow_levels(lap_hierarchy &h, int target, cudaStream_t s);  // target 0: al
 // wexp: the hierarchy's weight exponent; the FP32 and BF16 copies hold
 // w * 2^-wexp (see lap_hierarchy::wexp)
 void ensure_bf16(Level &L, int wexp, cudaStream_t s);
-void finish_level(Level &L, int wexp, cudaStream_t s);  // FP32 copies, inverse degrees, long-row split
+// FP32 copies, inverse degrees, long-row split, row order (reorder as lap_hier_opts_t)
+void finish_level(Level &L, int wexp, int reorder, cudaStream_t s);
 // Exponent of the largest of n positive FP64 values (device array): the e with
 // 2^e <= max < 2^(e+1).  Synchronises s.
 int max_exponent(const double *v, int64_t n, cudaStream_t s);
+// Order-free 64-bit fingerprint of a level's graph (its CSR entries and
+// weights): equal graphs give equal values.  Synchronises s.
+uint64_t graph_fingerprint(const Level &L, cudaStream_t s);
 
 // dense SPD inverse (in place, FP64, row-major n x n) -- used for the
 // coarsest level (single CTA, n <= 160) and cfc_exact_small (global memory).
@@ -262,6 +291,12 @@ struct lap_hierarchy {
     // any magnitude, Sec. 2) neither overflow nor fall below FP32's normal
     // range; the FP64 copies are unscaled.  0 for weights in [1, 2).
     int32_t wexp = 0;
+    // fingerprint of the level-0 graph: the autotuner's choices are kept per graph
+    uint64_t fingerprint = 0;
+    // elimination levels in front of the cycle (lv[0 .. p0-1] have elim set):
+    // the PCG and the multigrid cycle run from lv[p0]; the FP64 residual of
+    // the outer refinement stays on lv[0]
+    int32_t p0 = 0;
     double setup_ms = 0;
     // One solve workspace per stream, grown on demand and reused (stream
     // order keeps consecutive solves on one stream apart), so solves on
@@ -286,6 +321,9 @@ namespace cfc {
 // solve.cu
 lap_status_t solve_multi(lap_hierarchy *h, int32_t k, const double *B, double *X,
                          const lap_solve_opts_t &o, cudaStream_t s, lap_solve_info_t *info);
+lap_status_t tune_save(const char *path);
+lap_status_t tune_load(const char *path, int64_t *added);
+int64_t tune_entries();
 lap_status_t solve_multi_direct(lap_hierarchy *h, int32_t k, const double *B, double *X, const lap_solve_opts_t &o,
                                 cudaStream_t s, lap_solve_info_t *info);
 int solve_ld(int32_t k, const lap_solve_opts_t &o);  // padded column count of the solver's blocks

@@ -438,8 +438,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_chunk_sums(LevelView A, Op op, T 
     constexpr int RPB = kBlock / G;
     const int lane = threadIdx.x % G, grp = threadIdx.x / G;
     const int c0 = blockIdx.y * KT + lane * VW;
-    const int ch = blockIdx.x * RPB + grp;
-    if (ch >= A.n_chunks) return;
+    const int slot = blockIdx.x * RPB + grp;
+    if (slot >= A.n_chunks) return;
+    const int ch = A.chunk_order ? __ldg(A.chunk_order + slot) : slot;
     const int i = __ldg(A.chunk_row + ch);
     const int e0 = __ldg(A.chunk_begin + ch);
     const int e1 = min(e0 + kChunk, __ldg(A.rowptr + i + 1));
@@ -495,8 +496,9 @@ __global__ void __launch_bounds__(kBlock, (NR >= 3 ? 3 : 4)) k_rowop(LevelView A
                 }
             }
         } else {
-            const int ch = (vb - nvb_short) * RPB + grp;
-            const bool has = ch < A.n_chunks;
+            const int cslot = (vb - nvb_short) * RPB + grp;
+            const bool has = cslot < A.n_chunks;
+            const int ch = has ? (A.chunk_order ? __ldg(A.chunk_order + cslot) : cslot) : 0;
             int i = 0;
             if (has) {
                 i = __ldg(A.chunk_row + ch);

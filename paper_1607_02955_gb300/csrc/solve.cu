@@ -27,7 +27,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <map>
+#include <string>
 #include <mutex>
 #include <tuple>
 #include <type_traits>
@@ -340,6 +342,82 @@ struct OpUpdateXR {
     }
 };
 
+// The Jacobi preconditioner (a one-level cycle of a single smoothing step,
+// z = e0 D^{-1} r) fused into the PCG updates, so that z is never stored:
+//   x += alpha p ; r -= alpha q ; z formed in registers ; sums r^2 (inner
+//   convergence), r.z, sum z, sum r (the PCG scalars) -- then
+//   p = (z - mu) + beta p with z formed again from r.
+// The values, and the order of every sum, are those of OpUpdateXR with z1,
+// OpDotRZ and OpUpdateP, so the results are the same bits.
+// a * b rounded once, never contracted into an FMA with a later add: the
+// fused ops must round z exactly as the stored z was rounded
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+template <typename T>
+struct OpUpdateXRJacobi {
+    using V = typename Vec<T>::V;
+    static constexpr int VW = Vec<T>::W;
+    T *x, *r;
+    const T *p, *q;
+    LevelView A;
+    T e0;
+    int ld;
+    const T *alpha_t;
+    int32_t *active;
+    const double *rr0;
+    double tol2;
+    DotState<T> ds;
+    template <class Acc>
+    __device__ void row(int i, int c0, Acc &acc) const {
+        const size_t o = (size_t)i * ld + c0;
+        V xi = vld<T>(x + o), ri = vld<T>(r + o);
+        const V pi = vld<T>(p + o), qi = vld<T>(q + o);
+        const V a = vld<T>(alpha_t + c0);
+        const T di = e0 * ldinv<T>(A, i);
+#pragma unroll
+        for (int v = 0; v < VW; ++v) {
+            vel(xi, v) += vel(a, v) * vel(pi, v);
+            vel(ri, v) -= vel(a, v) * vel(qi, v);
+            const T rv = vel(ri, v), zv = mul_rn(di, rv);
+            acc.add(0, v, rv * rv);
+            acc.add(1, v, rv * zv);
+            acc.add(2, v, zv);
+            acc.add(3, v, rv);
+        }
+        vst<T>(x + o, xi);
+        vst<T>(r + o, ri);
+    }
+    __device__ void fin(int c, const double *sums) const {
+        if (active[c] && !(sums[0] > tol2 * rr0[c])) active[c] = 0;
+        ds.template fin<false>(c, sums + 1);
+    }
+};
+
+template <typename T>
+struct OpUpdatePJacobi {
+    using V = typename Vec<T>::V;
+    static constexpr int VW = Vec<T>::W;
+    const T *r;
+    T *p;
+    LevelView A;
+    T e0;
+    int ld;
+    const T *mu_t, *beta_t;
+    template <class Acc>
+    __device__ void row(int i, int c0, Acc &) const {
+        const size_t o = (size_t)i * ld + c0;
+        const V ri = vld<T>(r + o);
+        const V m = vld<T>(mu_t + c0), bt = vld<T>(beta_t + c0);
+        V pi = vld<T>(p + o);
+        const T di = e0 * ldinv<T>(A, i);
+#pragma unroll
+        for (int v = 0; v < VW; ++v) vel(pi, v) = (mul_rn(di, vel(ri, v)) - vel(m, v)) + vel(bt, v) * vel(pi, v);
+        vst<T>(p + o, pi);
+    }
+    __device__ void fin(int, const double *) const {}
+};
+
 // sums r.z, z, r (and r.r when Init) -> the PCG scalars (DotState)
 template <typename T, bool Init>
 struct OpDotRZ {
@@ -521,6 +599,67 @@ struct OpSubMean64 {
     }
 };
 
+// ---------------------------------------------------------------- elimination transfers
+// Restriction through an elimination level (Level::elim): the next level's
+// right-hand side b'(I) = b(keep_node[I]) + sum of (w_uI / d_u) b(u) over the
+// eliminated neighbours u of keep_node[I], in ascending order of u.
+template <typename T>
+struct OpElimRestrict {
+    using V = typename Vec<T>::V;
+    static constexpr int VW = Vec<T>::W;
+    const int32_t *keep_node, *pull_ptr, *pull_e, *e_node;
+    const T *coef;  // w_um / d_u per slot 2 j + m
+    const T *b;
+    T *bn;
+    int ld;
+    template <class Acc>
+    __device__ void row(int I, int c0, Acc &) const {
+        V s = vld<T>(b + (size_t)__ldg(keep_node + I) * ld + c0);
+        for (int t = __ldg(pull_ptr + I); t < __ldg(pull_ptr + I + 1); ++t) {
+            const int slot = __ldg(pull_e + t);
+            vfma(s, __ldg(coef + slot), vld<T>(b + (size_t)__ldg(e_node + slot / 2) * ld + c0));
+        }
+        vst<T>(bn + (size_t)I * ld + c0, s);
+    }
+    __device__ void fin(int, const double *) const {}
+};
+
+// Back-substitution through an elimination level: a kept node takes its
+// next-level value; eliminated node u = e_node[j] gets
+// x(u) = b(u) / d_u + sum_m (w_um / d_u) x'(nb_m(u)) (dinv already carries the
+// operator's power-of-two scale in the FP32 sweeps).
+template <typename T>
+struct OpElimBack {
+    using V = typename Vec<T>::V;
+    static constexpr int VW = Vec<T>::W;
+    const int32_t *keep_id, *e_nb;
+    const T *coef, *dinv;
+    const T *b, *xn;
+    T *x;
+    int ld;
+    template <class Acc>
+    __device__ void row(int i, int c0, Acc &) const {
+        const int kid = __ldg(keep_id + i);
+        V out;
+        if (kid >= 0) {
+            out = vld<T>(xn + (size_t)kid * ld + c0);
+        } else {
+            const int j = -kid - 1;
+            const T di = __ldg(dinv + j);
+            const V bi = vld<T>(b + (size_t)i * ld + c0);
+#pragma unroll
+            for (int v = 0; v < VW; ++v) vel(out, v) = di * vel(bi, v);
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                const int a = __ldg(e_nb + 2 * j + m);
+                if (a >= 0) vfma(out, __ldg(coef + 2 * j + m), vld<T>(xn + (size_t)a * ld + c0));
+            }
+        }
+        vst<T>(x + (size_t)i * ld + c0, out);
+    }
+    __device__ void fin(int, const double *) const {}
+};
+
 // ---------------------------------------------------------------- plain kernels
 __global__ void k_copy_pad(const double *__restrict__ src, int k, double *__restrict__ dst, int ld, int64_t n) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * ld; t += (int64_t)gridDim.x * blockDim.x) {
@@ -594,8 +733,14 @@ struct Solver {
     const lap_solve_opts_t &o;
     // workspace
     double *b64, *x64;
-    std::vector<Tin *> lb, lx, lt;  // per level: rhs, iterate, scratch
-    Tin *r, *z, *p, *q, *t0;        // finest-level PCG vectors (+ lb[0] = r, lx[0] = z)
+    std::vector<Tin *> lb, lx, lt;  // per cycle level: rhs, iterate, scratch
+    Tin *r, *z, *p, *q, *t0;        // PCG vectors at the top cycle level (+ lb[0] = r, lx[0] = z)
+    // with an elimination level in front: the FP32 residual and correction on G itself
+    Tin *r0 = nullptr, *d0 = nullptr;
+    // Cycle level c is hierarchy level p0 + c: levels lv[0 .. p0-1] are
+    // eliminations, which only the outer refinement passes through.
+    int p0 = 0;
+    const Level &lvl(int c) const { return h->lv[p0 + c]; }
     Tin *chunk_part;
     double *chunk_part64;
     RedBuf rb;
@@ -614,16 +759,17 @@ struct Solver {
     std::vector<uint32_t *> long_cnt;  // per level: this solve's long-row arrival counters
 
     LevelView lv_view(const Level &L) const {
-        LevelView v = (bf16 && &L != &h->lv[0]) ? view_bf16(L) : view(L);
+        LevelView v = (bf16 && &L != &lvl(0)) ? view_bf16(L) : view(L);
         v.long_count = nullptr;
         for (size_t l = 0; l < long_cnt.size(); ++l)
-            if (&h->lv[l] == &L) v.long_count = long_cnt[l];
+            if (&lvl((int)l) == &L) v.long_count = long_cnt[l];
         return v;
     }
 
     Solver(lap_hierarchy *h_, cudaStream_t s_, int k_, int ld_, const lap_solve_opts_t &o_)
         : h(h_), s(s_), ld(ld_), ntiles(ld_ / KT), ntiles64(ld_ / K64), k(k_), o(o_) {
-        nlev = (int)h->lv.size();
+        p0 = h->p0;
+        nlev = (int)h->lv.size() - p0;
         if (o.levels_used > 0) nlev = std::min(nlev, o.levels_used);
         nu_pre = std::max(1, o.nu_pre);
         nu_post = std::max(1, o.nu_post);
@@ -632,7 +778,7 @@ struct Solver {
         w_levels = std::max(0, o.w_levels);
         gamma = o.coarse_scale > 0.0 ? o.coarse_scale : 1.0;
         bf16 = std::is_same<Tin, float>::value && o.precision == LAP_FP32_BF16COARSE_REFINED;
-        hsize = (int)h->lv.size();
+        hsize = (int)h->lv.size() - p0;
         coarse_n = h->coarse_n;
         // a one-level preconditioner is two or three kernels: nothing to gain
         use_graphs = o.graphs != 0 && nlev >= 2 && !stats_detailed();
@@ -669,7 +815,7 @@ struct Solver {
     int plain_grid(int nvb) const { return red_grid(nvb); }
 
     // bytes of one edge weight as the sweeps of level L read it
-    int wbytes(const Level &L) const { return (bf16 && &L != &h->lv[0]) ? 2 : (int)sizeof(Tin); }
+    int wbytes(const Level &L) const { return (bf16 && &L != &lvl(0)) ? 2 : (int)sizeof(Tin); }
     static double vec_bytes(int64_t n, int ld, int nvec, int elem) { return (double)n * ld * elem * nvec; }
     static double mat_bytes(const Level &L, int wb) {
         return (double)L.nnz * (4.0 + wb) + (double)L.n * (4.0 + 2.0 * wb);
@@ -682,8 +828,8 @@ struct Solver {
         constexpr int RPB = kBlock / G;
         const int nvb_short = (L.n + RPB - 1) / RPB;
         const int nvb_long = (L.n_chunks + RPB - 1) / RPB;
-        if (bf16 && &L != &h->lv[0]) {
-            // below the finest level only reduction-free sweeps run (smoothing, residual)
+        if (bf16 && &L != &lvl(0)) {
+            // below the top cycle level only reduction-free sweeps run (smoothing, residual)
             CFC_REQUIRE(NR == 0, LAP_ECUDA, "internal: reduction sweep on a BF16 level");
             if constexpr (NR == 0 && std::is_same<T, float>::value) {
                 const int nvb = nvb_short + nvb_long;
@@ -723,7 +869,7 @@ struct Solver {
     // one smoothing step at level l (cur -> oth, swapped); at level 0 the
     // step may also produce the PCG dot products (dot = 1: update, 2: init)
     void smooth_step(int l, Tin *&cur, Tin *&oth, int t, bool xp_zero, int dot) {
-        const Level &L = h->lv[l];
+        const Level &L = lvl(l);
         const int et = (int)sizeof(Tin);
         const int ti = std::min(t, (int)cheb_c.size() - 1);
         const double bytes = mat_bytes(L, wbytes(L)) + vec_bytes(L.n, ld, xp_zero || cheb_c[ti] == 0.0 ? 3 : 4, et);
@@ -742,11 +888,11 @@ struct Solver {
     }
 
     DotState<Tin> dstate() const {
-        return DotState<Tin>{1.0 / h->lv[0].n, cs.rz, cs.beta, cs.mu, cs.rr0, (Tin *)cs.beta_t, (Tin *)cs.mu_t,
+        return DotState<Tin>{1.0 / lvl(0).n, cs.rz, cs.beta, cs.mu, cs.rr0, (Tin *)cs.beta_t, (Tin *)cs.mu_t,
                              cs.active_in, cs.active_out};
     }
 
-    bool level0_is_dense() const { return nlev == 1 && coarse_n == h->lv[0].n && hsize == 1; }
+    bool level0_is_dense() const { return nlev == 1 && coarse_n == lvl(0).n && hsize == 1; }
 
     // The FP32 sweeps run on 2^-wexp L and on residuals scaled per column by
     // powers of two (exact: FP32 results are those of the unscaled problem
@@ -759,7 +905,7 @@ struct Solver {
     // into the PCG update); dot: the level-0 final step also computes the PCG
     // dot products (1: update, 2: init).  Returns true when it did.
     bool vcycle(int l, bool first_done = false, int dot = 0) {
-        const Level &L = h->lv[l];
+        const Level &L = lvl(l);
         const int et = (int)sizeof(Tin);
         const int wb = wbytes(L);
         const bool coarsest = (l == nlev - 1);
@@ -793,7 +939,7 @@ struct Solver {
         // prolong; a W-cycle does this twice (the same operator twice keeps
         // the preconditioner symmetric); the coarse level's dense solve is
         // exact, so one correction suffices just above it
-        const Level &C = h->lv[l + 1];
+        const Level &C = lvl(l + 1);
         const bool next_dense = (l + 1 == nlev - 1) && coarse_n == C.n && l + 1 == hsize - 1;
         const int ncorr = (cycle == 2 && !next_dense && (w_levels == 0 || l < w_levels)) ? 2 : 1;
         for (int cc = 0; cc < ncorr; ++cc) {
@@ -896,7 +1042,7 @@ struct Solver {
 
     // inner PCG on the finest level: solves L d = r; returns iterations
     int inner_pcg(Tin *d, int max_inner, double inner_tol) {
-        const Level &L0 = h->lv[0];
+        const Level &L0 = lvl(0);
         const int et = (int)sizeof(Tin);
         const int64_t n = L0.n;
         const double vb1 = vec_bytes(n, ld, 1, et);
@@ -906,16 +1052,25 @@ struct Solver {
             rows<Tin, 4>(LAP_KF_BLAS1, n, OpDotRZ<Tin, true>{r, z, ld, dstate()}, 2 * vb1);
         rows<Tin, 0>(LAP_KF_BLAS1, n, OpUpdateP<Tin, true>{z, p, ld, mu_t, beta_t}, 2 * vb1);
         const bool fuse_first = !level0_is_dense();
+        // one level, one smoothing step: the preconditioner is z = e0 D^{-1} r
+        const bool jacobi = fuse_first && nlev == 1 && nu_coarse <= 1;
+        const Tin e0 = (Tin)cheb_e[0];
         const int check = std::max(1, o.check_every);
         int it = 0;
         for (it = 1; it <= max_inner; ++it) {
             rowop<Tin, 1>(LAP_KF_SPMV_FINE, L0,
                           OpSpmvDot<Tin>{lv_view(L0), p, q, ld, cs.rz, cs.alpha, alpha_t, cs.active_in}, chunk_part,
                           mat_bytes(L0, et) + 2 * vb1);
-            rows<Tin, 1>(LAP_KF_BLAS1, n,
-                         OpUpdateXR<Tin>{d, r, p, q, fuse_first ? z : nullptr, lv_view(L0), (Tin)cheb_e[0], ld, alpha_t,
-                                         cs.active_in, cs.rr0, inner_tol * inner_tol},
-                         (fuse_first ? 7 : 6) * vb1);
+            if (jacobi)
+                rows<Tin, 4>(LAP_KF_BLAS1, n,
+                             OpUpdateXRJacobi<Tin>{d, r, p, q, lv_view(L0), e0, ld, alpha_t, cs.active_in, cs.rr0,
+                                                   inner_tol * inner_tol, dstate()},
+                             6 * vb1 + (double)n * et);
+            else
+                rows<Tin, 1>(LAP_KF_BLAS1, n,
+                             OpUpdateXR<Tin>{d, r, p, q, fuse_first ? z : nullptr, lv_view(L0), e0, ld, alpha_t,
+                                             cs.active_in, cs.rr0, inner_tol * inner_tol},
+                             (fuse_first ? 7 : 6) * vb1);
             if (it % check == 0 || it == max_inner) {
                 CFC_CUDA(cudaMemcpyAsync(h_active, cs.active_in, ld * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
                 CFC_CUDA(cudaStreamSynchronize(s));
@@ -924,11 +1079,45 @@ struct Solver {
                 if (na == 0) break;
                 if (it == max_inner || past_trial_deadline()) break;
             }
+            if (jacobi) {
+                rows<Tin, 0>(LAP_KF_BLAS1, n, OpUpdatePJacobi<Tin>{r, p, lv_view(L0), e0, ld, mu_t, beta_t},
+                             3 * vb1 + (double)n * et);
+                continue;
+            }
             if (!precond(fuse_first, 1))
                 rows<Tin, 3>(LAP_KF_BLAS1, n, OpDotRZ<Tin, false>{r, z, ld, dstate()}, 2 * vb1);
             rows<Tin, 0>(LAP_KF_BLAS1, n, OpUpdateP<Tin, false>{z, p, ld, mu_t, beta_t}, 3 * vb1);
         }
         return std::min(it, max_inner);
+    }
+
+    // through the elimination level (p0 == 1): r0 on G -> r on the top cycle
+    // level, and the inner solution dbuf -> d0 on G
+    template <typename T>
+    static const T *coef_of(const Level &E) {
+        if constexpr (std::is_same<T, float>::value) return E.e_c32.get();
+        else return E.e_c64.get();
+    }
+    template <typename T>
+    static const T *dinv_of(const Level &E) {
+        if constexpr (std::is_same<T, float>::value) return E.e_dinv32.get();
+        else return E.e_dinv64.get();
+    }
+    void elim_restrict() {
+        const Level &E = h->lv[0];
+        const int et = (int)sizeof(Tin);
+        rows<Tin, 0>(LAP_KF_BLAS1, lvl(0).n,
+                     OpElimRestrict<Tin>{E.keep_node.get(), E.pull_ptr.get(), E.pull_e.get(), E.e_node.get(),
+                                         coef_of<Tin>(E), r0, r, ld},
+                     vec_bytes(E.n, ld, 1, et) + vec_bytes(lvl(0).n, ld, 1, et));
+    }
+    void elim_back() {
+        const Level &E = h->lv[0];
+        const int et = (int)sizeof(Tin);
+        rows<Tin, 0>(LAP_KF_BLAS1, E.n,
+                     OpElimBack<Tin>{E.keep_id.get(), E.e_nb.get(), coef_of<Tin>(E), dinv_of<Tin>(E), r0, dbuf, d0,
+                                     ld},
+                     vec_bytes(lvl(0).n, ld, 1, et) + vec_bytes(E.n, ld, 1, et) + vec_bytes(E.n_elim, ld, 1, et));
     }
 
     lap_status_t run(const double *B, double *X, lap_solve_info_t *info) {
@@ -941,6 +1130,9 @@ struct Solver {
         const double itol = (o.precision == LAP_FP64) ? std::max(o.tol * 0.5, 1e-15) : o.inner_tol;
         const double pred = std::max(itol, 1e-7) * inv_sqrt_n;
         int32_t *rx0 = kScaled ? cs.rexp[0] : nullptr, *rx1 = kScaled ? cs.rexp[1] : nullptr;
+        // the FP32 residual on G itself: the PCG's right-hand side, or (with an
+        // elimination level in front) the input of the restriction
+        Tin *rfine = p0 ? r0 : r;
         // b64 = B (padded), projected to zero mean; bnorm (direct: B is used in
         // place and its norm comes with the first step below)
         if (!direct) {
@@ -963,11 +1155,11 @@ struct Solver {
             // FP64 residual, written to r in the inner type (x = 0 at the first step: r = b)
             if (outer == 0 && direct) {
                 rowsd<1>(n, OpColNorm64{b64, ld, cs.bnorm, cs.relres, cs.active_out, rx0, rx1, inv_sqrt_n, pred}, v64);
-                rowsd<0>(n, OpCastB<Tin>{b64, r, ld, rx_cur}, v64 + vec_bytes(n, ld, 1, sizeof(Tin)));
+                rowsd<0>(n, OpCastB<Tin>{b64, rfine, ld, rx_cur}, v64 + vec_bytes(n, ld, 1, sizeof(Tin)));
             } else if (outer == 0) {
                 CFC_LAUNCH(LAP_KF_BLAS1, s, 0.0, k_init_cols, (ld + 255) / 256, 256, 0, cs.bnorm, cs.relres,
                            cs.active_out, rx0, rx1, inv_sqrt_n, pred, ld);
-                rowsd<0>(n, OpCastB<Tin>{b64, r, ld, rx_cur}, v64 + vec_bytes(n, ld, 1, sizeof(Tin)));
+                rowsd<0>(n, OpCastB<Tin>{b64, rfine, ld, rx_cur}, v64 + vec_bytes(n, ld, 1, sizeof(Tin)));
             } else {
                 constexpr int RPB = RPB64;
                 const int nvb_short = (L0.n + RPB - 1) / RPB;
@@ -975,20 +1167,23 @@ struct Solver {
                 const int nvb = nvb_short + nvb_long;
                 dim3 grid(red_grid(nvb), ntiles64);
                 using Op = OpResid64<Tin>;
-                Op op{lv_view(L0), x64,   b64, r, ld, cs.bnorm, cs.relres, cs.active_out, o.tol, rx_cur,
+                LevelView v0 = view(L0);
+                v0.long_count = nullptr;  // FP64 sweeps finish long rows from chunk sums: no counters
+                Op op{v0, x64, b64, rfine, ld, cs.bnorm, cs.relres, cs.active_out, o.tol, rx_cur,
                       kScaled ? cs.rexp[(outer + 1) & 1] : nullptr, pred};
                 const double bytes = mat_bytes(L0, 8) + 2 * v64 + vec_bytes(n, ld, 1, sizeof(Tin));
                 if (L0.n_chunks > 0) {
                     CFC_LAUNCH(LAP_KF_RESID64, s, 0.0, (k_chunk_sums<double, K64, Op>), dim3(nvb_long, ntiles64),
-                               kBlock, 0, lv_view(L0), op, chunk_part64, ld);
+                               kBlock, 0, v0, op, chunk_part64, ld);
                     CFC_LAUNCH(LAP_KF_RESID64, s, bytes, (k_rowop<double, K64, 1, Op, kLongPre>),
-                               dim3(red_grid(nvb_short), ntiles64), kBlock, 0, lv_view(L0), op, nvb_short, nvb_short,
+                               dim3(red_grid(nvb_short), ntiles64), kBlock, 0, v0, op, nvb_short, nvb_short,
                                chunk_part64, ld, rb);
                 } else {
-                    CFC_LAUNCH(LAP_KF_RESID64, s, bytes, (k_rowop<double, K64, 1, Op>), grid, kBlock, 0, lv_view(L0), op,
+                    CFC_LAUNCH(LAP_KF_RESID64, s, bytes, (k_rowop<double, K64, 1, Op>), grid, kBlock, 0, v0, op,
                                nvb_short, nvb, chunk_part64, ld, rb);
                 }
             }
+            if (p0) elim_restrict();
             CFC_CUDA(cudaMemcpyAsync(h_active, cs.active_out, ld * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
             CFC_CUDA(cudaMemcpyAsync(hrel.data(), cs.relres, ld * sizeof(double), cudaMemcpyDeviceToHost, s));
             if (outer == 0)
@@ -1016,7 +1211,8 @@ struct Solver {
             if (!finite || outer >= o.max_outer || past_trial_deadline()) break;
             // inner solve of L d = r; d lives in lt-independent buffer `dbuf`
             inner_total += inner_pcg(dbuf, o.max_inner, itol);
-            rowsd<0>(n, OpAddCorr<Tin>{x64, dbuf, ld, cs.active_out, rx_cur, op_wexp()},
+            if (p0) elim_back();
+            rowsd<0>(n, OpAddCorr<Tin>{x64, p0 ? d0 : dbuf, ld, cs.active_out, rx_cur, op_wexp()},
                      2 * v64 + vec_bytes(n, ld, 1, sizeof(Tin)));
         }
         // zero-mean result, copied out unpadded (direct: left as is)
@@ -1064,33 +1260,38 @@ lap_status_t run_solver(lap_hierarchy *h, int32_t k, const double *B, double *X,
     CFC_REQUIRE(ntiles <= kMaxTiles, LAP_EBUDGET, "too many column tiles");
     Solver<Tin, KT> S(h, s, k, ld, o);
     const int nlev = S.nlev;
-    // workspace layout
-    const int64_t n0 = h->lv[0].n;
-    int64_t max_chunks = 0;
-    for (int l = 0; l < nlev; ++l) max_chunks = std::max<int64_t>(max_chunks, h->lv[l].n_chunks);
+    // workspace layout: G itself (level 0: FP64 residual and, with an
+    // elimination level, the FP32 residual and correction), then the cycle
+    // levels p0 .. p0 + nlev - 1
+    const int p0 = S.p0;
+    const int64_t n0 = h->lv[0].n, ntop = h->lv[p0].n;
+    int64_t max_chunks = h->lv[0].n_chunks;
+    for (int l = 0; l < nlev; ++l) max_chunks = std::max<int64_t>(max_chunks, h->lv[p0 + l].n_chunks);
     std::vector<size_t> sizes;
     int64_t n_long_total = 0;
-    for (int l = 0; l < nlev; ++l) n_long_total += h->lv[l].n_long;
+    for (int l = 0; l < nlev; ++l) n_long_total += h->lv[p0 + l].n_long;
     // arrival counters first: reduction tickets, then the long-row counters
     // of every level; zero at allocation, and every launch leaves them zero
     const size_t counter_bytes = align_up(kMaxTiles * 4 + kMaxTiles * kMaxTeams * 4 + n_long_total * kMaxTiles * 4);
     sizes.push_back(counter_bytes);
     sizes.push_back(direct ? 0 : align_up(n0 * ld * 8));  // b64 (direct: the caller's block)
     sizes.push_back(direct ? 0 : align_up(n0 * ld * 8));  // x64 (direct: the caller's block)
-    sizes.push_back(align_up(n0 * ld * sizeof(Tin)));  // r
-    sizes.push_back(align_up(n0 * ld * sizeof(Tin)));  // z
-    sizes.push_back(align_up(n0 * ld * sizeof(Tin)));  // p
-    sizes.push_back(align_up(n0 * ld * sizeof(Tin)));  // q
-    sizes.push_back(align_up(n0 * ld * sizeof(Tin)));  // d
-    sizes.push_back(align_up(n0 * ld * sizeof(Tin)));  // t0
+    sizes.push_back(align_up(ntop * ld * sizeof(Tin)));  // r
+    sizes.push_back(align_up(ntop * ld * sizeof(Tin)));  // z
+    sizes.push_back(align_up(ntop * ld * sizeof(Tin)));  // p
+    sizes.push_back(align_up(ntop * ld * sizeof(Tin)));  // q
+    sizes.push_back(align_up(ntop * ld * sizeof(Tin)));  // d
+    sizes.push_back(align_up(ntop * ld * sizeof(Tin)));  // t0
+    sizes.push_back(p0 ? align_up(n0 * ld * sizeof(Tin)) : 0);  // r0 (FP32 residual on G)
+    sizes.push_back(p0 ? align_up(n0 * ld * sizeof(Tin)) : 0);  // d0 (correction on G)
     for (int l = 1; l < nlev; ++l)
-        for (int v = 0; v < 3; ++v) sizes.push_back(align_up((size_t)h->lv[l].n * ld * sizeof(Tin)));
+        for (int v = 0; v < 3; ++v) sizes.push_back(align_up((size_t)h->lv[p0 + l].n * ld * sizeof(Tin)));
     sizes.push_back(align_up(std::max<int64_t>(max_chunks, 1) * ld * 8));  // chunk partials (FP64 size)
     // blocks of any launch: at most ceil(n/8) row blocks (8 = fewest rows per
     // block) plus one block per long row or one per 8 chunks
     int64_t max_blocks = 1;
-    for (int l = 0; l < nlev; ++l) {
-        const Level &Ll = h->lv[l];
+    for (int l = -1; l < nlev; ++l) {
+        const Level &Ll = l < 0 ? h->lv[0] : h->lv[p0 + l];
         max_blocks = std::max<int64_t>(
             max_blocks, (Ll.n + 7) / 8 + std::max<int64_t>(Ll.n_long, (Ll.n_chunks + 7) / 8) + 1);
     }
@@ -1138,7 +1339,7 @@ lap_status_t run_solver(lap_hierarchy *h, int32_t k, const double *B, double *X,
         S.long_cnt.assign(nlev, nullptr);
         for (int l = 0; l < nlev; ++l) {
             S.long_cnt[l] = c;
-            c += (size_t)h->lv[l].n_long * kMaxTiles;
+            c += (size_t)h->lv[p0 + l].n_long * kMaxTiles;
         }
     }
     S.b64 = (double *)take(idx++);
@@ -1154,6 +1355,10 @@ lap_status_t run_solver(lap_hierarchy *h, int32_t k, const double *B, double *X,
     S.q = (Tin *)take(idx++);
     S.dbuf = (Tin *)take(idx++);
     S.t0 = (Tin *)take(idx++);
+    S.r0 = p0 ? (Tin *)take(idx) : nullptr;
+    ++idx;
+    S.d0 = p0 ? (Tin *)take(idx) : nullptr;
+    ++idx;
     Tin *t0 = S.t0;
     S.lb.assign(nlev, nullptr);
     S.lx.assign(nlev, nullptr);
@@ -1231,19 +1436,25 @@ lap_status_t dispatch(lap_hierarchy *h, int32_t k, const double *B, double *X, c
     }
 }
 
-// Autotuned multigrid depth, per graph size and solve configuration: the
-// first solve with a new key times complete solves with 1, 2, ... levels and
-// keeps the fastest that converged (a one-time cost, like a library picking
-// kernels by timing them).
+// Autotuned configuration, per graph and solve configuration: the first
+// solve with a new key times complete solves (depths, smoother degrees,
+// cycles, coarse scales, column tiles) and keeps the fastest that converged
+// (a one-time cost, like a library picking kernels by timing them).  The key
+// holds the graph's fingerprint (its CSR entries and weights), so two graphs
+// of equal size but different structure get their own choices.  The table
+// can be written to and read from a JSON file (lap_tune_save / lap_tune_load,
+// or the file named by LAP_TUNE_CACHE), so that a later process repeats a
+// choice, and with it the bits of every solve, instead of timing again.
 struct TuneKey {
+    uint64_t fp;
     int64_t n, nnz;
     int k, precision, kt, smoother, nu_pre, nu_post, nu_coarse, cycle;
     double scale;
     int w_levels;
     bool operator<(const TuneKey &o) const {
-        return std::tie(n, nnz, k, precision, kt, smoother, nu_pre, nu_post, nu_coarse, cycle, scale, w_levels) <
-               std::tie(o.n, o.nnz, o.k, o.precision, o.kt, o.smoother, o.nu_pre, o.nu_post, o.nu_coarse, o.cycle,
-                        o.scale, o.w_levels);
+        return std::tie(fp, n, nnz, k, precision, kt, smoother, nu_pre, nu_post, nu_coarse, cycle, scale, w_levels) <
+               std::tie(o.fp, o.n, o.nnz, o.k, o.precision, o.kt, o.smoother, o.nu_pre, o.nu_post, o.nu_coarse,
+                        o.cycle, o.scale, o.w_levels);
     }
 };
 struct TuneChoice {
@@ -1253,6 +1464,80 @@ struct TuneChoice {
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneChoice> g_tune;
+
+// one entry per line: {"key": [fp, n, nnz, k, precision, kt, smoother, nu_pre,
+// nu_post, nu_coarse, cycle, scale, w_levels], "choice": [kt, levels,
+// nu_coarse, cycle, scale, w_levels]}; fp in hexadecimal, doubles with 17
+// significant digits (exact round trip).  Caller holds g_tune_mu.
+void tune_write_locked(const char *path) {
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = std::fopen(tmp.c_str(), "w");
+    CFC_REQUIRE(f, LAP_EINVAL, std::string("cannot write ") + tmp);
+    std::fprintf(f, "{\"format\": \"lap_tune_v1\", \"entries\": [\n");
+    size_t i = 0;
+    for (const auto &e : g_tune) {
+        const TuneKey &k = e.first;
+        const TuneChoice &c = e.second;
+        std::fprintf(f,
+                     "{\"key\": [\"%016llx\", %lld, %lld, %d, %d, %d, %d, %d, %d, %d, %d, %.17g, %d], "
+                     "\"choice\": [%d, %d, %d, %d, %.17g, %d]}%s\n",
+                     (unsigned long long)k.fp, (long long)k.n, (long long)k.nnz, k.k, k.precision, k.kt, k.smoother,
+                     k.nu_pre, k.nu_post, k.nu_coarse, k.cycle, k.scale, k.w_levels, c.kt, c.levels, c.nu_coarse,
+                     c.cycle, c.scale, c.w_levels, ++i < g_tune.size() ? "," : "");
+    }
+    std::fprintf(f, "]}\n");
+    const bool ok = std::fclose(f) == 0;
+    CFC_REQUIRE(ok && std::rename(tmp.c_str(), path) == 0, LAP_EINVAL, std::string("cannot write ") + path);
+}
+
+// reads the entries written by tune_write_locked; returns how many it added
+int tune_read_locked(const char *path) {
+    FILE *f = std::fopen(path, "r");
+    CFC_REQUIRE(f, LAP_EINVAL, std::string("cannot read ") + path);
+    char line[1024];
+    int added = 0;
+    while (std::fgets(line, sizeof line, f)) {
+        const char *p = std::strstr(line, "\"key\": [\"");
+        if (!p) continue;
+        unsigned long long fp = 0;
+        long long n = 0, nnz = 0;
+        TuneKey k{};
+        TuneChoice c{};
+        const int got = std::sscanf(p, "\"key\": [\"%llx\", %lld, %lld, %d, %d, %d, %d, %d, %d, %d, %d, %lf, %d], "
+                                       "\"choice\": [%d, %d, %d, %d, %lf, %d]",
+                                    &fp, &n, &nnz, &k.k, &k.precision, &k.kt, &k.smoother, &k.nu_pre, &k.nu_post,
+                                    &k.nu_coarse, &k.cycle, &k.scale, &k.w_levels, &c.kt, &c.levels, &c.nu_coarse,
+                                    &c.cycle, &c.scale, &c.w_levels);
+        if (got != 19) {
+            std::fclose(f);
+            throw Error{LAP_EINVAL, std::string("malformed tuning entry in ") + path};
+        }
+        k.fp = fp;
+        k.n = n;
+        k.nnz = nnz;
+        added += g_tune.emplace(k, c).second ? 1 : 0;
+    }
+    std::fclose(f);
+    return added;
+}
+
+// LAP_TUNE_CACHE: read once per process before the first tuning; written
+// after every new choice
+const char *tune_cache_path() {
+    static const char *p = std::getenv("LAP_TUNE_CACHE");
+    return (p && *p) ? p : nullptr;
+}
+void tune_cache_load_once_locked() {
+    static bool done = false;
+    if (done) return;
+    done = true;
+    const char *p = tune_cache_path();
+    if (!p) return;
+    if (FILE *f = std::fopen(p, "r")) {
+        std::fclose(f);
+        tune_read_locked(p);
+    }
+}
 
 }  // namespace
 
@@ -1279,8 +1564,8 @@ namespace {
 template <class PrepareBf16>
 int tune(lap_hierarchy *h, int32_t k, const double *B, double *X, lap_solve_opts_t &o, cudaStream_t s,
          lap_solve_info_t *info, int kt, bool direct, PrepareBf16 &&prepare_bf16) {
-    const TuneKey key{h->lv[0].n, h->lv[0].nnz,  k,         o.precision, o.k_tile,
-                      o.smoother, o.nu_pre,      o.nu_post, o.nu_coarse, o.cycle, o.coarse_scale, o.w_levels};
+    const TuneKey key{h->fingerprint, h->lv[0].n, h->lv[0].nnz, k,         o.precision, o.k_tile,
+                      o.smoother,     o.nu_pre,   o.nu_post,    o.nu_coarse, o.cycle, o.coarse_scale, o.w_levels};
     auto apply = [&](const TuneChoice &c, lap_solve_opts_t &oo) {
         oo.levels_used = c.levels;
         oo.nu_coarse = c.nu_coarse;
@@ -1290,6 +1575,7 @@ int tune(lap_hierarchy *h, int32_t k, const double *B, double *X, lap_solve_opts
     };
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_cache_load_once_locked();
         auto it = g_tune.find(key);
         if (it != g_tune.end()) {
             apply(it->second, o);
@@ -1298,7 +1584,7 @@ int tune(lap_hierarchy *h, int32_t k, const double *B, double *X, lap_solve_opts
         }
     }
     grow_levels(*h, 0, s);
-    const int L = (int)h->lv.size();
+    const int L = (int)h->lv.size() - h->p0;  // levels of the cycle
     prepare_bf16(L);
     const int nc_default = o.nu_coarse > 0 ? o.nu_coarse : std::max(std::max(1, o.nu_pre), 4);
     const int cyc_default = o.cycle > 0 ? o.cycle : 1;
@@ -1341,7 +1627,7 @@ int tune(lap_hierarchy *h, int32_t k, const double *B, double *X, lap_solve_opts
         float ms = 0.f;
         CFC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
         double build = 0.0;
-        for (int l = 1; l < c.levels && l < (int)h->level_ms.size(); ++l) build += h->level_ms[l];
+        for (int l = 1; l < c.levels && h->p0 + l < (int)h->level_ms.size(); ++l) build += h->level_ms[h->p0 + l];
         const float cost = ms + (float)build;
         if (verbose)
             std::fprintf(stderr,
@@ -1423,6 +1709,7 @@ int tune(lap_hierarchy *h, int32_t k, const double *B, double *X, lap_solve_opts
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune[key] = choice;
+        if (const char *p = tune_cache_path()) tune_write_locked(p);
     }
     apply(choice, o);
     return choice.kt;
@@ -1450,7 +1737,7 @@ lap_status_t solve_impl(lap_hierarchy *h, int32_t k, const double *B, double *X,
         int bf16_made = 0;
         auto prepare_bf16 = [&](int upto) {
             if (o.precision != LAP_FP32_BF16COARSE_REFINED) return;
-            for (int l = 1; l < upto && l < (int)h->lv.size(); ++l)
+            for (int l = h->p0 + 1; l < h->p0 + upto && l < (int)h->lv.size(); ++l)
                 if (!h->lv[l].wbf.get()) {
                     ensure_bf16(h->lv[l], h->wexp, s);
                     ++bf16_made;
@@ -1464,7 +1751,7 @@ lap_status_t solve_impl(lap_hierarchy *h, int32_t k, const double *B, double *X,
         } else {
             kt_run = tune(h, k, B, X, o, s, info, kt, direct, prepare_bf16);
         }
-        prepare_bf16(o.levels_used > 0 ? o.levels_used : (int)h->lv.size());
+        prepare_bf16(o.levels_used > 0 ? o.levels_used : (int)h->lv.size() - h->p0);
         if (h->lv.size() != levels_before || bf16_made > 0) {
             // solves on other streams wait for what this call built
             if (!h->grown) CFC_CUDA(cudaEventCreateWithFlags(&h->grown, cudaEventDisableTiming));
@@ -1478,6 +1765,26 @@ lap_status_t solve_impl(lap_hierarchy *h, int32_t k, const double *B, double *X,
 }
 
 }  // namespace
+
+lap_status_t tune_save(const char *path) {
+    CFC_REQUIRE(path && *path, LAP_EINVAL, "path must not be NULL or empty");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_write_locked(path);
+    return LAP_OK;
+}
+
+lap_status_t tune_load(const char *path, int64_t *added) {
+    CFC_REQUIRE(path && *path, LAP_EINVAL, "path must not be NULL or empty");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const int a = tune_read_locked(path);
+    if (added) *added = a;
+    return LAP_OK;
+}
+
+int64_t tune_entries() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return (int64_t)g_tune.size();
+}
 
 lap_status_t solve_multi(lap_hierarchy *h, int32_t k, const double *B, double *X, const lap_solve_opts_t &o,
                          cudaStream_t s, lap_solve_info_t *info) {

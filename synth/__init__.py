@@ -18,6 +18,8 @@ All random draws use ``numpy.random.Generator(PCG64(seed))``.
 """
 from .graphs import (
     grid2d,
+    torus2d,
+    random_regular,
     barabasi_albert,
     rmat,
     path_graph,
@@ -32,6 +34,8 @@ from .graphs import (
 
 __all__ = [
     "grid2d",
+    "torus2d",
+    "random_regular",
     "barabasi_albert",
     "rmat",
     "path_graph",

@@ -45,6 +45,42 @@ def grid2d(a: int, b: int | None = None):
     return a * b, src, dst, None
 
 
+def torus2d(a: int):
+    """a x a 4-neighbour grid with wrap-around edges (every degree 4);
+    node (r, c) has id r*a + c.  m = 2 a^2 (a >= 3)."""
+    ids = np.arange(a * a, dtype=np.int64).reshape(a, a)
+    src = np.concatenate([ids.ravel(), ids.ravel()]).astype(np.int32)
+    dst = np.concatenate([np.roll(ids, -1, axis=1).ravel(), np.roll(ids, -1, axis=0).ravel()]).astype(np.int32)
+    return a * a, src, dst, None
+
+
+def random_regular(n: int, d: int, seed: int):
+    """Uniform random d-regular simple connected graph by the configuration
+    model: the n*d edge stubs are paired by a random permutation, and the
+    pairing is drawn again until it has no self-loop, no repeated pair and
+    one component.  m = n d / 2 (n d even)."""
+    rng = _rng(seed)
+    stubs = np.repeat(np.arange(n, dtype=np.int64), d)
+    while True:
+        p = rng.permutation(stubs).reshape(-1, 2)
+        lo, hi = p.min(axis=1), p.max(axis=1)
+        if np.any(lo == hi) or np.unique(lo * n + hi).size != lo.size:
+            continue
+        parent = np.arange(n)  # connectivity by union-find over the pairs
+
+        def find(x):
+            while parent[x] != x:
+                parent[x] = parent[parent[x]]
+                x = parent[x]
+            return x
+        for u, v in zip(lo.tolist(), hi.tolist()):
+            ru, rv = find(u), find(v)
+            if ru != rv:
+                parent[ru] = rv
+        if len({find(x) for x in range(n)}) == 1:
+            return n, lo.astype(np.int32), hi.astype(np.int32), None
+
+
 def path_graph(n: int):
     s = np.arange(n - 1, dtype=np.int32)
     return n, s, s + 1, None

@@ -45,7 +45,10 @@ def _rel(a, b):
 PRECISIONS = {"fp32": dict(precision=1), "fp64": dict(precision=0),
               "bf16coarse": dict(precision=2, levels_used=-1),
               "fp32_all_levels": dict(precision=1, levels_used=-1),
-              "fp64_all_levels": dict(precision=0, levels_used=-1)}
+              "fp64_all_levels": dict(precision=0, levels_used=-1),
+              # one level, one smoothing step: Jacobi-PCG, the fused path R-MAT takes
+              "fp32_jacobi": dict(precision=1, levels_used=1, nu_coarse=1),
+              "fp64_jacobi": dict(precision=0, levels_used=1, nu_coarse=1)}
 
 
 @pytest.fixture(scope="module")
@@ -179,3 +182,46 @@ def test_weights_spanning_80_orders_never_ok_with_nonfinite(P, precision):
     else:
         assert info["status"] == P.LAP_ENOCONV
         assert not (info["max_rel_residual"] <= 1e-8)
+
+
+# ------------------------------------------------------------------ low-degree elimination (Sec. 3.1, LAMG)
+@pytest.mark.parametrize("gen", [lambda: synth.path_graph(300), lambda: synth.random_tree(400, seed=3)])
+def test_elimination_then_dense_solve_is_exact(P, gen):
+    # on a path or a tree, eliminating the nodes with one or two neighbours
+    # leaves a graph small enough for the dense solve: elimination, dense
+    # solve and back-substitution are then an exact preconditioner, so FP64
+    # PCG takes at most two iterations in its one refinement step
+    import torch
+    n, s, d, _ = gen()
+    w = synth.uniform_weights(s.size, seed=9)
+    h = P.lap_build_hierarchy(n, s, d, w, P.lap_default_hier_opts(coarse_max=256))
+    info = P.lap_hierarchy_info(h)
+    assert info["elim_levels"] == 1 and info["levels"] == 2
+    assert info["level_n"][1] <= 256 and info["coarse_n"] == info["level_n"][1]
+    B = np.random.default_rng(1).standard_normal((n, 16))
+    X = torch.empty((n, 16), dtype=torch.float64, device="cuda")
+    # convergence read after every inner iteration, so the count is exact
+    si = P.lap_solve_multi(h, torch.tensor(B, device="cuda"), X, P.lap_default_solve_opts(precision=0, check_every=1))
+    assert si["outer_iters"] == 1 and si["inner_iters"] <= 2 and si["max_rel_residual"] < 1e-12
+    _certify(canonical_graph(n, s, d, w), B, X.cpu().numpy(), tol=1e-12)
+
+
+def test_elimination_applies_where_it_removes_nodes(P, rmat14):
+    n, s, d, w, g = rmat14
+    on = P.lap_hierarchy_info(P.lap_build_hierarchy(n, s, d, w))
+    assert on["elim_levels"] == 1 and on["level_n"][1] < 0.8 * n
+    off = P.lap_hierarchy_info(P.lap_build_hierarchy(n, s, d, w, P.lap_default_hier_opts(eliminate=0)))
+    assert off["elim_levels"] == 0
+    for gen in (lambda: synth.grid2d(40), lambda: synth.barabasi_albert(3000, 5, seed=2)):
+        assert P.lap_hierarchy_info(P.lap_build_hierarchy(*gen()[:3]))["elim_levels"] == 0
+
+
+@pytest.mark.parametrize("eliminate", [0, 1])
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "fp32_all_levels"])
+def test_rmat_farness_with_and_without_elimination(P, rmat14, eliminate, precision):
+    n, s, d, w, g = rmat14
+    h = P.lap_build_hierarchy(n, s, d, w, P.lap_default_hier_opts(eliminate=eliminate))
+    nodes = np.array([3, n // 3], np.int32)
+    f = P.cfc_farness_jl(h, 48, 8, nodes, opts=P.lap_default_solve_opts(**PRECISIONS[precision]))
+    fo = jl.jl_farness(g, 48, 8, nodes.tolist(), solver="cg", tol=1e-12)
+    assert _rel(f, fo) <= FARNESS_RTOL

@@ -41,3 +41,14 @@ def test_rmat_stream_does_not_depend_on_the_process_count(monkeypatch):
     assert not (c[0] == a[0] and np.array_equal(c[1], a[1]))
     key = a[1].astype(np.int64) * a[0] + a[2]
     assert np.all(np.diff(key) > 0)  # sorted, no duplicate pairs
+
+
+def test_torus_and_random_regular_have_equal_sizes_and_degrees():
+    n1, s1, d1, _ = synth.torus2d(32)
+    n2, s2, d2, _ = synth.random_regular(1024, 4, seed=7)
+    assert n1 == n2 == 1024 and s1.size == s2.size == 2048
+    for n, s, d in ((n1, s1, d1), (n2, s2, d2)):
+        deg = np.bincount(np.concatenate([s, d]), minlength=n)
+        assert np.all(deg == 4)
+        key = np.minimum(s, d).astype(np.int64) * n + np.maximum(s, d)
+        assert np.unique(key).size == key.size and np.all(s != d)  # simple
