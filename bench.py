@@ -26,8 +26,11 @@ grid4096_jl64 (the same step), serve_mix (16 resident graphs, Poisson
 arrivals) and accuracy (both estimators against the exact farness).
 
 --impl reference times the CPU FP64 oracle on the same workload and metric.
-Run with torchrun for N > 1 GPUs: every rank solves its own independent
-instance (weak scaling, no collective on the data path).
+Run with torchrun for N > 1 GPUs: the step becomes one JL query of 64 * N
+rows split over the GPUs (each rank builds the graph's hierarchy and solves
+its own 64 rows, cfc_farness_jl_rows), and one NCCL all-reduce adds the q
+partial farness sums, the split's only exchange (weak scaling; the line's
+split_check compares the result with the same query on one GPU).
 """
 from __future__ import annotations
 
@@ -622,9 +625,25 @@ def gpu_workload(P, torch, name, args, steps, warmup, local, world, clk=None, fu
         sopts.levels_used = args.levels
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
 
+    rank = int(os.environ.get("RANK", "0"))
+
+    def farness(h, nodes_arg, out):
+        """One GPU: the whole query.  N GPUs: one query of k * N rows, this
+        rank's k rows (cfc_farness_jl_rows), then one all-reduce of the q
+        partial sums on the device (the split's only exchange)."""
+        if world == 1:
+            P.cfc_farness_jl(h, k, wl["jl_seed"], nodes_arg, opts=sopts, out=out, stream=sp)
+            return
+        import torch.distributed as dist
+        P.cfc_farness_jl_rows(h, k * world, k * rank, k, wl["jl_seed"], nodes_arg, opts=sopts, out=out, stream=sp)
+        t = out if out.is_cuda else out.to(dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        if t is not out:
+            out.copy_(t.cpu())
+
     def step_device():
         h = P.lap_build_hierarchy(n, src_d, dst_d, w_d, stream=sp)
-        P.cfc_farness_jl(h, k, wl["jl_seed"], nodes_d, opts=sopts, out=far_d, stream=sp)
+        farness(h, nodes_d, far_d)
         h.destroy()
 
     # host-buffer variant: pinned host inputs, result read back to the host
@@ -635,7 +654,7 @@ def gpu_workload(P, torch, name, args, steps, warmup, local, world, clk=None, fu
 
     def step_host():
         h = P.lap_build_hierarchy(n, src_h, dst_h, w_h, stream=sp)
-        P.cfc_farness_jl(h, k, wl["jl_seed"], nodes, opts=sopts, out=far_h, stream=sp)
+        farness(h, nodes, far_h)
         h.destroy()
 
     def timed(step, K):
@@ -669,8 +688,19 @@ def gpu_workload(P, torch, name, args, steps, warmup, local, world, clk=None, fu
     torch.cuda.profiler.stop()
     P.lap_stats_set_log(False)
     stats = P.lap_stats_read()
+    if world > 1:
+        # the distributed result against the same query of k * N rows on this GPU alone
+        with torch.cuda.stream(stream):
+            step_device()
+            h = P.lap_build_hierarchy(n, src_d, dst_d, w_d, stream=sp)
+            one = P.cfc_farness_jl(h, k * world, wl["jl_seed"], nodes, opts=sopts, stream=sp)
+            h.destroy()
+        split_err = float(np.max(np.abs(far_d.cpu().numpy() - one) / np.abs(one)))
     out = {"wl": wl, "wl_name": name, "n": n, "m": int(s.size), "k": k, "dtype": dtype, "prec_text": prec_text, "sopts": sopts,
-           "graph": (n, src_d, dst_d, w_d), "stream": stream, "dev": dev, "launches": stats["launches_total"]}
+           "graph": (n, src_d, dst_d, w_d), "stream": stream, "dev": dev, "launches": stats["launches_total"],
+           "split_check": ({"quantity": f"farness of node(s) {wl['nodes']} from {world} row shards + all-reduce "
+                                        f"against the same {k * world}-row query on one GPU",
+                            "max_rel_err": split_err, "bound": 1e-6} if world > 1 else None)}
     if full and args.launch_log and int(os.environ.get("RANK", "0")) == 0:
         with open(args.launch_log, "w") as fh:
             json.dump({"workload": name, "steps": steps, "source_digest": kernel_source_digest(),
@@ -886,7 +916,9 @@ def main():
                        "solve": {key: sinfo[key] for key in ("outer_iters", "inner_iters", "max_rel_residual",
                                                               "k_tile", "levels_used", "nu_coarse", "cycle",
                                                               "coarse_scale", "w_levels")},
-                       "parallelism": f"{world} independent replicas" if world > 1 else "one GPU"},
+                       "parallelism": (f"one JL query of {k * world} rows split over {world} GPUs ({k} rows each, "
+                                       f"replicated graph), one NCCL all-reduce of the q partial sums"
+                                       if world > 1 else "one GPU")},
             "e2e": res["e2e"],
             "gpu_launches": res["launches"],
             "roofline": roof,
@@ -895,6 +927,8 @@ def main():
             "solve_roofline_ideal": ideal,
             "clocks": res["clocks"],
         }
+        if res.get("split_check"):
+            line["split_check"] = res["split_check"]
         if world == 1 and not args.no_compare:
             if large:
                 # the 100k-node BA configuration: its own rate and the FP64 comparison

@@ -80,7 +80,9 @@ enum {
 enum { LAP_SMOOTH_JACOBI = 0, LAP_SMOOTH_CHEBYSHEV = 1 };
 
 typedef struct {
-    int32_t coarse_max;   /* stop coarsening at n_l <= coarse_max (default 64, at most 256) */
+    int32_t coarse_max;   /* stop coarsening at n_l <= coarse_max (default 1024, at most 2048);
+                             the coarsest level (at most 2048 nodes) is solved with a dense
+                             inverse, FP64 in LAP_FP64 and an FP32 copy in the FP32 modes */
     int32_t max_levels;   /* cap on levels incl. the finest (default 24); 1 = no coarsening */
     int32_t agg_passes;   /* pairwise-matching passes per level (default 2: aggregates of ~4) */
     int32_t match_rounds; /* handshake rounds per pass (default 4) */
@@ -444,6 +446,9 @@ lap_status_t lap_stats_read_log(int32_t *families, int64_t capacity, int64_t *co
  * device memory fits the HBM budget next to the resident graphs and the
  * requests in flight, so requests that arrive while others run are admitted
  * while those are still on the GPU and their solves overlap on the device.
+ * A slot that takes the head of the queue also takes the queued requests on
+ * the same graph that fit (batch_columns) and solves their columns as one
+ * block.
  *
  * A graph's hierarchy is built completely when it is added, and the solver
  * configuration for its requests is autotuned once then and pinned, so a
@@ -467,6 +472,13 @@ typedef struct {
                                 charged to the budget); requests with n_pivots = 0 then solve
                                 only their q nodes' columns against it.  0 (default): none */
     uint64_t pivot_seed;
+    int32_t batch_columns;  /* continuous batching: when a slot takes the head of the queue it
+                               also takes the queued requests on the same graph and of the same
+                               kind (drawn pivots, or the resident set) that fit, and solves all
+                               their columns as one block, up to this many columns (default
+                               1024; at most 4096 and 64 tiles of the graph's pinned tile
+                               width); 1: one request per solve.  A request's result is the
+                               same alone and in a batch (columns are independent systems) */
 } cfc_server_opts_t;
 
 typedef struct {
@@ -485,6 +497,7 @@ typedef struct {
     double queries_per_s;   /* completed requests / (last completion - first submission) */
     double rhs_per_s;       /* their column solves per second over the same span */
     int64_t graph_bytes, budget_bytes, peak_in_flight_bytes;
+    int32_t max_batch;      /* most requests solved together in one block */
 } cfc_server_stats_t;
 
 void cfc_server_default_opts(cfc_server_opts_t *o);

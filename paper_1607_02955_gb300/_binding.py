@@ -64,7 +64,7 @@ class Stats(C.Structure):
 
 class ServerOpts(C.Structure):
     _fields_ = [("slots", C.c_int32), ("hbm_budget", C.c_int64), ("solve", SolveOpts),
-                ("resident_pivots", C.c_int32), ("pivot_seed", C.c_uint64)]
+                ("resident_pivots", C.c_int32), ("pivot_seed", C.c_uint64), ("batch_columns", C.c_int32)]
 
 
 class RequestInfo(C.Structure):
@@ -78,7 +78,7 @@ class ServerStats(C.Structure):
                 ("in_flight", C.c_int64), ("max_in_flight", C.c_int32), ("p50_ms", C.c_double),
                 ("p99_ms", C.c_double), ("mean_ms", C.c_double), ("max_ms", C.c_double),
                 ("queries_per_s", C.c_double), ("rhs_per_s", C.c_double), ("graph_bytes", C.c_int64),
-                ("budget_bytes", C.c_int64), ("peak_in_flight_bytes", C.c_int64)]
+                ("budget_bytes", C.c_int64), ("peak_in_flight_bytes", C.c_int64), ("max_batch", C.c_int32)]
 
 
 class LapError(RuntimeError):

@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstring>
 
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
 #include "internal.h"
@@ -373,6 +374,11 @@ __global__ void k_fill_chunks(const int32_t *__restrict__ rowptr, const int32_t 
     }
 }
 
+// FP32 copy of 2^e times an FP64 array (the scaled coarse inverse)
+__global__ void k_scaled_f32(const double *__restrict__ src, int64_t count, int e, float *__restrict__ dst) {
+    GRID_LOOP(t, count) dst[t] = (float)ldexp(src[t], e);
+}
+
 // dense M = L_c + J/n_c
 __global__ void k_fill(double *__restrict__ M, int64_t count, double v) {
     GRID_LOOP(t, count) M[t] = v;
@@ -419,28 +425,48 @@ __global__ void __launch_bounds__(1024) k_gj_smem(double *__restrict__ A, int n,
     for (int t = threadIdx.x; t < n * n; t += blockDim.x) A[t] = a[t];
 }
 
-// global-memory Gauss-Jordan: two launches per pivot
-__global__ void k_gj_pivot(const double *__restrict__ A, int n, int k, double *__restrict__ rowk,
-                           double *__restrict__ colk, int *__restrict__ flag) {
-    const double akk = A[(int64_t)k * n + k];
-    const double piv = akk > 0.0 ? 1.0 / akk : 0.0;
-    if (!(akk > 0.0) && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(flag, 1);
-    GRID_LOOP(j, n) {
-        rowk[j] = (j == k ? 1.0 : A[(int64_t)k * n + j]) * piv;
-        colk[j] = (j == k) ? 0.0 : A[(int64_t)j * n + k];
+// Gauss-Jordan in global memory in one cooperative launch, one grid barrier
+// per pivot.  Step k scales the pivot row by 1/a_kk and eliminates column k
+// from every other row (as the shared-memory version does); the threads that
+// update row k+1 and column k+1 also
+// write them to the other half of the double-buffered pivot row and column,
+// so the next step needs no separate pivot phase.  Every thread reads the
+// same pivot, so a non-positive one makes them all return together.
+__global__ void __launch_bounds__(256) k_gj_coop(double *__restrict__ A, int n, double *__restrict__ rows,
+                                                 double *__restrict__ cols, int *__restrict__ flag) {
+    namespace cg = cooperative_groups;
+    cg::grid_group g = cg::this_grid();
+    const int64_t nt = (int64_t)g.size(), tid = (int64_t)g.thread_rank();
+    const int64_t nn = (int64_t)n * n;
+    for (int64_t t = tid; t < n; t += nt) {  // pivot 0's row and column
+        rows[t] = A[t];
+        cols[t] = A[t * n];
     }
-}
-
-__global__ void k_gj_update(double *__restrict__ A, int n, int k, const double *__restrict__ rowk,
-                            const double *__restrict__ colk) {
-    GRID_LOOP(t, (int64_t)n * n) {
-        const int64_t i = t / n, j = t - i * n;
-        if (i == k) {
-            A[t] = rowk[j];
-        } else {
-            const double cur = (j == k) ? 0.0 : A[t];
-            A[t] = cur - colk[i] * rowk[j];
+    g.sync();
+    for (int k = 0; k < n; ++k) {
+        const double *rk = rows + (size_t)(k & 1) * n, *ck = cols + (size_t)(k & 1) * n;
+        double *rn = rows + (size_t)((k + 1) & 1) * n, *cn = cols + (size_t)((k + 1) & 1) * n;
+        const double akk = rk[k];
+        if (!(akk > 0.0)) {
+            if (tid == 0) atomicOr(flag, 1);
+            return;
         }
+        const double piv = 1.0 / akk;
+        for (int64_t t = tid; t < nn; t += nt) {
+            const int64_t i = t / n, j = t - i * n;
+            const double rowkj = (j == k ? 1.0 : rk[j]) * piv;
+            double v;
+            if (i == k) {
+                v = rowkj;
+            } else {
+                const double cur = (j == k) ? 0.0 : A[t];
+                v = cur - ((i == k) ? 0.0 : ck[i]) * rowkj;
+            }
+            A[t] = v;
+            if (i == k + 1) rn[j] = v;
+            if (j == k + 1) cn[i] = v;
+        }
+        g.sync();
     }
 }
 
@@ -606,13 +632,19 @@ __global__ void k_elim_tables(const int32_t *__restrict__ rowptr, const int32_t 
     }
 }
 
-// entries of the next level between two kept nodes: flags per entry
+// entries of the next level between two kept nodes: a flag per entry, and
+// the entry's column at the next level (keep_id is read once per entry)
 __global__ void k_keep_flags(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, int32_t n,
-                             const int32_t *__restrict__ elim, int32_t *__restrict__ flag) {
+                             const int32_t *__restrict__ keep_id, int32_t *__restrict__ flag,
+                             int32_t *__restrict__ newcol) {
     const int lane = threadIdx.x & 31;
     WARP_ROW_LOOP(i, n) {
-        const bool ki = !elim[i];
-        for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) flag[e] = (ki && !elim[col[e]]) ? 1 : 0;
+        const bool ki = keep_id[i] >= 0;
+        for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) {
+            const int32_t c = keep_id[col[e]];
+            flag[e] = (ki && c >= 0) ? 1 : 0;
+            newcol[e] = c;
+        }
     }
 }
 
@@ -642,10 +674,10 @@ __global__ void k_elim_emit_fill(const int32_t *__restrict__ e_nb, const int32_t
 // their own and merged with equal fills summed (ucol, uw, rows at fptr); then
 // each row's fills are merged into its kept run: a fill whose column the row
 // already has adds its weight there, the others are inserted in order.
-__global__ void k_elim_compact(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                               const double *__restrict__ w, int32_t n, const int32_t *__restrict__ elim,
-                               const int32_t *__restrict__ kidx, const int32_t *__restrict__ flag,
-                               const int32_t *__restrict__ pos, int32_t *__restrict__ kcol,
+__global__ void k_elim_compact(const int32_t *__restrict__ rowptr, const double *__restrict__ w, int32_t n,
+                               const int32_t *__restrict__ elim, const int32_t *__restrict__ kidx,
+                               const int32_t *__restrict__ flag, const int32_t *__restrict__ pos,
+                               const int32_t *__restrict__ newcol, int32_t *__restrict__ kcol,
                                double *__restrict__ kw, int32_t *__restrict__ kstart) {
     const int lane = threadIdx.x & 31;
     WARP_ROW_LOOP(i, n) {
@@ -653,7 +685,7 @@ __global__ void k_elim_compact(const int32_t *__restrict__ rowptr, const int32_t
         if (lane == 0) kstart[kidx[i]] = pos[rowptr[i]];
         for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) {
             if (!flag[e]) continue;
-            kcol[pos[e]] = kidx[col[e]];
+            kcol[pos[e]] = newcol[e];
             kw[pos[e]] = w[e];
         }
     }
@@ -713,6 +745,19 @@ __global__ void k_elim_write(const int32_t *__restrict__ kcol, const double *__r
             col_n[base + q + (fnew_pref[f] - fnew_pref[f0])] = ucol[f];
             w_n[base + q + (fnew_pref[f] - fnew_pref[f0])] = uw[f];
         }
+    }
+}
+
+// the restriction's operands per pull entry, read directly by the solve
+__global__ void k_elim_pull_direct(const int32_t *__restrict__ pull_e, int64_t npull, const int32_t *__restrict__ e_node,
+                                   const double *__restrict__ e_c64, const float *__restrict__ e_c32,
+                                   int32_t *__restrict__ pull_u, double *__restrict__ pull_c64,
+                                   float *__restrict__ pull_c32) {
+    GRID_LOOP(t, npull) {
+        const int slot = pull_e[t];
+        pull_u[t] = e_node[slot / 2];
+        pull_c64[t] = e_c64[slot];
+        pull_c32[t] = e_c32[slot];
     }
 }
 
@@ -861,9 +906,9 @@ bool eliminate_level(lap_hierarchy &h, double min_frac, cudaStream_t s) {
                F.e_dinv64.get(), F.e_dinv32.get(), fill_cnt.get(), pull_cnt.get(), fill_w.get());
     // next-level entries: the kept ones (already in order), merged row by row
     // with the fill edges (sorted and summed on their own)
-    DBuf<int32_t> flag(F.nnz, s), pos(F.nnz, s);
+    DBuf<int32_t> flag(F.nnz, s), pos(F.nnz, s), newcol(F.nnz, s);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_keep_flags, grid_for(32 * (int64_t)n), kBlock, 0, F.rowptr.get(), F.col.get(),
-               n, elim.get(), flag.get());
+               n, F.keep_id.get(), flag.get(), newcol.get());
     DBuf<int64_t> tot2(3, s);
     tot2.zero(s);
     scan_exclusive_i32_total(flag.get(), pos.get(), F.nnz, tot2.get(), s);
@@ -881,11 +926,12 @@ bool eliminate_level(lap_hierarchy &h, double min_frac, cudaStream_t s) {
         DBuf<int32_t> kcol(std::max<int64_t>(nkept, 1), s), kstart(nk + 1, s);
         DBuf<double> kw(std::max<int64_t>(nkept, 1), s);
         CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_elim_compact, grid_for(32 * (int64_t)n), kBlock, 0, F.rowptr.get(),
-                   F.col.get(), F.w64.get(), n, elim.get(), kidx.get(), flag.get(), pos.get(), kcol.get(), kw.get(),
+                   F.w64.get(), n, elim.get(), kidx.get(), flag.get(), pos.get(), newcol.get(), kcol.get(), kw.get(),
                    kstart.get());
         CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_set_last, 1, 1, 0, kstart.get(), nk, (int32_t)nkept);
         flag.release();
         pos.release();
+        newcol.release();
         // fill edges: sort, sum equal pairs, count per row
         DBuf<int32_t> ucol(std::max<int64_t>(nfill, 1), s), fptr(nk + 1, s), fcnt(nk + 1, s);
         DBuf<double> uw(std::max<int64_t>(nfill, 1), s);
@@ -940,6 +986,12 @@ bool eliminate_level(lap_hierarchy &h, double min_frac, cudaStream_t s) {
                    (int32_t)npull);
         scan_exclusive_i32(cnt.get(), F.pull_ptr.get(), nk, s);
         CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_set_last, 1, 1, 0, F.pull_ptr.get(), nk, (int32_t)npull);
+        F.pull_u.alloc_persistent(std::max<int64_t>(npull, 1));
+        F.pull_c64.alloc_persistent(std::max<int64_t>(npull, 1));
+        F.pull_c32.alloc_persistent(std::max<int64_t>(npull, 1));
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_elim_pull_direct, grid_for(npull), kBlock, 0, F.pull_e.get(), npull,
+                   F.e_node.get(), F.e_c64.get(), F.e_c32.get(), F.pull_u.get(), F.pull_c64.get(),
+                   F.pull_c32.get());
     }
     Level Cl;
     Cl.n = nk;
@@ -969,13 +1021,19 @@ void dense_spd_inverse_small(double *A, int n, int *d_flag, cudaStream_t s) {
 }
 
 void dense_spd_inverse_large(double *A, int n, int *d_flag, cudaStream_t s) {
-    DBuf<double> rowk(n, s), colk(n, s);
-    for (int k = 0; k < n; ++k) {
-        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_gj_pivot, grid_for(n), kBlock, 0, A, n, k, rowk.get(), colk.get(),
-                   d_flag);
-        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_gj_update, grid_for((int64_t)n * n), kBlock, 0, A, n, k, rowk.get(),
-                   colk.get());
-    }
+    DBuf<double> rows(2 * (size_t)n, s), cols(2 * (size_t)n, s);
+    int per_sm = 0;
+    CFC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_coop, kBlock, 0));
+    int dev = 0, sms = 0;
+    CFC_CUDA(cudaGetDevice(&dev));
+    CFC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t want = ((int64_t)n * n + kBlock - 1) / kBlock;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(1, per_sm) * sms, want));
+    double *a = A, *r = rows.get(), *c = cols.get();
+    int nn = n, *f = d_flag;
+    void *args[] = {&a, &nn, &r, &c, &f};
+    ::cfc::LaunchScope scope_(LAP_KF_SETUP, s, 0.0);
+    CFC_CUDA(cudaLaunchCooperativeKernel((const void *)k_gj_coop, blocks, kBlock, args, 0, s));
 }
 
 void build_dense(const int32_t *rowptr, const int32_t *col, const double *w, const double *deg, int32_t n,
@@ -1005,7 +1063,7 @@ void init_levels(lap_hierarchy &h, Csr64 &fine, const lap_hier_opts_t &o, cudaSt
     // low-degree elimination when it removes at least 5 % of the nodes
     if (o.eliminate && L0.n > 256 && eliminate_level(h, 0.05, s)) h.p0 = 1;
     const Level &T = h.lv.back();
-    if (T.n <= std::min(256, std::max(2, o.coarse_max)) || o.max_levels <= 1) grow_levels(h, 0, s);
+    if (T.n <= std::min(kDenseMax, std::max(2, o.coarse_max)) || o.max_levels <= 1) grow_levels(h, 0, s);
 }
 
 // Coarsen until the hierarchy has `target` levels (0: until coarsening stops:
@@ -1014,7 +1072,7 @@ void init_levels(lap_hierarchy &h, Csr64 &fine, const lap_hier_opts_t &o, cudaSt
 void grow_levels(lap_hierarchy &h, int target, cudaStream_t s) {
     if (h.complete) return;
     const lap_hier_opts_t &o = h.hopts;
-    const int coarse_max = std::min(256, std::max(2, o.coarse_max));
+    const int coarse_max = std::min(kDenseMax, std::max(2, o.coarse_max));
     const int max_levels = std::max(1, std::min(32, o.max_levels));
     bool stalled = false;
     cudaEvent_t ev0, ev1;
@@ -1091,7 +1149,7 @@ void grow_levels(lap_hierarchy &h, int target, cudaStream_t s) {
     Level &Lc = h.lv.back();
     h.coarse_n = 0;
     CFC_CUDA(cudaEventRecord(ev0, s));
-    if (Lc.n <= 256) {
+    if (Lc.n <= kDenseMax) {
         const int nc = Lc.n;
         h.coarse_inv.alloc_persistent((size_t)nc * nc);
         // the constant mode gets eigenvalue 2^wexp, of the order of the weights
@@ -1108,8 +1166,14 @@ void grow_levels(lap_hierarchy &h, int target, cudaStream_t s) {
         // means FP64 lost the matrix's definiteness (weights many orders of
         // magnitude apart): the coarsest level is then smoothed instead of
         // solved densely, which keeps the cycle a valid preconditioner.
-        if (hf == 0) h.coarse_n = nc;
-        else h.coarse_inv.release();
+        if (hf == 0) {
+            h.coarse_n = nc;
+            h.coarse_inv32.alloc_persistent((size_t)nc * nc);
+            CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_scaled_f32, grid_for((int64_t)nc * nc), kBlock, 0, h.coarse_inv.get(),
+                       (int64_t)nc * nc, h.wexp, h.coarse_inv32.get());
+        } else {
+            h.coarse_inv.release();
+        }
         CFC_CUDA(cudaEventRecord(ev1, s));
         CFC_CUDA(cudaEventSynchronize(ev1));
         float ms = 0.f;

@@ -189,14 +189,15 @@ void release_workspace(lap_hierarchy *h, cudaStream_t s) {
 
 int64_t hierarchy_bytes(const lap_hierarchy *h) {
     auto b = [](const auto &d) { return (int64_t)(d.n * sizeof(*d.p)); };
-    int64_t t = b(h->eid) + b(h->coarse_inv);
+    int64_t t = b(h->eid) + b(h->coarse_inv) + b(h->coarse_inv32);
     for (const Level &L : h->lv)
         t += b(L.rowptr) + b(L.col) + b(L.w64) + b(L.deg64) + b(L.dinv64) + b(L.w32) + b(L.deg32) + b(L.dinv32) +
              b(L.wbf) + b(L.degbf) + b(L.dinvbf) + b(L.chunk_row) + b(L.chunk_begin) + b(L.chunk_long) +
              b(L.long_first) + b(L.long_of_row) + b(L.order) + b(L.chunk_order) + b(L.agg) + b(L.mem_ptr) +
              b(L.mem) +
              b(L.keep_id) + b(L.keep_node) + b(L.e_node) + b(L.e_nb) + b(L.e_c64) + b(L.e_c32) +
-             b(L.e_dinv64) + b(L.e_dinv32) + b(L.pull_ptr) + b(L.pull_e);
+             b(L.e_dinv64) + b(L.e_dinv32) + b(L.pull_ptr) + b(L.pull_e) + b(L.pull_u) + b(L.pull_c64) +
+             b(L.pull_c32);
     return t;
 }
 
@@ -209,7 +210,7 @@ extern "C" {
 
 void lap_default_hier_opts(lap_hier_opts_t *o) {
     if (!o) return;
-    o->coarse_max = 64;
+    o->coarse_max = 1024;
     o->max_levels = 24;
     o->agg_passes = 2;
     o->match_rounds = 4;

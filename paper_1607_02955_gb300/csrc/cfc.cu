@@ -6,6 +6,7 @@
 //  * exact farness of small graphs from the dense pseudoinverse (Sec. 4).
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -101,21 +102,37 @@ __device__ __forceinline__ double i64_scaled_to_double(long long a, int e2) {
                                             (mant & ((1ull << 52) - 1))));
 }
 
-// per CSR entry: sgn * round(sqrt(w_e) * 2^S_u); one thread per entry, its
-// row found by binary search in rowptr
+// per CSR entry: sgn * round(sqrt(w_e) * 2^S_u).  A thread takes 8
+// consecutive entries: it finds the row of the first by binary search in
+// rowptr and walks forward from there, recomputing the row's scale when the
+// row changes.  A unit weight skips the square root (sqrt(1) = 1 exactly).
+constexpr int kTermsPerThread = 8;
 __global__ void k_jl_terms(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                            const double *__restrict__ w, const double *__restrict__ deg, int32_t n, int64_t nnz,
                            double inv_k, double inv_sqrt_k, long long *__restrict__ a) {
-    GRID_LOOP(e, nnz) {
-        int lo = 0, hi = n - 1;  // last row with rowptr[row] <= e
+    GRID_LOOP(t, (nnz + kTermsPerThread - 1) / kTermsPerThread) {
+        const int64_t e0 = t * kTermsPerThread;
+        const int64_t e1 = min(e0 + kTermsPerThread, nnz);
+        int lo = 0, hi = n - 1;  // last row with rowptr[row] <= e0
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(rowptr + mid) <= (int32_t)e) lo = mid;
+            if (__ldg(rowptr + mid) <= (int32_t)e0) lo = mid;
             else hi = mid - 1;
         }
-        const double sc = pow2(jl_row_shift(rowptr, deg, lo, inv_k)) * inv_sqrt_k;
-        const long long t = llrint(sqrt(w[e]) * sc);
-        a[e] = (lo < col[e]) ? t : -t;
+        int u = lo, next = __ldg(rowptr + u + 1);
+        double sc = pow2(jl_row_shift(rowptr, deg, u, inv_k)) * inv_sqrt_k;
+        long long t1 = llrint(sc);
+        for (int64_t e = e0; e < e1; ++e) {
+            if (e >= next) {
+                do next = __ldg(rowptr + (++u) + 1);
+                while (e >= next);
+                sc = pow2(jl_row_shift(rowptr, deg, u, inv_k)) * inv_sqrt_k;
+                t1 = llrint(sc);
+            }
+            const double we = w[e];
+            const long long tv = we == 1.0 ? t1 : llrint(sqrt(we) * sc);
+            a[e] = (u < col[e]) ? tv : -tv;
+        }
     }
 }
 
@@ -382,8 +399,9 @@ void jl_rhs(lap_hierarchy *h, int k_total, int row0, int k, int ld, uint64_t see
     const double inv_sqrt_k = 1.0 / std::sqrt((double)k_total), inv_k = 1.0 / k_total;
     const int cb_off = row0 / 32;
     DBuf<long long> a(std::max<int64_t>(L.nnz, 1), s);
-    CFC_LAUNCH(LAP_KF_CFC, s, (double)L.nnz * 20, k_jl_terms, grid_for(L.nnz), kBlock, 0, L.rowptr.get(),
-               L.col.get(), L.w64.get(), L.deg64.get(), n, L.nnz, inv_k, inv_sqrt_k, a.get());
+    CFC_LAUNCH(LAP_KF_CFC, s, (double)L.nnz * 20, k_jl_terms, grid_for((L.nnz + kTermsPerThread - 1) / kTermsPerThread),
+               kBlock, 0, L.rowptr.get(), L.col.get(), L.w64.get(), L.deg64.get(), n, L.nnz, inv_k, inv_sqrt_k,
+               a.get());
     const double bytes = (double)L.nnz * (4 + 8) + (double)n * 12 + (double)n * ld * 8;
     CFC_LAUNCH(LAP_KF_CFC, s, bytes, k_jl_short, grid_for((int64_t)n * ncb, 128), 128, 0, L.rowptr.get(),
                h->eid.get(), a.get(), L.deg64.get(), n, k, ld, cb_off, seed, inv_k, Y);
@@ -614,6 +632,60 @@ lap_status_t farness_sampled_resident(lap_hierarchy *h, const double *XS, const 
                dn, q, f.get());
     copy_out(farness, f.get(), q, s);
     CFC_CUDA(cudaStreamSynchronize(s));
+    return st;
+}
+
+// Several sampling queries on one hierarchy as one block solve: each query's
+// pivot columns (drawn with its own seed) and node columns sit side by side,
+// one solve covers them all, and each query's farness comes from its own
+// columns (Sec. 5.1, Proposition 1).  A column's solution does not depend on
+// the other columns of the block (per-column PCG scalars and stopping tests,
+// reductions in a fixed order per column), so at the same tile width a query
+// gets the same bits alone and in a batch.  With kp > 0 every query uses the
+// resident pivot set (XS, piv_res) and contributes only its node columns.
+lap_status_t farness_sampled_batch(lap_hierarchy *h, const SampledQuery *qs, int nq, const double *XS,
+                                   const int32_t *piv_res, int32_t kp, const lap_solve_opts_t &o, cudaStream_t s) {
+    const int64_t n = h->lv[0].n;
+    CFC_REQUIRE(nq >= 1, LAP_EINVAL, "empty batch");
+    std::vector<int64_t> cbase(nq), pbase(nq), qbase(nq);
+    int64_t cols = 0, npiv = 0, nnodes = 0;
+    for (int i = 0; i < nq; ++i) {
+        CFC_REQUIRE((kp > 0) == (qs[i].kk == 0) && qs[i].q >= 1, LAP_EINVAL, "mixed batch");
+        cbase[i] = cols;
+        pbase[i] = npiv;
+        qbase[i] = nnodes;
+        cols += qs[i].kk + qs[i].q;
+        npiv += qs[i].kk;
+        nnodes += qs[i].q;
+    }
+    CFC_REQUIRE(cols <= 4096, LAP_EBUDGET, "a batch holds at most 4096 columns");
+    std::vector<int32_t> hn(nnodes);
+    for (int i = 0; i < nq; ++i) std::memcpy(hn.data() + qbase[i], qs[i].nodes, qs[i].q * sizeof(int32_t));
+    DBuf<int32_t> dn(nnodes, s), piv(std::max<int64_t>(npiv, 1), s);
+    CFC_CUDA(cudaMemcpyAsync(dn.get(), hn.data(), nnodes * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    DBuf<double> B((size_t)n * cols, s), X((size_t)n * cols, s), f(nnodes, s);
+    B.zero(s);
+    for (int i = 0; i < nq; ++i) {
+        if (qs[i].kk > 0) sample_pivots(n, qs[i].kk, qs[i].seed, piv.get() + pbase[i], s);
+        CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_unit_columns, grid_for(qs[i].kk + qs[i].q), kBlock, 0, piv.get() + pbase[i],
+                   qs[i].kk, dn.get() + qbase[i], qs[i].q, (int)cols, B.get() + cbase[i]);
+    }
+    const lap_status_t st = solve_multi(h, (int32_t)cols, B.get(), X.get(), o, s, nullptr);
+    if (st != LAP_OK && st != LAP_ENOCONV) return st;
+    for (int i = 0; i < nq; ++i) {
+        const int q = qs[i].q;
+        if (kp > 0)
+            CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_sample_farness, (q + 7) / 8, 256, 0, XS, kp, 0, X.get(), (int)cols,
+                       (int)cbase[i], n, piv_res, kp, dn.get() + qbase[i], q, f.get() + qbase[i]);
+        else
+            CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_sample_farness, (q + 7) / 8, 256, 0, X.get(), (int)cols, (int)cbase[i],
+                       X.get(), (int)cols, (int)(cbase[i] + qs[i].kk), n, piv.get() + pbase[i], qs[i].kk,
+                       dn.get() + qbase[i], q, f.get() + qbase[i]);
+    }
+    std::vector<double> hf(nnodes);
+    CFC_CUDA(cudaMemcpyAsync(hf.data(), f.get(), nnodes * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CFC_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < nq; ++i) std::memcpy(qs[i].farness, hf.data() + qbase[i], qs[i].q * sizeof(double));
     return st;
 }
 

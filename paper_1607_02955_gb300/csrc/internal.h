@@ -196,9 +196,13 @@ struct Level {
     DBuf<double> e_dinv64;       // [n_elim] 1 / d_u
     DBuf<float> e_dinv32;        //          2^wexp / d_u (the FP32 operators are 2^-wexp L)
     DBuf<int32_t> pull_ptr;      // [n_next + 1] eliminated neighbours of each next-level node,
-    DBuf<int32_t> pull_e;        //   as slots 2 j + m of e_nb / e_c (ascending j)
+    DBuf<int32_t> pull_e;        //   as slots 2 j + m of e_nb / e_c (ascending j),
+    DBuf<int32_t> pull_u;        //   the eliminated node of each slot,
+    DBuf<double> pull_c64;       //   and its coefficient w_um / d_u
+    DBuf<float> pull_c32;
 };
 
+constexpr int kDenseMax = 2048;  // largest coarsest level solved by a dense inverse
 constexpr int kLongRow = 32;     // rows with more nonzeros are split into chunks
 constexpr int kChunk = 16;       // nonzeros per chunk of a split row
 constexpr int kMaxTiles = 64;    // column tiles per launch (k <= 64 * 64)
@@ -285,6 +289,7 @@ struct lap_hierarchy {
     std::vector<double> level_ms;     // device time to build each level (level 0: ingest)
     int32_t coarse_n = 0;             // dense coarsest size (0: none)
     cfc::DBuf<double> coarse_inv;     // (L_c + 2^wexp J/n_c)^{-1}, row-major
+    cfc::DBuf<float> coarse_inv32;    // 2^wexp times it in FP32 (the FP32 modes' coarse solve)
     // Weight exponent: the largest level-0 weight lies in [2^wexp, 2^(wexp+1)).
     // The FP32 (and BF16) operators of every level are those of 2^-wexp L, an
     // exact power-of-two scaling, so that weights far from 1 (conductances of
@@ -363,6 +368,18 @@ lap_status_t pivot_solutions(lap_hierarchy *h, int32_t kk, uint64_t seed, double
 lap_status_t farness_sampled_resident(lap_hierarchy *h, const double *XS, const int32_t *piv, int32_t kk, int32_t q,
                                       const int32_t *nodes, double *farness, const lap_solve_opts_t &o,
                                       cudaStream_t s);
+// Several sampling queries as one block solve (the serving loop's batches):
+// all with drawn pivots (kk > 0, kp = 0), or all on the resident pivot set
+// (kk = 0; XS n x kp, piv_res).  Host nodes and outputs.
+struct SampledQuery {
+    int32_t kk;
+    uint64_t seed;
+    int32_t q;
+    const int32_t *nodes;
+    double *farness;
+};
+lap_status_t farness_sampled_batch(lap_hierarchy *h, const SampledQuery *qs, int nq, const double *XS,
+                                   const int32_t *piv_res, int32_t kp, const lap_solve_opts_t &o, cudaStream_t s);
 lap_status_t exact_small(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const double *w,
                          double *farness, double *closeness, cudaStream_t s);
 }  // namespace cfc

@@ -60,7 +60,7 @@ struct cfc_server {
     std::map<int64_t, std::unique_ptr<Request>> reqs;  // not yet polled
     int64_t next_id = 1;
     int64_t graph_bytes = 0, inflight_bytes = 0, peak_inflight_bytes = 0;
-    int in_flight = 0, max_in_flight = 0;
+    int in_flight = 0, max_in_flight = 0, max_batch = 0;
     bool stopping = false;
     // statistics of completed requests
     std::vector<double> lat_ms;
@@ -86,33 +86,65 @@ struct cfc_server {
         return graph_bytes + inflight_bytes + r.bytes <= budget;
     }
 
+    // columns a batch may hold: the option, at most 4096 columns and 64 tiles
+    // of the graph's pinned tile width (so the tile, and with it every
+    // column's bits, is the same as for the request alone)
+    int64_t batch_limit(const Graph &g) const {
+        const int64_t kt = g.opts.k_tile > 0 ? g.opts.k_tile : 64;
+        return std::max<int64_t>(1, std::min<int64_t>({(int64_t)o.batch_columns, 4096, 64 * kt}));
+    }
+
     void worker(int slot) {
         cudaSetDevice(device);
         cudaStream_t s = streams[slot];
         for (;;) {
-            Request *r = nullptr;
+            // the head of the queue, and (continuous batching) the queued
+            // requests on the same graph and of the same kind that fit beside
+            // it: one block solve for all their columns
+            std::vector<Request *> batch;
             const Graph *gp = nullptr;
+            int64_t batch_bytes = 0;
             {
                 std::unique_lock<std::mutex> lk(mu);
                 cv_work.wait(lk, [&] { return stopping || head_admissible(); });
                 if (stopping) return;
-                r = reqs.at(queue.front()).get();
+                Request *r = reqs.at(queue.front()).get();
                 queue.pop_front();
                 gp = &graphs[r->graph];
-                inflight_bytes += r->bytes;
+                batch.push_back(r);
+                int64_t cols = r->kk + r->q;
+                batch_bytes = r->bytes;
+                const int64_t limit = batch_limit(*gp);
+                for (auto it = queue.begin(); it != queue.end() && cols < limit;) {
+                    Request *c = reqs.at(*it).get();
+                    const int64_t cc = c->kk + c->q;
+                    const int64_t nb = request_bytes(gp->n, (int32_t)(cols + cc));
+                    if (c->graph == r->graph && (c->kk > 0) == (r->kk > 0) && cols + cc <= limit &&
+                        graph_bytes + inflight_bytes + nb <= budget) {
+                        batch.push_back(c);
+                        cols += cc;
+                        batch_bytes = nb;
+                        it = queue.erase(it);
+                    } else {
+                        ++it;
+                    }
+                }
+                inflight_bytes += batch_bytes;
                 peak_inflight_bytes = std::max(peak_inflight_bytes, inflight_bytes);
-                ++in_flight;
+                in_flight += (int)batch.size();
                 max_in_flight = std::max(max_in_flight, in_flight);
-                r->t_admit = Clock::now();
+                max_batch = std::max(max_batch, (int)batch.size());
+                const Clock::time_point now = Clock::now();
+                for (Request *b : batch) b->t_admit = now;
             }
             lap_status_t st;
             try {
                 const Graph &g = *gp;
-                if (r->kk > 0)
-                    st = cfc::farness_sampled(g.h, r->kk, r->seed, r->q, r->nodes.data(), r->far.data(), g.opts, s);
-                else
-                    st = cfc::farness_sampled_resident(g.h, g.xs.get(), g.piv.get(), g.kp, r->q, r->nodes.data(),
-                                                       r->far.data(), g.opts, s);
+                std::vector<cfc::SampledQuery> qs;
+                for (Request *b : batch) qs.push_back({b->kk, b->seed, b->q, b->nodes.data(), b->far.data()});
+                const bool resident = batch[0]->kk == 0;
+                st = cfc::farness_sampled_batch(g.h, qs.data(), (int)qs.size(), resident ? g.xs.get() : nullptr,
+                                                resident ? g.piv.get() : nullptr, resident ? g.kp : 0, g.opts, s);
                 cfc::release_workspace(g.h, s);  // back to the pool, for the next admission
                 cudaError_t e = cudaStreamSynchronize(s);
                 if (e != cudaSuccess && st == LAP_OK) st = LAP_ECUDA;
@@ -127,16 +159,19 @@ struct cfc_server {
             }
             {
                 std::lock_guard<std::mutex> lk(mu);
-                r->status = st;
-                r->t_done = Clock::now();
-                r->done = true;
-                inflight_bytes -= r->bytes;
-                --in_flight;
-                if (st == LAP_OK) {
-                    lat_ms.push_back(ms_between(r->t_submit, r->t_done));
-                    ++completed;
-                    rhs_done += r->kk + r->q;  // resident requests: kk = 0, their q columns
-                    span1 = r->t_done;
+                const Clock::time_point now = Clock::now();
+                inflight_bytes -= batch_bytes;
+                in_flight -= (int)batch.size();
+                for (Request *r : batch) {
+                    r->status = st;
+                    r->t_done = now;
+                    r->done = true;
+                    if (st == LAP_OK) {
+                        lat_ms.push_back(ms_between(r->t_submit, r->t_done));
+                        ++completed;
+                        rhs_done += r->kk + r->q;  // resident requests: kk = 0, their q columns
+                        span1 = r->t_done;
+                    }
                 }
             }
             cv_done.notify_all();
@@ -152,6 +187,7 @@ void cfc_server_default_opts(cfc_server_opts_t *o) {
     std::memset(o, 0, sizeof(*o));
     o->slots = 4;
     o->hbm_budget = 0;
+    o->batch_columns = 1024;
     lap_default_solve_opts(&o->solve);
 }
 
@@ -160,6 +196,7 @@ lap_status_t cfc_server_create(const cfc_server_opts_t *o, cfc_server_t **out) {
         CFC_REQUIRE(o && out, LAP_EINVAL, "NULL argument");
         CFC_REQUIRE(o->slots >= 1 && o->slots <= 64, LAP_EINVAL, "need 1 <= slots <= 64");
         CFC_REQUIRE(o->hbm_budget >= 0, LAP_EINVAL, "hbm_budget must be >= 0");
+        CFC_REQUIRE(o->batch_columns >= 0, LAP_EINVAL, "batch_columns must be >= 0");
         *out = nullptr;
         auto sv = std::make_unique<cfc_server>();
         sv->o = *o;
@@ -329,6 +366,7 @@ lap_status_t cfc_server_stats(cfc_server_t *sv, cfc_server_stats_t *out) {
         out->graph_bytes = sv->graph_bytes;
         out->budget_bytes = sv->budget;
         out->peak_in_flight_bytes = sv->peak_inflight_bytes;
+        out->max_batch = sv->max_batch;
         if (!sv->lat_ms.empty()) {
             std::vector<double> v = sv->lat_ms;
             std::sort(v.begin(), v.end());
@@ -360,6 +398,7 @@ void cfc_server_reset_stats(cfc_server_t *sv) {
     sv->completed = sv->rhs_done = 0;
     sv->submitted = (int64_t)sv->queue.size() + sv->in_flight;
     sv->max_in_flight = sv->in_flight;
+    sv->max_batch = 0;
     sv->peak_inflight_bytes = sv->inflight_bytes;
     sv->have_span = false;
     if (!sv->queue.empty() || sv->in_flight > 0) {

@@ -602,23 +602,34 @@ struct OpSubMean64 {
 // ---------------------------------------------------------------- elimination transfers
 // Restriction through an elimination level (Level::elim): the next level's
 // right-hand side b'(I) = b(keep_node[I]) + sum of (w_uI / d_u) b(u) over the
-// eliminated neighbours u of keep_node[I], in ascending order of u.
+// eliminated neighbours u of keep_node[I], in ascending order of u; four
+// neighbours in flight per lane (a hub may pull thousands of leaves).
 template <typename T>
 struct OpElimRestrict {
     using V = typename Vec<T>::V;
     static constexpr int VW = Vec<T>::W;
-    const int32_t *keep_node, *pull_ptr, *pull_e, *e_node;
-    const T *coef;  // w_um / d_u per slot 2 j + m
+    const int32_t *keep_node, *pull_ptr, *pull_u;
+    const T *coef;  // w_uI / d_u per pull entry
     const T *b;
     T *bn;
     int ld;
     template <class Acc>
     __device__ void row(int I, int c0, Acc &) const {
         V s = vld<T>(b + (size_t)__ldg(keep_node + I) * ld + c0);
-        for (int t = __ldg(pull_ptr + I); t < __ldg(pull_ptr + I + 1); ++t) {
-            const int slot = __ldg(pull_e + t);
-            vfma(s, __ldg(coef + slot), vld<T>(b + (size_t)__ldg(e_node + slot / 2) * ld + c0));
+        const int t1 = __ldg(pull_ptr + I + 1);
+        int t = __ldg(pull_ptr + I);
+        for (; t + 4 <= t1; t += 4) {
+            V x[4];
+            T c[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                c[q] = __ldg(coef + t + q);
+                x[q] = vld<T>(b + (size_t)__ldg(pull_u + t + q) * ld + c0);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) vfma(s, c[q], x[q]);
         }
+        for (; t < t1; ++t) vfma(s, __ldg(coef + t), vld<T>(b + (size_t)__ldg(pull_u + t) * ld + c0));
         vst<T>(bn + (size_t)I * ld + c0, s);
     }
     __device__ void fin(int, const double *) const {}
@@ -688,6 +699,35 @@ __global__ void k_coarse_dense(const double *__restrict__ Minv, int nc, const T 
         double s = 0.0;
         for (int J = 0; J < nc; ++J) s += row[J] * (double)b[(size_t)J * ld + c];
         x[(size_t)I * ld + c] = (T)scale2(s, e);
+    }
+}
+
+// The same in FP32 (the FP32 modes): x_c = (2^wexp M^{-1}) b_c with the FP32
+// copy of the scaled inverse (entries of order one whatever the weights) and
+// FP32 sums in a fixed order (GB300's FP64 rate would make the FP64 product
+// the cost of the whole coarse solve at n_c in the thousands).  One warp per
+// coarse row I, a lane per column of a 32-column chunk; the row of the
+// inverse is read once per warp and broadcast.
+__global__ void __launch_bounds__(256) k_coarse_dense32(const float *__restrict__ Minv, int nc,
+                                                        const float *__restrict__ b, float *__restrict__ x, int ld,
+                                                        int k) {
+    const int lane = threadIdx.x & 31;
+    const int chunks = (k + 31) / 32;
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nc * chunks; w += (gridDim.x * blockDim.x) >> 5) {
+        const int I = w / chunks, c = (w - I * chunks) * 32 + lane;
+        const float *row = Minv + (size_t)I * nc;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        if (c < k) {
+            int J = 0;
+            for (; J + 4 <= nc; J += 4) {
+                s0 = fmaf(__ldg(row + J), __ldg(b + (size_t)J * ld + c), s0);
+                s1 = fmaf(__ldg(row + J + 1), __ldg(b + (size_t)(J + 1) * ld + c), s1);
+                s2 = fmaf(__ldg(row + J + 2), __ldg(b + (size_t)(J + 2) * ld + c), s2);
+                s3 = fmaf(__ldg(row + J + 3), __ldg(b + (size_t)(J + 3) * ld + c), s3);
+            }
+            for (; J < nc; ++J) s0 = fmaf(__ldg(row + J), __ldg(b + (size_t)J * ld + c), s0);
+            x[(size_t)I * ld + c] = (s0 + s1) + (s2 + s3);
+        }
     }
 }
 
@@ -911,10 +951,18 @@ struct Solver {
         const bool coarsest = (l == nlev - 1);
         if (coarsest && coarse_n == L.n && l == hsize - 1) {
             const int nc = L.n;
-            const int threads = 128;
-            const int blocks = std::max(1, std::min((nc * ld + threads - 1) / threads, 8 * num_sms()));
-            CFC_LAUNCH(LAP_KF_COARSE_LEVELS, s, (double)nc * nc * 8 + 2.0 * nc * ld * et, k_coarse_dense<Tin>,
-                       blocks, threads, 0, h->coarse_inv.get(), nc, lb[l], lx[l], ld, ld, op_wexp());
+            const double bytes = (double)nc * nc * (kScaled ? 4 : 8) + 2.0 * nc * ld * et;
+            if constexpr (kScaled) {
+                const int chunks = (ld + 31) / 32;
+                const int blocks = std::max(1, std::min((nc * chunks + 7) / 8, 8 * num_sms()));
+                CFC_LAUNCH(LAP_KF_COARSE_LEVELS, s, bytes, k_coarse_dense32, blocks, 256, 0, h->coarse_inv32.get(), nc,
+                           (const float *)lb[l], (float *)lx[l], ld, ld);
+            } else {
+                const int threads = 128;
+                const int blocks = std::max(1, std::min((nc * ld + threads - 1) / threads, 8 * num_sms()));
+                CFC_LAUNCH(LAP_KF_COARSE_LEVELS, s, bytes, k_coarse_dense<Tin>, blocks, threads, 0, h->coarse_inv.get(),
+                           nc, lb[l], lx[l], ld, ld, op_wexp());
+            }
             return false;
         }
         // pre-smoothing from zero
@@ -1099,6 +1147,11 @@ struct Solver {
         else return E.e_c64.get();
     }
     template <typename T>
+    static const T *pull_coef_of(const Level &E) {
+        if constexpr (std::is_same<T, float>::value) return E.pull_c32.get();
+        else return E.pull_c64.get();
+    }
+    template <typename T>
     static const T *dinv_of(const Level &E) {
         if constexpr (std::is_same<T, float>::value) return E.e_dinv32.get();
         else return E.e_dinv64.get();
@@ -1107,8 +1160,8 @@ struct Solver {
         const Level &E = h->lv[0];
         const int et = (int)sizeof(Tin);
         rows<Tin, 0>(LAP_KF_BLAS1, lvl(0).n,
-                     OpElimRestrict<Tin>{E.keep_node.get(), E.pull_ptr.get(), E.pull_e.get(), E.e_node.get(),
-                                         coef_of<Tin>(E), r0, r, ld},
+                     OpElimRestrict<Tin>{E.keep_node.get(), E.pull_ptr.get(), E.pull_u.get(), pull_coef_of<Tin>(E),
+                                         r0, r, ld},
                      vec_bytes(E.n, ld, 1, et) + vec_bytes(lvl(0).n, ld, 1, et));
     }
     void elim_back() {

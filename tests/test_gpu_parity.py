@@ -43,14 +43,17 @@ def _rel(a, b):
 # ------------------------------------------------------------------ ingest / hierarchy
 def test_hierarchy_sizes(P):
     n, s, d, w = _graph(synth.grid2d(48))
-    h = P.lap_build_hierarchy(n, s, d, w, P.lap_default_hier_opts(eager=1))
+    h = P.lap_build_hierarchy(n, s, d, w, P.lap_default_hier_opts(eager=1, coarse_max=64))
     info = P.lap_hierarchy_info(h)
     assert info["n"] == 2304 and info["m"] == 4512
     assert info["level_nnz"][0] == 2 * 4512
-    assert info["levels"] >= 2
+    assert info["levels"] >= 3
     assert info["coarse_n"] == info["level_n"][-1] <= 64
     for a, b in zip(info["level_n"], info["level_n"][1:]):
         assert b < a
+    # the default stops at 1024 nodes or fewer and solves that level densely
+    dflt = P.lap_hierarchy_info(P.lap_build_hierarchy(n, s, d, w, P.lap_default_hier_opts(eager=1)))
+    assert dflt["levels"] == 2 and dflt["coarse_n"] == dflt["level_n"][-1] <= 1024
 
 
 def test_duplicates_selfloops_merged(P):
@@ -159,7 +162,7 @@ def test_solve_is_deterministic_and_column_independent(P):
 def test_lazy_levels_and_depth_choices(P):
     import torch
     n, s, d, w = _graph(synth.grid2d(64))
-    h = P.lap_build_hierarchy(n, s, d, w)
+    h = P.lap_build_hierarchy(n, s, d, w, P.lap_default_hier_opts(coarse_max=64))
     assert P.lap_hierarchy_info(h)["levels"] == 1  # coarse levels are built on demand
     B = torch.randn((n, 16), dtype=torch.float64, device="cuda")
     X = torch.empty_like(B)
@@ -234,7 +237,7 @@ def test_graph_replay_matches_plain_launches(P, cycle, w_levels):
     # the captured cycle is the same kernels in the same order: identical bits
     import torch
     n, s, d, w = _graph(synth.grid2d(64))
-    h = P.lap_build_hierarchy(n, s, d, w, P.lap_default_hier_opts(eager=1))
+    h = P.lap_build_hierarchy(n, s, d, w, P.lap_default_hier_opts(eager=1, coarse_max=64))
     assert P.lap_hierarchy_info(h)["levels"] >= 3
     rng = np.random.default_rng(4)
     B = torch.tensor(rng.standard_normal((n, 24)), device="cuda")
@@ -254,7 +257,7 @@ def test_bf16_coarse_changes_only_the_preconditioner(P):
     # tolerance; the coarse operators differ, so the inner iterations may differ
     import torch
     n, s, d, w = _graph(synth.grid2d(64))
-    h = P.lap_build_hierarchy(n, s, d, w, P.lap_default_hier_opts(eager=1))
+    h = P.lap_build_hierarchy(n, s, d, w, P.lap_default_hier_opts(eager=1, coarse_max=64))
     assert P.lap_hierarchy_info(h)["levels"] >= 3
     rng = np.random.default_rng(3)
     B = torch.tensor(rng.standard_normal((n, 16)), device="cuda")

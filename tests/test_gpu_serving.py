@@ -161,3 +161,32 @@ def test_server_resident_pivot_sets(P):
         assert e.value.status == P.LAP_EINVAL
     finally:
         plain.destroy()
+
+
+@pytest.mark.parametrize("resident", [False, True])
+def test_server_merges_queued_requests_with_the_same_bits(P, resident):
+    # one slot: while the first request runs, the rest queue up and the next
+    # admission solves the queued requests on the same graph as one block;
+    # every result equals the one the request got alone
+    graphs = _graphs()[:2]
+    opts = P.cfc_server_default_opts(slots=1, batch_columns=1024, resident_pivots=60 if resident else 0,
+                                     pivot_seed=7)
+    sv = P.cfc_server_create(opts)
+    try:
+        for n, s, d, w in graphs:
+            P.cfc_server_add_graph(sv, n, s, d, w)
+        qs = [(gid, nodes, 0 if resident else kk, seed) for gid, nodes, kk, seed in _queries(graphs, 12, 9)]
+        alone = []
+        for gid, nodes, kk, seed in qs:
+            f, info = P.cfc_server_poll(sv, P.cfc_server_submit(sv, gid, nodes, kk, seed), -1)
+            assert info["status"] == P.LAP_OK
+            alone.append(f)
+        P.cfc_server_reset_stats(sv)
+        rids = [P.cfc_server_submit(sv, gid, nodes, kk, seed) for gid, nodes, kk, seed in qs]
+        merged = [P.cfc_server_poll(sv, r, -1)[0] for r in rids]
+        st = P.cfc_server_stats(sv)
+        assert st["max_batch"] >= 2 and st["completed"] == len(qs)
+        for a, m in zip(alone, merged):
+            assert np.array_equal(a, m)
+    finally:
+        sv.destroy()
