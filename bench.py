@@ -601,6 +601,18 @@ def serve_main(args):
                       "serving": r}), flush=True)
 
 
+def hier_opts(P, args):
+    """Hierarchy options from the command line (library defaults otherwise)."""
+    kw = {}
+    if getattr(args, "coarse_max", None) is not None:
+        kw["coarse_max"] = args.coarse_max
+    if getattr(args, "aggregation", None) is not None:
+        kw["aggregation"] = {"strength": 0, "affinity": 1}[args.aggregation]
+    if getattr(args, "hub_factor", None) is not None:
+        kw["hub_factor"] = args.hub_factor
+    return P.lap_default_hier_opts(**kw)
+
+
 def gpu_workload(P, torch, name, args, steps, warmup, local, world, clk=None, full=True):
     """Times `steps` steps of a workload on this rank's GPU (after `warmup`
     untimed ones), device-resident inputs, L2 flushed between steps.  With
@@ -623,6 +635,7 @@ def gpu_workload(P, torch, name, args, steps, warmup, local, world, clk=None, fu
     sopts = P.lap_default_solve_opts(precision=prec_mode)
     if args.levels is not None:
         sopts.levels_used = args.levels
+    hopts = hier_opts(P, args)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
 
     rank = int(os.environ.get("RANK", "0"))
@@ -642,7 +655,7 @@ def gpu_workload(P, torch, name, args, steps, warmup, local, world, clk=None, fu
             out.copy_(t.cpu())
 
     def step_device():
-        h = P.lap_build_hierarchy(n, src_d, dst_d, w_d, stream=sp)
+        h = P.lap_build_hierarchy(n, src_d, dst_d, w_d, hopts, stream=sp)
         farness(h, nodes_d, far_d)
         h.destroy()
 
@@ -653,7 +666,7 @@ def gpu_workload(P, torch, name, args, steps, warmup, local, world, clk=None, fu
     far_h = torch.empty(len(nodes), dtype=torch.float64).pin_memory()
 
     def step_host():
-        h = P.lap_build_hierarchy(n, src_h, dst_h, w_h, stream=sp)
+        h = P.lap_build_hierarchy(n, src_h, dst_h, w_h, hopts, stream=sp)
         farness(h, nodes, far_h)
         h.destroy()
 
@@ -692,7 +705,7 @@ def gpu_workload(P, torch, name, args, steps, warmup, local, world, clk=None, fu
         # the distributed result against the same query of k * N rows on this GPU alone
         with torch.cuda.stream(stream):
             step_device()
-            h = P.lap_build_hierarchy(n, src_d, dst_d, w_d, stream=sp)
+            h = P.lap_build_hierarchy(n, src_d, dst_d, w_d, hopts, stream=sp)
             one = P.cfc_farness_jl(h, k * world, wl["jl_seed"], nodes, opts=sopts, stream=sp)
             h.destroy()
         split_err = float(np.max(np.abs(far_d.cpu().numpy() - one) / np.abs(one)))
@@ -849,6 +862,12 @@ def main():
     ap.add_argument("--print-digest", action="store_true", help="print the kernel source digest and exit")
     ap.add_argument("--levels", type=int, default=None,
                     help="levels_used of the V-cycle (default: autotuned; -1: every level)")
+    ap.add_argument("--coarse-max", type=int, default=None,
+                    help="hierarchy option coarse_max (default: the library's, 1024)")
+    ap.add_argument("--aggregation", default=None, choices=["strength", "affinity"],
+                    help="hierarchy option aggregation (default: strength)")
+    ap.add_argument("--hub-factor", type=int, default=None,
+                    help="hierarchy option hub_factor (default 0: no hub rule)")
     ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS),
                     help="arithmetic of the solve (fp32: FP32 PCG + V-cycle in FP64 refinement)")
     ap.add_argument("--launch-log", default=None,
@@ -891,7 +910,8 @@ def main():
     # setup alone (ingest + hierarchy) and solver iteration counts, for context
     gn, src_d, dst_d, w_d = res["graph"]
     sp = res["stream"].cuda_stream
-    h = P.lap_build_hierarchy(gn, src_d, dst_d, w_d, stream=sp)
+    hopts = hier_opts(P, args)
+    h = P.lap_build_hierarchy(gn, src_d, dst_d, w_d, hopts, stream=sp)
     Y = torch.empty((n, k), dtype=torch.float64, device=res["dev"])
     X = torch.empty_like(Y)
     P.cfc_jl_rhs(h, k, wl["jl_seed"], Y, stream=sp)
@@ -912,7 +932,9 @@ def main():
                        "l2": "flushed between steps (256 MiB write, untimed)" +
                              ("; every FP32 block (n x 64 x 4 B) is larger than L2" if large else ""),
                        "levels_built": hinfo["levels"], "level_n": hinfo["level_n"], "setup_ms": hinfo["setup_ms"],
-                       "level_row_order": hinfo["level_row_order"],
+                       "level_row_order": hinfo["level_row_order"], "elim_levels": hinfo["elim_levels"],
+                       "hier_opts": {"coarse_max": hopts.coarse_max, "aggregation": hopts.aggregation,
+                                     "hub_factor": hopts.hub_factor, "eliminate": hopts.eliminate},
                        "solve": {key: sinfo[key] for key in ("outer_iters", "inner_iters", "max_rel_residual",
                                                               "k_tile", "levels_used", "nu_coarse", "cycle",
                                                               "coarse_scale", "w_levels")},

@@ -79,6 +79,13 @@ enum {
 /* Smoother of the V-cycle. */
 enum { LAP_SMOOTH_JACOBI = 0, LAP_SMOOTH_CHEBYSHEV = 1 };
 
+/* How the pairwise matching of the aggregation ranks a neighbour j of node i
+ * (Sec. 3.1 names LAMG's affinity-based aggregation without a formula):
+ * LAP_AGG_STRENGTH  w_ij / max(D_ii, D_jj);
+ * LAP_AGG_AFFINITY  (x_i . x_j)^2 / ((x_i . x_i)(x_j . x_j)) over 8 test vectors
+ *                   relaxed by 4 damped Jacobi sweeps on L x = 0 of that graph. */
+enum { LAP_AGG_STRENGTH = 0, LAP_AGG_AFFINITY = 1 };
+
 typedef struct {
     int32_t coarse_max;   /* stop coarsening at n_l <= coarse_max (default 1024, at most 2048);
                              the coarsest level (at most 2048 nodes) is solved with a dense
@@ -98,6 +105,10 @@ typedef struct {
                              nodes keep their labels): 0 (default) longest rows first on
                              levels whose row lengths are very uneven, natural order
                              elsewhere; 1 natural order; 2 longest first everywhere */
+    int32_t aggregation;  /* LAP_AGG_STRENGTH (default) | LAP_AGG_AFFINITY */
+    int32_t hub_factor;   /* > 0: a node with more than hub_factor x the mean row length of
+                             its level neither joins nor absorbs an aggregate (it stays a
+                             singleton); 0 (default): no hub rule.  At most 1000000 */
 } lap_hier_opts_t;
 
 typedef struct {

@@ -29,6 +29,8 @@ from ._binding import (  # noqa: F401
     LAP_FP32_BF16COARSE_REFINED,
     LAP_SMOOTH_JACOBI,
     LAP_SMOOTH_CHEBYSHEV,
+    LAP_AGG_STRENGTH,
+    LAP_AGG_AFFINITY,
     KERNEL_FAMILIES,
     lib,
     lib_path,

@@ -13,6 +13,7 @@ lib_path = os.path.join(_HERE, "lib", "libcfc_gb300.so")
  LAP_EPENDING) = range(9)
 LAP_FP64, LAP_FP32_REFINED, LAP_FP32_BF16COARSE_REFINED = 0, 1, 2
 LAP_SMOOTH_JACOBI, LAP_SMOOTH_CHEBYSHEV = 0, 1
+LAP_AGG_STRENGTH, LAP_AGG_AFFINITY = 0, 1
 KERNEL_FAMILIES = ["spmv_fine", "smooth_fine", "restrict_fine", "blas1", "coarse_levels", "resid64", "setup",
                    "cfc"]
 
@@ -32,7 +33,7 @@ SYMBOLS = [
 class HierOpts(C.Structure):
     _fields_ = [("coarse_max", C.c_int32), ("max_levels", C.c_int32), ("agg_passes", C.c_int32),
                 ("match_rounds", C.c_int32), ("eager", C.c_int32), ("eliminate", C.c_int32),
-                ("reorder", C.c_int32)]
+                ("reorder", C.c_int32), ("aggregation", C.c_int32), ("hub_factor", C.c_int32)]
 
 
 class SolveOpts(C.Structure):

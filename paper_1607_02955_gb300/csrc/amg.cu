@@ -86,18 +86,45 @@ __device__ __forceinline__ Cand warp_best(Cand c) {
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < (count);       \
          i += ((int64_t)gridDim.x * blockDim.x) >> 5)
 
+// How the pairwise matching ranks a neighbour j of node i.
+//  - X null: the strength w_ij / max(D_ii, D_jj);
+//  - X set: LAMG's affinity (Sec. 3.1, affinity-based aggregation) of the
+//    relaxed test vectors, (X_i . X_j)^2 / ((X_i . X_i)(X_j . X_j)), in [0, 1];
+//  - hub_len > 0: a node with more than hub_len neighbours stays a singleton
+//    (it neither proposes, nor is proposed to, nor takes in a leftover).
+constexpr int kTestVecs = 8;
+struct Strength {
+    const float *X;   // [n][kTestVecs], or null
+    int32_t hub_len;  // 0: no hub rule
+};
+__device__ __forceinline__ bool is_hub(const int32_t *rowptr, int32_t i, const Strength &st) {
+    return st.hub_len > 0 && rowptr[i + 1] - rowptr[i] > st.hub_len;
+}
+__device__ __forceinline__ float affinity(const float *X, int32_t i, int32_t j) {
+    float xy = 0.f, xx = 0.f, yy = 0.f;
+#pragma unroll
+    for (int t = 0; t < kTestVecs; ++t) {
+        const float a = __ldg(X + (size_t)i * kTestVecs + t), b = __ldg(X + (size_t)j * kTestVecs + t);
+        xy = fmaf(a, b, xy);
+        xx = fmaf(a, a, xx);
+        yy = fmaf(b, b, yy);
+    }
+    return (xx > 0.f && yy > 0.f) ? (xy * xy) / (xx * yy) : 0.f;
+}
+
 // strongest neighbour of row i among those with (match[j] < 0) == want_unmatched;
 // one warp per row, lanes stride over the row
 __device__ __forceinline__ Cand best_neighbour(const int32_t *rowptr, const int32_t *col, const double *w,
                                                const double *deg, const int32_t *match, int32_t i,
-                                               bool want_unmatched) {
+                                               bool want_unmatched, const Strength &st) {
     const int lane = threadIdx.x & 31;
     const double di = deg[i];
     Cand b{-1.f, 0u, -1};
     for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) {
         const int32_t j = col[e];
-        if ((match[j] < 0) != want_unmatched) continue;
-        Cand c{(float)(w[e] / fmax(di, deg[j])), edge_hash((uint32_t)i, (uint32_t)j), j};
+        if ((match[j] < 0) != want_unmatched || is_hub(rowptr, j, st)) continue;
+        const float sv = st.X ? affinity(st.X, i, j) : (float)(w[e] / fmax(di, deg[j]));
+        Cand c{sv, edge_hash((uint32_t)i, (uint32_t)j), j};
         if (better(c, b)) b = c;
     }
     return warp_best(b);
@@ -105,14 +132,59 @@ __device__ __forceinline__ Cand best_neighbour(const int32_t *rowptr, const int3
 
 __global__ void k_propose(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                           const double *__restrict__ w, const double *__restrict__ deg, int32_t n,
-                          const int32_t *__restrict__ match, int32_t *__restrict__ prop) {
+                          const int32_t *__restrict__ match, int32_t *__restrict__ prop, Strength st) {
     WARP_ROW_LOOP(i, n) {
-        if (match[i] >= 0) {
+        if (match[i] >= 0 || is_hub(rowptr, (int32_t)i, st)) {
             if ((threadIdx.x & 31) == 0) prop[i] = -1;
             continue;
         }
-        const Cand b = best_neighbour(rowptr, col, w, deg, match, (int32_t)i, true);
+        const Cand b = best_neighbour(rowptr, col, w, deg, match, (int32_t)i, true, st);
         if ((threadIdx.x & 31) == 0) prop[i] = b.j;
+    }
+}
+
+// Test vectors of the affinity: kTestVecs vectors with entries from a hash of
+// (node, vector) in [-1, 1), then damped Jacobi sweeps on L x = 0
+// (x <- (1 - omega) x + omega D^{-1} A x), which leave mostly the smooth
+// components the coarse levels must represent.
+__global__ void k_tv_init(int32_t n, float *__restrict__ X) {
+    GRID_LOOP(t, (int64_t)n * kTestVecs) {
+        uint32_t h = (uint32_t)t * 0x9E3779B1u + 0x7F4A7C15u;
+        h ^= h >> 16;
+        h *= 0x85ebca6bu;
+        h ^= h >> 13;
+        h *= 0xc2b2ae35u;
+        h ^= h >> 16;
+        X[t] = (float)(h >> 8) * (1.0f / 8388608.0f) - 1.0f;
+    }
+}
+
+// one warp per row: lanes over the neighbours, a fixed shuffle tree per vector
+__global__ void k_tv_relax(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                          const double *__restrict__ w, const double *__restrict__ deg, int32_t n,
+                          const float *__restrict__ X, float *__restrict__ Xn, float omega) {
+    const int lane = threadIdx.x & 31;
+    WARP_ROW_LOOP(i, n) {
+        float acc[kTestVecs];
+#pragma unroll
+        for (int t = 0; t < kTestVecs; ++t) acc[t] = 0.f;
+        for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) {
+            const float we = (float)w[e];
+            const int32_t j = col[e];
+#pragma unroll
+            for (int t = 0; t < kTestVecs; ++t) acc[t] = fmaf(we, X[(size_t)j * kTestVecs + t], acc[t]);
+        }
+#pragma unroll
+        for (int t = 0; t < kTestVecs; ++t)
+            for (int o = 16; o > 0; o >>= 1) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+        if (lane < kTestVecs) {
+            float a = acc[0];
+#pragma unroll
+            for (int t = 1; t < kTestVecs; ++t)
+                if (lane == t) a = acc[t];
+            const float di = (float)(1.0 / deg[i]);
+            Xn[(size_t)i * kTestVecs + lane] = (1.f - omega) * X[(size_t)i * kTestVecs + lane] + omega * di * a;
+        }
     }
 }
 
@@ -128,14 +200,16 @@ __global__ void k_accept(const int32_t *__restrict__ prop, int32_t n, int32_t *_
 __global__ void k_leaders(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                           const double *__restrict__ w, const double *__restrict__ deg, int32_t n,
                           const int32_t *__restrict__ match, int32_t *__restrict__ leader,
-                          int32_t *__restrict__ is_leader) {
+                          int32_t *__restrict__ is_leader, Strength st) {
     WARP_ROW_LOOP(i, n) {
         const int32_t mi = match[i];
         int32_t l;
         if (mi >= 0) {
             l = min((int32_t)i, mi);
+        } else if (is_hub(rowptr, (int32_t)i, st)) {
+            l = (int32_t)i;  // a hub stays a singleton
         } else {
-            const Cand b = best_neighbour(rowptr, col, w, deg, match, (int32_t)i, false);
+            const Cand b = best_neighbour(rowptr, col, w, deg, match, (int32_t)i, false, st);
             l = b.j >= 0 ? min(b.j, match[b.j]) : (int32_t)i;
         }
         if ((threadIdx.x & 31) == 0) {
@@ -477,18 +551,45 @@ struct Graph64 {
     DBuf<double> w, deg;
 };
 
-// one pairwise-matching pass: agg[n], returns the number of aggregates
+// kTestVecs relaxed test vectors of the graph (rowptr, col, w, deg): hashed
+// start, kTvSweeps damped Jacobi sweeps with omega = 0.7
+constexpr int kTvSweeps = 4;
+DBuf<float> test_vectors(const int32_t *rowptr, const int32_t *col, const double *w, const double *deg, int32_t n,
+                         cudaStream_t s) {
+    DBuf<float> X((size_t)n * kTestVecs, s), Y((size_t)n * kTestVecs, s);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_tv_init, grid_for((int64_t)n * kTestVecs), kBlock, 0, n, X.get());
+    for (int t = 0; t < kTvSweeps; ++t) {
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_tv_relax, grid_for(32 * (int64_t)n), kBlock, 0, rowptr, col, w, deg, n,
+                   X.get(), Y.get(), 0.7f);
+        std::swap(X, Y);
+    }
+    return X;
+}
+
+// one pairwise-matching pass: agg[n], returns the number of aggregates.
+// aggregation: LAP_AGG_STRENGTH or LAP_AGG_AFFINITY; hub_factor > 0: nodes
+// with more than hub_factor x the mean row length stay singletons.
 int32_t pairwise_pass(const int32_t *rowptr, const int32_t *col, const double *w, const double *deg, int32_t n,
-                      int rounds, int32_t *agg, cudaStream_t s) {
+                      int64_t nnz, int rounds, int aggregation, int hub_factor, int32_t *agg, cudaStream_t s) {
     DBuf<int32_t> match(n, s), prop(n, s), leader(n, s), isl(n, s), lid(n, s);
+    DBuf<float> X;
+    Strength st{nullptr, 0};
+    if (hub_factor > 0 && n > 0) {
+        const double len = (double)hub_factor * (double)nnz / (double)n;
+        st.hub_len = (int32_t)std::min<double>(std::max(1.0, std::ceil(len)), 2e9);
+    }
+    if (aggregation == LAP_AGG_AFFINITY && n > 0) {
+        X = test_vectors(rowptr, col, w, deg, n, s);
+        st.X = X.get();
+    }
     CFC_CUDA(cudaMemsetAsync(match.get(), 0xff, n * sizeof(int32_t), s));
     for (int r = 0; r < rounds; ++r) {
         CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_propose, grid_for(32 * (int64_t)n), kBlock, 0, rowptr, col, w, deg, n,
-                   match.get(), prop.get());
+                   match.get(), prop.get(), st);
         CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_accept, grid_for(n), kBlock, 0, prop.get(), n, match.get());
     }
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_leaders, grid_for(32 * (int64_t)n), kBlock, 0, rowptr, col, w, deg, n,
-               match.get(), leader.get(), isl.get());
+               match.get(), leader.get(), isl.get(), st);
     const int64_t nc = scan_exclusive_i32(isl.get(), lid.get(), n, s);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_assign, grid_for(n), kBlock, 0, leader.get(), lid.get(), n, agg);
     return (int32_t)nc;
@@ -1093,14 +1194,15 @@ void grow_levels(lap_hierarchy &h, int target, cudaStream_t s) {
         const int32_t n = F.n;
         DBuf<int32_t> agg;
         agg.alloc_persistent(n);
-        int32_t nc = pairwise_pass(F.rowptr.get(), F.col.get(), F.w64.get(), F.deg64.get(), n,
-                                   std::max(1, o.match_rounds), agg.get(), s);
+        int32_t nc = pairwise_pass(F.rowptr.get(), F.col.get(), F.w64.get(), F.deg64.get(), n, F.nnz,
+                                   std::max(1, o.match_rounds), o.aggregation, o.hub_factor, agg.get(), s);
         for (int p = 1; p < o.agg_passes && nc > coarse_max; ++p) {
             Graph64 mid;
             contract(F.rowptr.get(), F.col.get(), F.w64.get(), n, F.nnz, agg.get(), nc, false, mid, s);
             DBuf<int32_t> agg2(nc, s);
             const int32_t nc2 = pairwise_pass(mid.rowptr.get(), mid.col.get(), mid.w.get(), mid.deg.get(), nc,
-                                              std::max(1, o.match_rounds), agg2.get(), s);
+                                              mid.nnz, std::max(1, o.match_rounds), o.aggregation, o.hub_factor,
+                                              agg2.get(), s);
             CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_compose, grid_for(n), kBlock, 0, agg.get(), agg2.get(), n);
             nc = nc2;
         }

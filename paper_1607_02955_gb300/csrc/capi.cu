@@ -217,6 +217,8 @@ void lap_default_hier_opts(lap_hier_opts_t *o) {
     o->eager = 0;
     o->eliminate = 1;
     o->reorder = 0;
+    o->aggregation = LAP_AGG_STRENGTH;
+    o->hub_factor = 0;
 }
 
 void lap_default_solve_opts(lap_solve_opts_t *o) {
@@ -267,6 +269,9 @@ lap_status_t lap_build_hierarchy(int64_t n, int64_t m, const int32_t *src, const
         CFC_REQUIRE(o.agg_passes >= 1 && o.agg_passes <= 4, LAP_EINVAL, "agg_passes must be 1..4");
         CFC_REQUIRE(o.eliminate == 0 || o.eliminate == 1, LAP_EINVAL, "eliminate must be 0 or 1");
         CFC_REQUIRE(o.reorder >= 0 && o.reorder <= 2, LAP_EINVAL, "reorder must be 0, 1 or 2");
+        CFC_REQUIRE(o.aggregation == LAP_AGG_STRENGTH || o.aggregation == LAP_AGG_AFFINITY, LAP_EINVAL,
+                    "aggregation must be LAP_AGG_STRENGTH or LAP_AGG_AFFINITY");
+        CFC_REQUIRE(o.hub_factor >= 0 && o.hub_factor <= 1000000, LAP_EINVAL, "hub_factor must be in [0, 1e6]");
         cudaStream_t s = (cudaStream_t)stream;
         auto *h = new lap_hierarchy();
         try {

@@ -13,6 +13,9 @@
   farness of c w is the farness of w over c); weights spanning 80 orders of
   magnitude either converge or report LAP_ENOCONV, never LAP_OK with a
   non-finite value.
+* The aggregation options of Sec. 3.1 (LAMG's affinity-based aggregation,
+  and hubs kept out of aggregates): every combination gives the oracle's
+  answer; the hub rule does what it says on a star.
 """
 import numpy as np
 import pytest
@@ -225,3 +228,57 @@ def test_rmat_farness_with_and_without_elimination(P, rmat14, eliminate, precisi
     f = P.cfc_farness_jl(h, 48, 8, nodes, opts=P.lap_default_solve_opts(**PRECISIONS[precision]))
     fo = jl.jl_farness(g, 48, 8, nodes.tolist(), solver="cg", tol=1e-12)
     assert _rel(f, fo) <= FARNESS_RTOL
+
+
+# ------------------------------------------------------------------ aggregation: affinity, hub rule (Sec. 3.1)
+AGGREGATIONS = {"strength": dict(aggregation=0), "affinity": dict(aggregation=1),
+                "strength_hubs": dict(aggregation=0, hub_factor=4),
+                "affinity_hubs": dict(aggregation=1, hub_factor=4)}
+
+
+@pytest.mark.parametrize("agg", sorted(AGGREGATIONS))
+@pytest.mark.parametrize("precision", ["fp32_all_levels", "fp64_all_levels", "bf16coarse"])
+def test_rmat_farness_with_each_aggregation(P, rmat14, agg, precision):
+    n, s, d, w, g = rmat14
+    h = P.lap_build_hierarchy(n, s, d, w, P.lap_default_hier_opts(eager=1, **AGGREGATIONS[agg]))
+    assert P.lap_hierarchy_info(h)["levels"] >= 3
+    hub = int(np.argmax(np.bincount(np.concatenate([s, d]))))
+    nodes = np.array([1, hub, n - 2], np.int32)
+    f = P.cfc_farness_jl(h, 32, 6, nodes, opts=P.lap_default_solve_opts(**PRECISIONS[precision]))
+    fo = jl.jl_farness(g, 32, 6, nodes.tolist(), solver="cg", tol=1e-12)
+    assert _rel(f, fo) <= FARNESS_RTOL
+
+
+@pytest.mark.parametrize("agg", sorted(AGGREGATIONS))
+def test_grid_solve_with_each_aggregation(P, agg):
+    import torch
+    n, s, d, _ = synth.grid2d(90, 70)
+    w = synth.uniform_weights(s.size, seed=4)
+    h = P.lap_build_hierarchy(n, s, d, w, P.lap_default_hier_opts(coarse_max=64, **AGGREGATIONS[agg]))
+    B = np.random.default_rng(8).standard_normal((n, 24))
+    X = torch.empty((n, 24), dtype=torch.float64, device="cuda")
+    info = P.lap_solve_multi(h, torch.tensor(B, device="cuda"), X, P.lap_default_solve_opts(precision=1, levels_used=-1))
+    assert info["max_rel_residual"] <= 1e-8
+    assert P.lap_hierarchy_info(h)["levels"] >= 4  # coarsening went on to the coarse_max cap
+    _certify(canonical_graph(n, s, d, w), B, X.cpu().numpy())
+
+
+@pytest.mark.parametrize("aggregation", [0, 1])
+def test_hub_rule_keeps_a_star_centre_out_of_every_aggregate(P, aggregation):
+    # a star without elimination: the centre's only neighbours are leaves, and
+    # a leaf's only neighbour is the centre.  With the hub rule the centre
+    # stays a singleton and so does every leaf: coarsening stalls at one
+    # level.  Without it the pairwise matching merges the star.
+    n, s, d, _ = synth.star_graph(3000)
+    ho = dict(eliminate=0, coarse_max=16, eager=1, aggregation=aggregation)
+    with_rule = P.lap_hierarchy_info(P.lap_build_hierarchy(n, s, d, None, P.lap_default_hier_opts(hub_factor=8, **ho)))
+    without = P.lap_hierarchy_info(P.lap_build_hierarchy(n, s, d, None, P.lap_default_hier_opts(**ho)))
+    assert with_rule["levels"] == 1
+    assert without["levels"] >= 2 and without["level_n"][1] < n // 2
+
+
+def test_aggregation_options_are_validated(P):
+    n, s, d, _ = synth.grid2d(8)
+    for bad in (dict(aggregation=2), dict(aggregation=-1), dict(hub_factor=-1), dict(hub_factor=2000000)):
+        with pytest.raises(P.LapError):
+            P.lap_build_hierarchy(n, s, d, None, P.lap_default_hier_opts(**bad))
