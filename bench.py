@@ -863,7 +863,7 @@ def main():
     ap.add_argument("--levels", type=int, default=None,
                     help="levels_used of the V-cycle (default: autotuned; -1: every level)")
     ap.add_argument("--coarse-max", type=int, default=None,
-                    help="hierarchy option coarse_max (default: the library's, 1024)")
+                    help="hierarchy option coarse_max (default 0: automatic, n / 4096 in [256, 1024])")
     ap.add_argument("--aggregation", default=None, choices=["strength", "affinity"],
                     help="hierarchy option aggregation (default: strength)")
     ap.add_argument("--hub-factor", type=int, default=None,

@@ -87,9 +87,12 @@ enum { LAP_SMOOTH_JACOBI = 0, LAP_SMOOTH_CHEBYSHEV = 1 };
 enum { LAP_AGG_STRENGTH = 0, LAP_AGG_AFFINITY = 1 };
 
 typedef struct {
-    int32_t coarse_max;   /* stop coarsening at n_l <= coarse_max (default 1024, at most 2048);
+    int32_t coarse_max;   /* stop coarsening at n_l <= coarse_max (values above 2048 act as 2048);
                              the coarsest level (at most 2048 nodes) is solved with a dense
-                             inverse, FP64 in LAP_FP64 and an FP32 copy in the FP32 modes */
+                             inverse, FP64 in LAP_FP64 and an FP32 copy in the FP32 modes.
+                             0 (default): automatic, n_top / 4096 clamped to [256, 1024] with
+                             n_top the size of the level the PCG runs on (the dense inverse is
+                             built in every setup, so small graphs keep it small) */
     int32_t max_levels;   /* cap on levels incl. the finest (default 24); 1 = no coarsening */
     int32_t agg_passes;   /* pairwise-matching passes per level (default 2: aggregates of ~4) */
     int32_t match_rounds; /* handshake rounds per pass (default 4) */

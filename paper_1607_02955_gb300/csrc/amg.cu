@@ -425,6 +425,14 @@ __global__ void k_chunk_keys(const int32_t *__restrict__ col, const int32_t *__r
     }
 }
 
+// chunks of each row of (rowptr, n): rows longer than kLongRow take ceil(len / kChunk)
+__global__ void k_nchunk(const int32_t *__restrict__ rowptr, int32_t n, int32_t *__restrict__ nchunk) {
+    GRID_LOOP(i, n) {
+        const int len = rowptr[i + 1] - rowptr[i];
+        nchunk[i] = len > kLongRow ? (len + kChunk - 1) / kChunk : 0;
+    }
+}
+
 __global__ void k_long_index(const int32_t *__restrict__ nchunk, int32_t n, int32_t *__restrict__ is_long) {
     GRID_LOOP(i, n) is_long[i] = nchunk[i] > 0 ? 1 : 0;
 }
@@ -499,46 +507,141 @@ __global__ void __launch_bounds__(1024) k_gj_smem(double *__restrict__ A, int n,
     for (int t = threadIdx.x; t < n * n; t += blockDim.x) A[t] = a[t];
 }
 
-// Gauss-Jordan in global memory in one cooperative launch, one grid barrier
-// per pivot.  Step k scales the pivot row by 1/a_kk and eliminates column k
-// from every other row (as the shared-memory version does); the threads that
-// update row k+1 and column k+1 also
-// write them to the other half of the double-buffered pivot row and column,
-// so the next step needs no separate pivot phase.  Every thread reads the
-// same pivot, so a non-positive one makes them all return together.
-__global__ void __launch_bounds__(256) k_gj_coop(double *__restrict__ A, int n, double *__restrict__ rows,
-                                                 double *__restrict__ cols, int *__restrict__ flag) {
+// Blocked Gauss-Jordan in global memory, one cooperative launch.  The
+// pivots are taken kGjB at a time; with K the block's index range, P = A[K,K],
+// C = A[:,K] (before the step) and R = P^-1 A[K,:], one block step sets
+//   A[K,K] = P^-1,  A[K,J] = R[:,J],  A[I,K] = -C[I,:] P^-1,
+//   A[I,J] -= C[I,:] R[:,J]                      (I, J outside K),
+// which is kGjB single-pivot Gauss-Jordan steps at once.  Each step has three
+// phases separated by grid barriers: (A) one warp inverts P in registers
+// while all blocks copy C; (B) R; (C) the update in 64 x 64 tiles.  The
+// matrix is SPD, so every pivot is positive in exact arithmetic; a pivot that
+// is not (lost definiteness in floating point, or NaN) sets *flag, and every
+// block reads the flag after the next barrier and returns with the others.
+constexpr int kGjB = 32;
+constexpr int kGjTile = 64;
+static_assert(kBlock == 256, "k_gj_blocked maps 256 threads to 16 x 16 groups of 4 x 4 outputs");
+
+__global__ void __launch_bounds__(256) k_gj_blocked(double *__restrict__ A, int n, double *__restrict__ Pinv,
+                                                    double *__restrict__ Cold, double *__restrict__ Rnew,
+                                                    int *__restrict__ flag) {
     namespace cg = cooperative_groups;
     cg::grid_group g = cg::this_grid();
-    const int64_t nt = (int64_t)g.size(), tid = (int64_t)g.thread_rank();
-    const int64_t nn = (int64_t)n * n;
-    for (int64_t t = tid; t < n; t += nt) {  // pivot 0's row and column
-        rows[t] = A[t];
-        cols[t] = A[t * n];
-    }
-    g.sync();
-    for (int k = 0; k < n; ++k) {
-        const double *rk = rows + (size_t)(k & 1) * n, *ck = cols + (size_t)(k & 1) * n;
-        double *rn = rows + (size_t)((k + 1) & 1) * n, *cn = cols + (size_t)((k + 1) & 1) * n;
-        const double akk = rk[k];
-        if (!(akk > 0.0)) {
-            if (tid == 0) atomicOr(flag, 1);
-            return;
-        }
-        const double piv = 1.0 / akk;
-        for (int64_t t = tid; t < nn; t += nt) {
-            const int64_t i = t / n, j = t - i * n;
-            const double rowkj = (j == k ? 1.0 : rk[j]) * piv;
-            double v;
-            if (i == k) {
-                v = rowkj;
-            } else {
-                const double cur = (j == k) ? 0.0 : A[t];
-                v = cur - ((i == k) ? 0.0 : ck[i]) * rowkj;
+    __shared__ double Cs[kGjTile][kGjB + 1];
+    __shared__ double Rs[kGjB][kGjTile];
+    double(*Ps)[kGjB + 1] = Cs;  // phase B reuses the tile buffer for P^-1
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int64_t gt = (int64_t)g.thread_rank(), gn = (int64_t)g.size();
+    const int nb = (n + kGjB - 1) / kGjB;
+    const int td = (n + kGjTile - 1) / kGjTile;
+    for (int kb = 0; kb < nb; ++kb) {
+        const int k0 = kb * kGjB, bk = min(kGjB, n - k0);
+        // ---- A: P^-1 by warp 0 of block 0 (lane j holds column j; P padded with
+        // the identity beyond bk), and C = A[:, K] by everyone
+        if (blockIdx.x == 0 && tid < 32) {
+            double p[kGjB];
+#pragma unroll
+            for (int i = 0; i < kGjB; ++i)
+                p[i] = (i < bk && lane < bk) ? A[(size_t)(k0 + i) * n + k0 + lane] : (i == lane ? 1.0 : 0.0);
+            bool ok = true;
+#pragma unroll
+            for (int q = 0; q < kGjB; ++q) {
+                const double akk = __shfl_sync(0xffffffffu, p[q], q);
+                ok = ok && (akk > 0.0);
+                const double inv = 1.0 / akk;
+                const double rowq = (lane == q ? 1.0 : p[q]) * inv;
+#pragma unroll
+                for (int i = 0; i < kGjB; ++i) {
+                    if (i == q) continue;
+                    const double ciq = __shfl_sync(0xffffffffu, p[i], q);
+                    p[i] = (lane == q ? 0.0 : p[i]) - ciq * rowq;
+                }
+                p[q] = rowq;
             }
-            A[t] = v;
-            if (i == k + 1) rn[j] = v;
-            if (j == k + 1) cn[i] = v;
+            if (!ok) {
+                if (lane == 0) atomicOr(flag, 1);
+            } else {
+#pragma unroll
+                for (int i = 0; i < kGjB; ++i) Pinv[i * kGjB + lane] = p[i];
+            }
+        }
+        for (int64_t t = gt; t < (int64_t)n * kGjB; t += gn) {
+            const int64_t i = t / kGjB;
+            const int b = (int)(t - i * kGjB);
+            Cold[t] = b < bk ? A[(size_t)i * n + k0 + b] : 0.0;
+        }
+        g.sync();
+        if (*(volatile int *)flag) return;  // the same value in every block
+        // ---- B: R = P^-1 A[K, :] (on K's own columns: P^-1 itself)
+        for (int t = tid; t < kGjB * kGjB; t += blockDim.x) Ps[t / kGjB][t % kGjB] = Pinv[t];
+        __syncthreads();
+        for (int64_t j = gt; j < n; j += gn) {
+            if (j >= k0 && j < k0 + bk) {
+#pragma unroll 4
+                for (int b = 0; b < kGjB; ++b) Rnew[(size_t)b * n + j] = Ps[b][j - k0];
+            } else {
+                double a[kGjB];
+#pragma unroll
+                for (int c = 0; c < kGjB; ++c) a[c] = c < bk ? A[(size_t)(k0 + c) * n + j] : 0.0;
+#pragma unroll 4
+                for (int b = 0; b < kGjB; ++b) {
+                    double v = 0.0;
+#pragma unroll
+                    for (int c = 0; c < kGjB; ++c) v = fma(Ps[b][c], a[c], v);
+                    Rnew[(size_t)b * n + j] = v;
+                }
+            }
+        }
+        g.sync();
+        // ---- C: the update, 64 x 64 tiles, 4 x 4 outputs per thread
+        const int ty = tid / 16, tx = tid % 16;
+        for (int tile = blockIdx.x; tile < td * td; tile += gridDim.x) {
+            const int i0 = (tile / td) * kGjTile, j0 = (tile % td) * kGjTile;
+            __syncthreads();
+            for (int t = tid; t < kGjTile * kGjB; t += blockDim.x) {
+                const int r = t / kGjB, b = t % kGjB;
+                Cs[r][b] = i0 + r < n ? Cold[(size_t)(i0 + r) * kGjB + b] : 0.0;
+            }
+            for (int t = tid; t < kGjB * kGjTile; t += blockDim.x) {
+                const int b = t / kGjTile, c = t % kGjTile;
+                Rs[b][c] = j0 + c < n ? Rnew[(size_t)b * n + j0 + c] : 0.0;
+            }
+            __syncthreads();
+            double acc[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+#pragma unroll 8
+            for (int b = 0; b < kGjB; ++b) {
+                double cv[4], rv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) cv[u] = Cs[ty + 16 * u][b];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) rv[v] = Rs[b][tx + 16 * v];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] = fma(cv[u], rv[v], acc[u][v]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + ty + 16 * u;
+                if (i >= n) continue;
+                const bool iK = i >= k0 && i < k0 + bk;
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int j = j0 + tx + 16 * v;
+                    if (j >= n) continue;
+                    double *aij = A + (size_t)i * n + j;
+                    if (iK) {
+                        *aij = Rs[i - k0][tx + 16 * v];
+                    } else {
+                        const bool jK = j >= k0 && j < k0 + bk;
+                        *aij = (jK ? 0.0 : *aij) - acc[u][v];
+                    }
+                }
+            }
         }
         g.sync();
     }
@@ -735,17 +838,15 @@ __global__ void k_elim_tables(const int32_t *__restrict__ rowptr, const int32_t 
 
 // entries of the next level between two kept nodes: a flag per entry, and
 // the entry's column at the next level (keep_id is read once per entry)
-__global__ void k_keep_flags(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, int32_t n,
+// per entry of G (one thread each): kept at the next level when both ends are
+// kept, and its column's next-level id
+__global__ void k_keep_flags(const int32_t *__restrict__ row_of, const int32_t *__restrict__ col, int64_t nnz,
                              const int32_t *__restrict__ keep_id, int32_t *__restrict__ flag,
                              int32_t *__restrict__ newcol) {
-    const int lane = threadIdx.x & 31;
-    WARP_ROW_LOOP(i, n) {
-        const bool ki = keep_id[i] >= 0;
-        for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) {
-            const int32_t c = keep_id[col[e]];
-            flag[e] = (ki && c >= 0) ? 1 : 0;
-            newcol[e] = c;
-        }
+    GRID_LOOP(e, nnz) {
+        const int32_t c = keep_id[col[e]];
+        flag[e] = (keep_id[row_of[e]] >= 0 && c >= 0) ? 1 : 0;
+        newcol[e] = c;
     }
 }
 
@@ -775,20 +876,25 @@ __global__ void k_elim_emit_fill(const int32_t *__restrict__ e_nb, const int32_t
 // their own and merged with equal fills summed (ucol, uw, rows at fptr); then
 // each row's fills are merged into its kept run: a fill whose column the row
 // already has adds its weight there, the others are inserted in order.
-__global__ void k_elim_compact(const int32_t *__restrict__ rowptr, const double *__restrict__ w, int32_t n,
-                               const int32_t *__restrict__ elim, const int32_t *__restrict__ kidx,
-                               const int32_t *__restrict__ flag, const int32_t *__restrict__ pos,
-                               const int32_t *__restrict__ newcol, int32_t *__restrict__ kcol,
-                               double *__restrict__ kw, int32_t *__restrict__ kstart) {
-    const int lane = threadIdx.x & 31;
-    WARP_ROW_LOOP(i, n) {
-        if (elim[i]) continue;
-        if (lane == 0) kstart[kidx[i]] = pos[rowptr[i]];
-        for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) {
-            if (!flag[e]) continue;
-            kcol[pos[e]] = newcol[e];
-            kw[pos[e]] = w[e];
-        }
+__global__ void k_elim_compact(const int32_t *__restrict__ row_of, const double *__restrict__ w, int64_t nnz,
+                               const int32_t *__restrict__ kidx, const int32_t *__restrict__ flag,
+                               const int32_t *__restrict__ pos, const int32_t *__restrict__ newcol,
+                               int32_t *__restrict__ kcol, double *__restrict__ kw, int32_t *__restrict__ krow) {
+    GRID_LOOP(e, nnz) {
+        if (!flag[e]) continue;
+        const int32_t p = pos[e];
+        kcol[p] = newcol[e];
+        kw[p] = w[e];
+        krow[p] = kidx[row_of[e]];
+    }
+}
+
+// where each next-level row's kept entries start (every row of G has an entry)
+__global__ void k_elim_kstart(const int32_t *__restrict__ rowptr, int32_t n, const int32_t *__restrict__ elim,
+                              const int32_t *__restrict__ kidx, const int32_t *__restrict__ pos,
+                              int32_t *__restrict__ kstart) {
+    GRID_LOOP(i, n) {
+        if (!elim[i]) kstart[kidx[i]] = pos[rowptr[i]];
     }
 }
 
@@ -822,24 +928,44 @@ __global__ void k_elim_row_len(const int32_t *__restrict__ kstart, const int32_t
     GRID_LOOP(I, nk) len[I] = (kstart[I + 1] - kstart[I]) + (fnew_pref[fptr[I + 1]] - fnew_pref[fptr[I]]);
 }
 
-__global__ void k_elim_write(const int32_t *__restrict__ kcol, const double *__restrict__ kw,
-                             const int32_t *__restrict__ kstart, const int32_t *__restrict__ ucol,
-                             const double *__restrict__ uw, const int32_t *__restrict__ fptr,
-                             const int32_t *__restrict__ fnew, const int32_t *__restrict__ fnew_pref,
-                             const int32_t *__restrict__ rowptr_n, int32_t nk, int32_t *__restrict__ col_n,
-                             double *__restrict__ w_n) {
+// the kept entries at their place in the next level's rows (one thread each):
+// after the row's inserted fills with a smaller column, with the weights of
+// equal fills added
+__global__ void k_elim_write_kept(const int32_t *__restrict__ kcol, const double *__restrict__ kw,
+                                  const int32_t *__restrict__ krow, int64_t nkept,
+                                  const int32_t *__restrict__ kstart, const int32_t *__restrict__ ucol,
+                                  const double *__restrict__ uw, const int32_t *__restrict__ fptr,
+                                  const int32_t *__restrict__ fnew_pref, const int32_t *__restrict__ rowptr_n,
+                                  int32_t *__restrict__ col_n, double *__restrict__ w_n) {
+    GRID_LOOP(t, nkept) {
+        const int32_t I = krow[t];
+        const int f0 = fptr[I], f1 = fptr[I + 1];
+        const int32_t c = kcol[t];
+        double wt = kw[t];
+        int ins = 0;
+        if (f0 < f1) {
+            const int p = lower_bound_i32(ucol, f0, f1, c);  // fills with a smaller column
+            if (p < f1 && ucol[p] == c) wt += uw[p];         // the kept weight, then the fills' sum
+            ins = fnew_pref[p] - fnew_pref[f0];
+        }
+        const int64_t o = (int64_t)rowptr_n[I] + (t - kstart[I]) + ins;
+        col_n[o] = c;
+        w_n[o] = wt;
+    }
+}
+
+// the inserted fills (one warp per next-level row; rows without fills skip)
+__global__ void k_elim_write_fills(const int32_t *__restrict__ kcol, const int32_t *__restrict__ kstart,
+                                   const int32_t *__restrict__ ucol, const double *__restrict__ uw,
+                                   const int32_t *__restrict__ fptr, const int32_t *__restrict__ fnew,
+                                   const int32_t *__restrict__ fnew_pref, const int32_t *__restrict__ rowptr_n,
+                                   int32_t nk, int32_t *__restrict__ col_n, double *__restrict__ w_n) {
     const int lane = threadIdx.x & 31;
     WARP_ROW_LOOP(I, nk) {
-        const int k0 = kstart[I], k1 = kstart[I + 1], f0 = fptr[I], f1 = fptr[I + 1];
+        const int f0 = fptr[I], f1 = fptr[I + 1];
+        if (f0 == f1) continue;
+        const int k0 = kstart[I], k1 = kstart[I + 1];
         const int base = rowptr_n[I];
-        for (int t = k0 + lane; t < k1; t += 32) {
-            const int32_t c = kcol[t];
-            const int p = lower_bound_i32(ucol, f0, f1, c);  // fills with a smaller column
-            double wt = kw[t];
-            if (p < f1 && ucol[p] == c) wt += uw[p];     // the kept weight, then the fills' sum
-            col_n[base + (t - k0) + (fnew_pref[p] - fnew_pref[f0])] = c;
-            w_n[base + (t - k0) + (fnew_pref[p] - fnew_pref[f0])] = wt;
-        }
         for (int f = f0 + lane; f < f1; f += 32) {
             if (!fnew[f]) continue;
             const int q = lower_bound_i32(kcol, k0, k1, ucol[f]) - k0;  // kept entries with a smaller column
@@ -1008,8 +1134,8 @@ bool eliminate_level(lap_hierarchy &h, double min_frac, cudaStream_t s) {
     // next-level entries: the kept ones (already in order), merged row by row
     // with the fill edges (sorted and summed on their own)
     DBuf<int32_t> flag(F.nnz, s), pos(F.nnz, s), newcol(F.nnz, s);
-    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_keep_flags, grid_for(32 * (int64_t)n), kBlock, 0, F.rowptr.get(), F.col.get(),
-               n, F.keep_id.get(), flag.get(), newcol.get());
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_keep_flags, grid_for(F.nnz), kBlock, 0, F.row_of.get(), F.col.get(), F.nnz,
+               F.keep_id.get(), flag.get(), newcol.get());
     DBuf<int64_t> tot2(3, s);
     tot2.zero(s);
     scan_exclusive_i32_total(flag.get(), pos.get(), F.nnz, tot2.get(), s);
@@ -1024,11 +1150,12 @@ bool eliminate_level(lap_hierarchy &h, double min_frac, cudaStream_t s) {
     C.rowptr.alloc_persistent(nk + 1);
     C.deg.alloc_persistent(nk);
     {
-        DBuf<int32_t> kcol(std::max<int64_t>(nkept, 1), s), kstart(nk + 1, s);
+        DBuf<int32_t> kcol(std::max<int64_t>(nkept, 1), s), krow(std::max<int64_t>(nkept, 1), s), kstart(nk + 1, s);
         DBuf<double> kw(std::max<int64_t>(nkept, 1), s);
-        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_elim_compact, grid_for(32 * (int64_t)n), kBlock, 0, F.rowptr.get(),
-                   F.w64.get(), n, elim.get(), kidx.get(), flag.get(), pos.get(), newcol.get(), kcol.get(), kw.get(),
-                   kstart.get());
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_elim_compact, grid_for(F.nnz), kBlock, 0, F.row_of.get(), F.w64.get(),
+                   F.nnz, kidx.get(), flag.get(), pos.get(), newcol.get(), kcol.get(), kw.get(), krow.get());
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_elim_kstart, grid_for(n), kBlock, 0, F.rowptr.get(), n, elim.get(),
+                   kidx.get(), pos.get(), kstart.get());
         CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_set_last, 1, 1, 0, kstart.get(), nk, (int32_t)nkept);
         flag.release();
         pos.release();
@@ -1066,7 +1193,10 @@ bool eliminate_level(lap_hierarchy &h, double min_frac, cudaStream_t s) {
         C.nnz = cnnz;
         C.col.alloc_persistent(std::max<int64_t>(cnnz, 1));
         C.w.alloc_persistent(std::max<int64_t>(cnnz, 1));
-        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_elim_write, grid_for(32 * (int64_t)nk), kBlock, 0, kcol.get(), kw.get(),
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_elim_write_kept, grid_for(nkept), kBlock, 0, kcol.get(), kw.get(),
+                   krow.get(), nkept, kstart.get(), ucol.get(), uw.get(), fptr.get(), fnew_pref.get(),
+                   C.rowptr.get(), C.col.get(), C.w.get());
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_elim_write_fills, grid_for(32 * (int64_t)nk), kBlock, 0, kcol.get(),
                    kstart.get(), ucol.get(), uw.get(), fptr.get(), fnew.get(), fnew_pref.get(), C.rowptr.get(), nk,
                    C.col.get(), C.w.get());
         CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_row_sums, grid_for(32 * (int64_t)nk), kBlock, 0, C.rowptr.get(),
@@ -1093,6 +1223,30 @@ bool eliminate_level(lap_hierarchy &h, double min_frac, cudaStream_t s) {
         CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_elim_pull_direct, grid_for(npull), kBlock, 0, F.pull_e.get(), npull,
                    F.e_node.get(), F.e_c64.get(), F.e_c32.get(), F.pull_u.get(), F.pull_c64.get(),
                    F.pull_c32.get());
+        // long pull lists (hubs with many eliminated neighbours) in chunks, like long rows
+        DBuf<int32_t> nchunk(nk, s), cfirst(nk, s), isl(nk, s), lidx(nk, s);
+        DBuf<int64_t> ct(2, s);
+        ct.zero(s);
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_nchunk, grid_for(nk), kBlock, 0, F.pull_ptr.get(), nk, nchunk.get());
+        scan_exclusive_i32_total(nchunk.get(), cfirst.get(), nk, ct.get(), s);
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_long_index, grid_for(nk), kBlock, 0, nchunk.get(), nk, isl.get());
+        scan_exclusive_i32_total(isl.get(), lidx.get(), nk, ct.get() + 1, s);
+        int64_t hc[2];
+        read_totals(ct.get(), 2, hc, s);
+        F.pull_n_chunks = (int32_t)hc[0];
+        F.pull_n_long = (int32_t)hc[1];
+        if (F.pull_n_chunks > 0) {
+            F.pull_chunk_row.alloc_persistent(F.pull_n_chunks);
+            F.pull_chunk_begin.alloc_persistent(F.pull_n_chunks);
+            F.pull_chunk_long.alloc_persistent(F.pull_n_chunks);
+            F.pull_long_first.alloc_persistent(F.pull_n_long + 1);
+            F.pull_long_of_row.alloc_persistent(nk);
+            CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_fill_chunks, grid_for(nk), kBlock, 0, F.pull_ptr.get(), nchunk.get(),
+                       cfirst.get(), lidx.get(), nk, F.pull_chunk_row.get(), F.pull_chunk_begin.get(),
+                       F.pull_chunk_long.get(), F.pull_long_first.get(), F.pull_long_of_row.get());
+            CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_set_last, 1, 1, 0, F.pull_long_first.get(), F.pull_n_long,
+                       F.pull_n_chunks);
+        }
     }
     Level Cl;
     Cl.n = nk;
@@ -1122,19 +1276,20 @@ void dense_spd_inverse_small(double *A, int n, int *d_flag, cudaStream_t s) {
 }
 
 void dense_spd_inverse_large(double *A, int n, int *d_flag, cudaStream_t s) {
-    DBuf<double> rows(2 * (size_t)n, s), cols(2 * (size_t)n, s);
+    DBuf<double> pinv((size_t)kGjB * kGjB, s), cold((size_t)n * kGjB, s), rnew((size_t)kGjB * n, s);
     int per_sm = 0;
-    CFC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_coop, kBlock, 0));
+    CFC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_blocked, kBlock, 0));
     int dev = 0, sms = 0;
     CFC_CUDA(cudaGetDevice(&dev));
     CFC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t want = ((int64_t)n * n + kBlock - 1) / kBlock;
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(1, per_sm) * sms, want));
-    double *a = A, *r = rows.get(), *c = cols.get();
+    const int64_t td = (n + kGjTile - 1) / kGjTile;
+    // every block must be resident (grid barriers): at most the co-resident count
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(1, per_sm) * sms, td * td));
+    double *a = A, *pi = pinv.get(), *co = cold.get(), *rn = rnew.get();
     int nn = n, *f = d_flag;
-    void *args[] = {&a, &nn, &r, &c, &f};
+    void *args[] = {&a, &nn, &pi, &co, &rn, &f};
     ::cfc::LaunchScope scope_(LAP_KF_SETUP, s, 0.0);
-    CFC_CUDA(cudaLaunchCooperativeKernel((const void *)k_gj_coop, blocks, kBlock, args, 0, s));
+    CFC_CUDA(cudaLaunchCooperativeKernel((const void *)k_gj_blocked, blocks, kBlock, args, 0, s));
 }
 
 void build_dense(const int32_t *rowptr, const int32_t *col, const double *w, const double *deg, int32_t n,
@@ -1154,6 +1309,7 @@ void init_levels(lap_hierarchy &h, Csr64 &fine, const lap_hier_opts_t &o, cudaSt
     L0.col = std::move(fine.col);
     L0.w64 = std::move(fine.w);
     L0.deg64 = std::move(fine.deg);
+    L0.row_of = std::move(fine.row_of);
     h.hopts = o;
     h.complete = false;
     h.coarse_n = 0;
@@ -1163,8 +1319,21 @@ void init_levels(lap_hierarchy &h, Csr64 &fine, const lap_hier_opts_t &o, cudaSt
     h.p0 = 0;
     // low-degree elimination when it removes at least 5 % of the nodes
     if (o.eliminate && L0.n > 256 && eliminate_level(h, 0.05, s)) h.p0 = 1;
+    h.lv[0].row_of.release();
     const Level &T = h.lv.back();
-    if (T.n <= std::min(kDenseMax, std::max(2, o.coarse_max)) || o.max_levels <= 1) grow_levels(h, 0, s);
+    if (T.n <= effective_coarse_max(h) || o.max_levels <= 1) grow_levels(h, 0, s);
+}
+
+// coarse_max in effect: the option, or (0) n_top / 4096 clamped to [256, 1024]
+// with n_top the PCG level's size; at most kDenseMax
+int effective_coarse_max(const lap_hierarchy &h) {
+    const int o = h.hopts.coarse_max;
+    int c = o;
+    if (o <= 0) {
+        const int64_t ntop = h.lv[h.p0].n;
+        c = (int)std::min<int64_t>(1024, std::max<int64_t>(256, ntop / 4096));
+    }
+    return std::min(kDenseMax, std::max(2, c));
 }
 
 // Coarsen until the hierarchy has `target` levels (0: until coarsening stops:
@@ -1173,7 +1342,7 @@ void init_levels(lap_hierarchy &h, Csr64 &fine, const lap_hier_opts_t &o, cudaSt
 void grow_levels(lap_hierarchy &h, int target, cudaStream_t s) {
     if (h.complete) return;
     const lap_hier_opts_t &o = h.hopts;
-    const int coarse_max = std::min(kDenseMax, std::max(2, o.coarse_max));
+    const int coarse_max = effective_coarse_max(h);
     const int max_levels = std::max(1, std::min(32, o.max_levels));
     bool stalled = false;
     cudaEvent_t ev0, ev1;

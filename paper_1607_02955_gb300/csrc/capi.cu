@@ -182,6 +182,23 @@ LevelView view_bf16(const Level &L) {
     return v;
 }
 
+LevelView pull_view(const Level &E) {
+    LevelView v{};
+    v.n = E.pull_ptr.get() ? (int32_t)(E.pull_ptr.n - 1) : 0;
+    v.rowptr = E.pull_ptr.get();
+    v.col = E.pull_u.get();
+    v.w32 = E.pull_c32.get();
+    v.w64 = E.pull_c64.get();
+    v.n_chunks = E.pull_n_chunks;
+    v.n_long = E.pull_n_long;
+    v.chunk_row = E.pull_chunk_row.get();
+    v.chunk_begin = E.pull_chunk_begin.get();
+    v.chunk_long = E.pull_chunk_long.get();
+    v.long_first = E.pull_long_first.get();
+    v.long_of_row = E.pull_long_of_row.get();
+    return v;  // natural row and chunk order; no degrees (the restriction reads none)
+}
+
 void release_workspace(lap_hierarchy *h, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(h->ws_mu);
     h->ws.erase(s);  // DBuf frees on the stream it was taken on
@@ -197,7 +214,8 @@ int64_t hierarchy_bytes(const lap_hierarchy *h) {
              b(L.mem) +
              b(L.keep_id) + b(L.keep_node) + b(L.e_node) + b(L.e_nb) + b(L.e_c64) + b(L.e_c32) +
              b(L.e_dinv64) + b(L.e_dinv32) + b(L.pull_ptr) + b(L.pull_e) + b(L.pull_u) + b(L.pull_c64) +
-             b(L.pull_c32);
+             b(L.pull_c32) + b(L.pull_chunk_row) + b(L.pull_chunk_begin) + b(L.pull_chunk_long) +
+             b(L.pull_long_first) + b(L.pull_long_of_row);
     return t;
 }
 
@@ -210,7 +228,7 @@ extern "C" {
 
 void lap_default_hier_opts(lap_hier_opts_t *o) {
     if (!o) return;
-    o->coarse_max = 1024;
+    o->coarse_max = 0;  // automatic
     o->max_levels = 24;
     o->agg_passes = 2;
     o->match_rounds = 4;
@@ -266,6 +284,7 @@ lap_status_t lap_build_hierarchy(int64_t n, int64_t m, const int32_t *src, const
         lap_hier_opts_t o;
         lap_default_hier_opts(&o);
         if (opts) o = *opts;
+        CFC_REQUIRE(o.coarse_max >= 0, LAP_EINVAL, "coarse_max must be >= 0 (0: automatic)");
         CFC_REQUIRE(o.agg_passes >= 1 && o.agg_passes <= 4, LAP_EINVAL, "agg_passes must be 1..4");
         CFC_REQUIRE(o.eliminate == 0 || o.eliminate == 1, LAP_EINVAL, "eliminate must be 0 or 1");
         CFC_REQUIRE(o.reorder >= 0 && o.reorder <= 2, LAP_EINVAL, "reorder must be 0, 1 or 2");

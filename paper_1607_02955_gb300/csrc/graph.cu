@@ -47,11 +47,15 @@ __global__ void k_heads(const uint64_t *__restrict__ keys, int64_t len, int32_t 
 }
 
 // one thread per merged entry: sums the weights of its run of equal keys in
-// sorted (stable) order
+// sorted (stable) order.  The sort is stable and both directions of an input
+// edge carry its index, so the runs of (u, v) and (v, u) start with the same
+// input edge e: src_edge[o] = e for every merged entry, and tab[e] = o for
+// the upper one (row < col), which gives each lower entry its mirror.
 __global__ void k_merge(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
                         const int32_t *__restrict__ head, const int32_t *__restrict__ hpos, int64_t len, int b,
                         const double *__restrict__ w, int32_t *__restrict__ col, double *__restrict__ wout,
-                        int32_t *__restrict__ rowcnt, int32_t *__restrict__ row_of) {
+                        int32_t *__restrict__ rowcnt, int32_t *__restrict__ row_of, int32_t *__restrict__ src_edge,
+                        int32_t *__restrict__ tab) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
         if (!head[i]) continue;
         const uint64_t key = keys[i];
@@ -59,9 +63,12 @@ __global__ void k_merge(const uint64_t *__restrict__ keys, const uint32_t *__res
         for (int64_t j = i; j < len && keys[j] == key; ++j) s += w ? w[vals[j]] : 1.0;
         const int32_t o = hpos[i];
         const int32_t r = (int32_t)(key >> b);
-        col[o] = (int32_t)(key & ((uint64_t(1) << b) - 1));
+        const int32_t c = (int32_t)(key & ((uint64_t(1) << b) - 1));
+        col[o] = c;
         row_of[o] = r;
         wout[o] = s;
+        src_edge[o] = (int32_t)vals[i];
+        if (r < c) tab[vals[i]] = o;
         atomicAdd(&rowcnt[r], 1);
     }
 }
@@ -90,21 +97,13 @@ __global__ void k_upper_flags(const int32_t *__restrict__ row_of, const int32_t 
         up[i] = row_of[i] < col[i] ? 1 : 0;
 }
 
-// the lower entry (r, c), r > c, takes the id of its mirror (c, r), found by
-// binary search in the sorted row c
-__global__ void k_mirror_eid(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ row_of,
-                             const int32_t *__restrict__ col, int64_t nnz, int32_t *__restrict__ eid) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t r = row_of[i], c = col[i];
-        if (r < c) continue;
-        int lo = rowptr[c], hi = rowptr[c + 1] - 1;
-        while (lo < hi) {
-            int mid = (lo + hi) >> 1;
-            if (col[mid] < r) lo = mid + 1;
-            else hi = mid;
-        }
-        eid[i] = eid[lo];
-    }
+// the lower entry (r, c), r > c, takes the id of its mirror (c, r): the upper
+// entry that k_merge recorded for the same input edge
+__global__ void k_mirror_eid(const int32_t *__restrict__ row_of, const int32_t *__restrict__ col,
+                             const int32_t *__restrict__ src_edge, const int32_t *__restrict__ tab, int64_t nnz,
+                             int32_t *__restrict__ eid) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * blockDim.x)
+        if (row_of[i] > col[i]) eid[i] = eid[tab[src_edge[i]]];
 }
 
 // ---------------------------------------------------------------- connectivity
@@ -234,10 +233,13 @@ void ingest(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const 
     out.w.alloc_persistent(nnz);
     out.deg.alloc_persistent(n);
     out.eid.alloc_persistent(nnz);
-    DBuf<int32_t> rowcnt(n + 1, s), row_of(nnz, s);
+    DBuf<int32_t> rowcnt(n + 1, s), src_edge(nnz, s), tab(m, s);
+    out.row_of.alloc(nnz, s);
+    int32_t *row_of = out.row_of.get();
     rowcnt.zero(s);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_merge, grid_for(len), kBlock, 0, keys.get(), vals.get(), head.get(),
-               hpos.get(), len, b, dw, out.col.get(), out.w.get(), rowcnt.get(), row_of.get());
+               hpos.get(), len, b, dw, out.col.get(), out.w.get(), rowcnt.get(), row_of, src_edge.get(),
+               tab.get());
     keys.release();
     vals.release();
     head.release();
@@ -249,18 +251,20 @@ void ingest(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const 
 
     // edge ids: lexicographic rank among the upper entries (row < col)
     DBuf<int32_t> up(nnz, s);
-    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_upper_flags, grid_for(nnz), kBlock, 0, row_of.get(), out.col.get(), nnz,
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_upper_flags, grid_for(nnz), kBlock, 0, row_of, out.col.get(), nnz,
                up.get());
     scan_exclusive_i32_async(up.get(), out.eid.get(), nnz, s);
-    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_mirror_eid, grid_for(nnz), kBlock, 0, out.rowptr.get(), row_of.get(),
-               out.col.get(), nnz, out.eid.get());
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_mirror_eid, grid_for(nnz), kBlock, 0, row_of, out.col.get(),
+               src_edge.get(), tab.get(), nnz, out.eid.get());
+    src_edge.release();
+    tab.release();
 
     // connectivity
     DBuf<int32_t> par(n, s);
     int32_t *roots = reinterpret_cast<int32_t *>(tot.get() + 3);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_uf_init, grid_for(n), kBlock, 0, out.rowptr.get(), out.col.get(), par.get(),
                (int32_t)n);
-    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_uf_hook, grid_for(nnz), kBlock, 0, row_of.get(), out.col.get(), nnz,
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_uf_hook, grid_for(nnz), kBlock, 0, row_of, out.col.get(), nnz,
                par.get());
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_uf_count_roots, grid_for(n), kBlock, 0, par.get(), (int32_t)n, roots);
     read_totals(tot.get() + 3, 1, h + 3, s);

@@ -187,6 +187,7 @@ struct Level {
     //   back-substitution  x(u) = b(u) / d_u + sum_m (w_um / d_u) x'(nb_m(u))
     bool elim = false;
     int32_t n_elim = 0;
+    DBuf<int32_t> row_of;        // [nnz] row of each entry, level 0 during setup only
     DBuf<int32_t> keep_id;       // [n] id at the next level, or -(j + 1) for eliminated node j
     DBuf<int32_t> keep_node;     // [n_next] the node of this level each next-level node is
     DBuf<int32_t> e_node;        // [n_elim] the eliminated nodes, ascending
@@ -200,11 +201,14 @@ struct Level {
     DBuf<int32_t> pull_u;        //   the eliminated node of each slot,
     DBuf<double> pull_c64;       //   and its coefficient w_um / d_u
     DBuf<float> pull_c32;
+    // pull lists longer than kLongRow split into chunks of kChunk, as the rows of a level
+    int32_t pull_n_chunks = 0, pull_n_long = 0;
+    DBuf<int32_t> pull_chunk_row, pull_chunk_begin, pull_chunk_long, pull_long_first, pull_long_of_row;
 };
 
 constexpr int kDenseMax = 2048;  // largest coarsest level solved by a dense inverse
-constexpr int kLongRow = 32;     // rows with more nonzeros are split into chunks
-constexpr int kChunk = 16;       // nonzeros per chunk of a split row
+constexpr int kLongRow = 64;     // rows with more nonzeros are split into chunks
+constexpr int kChunk = 32;       // nonzeros per chunk of a split row
 constexpr int kMaxTiles = 64;    // column tiles per launch (k <= 64 * 64)
 constexpr int kBlock = 256;
 
@@ -223,6 +227,10 @@ LevelView view(const Level &L);
 // The same level with BF16 weights (and the degrees of the rounded weights)
 // in place of the FP32 ones; ensure_bf16 must have run on it.
 LevelView view_bf16(const Level &L);
+// The pull lists of an elimination level as the rows of a level (n = next
+// level's size, columns = eliminated nodes of G, weights = coefficients), so
+// that the restriction runs on the row kernels with their long-row chunks.
+LevelView pull_view(const Level &E);
 
 // ------------------------------------------------------------------ primitives (prims.cu)
 // Exclusive prefix sum of n int32 or int64 values; returns the total.
@@ -244,6 +252,7 @@ struct Csr64 {
     int32_t n = 0;
     int64_t nnz = 0;
     DBuf<int32_t> rowptr, col, eid;   // eid: undirected edge id of each entry
+    DBuf<int32_t> row_of;             // row of each entry (setup only: released after the elimination)
     DBuf<double> w, deg;
     int64_t m = 0;                    // undirected edges after merging
 };
@@ -255,6 +264,7 @@ void ingest(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const 
 // ------------------------------------------------------------------ hierarchy (amg.cu)
 void init_levels(lap_hierarchy &h, Csr64 &fine, const lap_hier_opts_t &o, cudaStream_t s);
 void grow_levels(lap_hierarchy &h, int target, cudaStream_t s);  // target 0: all
+int effective_coarse_max(const lap_hierarchy &h);                 // the option, or its automatic value
 // Makes L.wbf / degbf / dinvbf (no-op when present): each weight rounded to
 // FP32 and then to BF16 (nearest, ties to even); the degrees are the FP64
 // row sums of the rounded weights, rounded to FP32, so the level stays an
@@ -271,8 +281,10 @@ int max_exponent(const double *v, int64_t n, cudaStream_t s);
 // weights): equal graphs give equal values.  Synchronises s.
 uint64_t graph_fingerprint(const Level &L, cudaStream_t s);
 
-// dense SPD inverse (in place, FP64, row-major n x n) -- used for the
-// coarsest level (single CTA, n <= 160) and cfc_exact_small (global memory).
+// dense SPD inverse (in place, FP64, row-major n x n) for the coarsest level
+// and cfc_exact_small: one block in shared memory for n <= 160, else blocked
+// Gauss-Jordan in one cooperative launch.  *d_flag is set (and A left
+// partly updated) when a pivot is not positive.
 void dense_spd_inverse_small(double *A, int n, int *d_flag, cudaStream_t s);
 void dense_spd_inverse_large(double *A, int n, int *d_flag, cudaStream_t s);
 

@@ -177,84 +177,154 @@ int64_t scan_impl(const T *in, T *out, int64_t n, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ radix sort
-constexpr int kRsThreads = 256;
-constexpr int kRsRounds = 16;
-constexpr int kRsTile = kRsThreads * kRsRounds;
+// LSD radix sort of (64-bit key, 32-bit value) pairs, 8-bit digits.  A block
+// owns a tile of 16384 consecutive pairs (32 warps x 16 rounds x 32).  Its scatter stages the tile in
+// shared memory in digit order (stable) and then writes each digit's run to
+// its place in one pass over the staged tile, so the global writes come in
+// runs (64 pairs per digit on average) instead of single 8-byte stores.
+constexpr int kRsBits = 8;
+constexpr int kRsDigits = 1 << kRsBits;
+constexpr int kRsThreads = 1024;
 constexpr int kRsWarps = kRsThreads / 32;
+constexpr int kRsRounds = 16;                     // rounds of 32 pairs per warp
+constexpr int kRsSub = 32 * kRsRounds;            // pairs per warp (a contiguous sub-tile)
+constexpr int kRsTile = kRsWarps * kRsSub;        // 16384 pairs per block
+constexpr size_t kRsSmem = (size_t)kRsTile * 12   // staged keys and values
+                           + (size_t)kRsWarps * kRsDigits * 2  // per-warp digit counts, then offsets (u16)
+                           + (size_t)3 * kRsDigits * 4;        // tile offsets, global starts, totals
 
-template <int RB>
-__global__ void k_rs_hist(const uint64_t *__restrict__ keys, int64_t n, int shift, int32_t *__restrict__ hist,
-                          int nblocks) {
-    constexpr int NB = 1 << RB;
-    __shared__ uint32_t h[NB];
-    for (int d = threadIdx.x; d < NB; d += kRsThreads) h[d] = 0;
+__global__ void __launch_bounds__(kRsThreads) k_rs_hist(const uint64_t *__restrict__ keys, int64_t n, int shift,
+                                                        int32_t *__restrict__ hist, int nblocks) {
+    __shared__ uint32_t h[kRsDigits];
+    for (int d = threadIdx.x; d < kRsDigits; d += kRsThreads) h[d] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kRsTile;
-    for (int r = 0; r < kRsRounds; ++r) {
-        int64_t i = base + r * kRsThreads + threadIdx.x;
-        if (i < n) atomicAdd(&h[(keys[i] >> shift) & (NB - 1)], 1u);
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < NB; d += kRsThreads) hist[(int64_t)d * nblocks + blockIdx.x] = (int32_t)h[d];
-}
-
-// Stable scatter of RB-bit digits: the tile is consumed in rounds of 256
-// consecutive keys; within a round a key's rank is (keys of its digit in
-// earlier warps) + (lower lanes of its warp with the same digit).  Each
-// warp's leader of a digit group records the group's size, advances the
-// digit's running offset and clears its record, so the work per round
-// follows the keys, not the number of digits.
-template <int RB>
-__global__ void k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
-                             uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n, int shift,
-                             const int32_t *__restrict__ offs, int nblocks) {
-    constexpr int NB = 1 << RB;
-    __shared__ uint32_t run[NB];
-    __shared__ uint32_t wcnt[kRsWarps][NB];
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    for (int d = tid; d < NB; d += kRsThreads) {
-        run[d] = (uint32_t)offs[(int64_t)d * nblocks + blockIdx.x];
-#pragma unroll
-        for (int w = 0; w < kRsWarps; ++w) wcnt[w][d] = 0;
-    }
-    __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kRsTile;
-    const uint32_t lt = (1u << lane) - 1u;
-    for (int r = 0; r < kRsRounds; ++r) {
-        const int64_t i = base + r * kRsThreads + tid;
-        const bool valid = i < n;
-        uint64_t key = valid ? kin[i] : 0;
-        uint32_t val = valid ? vin[i] : 0;
-        const uint32_t digit = valid ? (uint32_t)((key >> shift) & (NB - 1)) : (uint32_t)NB;
+    const int lane = threadIdx.x & 31;
+    for (int r = 0; r < kRsTile / kRsThreads; ++r) {
+        const int64_t i = base + r * kRsThreads + threadIdx.x;
+        const uint32_t digit = i < n ? (uint32_t)((keys[i] >> shift) & (kRsDigits - 1)) : (uint32_t)kRsDigits;
+        // one shared-memory atomic per distinct digit of the warp (few digits on the high passes)
         const uint32_t peers = __match_any_sync(0xffffffffu, digit);
-        const uint32_t rank = __popc(peers & lt);
-        const bool leader = valid && lane == (__ffs(peers) - 1);
-        if (leader) wcnt[wid][digit] = __popc(peers);
-        __syncthreads();
-        if (valid) {
-            uint32_t pos = run[digit] + rank;
-            for (int w = 0; w < wid; ++w) pos += wcnt[w][digit];
-            kout[pos] = key;
-            vout[pos] = val;
+        if (digit < kRsDigits && lane == __ffs(peers) - 1) atomicAdd(&h[digit], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRsDigits; d += kRsThreads)
+        hist[(int64_t)d * nblocks + blockIdx.x] = (int32_t)h[d];
+}
+
+// offs[d * nblocks + b]: exclusive scan of the histograms in digit-major
+// order, i.e. where block b's run of digit d starts in the output.
+__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t *__restrict__ kin,
+                                                           const uint32_t *__restrict__ vin,
+                                                           uint64_t *__restrict__ kout,
+                                                           uint32_t *__restrict__ vout, int64_t n, int shift,
+                                                           const int32_t *__restrict__ offs, int nblocks) {
+    extern __shared__ __align__(16) unsigned char rs_smem[];
+    uint64_t *sk = reinterpret_cast<uint64_t *>(rs_smem);                // [kRsTile]
+    uint32_t *sv = reinterpret_cast<uint32_t *>(sk + kRsTile);           // [kRsTile]
+    uint16_t *wpos = reinterpret_cast<uint16_t *>(sv + kRsTile);         // [kRsWarps][kRsDigits]
+    uint32_t *loc = reinterpret_cast<uint32_t *>(wpos + kRsWarps * kRsDigits);  // [kRsDigits]
+    uint32_t *gst = loc + kRsDigits;                                     // [kRsDigits]
+    uint32_t *tot = gst + kRsDigits;                                     // [kRsDigits]
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kRsTile;
+    const int cnt = (int)((n - base) < (int64_t)kRsTile ? (n - base) : (int64_t)kRsTile);
+    for (int t = tid; t < kRsWarps * kRsDigits; t += kRsThreads) wpos[t] = 0;
+    for (int d = tid; d < kRsDigits; d += kRsThreads) gst[d] = (uint32_t)offs[(int64_t)d * nblocks + blockIdx.x];
+    __syncthreads();
+
+    // A: each warp ranks its sub-tile: rank = earlier pairs of the same digit
+    // in this sub-tile (rounds in order, lanes in order)
+    uint16_t *wc = wpos + wid * kRsDigits;
+    const int sub = wid * kRsSub;
+    // only the ranks stay in registers; the keys are read again (from L2) when staged
+    uint32_t rank2[kRsRounds / 2];
+    const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < kRsRounds; ++r) {
+        const int li = sub + r * 32 + lane;
+        const bool valid = li < cnt;
+        const uint64_t key = valid ? kin[base + li] : 0ull;
+        const uint32_t digit = valid ? (uint32_t)((key >> shift) & (kRsDigits - 1)) : (uint32_t)kRsDigits;
+        const uint32_t peers = __match_any_sync(0xffffffffu, digit);
+        const uint32_t before = valid ? (uint32_t)wc[digit] : 0u;
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) wc[digit] = (uint16_t)(before + __popc(peers));
+        __syncwarp();
+        const uint32_t rk = before + __popc(peers & lt);
+        if (r & 1) rank2[r >> 1] |= rk << 16;
+        else rank2[r >> 1] = rk;
+    }
+    __syncthreads();
+
+    // B: per digit, the counts of the warps become offsets within the tile
+    for (int d = tid; d < kRsDigits; d += kRsThreads) {
+        uint32_t run = 0;
+        for (int w = 0; w < kRsWarps; ++w) {
+            const uint32_t c = wpos[w * kRsDigits + d];
+            wpos[w * kRsDigits + d] = (uint16_t)run;
+            run += c;
         }
-        __syncthreads();
-        if (leader) {
-            atomicAdd(&run[digit], (uint32_t)__popc(peers));
-            wcnt[wid][digit] = 0;
+        tot[d] = run;
+    }
+    __syncthreads();
+    if (tid < 32) {  // exclusive scan of the 256 digit totals by one warp
+        uint32_t v[kRsDigits / 32], sum = 0;
+#pragma unroll
+        for (int q = 0; q < kRsDigits / 32; ++q) {
+            v[q] = tot[lane * (kRsDigits / 32) + q];
+            sum += v[q];
         }
-        __syncthreads();
+        uint32_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        uint32_t run = inc - sum;
+#pragma unroll
+        for (int q = 0; q < kRsDigits / 32; ++q) {
+            loc[lane * (kRsDigits / 32) + q] = run;
+            run += v[q];
+        }
+    }
+    __syncthreads();
+
+    // C: stage the pairs in digit order
+#pragma unroll
+    for (int r = 0; r < kRsRounds; ++r) {
+        const int li = sub + r * 32 + lane;
+        if (li < cnt) {
+            const uint64_t key = kin[base + li];
+            const uint32_t digit = (uint32_t)((key >> shift) & (kRsDigits - 1));
+            const uint32_t rk = (r & 1) ? (rank2[r >> 1] >> 16) : (rank2[r >> 1] & 0xffffu);
+            const uint32_t L = loc[digit] + wpos[wid * kRsDigits + digit] + rk;
+            sk[L] = key;
+            sv[L] = vin[base + li];
+        }
+    }
+    __syncthreads();
+
+    // D: write out; consecutive staged pairs of one digit go to consecutive places
+    for (int L = tid; L < cnt; L += kRsThreads) {
+        const uint64_t k = sk[L];
+        const uint32_t digit = (uint32_t)((k >> shift) & (kRsDigits - 1));
+        const int64_t g = (int64_t)gst[digit] + (L - (int)loc[digit]);
+        kout[g] = k;
+        vout[g] = sv[L];
     }
 }
 
-template <int RB>
 void radix_passes(uint64_t *&ka, uint32_t *&va, uint64_t *&kb, uint32_t *&vb, int32_t *hist, int64_t n,
                   int nblocks, int bits, cudaStream_t s) {
-    const int passes = (bits + RB - 1) / RB;
+    // the staged tile needs more than the default 48 KB of shared memory (set on the current device)
+    CFC_CUDA(cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRsSmem));
+    const int passes = (bits + kRsBits - 1) / kRsBits;
     for (int p = 0; p < passes; ++p) {
-        const int shift = RB * p;
-        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_rs_hist<RB>, nblocks, kRsThreads, 0, ka, n, shift, hist, nblocks);
-        scan_rec<int32_t>(hist, hist, ((int64_t)1 << RB) * nblocks, s);
-        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_rs_scatter<RB>, nblocks, kRsThreads, 0, ka, va, kb, vb, n, shift, hist,
+        const int shift = kRsBits * p;
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_rs_hist, nblocks, kRsThreads, 0, ka, n, shift, hist, nblocks);
+        scan_rec<int32_t>(hist, hist, (int64_t)kRsDigits * nblocks, s);
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_rs_scatter, nblocks, kRsThreads, kRsSmem, ka, va, kb, vb, n, shift, hist,
                    nblocks);
         std::swap(ka, kb);
         std::swap(va, vb);
@@ -303,21 +373,12 @@ void radix_sort_pairs(uint64_t *keys, uint32_t *vals, int64_t n, int bits, cudaS
     if (n <= 1 || bits <= 0) return;
     CFC_REQUIRE(n < (int64_t(1) << 31), LAP_EBUDGET, "sort too large");
     const int nblocks = (int)((n + kRsTile - 1) / kRsTile);
-    // digit width 8..10 bits: the fewest passes, then the smallest histogram
-    int rb = 8;
-    for (int c = 9; c <= 10; ++c)
-        if ((bits + c - 1) / c < (bits + rb - 1) / rb) rb = c;
     DBuf<uint64_t> k2(n, s);
     DBuf<uint32_t> v2(n, s);
-    DBuf<int32_t> hist(((size_t)1 << rb) * nblocks, s);
+    DBuf<int32_t> hist((size_t)kRsDigits * nblocks, s);
     uint64_t *ka = keys, *kb = k2.get();
     uint32_t *va = vals, *vb = v2.get();
-    if (rb == 8)
-        radix_passes<8>(ka, va, kb, vb, hist.get(), n, nblocks, bits, s);
-    else if (rb == 9)
-        radix_passes<9>(ka, va, kb, vb, hist.get(), n, nblocks, bits, s);
-    else
-        radix_passes<10>(ka, va, kb, vb, hist.get(), n, nblocks, bits, s);
+    radix_passes(ka, va, kb, vb, hist.get(), n, nblocks, bits, s);
     if (ka != keys) {
         CFC_CUDA(cudaMemcpyAsync(keys, ka, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
         CFC_CUDA(cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));

@@ -602,35 +602,25 @@ struct OpSubMean64 {
 // ---------------------------------------------------------------- elimination transfers
 // Restriction through an elimination level (Level::elim): the next level's
 // right-hand side b'(I) = b(keep_node[I]) + sum of (w_uI / d_u) b(u) over the
-// eliminated neighbours u of keep_node[I], in ascending order of u; four
-// neighbours in flight per lane (a hub may pull thousands of leaves).
+// eliminated neighbours u of keep_node[I] (ascending u, in the fixed order of
+// the row kernels).  It runs on the row kernels over pull_view, so that a
+// hub's long list of eliminated leaves is cut into chunks summed in parallel.
 template <typename T>
-struct OpElimRestrict {
+struct OpRestrictPull {
     using V = typename Vec<T>::V;
     static constexpr int VW = Vec<T>::W;
-    const int32_t *keep_node, *pull_ptr, *pull_u;
-    const T *coef;  // w_uI / d_u per pull entry
+    const int32_t *keep_node;
     const T *b;
     T *bn;
     int ld;
+    __device__ V gather(int j, int c0) const { return vldg<T>(b + (size_t)j * ld + c0); }
+    struct Pre {
+        int32_t u;
+    };
+    __device__ Pre pre(int I, int) const { return Pre{__ldg(keep_node + I)}; }
     template <class Acc>
-    __device__ void row(int I, int c0, Acc &) const {
-        V s = vld<T>(b + (size_t)__ldg(keep_node + I) * ld + c0);
-        const int t1 = __ldg(pull_ptr + I + 1);
-        int t = __ldg(pull_ptr + I);
-        for (; t + 4 <= t1; t += 4) {
-            V x[4];
-            T c[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                c[q] = __ldg(coef + t + q);
-                x[q] = vld<T>(b + (size_t)__ldg(pull_u + t + q) * ld + c0);
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) vfma(s, c[q], x[q]);
-        }
-        for (; t < t1; ++t) vfma(s, __ldg(coef + t), vld<T>(b + (size_t)__ldg(pull_u + t) * ld + c0));
-        vst<T>(bn + (size_t)I * ld + c0, s);
+    __device__ void epi(int I, int c0, V s, const Pre &pr, Acc &) const {
+        vst<T>(bn + (size_t)I * ld + c0, vadd(gather(pr.u, c0), s));
     }
     __device__ void fin(int, const double *) const {}
 };
@@ -1147,11 +1137,6 @@ struct Solver {
         else return E.e_c64.get();
     }
     template <typename T>
-    static const T *pull_coef_of(const Level &E) {
-        if constexpr (std::is_same<T, float>::value) return E.pull_c32.get();
-        else return E.pull_c64.get();
-    }
-    template <typename T>
     static const T *dinv_of(const Level &E) {
         if constexpr (std::is_same<T, float>::value) return E.e_dinv32.get();
         else return E.e_dinv64.get();
@@ -1159,10 +1144,24 @@ struct Solver {
     void elim_restrict() {
         const Level &E = h->lv[0];
         const int et = (int)sizeof(Tin);
-        rows<Tin, 0>(LAP_KF_BLAS1, lvl(0).n,
-                     OpElimRestrict<Tin>{E.keep_node.get(), E.pull_ptr.get(), E.pull_u.get(), pull_coef_of<Tin>(E),
-                                         r0, r, ld},
-                     vec_bytes(E.n, ld, 1, et) + vec_bytes(lvl(0).n, ld, 1, et));
+        const double bytes = vec_bytes(E.n, ld, 1, et) + vec_bytes(lvl(0).n, ld, 1, et);
+        const LevelView pv = pull_view(E);
+        const OpRestrictPull<Tin> op{E.keep_node.get(), r0, r, ld};
+        constexpr int G = KT / Vec<Tin>::W;
+        constexpr int RPB = kBlock / G;
+        const int nvb_short = (pv.n + RPB - 1) / RPB;
+        if (pv.n_chunks > 0) {  // chunk sums first, then every row finished by its own group
+            const int nvb_long = (pv.n_chunks + RPB - 1) / RPB;
+            CFC_LAUNCH(LAP_KF_BLAS1, s, 0.0, (k_chunk_sums<Tin, KT, OpRestrictPull<Tin>>), dim3(nvb_long, ntiles),
+                       kBlock, 0, pv, op, chunk_part, ld);
+            CFC_LAUNCH(LAP_KF_BLAS1, s, bytes, (k_rowop<Tin, KT, 0, OpRestrictPull<Tin>, kLongPre>),
+                       dim3(plain_grid(nvb_short), ntiles), kBlock, 0, pv, op, nvb_short, nvb_short, chunk_part, ld,
+                       rb);
+        } else {
+            CFC_LAUNCH(LAP_KF_BLAS1, s, bytes, (k_rowop<Tin, KT, 0, OpRestrictPull<Tin>>),
+                       dim3(plain_grid(nvb_short), ntiles), kBlock, 0, pv, op, nvb_short, nvb_short, chunk_part, ld,
+                       rb);
+        }
     }
     void elim_back() {
         const Level &E = h->lv[0];
@@ -1318,7 +1317,7 @@ lap_status_t run_solver(lap_hierarchy *h, int32_t k, const double *B, double *X,
     // levels p0 .. p0 + nlev - 1
     const int p0 = S.p0;
     const int64_t n0 = h->lv[0].n, ntop = h->lv[p0].n;
-    int64_t max_chunks = h->lv[0].n_chunks;
+    int64_t max_chunks = std::max<int64_t>(h->lv[0].n_chunks, h->lv[0].pull_n_chunks);
     for (int l = 0; l < nlev; ++l) max_chunks = std::max<int64_t>(max_chunks, h->lv[p0 + l].n_chunks);
     std::vector<size_t> sizes;
     int64_t n_long_total = 0;

@@ -76,7 +76,7 @@ def test_rmat_takes_the_longest_first_row_order(P, rmat14):
     h = P.lap_build_hierarchy(n, s, d, w)
     info = P.lap_hierarchy_info(h)
     assert info["level_row_order"][0] == 1
-    assert np.bincount(np.concatenate([s, d])).max() > 32  # hubs: rows split into chunks
+    assert np.bincount(np.concatenate([s, d])).max() > 128  # hubs: rows split into several chunks
     grid = P.lap_build_hierarchy(*synth.grid2d(32)[:3])
     assert P.lap_hierarchy_info(grid)["level_row_order"][0] == 0
 
@@ -205,8 +205,10 @@ def test_elimination_then_dense_solve_is_exact(P, gen):
     X = torch.empty((n, 16), dtype=torch.float64, device="cuda")
     # convergence read after every inner iteration, so the count is exact
     si = P.lap_solve_multi(h, torch.tensor(B, device="cuda"), X, P.lap_default_solve_opts(precision=0, check_every=1))
-    assert si["outer_iters"] == 1 and si["inner_iters"] <= 2 and si["max_rel_residual"] < 1e-12
-    _certify(canonical_graph(n, s, d, w), B, X.cpu().numpy(), tol=1e-12)
+    # what is left is FP64 rounding: about eps x cond(L) of the eliminated graph
+    # (a weighted path of ~150 nodes: cond ~ 1e4, so ~1e-12), far below the 1e-8 target
+    assert si["outer_iters"] == 1 and si["inner_iters"] <= 2 and si["max_rel_residual"] < 1e-10
+    _certify(canonical_graph(n, s, d, w), B, X.cpu().numpy(), tol=1e-10)
 
 
 def test_elimination_applies_where_it_removes_nodes(P, rmat14):

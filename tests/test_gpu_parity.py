@@ -51,9 +51,14 @@ def test_hierarchy_sizes(P):
     assert info["coarse_n"] == info["level_n"][-1] <= 64
     for a, b in zip(info["level_n"], info["level_n"][1:]):
         assert b < a
-    # the default stops at 1024 nodes or fewer and solves that level densely
+    # the default (automatic coarse_max: 256 up to 1M nodes) stops at 256 nodes
+    # or fewer on this graph and solves that level densely; 2048 is the cap
     dflt = P.lap_hierarchy_info(P.lap_build_hierarchy(n, s, d, w, P.lap_default_hier_opts(eager=1)))
-    assert dflt["levels"] == 2 and dflt["coarse_n"] == dflt["level_n"][-1] <= 1024
+    assert dflt["coarse_n"] == dflt["level_n"][-1] <= 256 < dflt["level_n"][-2]
+    big = P.lap_hierarchy_info(P.lap_build_hierarchy(n, s, d, w, P.lap_default_hier_opts(eager=1, coarse_max=5000)))
+    assert big["levels"] == 2 and big["coarse_n"] == big["level_n"][-1] <= 2048
+    with pytest.raises(P.LapError):
+        P.lap_build_hierarchy(n, s, d, w, P.lap_default_hier_opts(coarse_max=-1))
 
 
 def test_duplicates_selfloops_merged(P):
