@@ -215,7 +215,8 @@ int64_t hierarchy_bytes(const lap_hierarchy *h) {
              b(L.keep_id) + b(L.keep_node) + b(L.e_node) + b(L.e_nb) + b(L.e_c64) + b(L.e_c32) +
              b(L.e_dinv64) + b(L.e_dinv32) + b(L.pull_ptr) + b(L.pull_e) + b(L.pull_u) + b(L.pull_c64) +
              b(L.pull_c32) + b(L.pull_chunk_row) + b(L.pull_chunk_begin) + b(L.pull_chunk_long) +
-             b(L.pull_long_first) + b(L.pull_long_of_row);
+             b(L.pull_long_first) + b(L.pull_long_of_row) + b(L.jl_chunk_row) + b(L.jl_chunk_begin) +
+             b(L.jl_long_first);
     return t;
 }
 

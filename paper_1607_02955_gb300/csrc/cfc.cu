@@ -102,63 +102,46 @@ __device__ __forceinline__ double i64_scaled_to_double(long long a, int e2) {
                                             (mant & ((1ull << 52) - 1))));
 }
 
-// per CSR entry: sgn * round(sqrt(w_e) * 2^S_u).  A thread takes 8
-// consecutive entries: it finds the row of the first by binary search in
-// rowptr and walks forward from there, recomputing the row's scale when the
-// row changes.  A unit weight skips the square root (sqrt(1) = 1 exactly).
-constexpr int kTermsPerThread = 8;
-__global__ void k_jl_terms(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                           const double *__restrict__ w, const double *__restrict__ deg, int32_t n, int64_t nnz,
-                           double inv_k, double inv_sqrt_k, long long *__restrict__ a) {
-    GRID_LOOP(t, (nnz + kTermsPerThread - 1) / kTermsPerThread) {
-        const int64_t e0 = t * kTermsPerThread;
-        const int64_t e1 = min(e0 + kTermsPerThread, nnz);
-        int lo = 0, hi = n - 1;  // last row with rowptr[row] <= e0
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(rowptr + mid) <= (int32_t)e0) lo = mid;
-            else hi = mid - 1;
-        }
-        int u = lo, next = __ldg(rowptr + u + 1);
-        double sc = pow2(jl_row_shift(rowptr, deg, u, inv_k)) * inv_sqrt_k;
-        long long t1 = llrint(sc);
-        for (int64_t e = e0; e < e1; ++e) {
-            if (e >= next) {
-                do next = __ldg(rowptr + (++u) + 1);
-                while (e >= next);
-                sc = pow2(jl_row_shift(rowptr, deg, u, inv_k)) * inv_sqrt_k;
-                t1 = llrint(sc);
-            }
-            const double we = w[e];
-            const long long tv = we == 1.0 ? t1 : llrint(sqrt(we) * sc);
-            a[e] = (u < col[e]) ? tv : -tv;
-        }
-    }
+// Row u's fixed-point scale 2^S_u / sqrt(k) and its unit term round(2^S_u / sqrt(k)).
+struct JlRow {
+    double sc;
+    long long t1;
+};
+__device__ __forceinline__ JlRow jl_row(const int32_t *rowptr, const double *deg, int u, double inv_k,
+                                        double inv_sqrt_k) {
+    const double sc = pow2(jl_row_shift(rowptr, deg, u, inv_k)) * inv_sqrt_k;
+    return JlRow{sc, llrint(sc)};
 }
 
-// sum over entries [e0, e1) of a_e * q_{i,e} for the 32 rows i = cb*32 ..
-__device__ __forceinline__ void jl_accum(const int32_t *eid, const long long *a, int e0, int e1, int cb,
-                                         uint64_t seed, long long (&acc)[32]) {
+// sum over entries [e0, e1) of row u of a_e * q_{i,e} for the 32 rows
+// i = cb*32 .., with a_e = sgn * round(sqrt(w_e) * 2^S_u / sqrt(k)) computed on
+// the spot (a unit weight skips the square root: sqrt(1) = 1 exactly)
+__device__ __forceinline__ void jl_accum(const int32_t *eid, const int32_t *col, const double *w, int u,
+                                         const JlRow &jr, int e0, int e1, int cb, uint64_t seed,
+                                         long long (&acc)[32]) {
     for (int e = e0; e < e1; ++e) {
-        const long long t = a[e];
-        const uint32_t bits = jl_bits32((uint64_t)eid[e], cb, seed);
+        const double we = __ldg(w + e);
+        long long t = we == 1.0 ? jr.t1 : llrint(sqrt(we) * jr.sc);
+        if (u > __ldg(col + e)) t = -t;
+        const uint32_t bits = jl_bits32((uint64_t)__ldg(eid + e), cb, seed);
 #pragma unroll
         for (int q = 0; q < 32; ++q) acc[q] += ((bits >> q) & 1u) ? -t : t;
     }
 }
 
 __global__ void k_jl_short(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ eid,
-                           const long long *__restrict__ a, const double *__restrict__ deg, int32_t n, int k, int ld,
-                           int cb_off, uint64_t seed, double inv_k, double *__restrict__ Y) {
+                           const int32_t *__restrict__ col, const double *__restrict__ w,
+                           const double *__restrict__ deg, int32_t n, int k, int ld, int cb_off, uint64_t seed,
+                           double inv_k, double inv_sqrt_k, double *__restrict__ Y) {
     const int ncb = (ld + 31) / 32;
     GRID_LOOP(t, (int64_t)n * ncb) {
         const int u = (int)(t / ncb), cb = (int)(t - (int64_t)u * ncb);
         const int e0 = rowptr[u], e1 = rowptr[u + 1];
-        if (e1 - e0 > kLongRow) continue;
+        if (e1 - e0 > kJlRow) continue;
         long long acc[32];
 #pragma unroll
         for (int q = 0; q < 32; ++q) acc[q] = 0;
-        jl_accum(eid, a, e0, e1, cb_off + cb, seed, acc);
+        jl_accum(eid, col, w, u, jl_row(rowptr, deg, u, inv_k, inv_sqrt_k), e0, e1, cb_off + cb, seed, acc);
         const int sh = -jl_row_shift(rowptr, deg, u, inv_k);
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
@@ -169,18 +152,19 @@ __global__ void k_jl_short(const int32_t *__restrict__ rowptr, const int32_t *__
 }
 
 __global__ void k_jl_chunks(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ eid,
-                            const long long *__restrict__ a, const int32_t *__restrict__ chunk_row,
+                            const int32_t *__restrict__ col, const double *__restrict__ w,
+                            const double *__restrict__ deg, const int32_t *__restrict__ chunk_row,
                             const int32_t *__restrict__ chunk_begin, int32_t n_chunks, int ld, int cb_off,
-                            uint64_t seed, long long *__restrict__ part) {
+                            uint64_t seed, double inv_k, double inv_sqrt_k, long long *__restrict__ part) {
     const int ncb = (ld + 31) / 32;
     GRID_LOOP(t, (int64_t)n_chunks * ncb) {
         const int ch = (int)(t / ncb), cb = (int)(t - (int64_t)ch * ncb);
         const int u = chunk_row[ch];
-        const int e0 = chunk_begin[ch], e1 = min(e0 + kChunk, rowptr[u + 1]);
+        const int e0 = chunk_begin[ch], e1 = min(e0 + kJlChunk, rowptr[u + 1]);
         long long acc[32];
 #pragma unroll
         for (int q = 0; q < 32; ++q) acc[q] = 0;
-        jl_accum(eid, a, e0, e1, cb_off + cb, seed, acc);
+        jl_accum(eid, col, w, u, jl_row(rowptr, deg, u, inv_k, inv_sqrt_k), e0, e1, cb_off + cb, seed, acc);
 #pragma unroll
         for (int q = 0; q < 32; ++q) part[((size_t)ch * ncb + cb) * 32 + q] = acc[q];
     }
@@ -398,20 +382,18 @@ void jl_rhs(lap_hierarchy *h, int k_total, int row0, int k, int ld, uint64_t see
     // the scale (and the fixed-point bound) are those of the full k_total-row Q
     const double inv_sqrt_k = 1.0 / std::sqrt((double)k_total), inv_k = 1.0 / k_total;
     const int cb_off = row0 / 32;
-    DBuf<long long> a(std::max<int64_t>(L.nnz, 1), s);
-    CFC_LAUNCH(LAP_KF_CFC, s, (double)L.nnz * 20, k_jl_terms, grid_for((L.nnz + kTermsPerThread - 1) / kTermsPerThread),
-               kBlock, 0, L.rowptr.get(), L.col.get(), L.w64.get(), L.deg64.get(), n, L.nnz, inv_k, inv_sqrt_k,
-               a.get());
-    const double bytes = (double)L.nnz * (4 + 8) + (double)n * 12 + (double)n * ld * 8;
+    // entries: eid, col, weight (16 B); rows: rowptr, degree; the block of Y
+    const double bytes = (double)L.nnz * 16 + (double)n * 12 + (double)n * ld * 8;
     CFC_LAUNCH(LAP_KF_CFC, s, bytes, k_jl_short, grid_for((int64_t)n * ncb, 128), 128, 0, L.rowptr.get(),
-               h->eid.get(), a.get(), L.deg64.get(), n, k, ld, cb_off, seed, inv_k, Y);
-    if (L.n_chunks > 0) {
-        DBuf<long long> part((size_t)L.n_chunks * ncb * 32, s);
-        CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_jl_chunks, grid_for((int64_t)L.n_chunks * ncb, 128), 128, 0,
-                   L.rowptr.get(), h->eid.get(), a.get(), L.chunk_row.get(), L.chunk_begin.get(), L.n_chunks, ld,
-                   cb_off, seed, part.get());
-        CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_jl_long, grid_for((int64_t)L.n_long * ld, 128), 128, 0, L.rowptr.get(),
-                   L.deg64.get(), L.chunk_row.get(), L.long_first.get(), L.n_long, k, ld, inv_k, part.get(), Y);
+               h->eid.get(), L.col.get(), L.w64.get(), L.deg64.get(), n, k, ld, cb_off, seed, inv_k, inv_sqrt_k, Y);
+    if (L.jl_n_chunks > 0) {  // rows longer than kJlRow: chunk partials, then exact sums per row
+        DBuf<long long> part((size_t)L.jl_n_chunks * ncb * 32, s);
+        CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_jl_chunks, grid_for((int64_t)L.jl_n_chunks * ncb, 128), 128, 0,
+                   L.rowptr.get(), h->eid.get(), L.col.get(), L.w64.get(), L.deg64.get(), L.jl_chunk_row.get(),
+                   L.jl_chunk_begin.get(), L.jl_n_chunks, ld, cb_off, seed, inv_k, inv_sqrt_k, part.get());
+        CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_jl_long, grid_for((int64_t)L.jl_n_long * ld, 128), 128, 0,
+                   L.rowptr.get(), L.deg64.get(), L.jl_chunk_row.get(), L.jl_long_first.get(), L.jl_n_long, k, ld,
+                   inv_k, part.get(), Y);
     }
 }
 

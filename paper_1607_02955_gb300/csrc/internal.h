@@ -201,14 +201,20 @@ struct Level {
     DBuf<int32_t> pull_u;        //   the eliminated node of each slot,
     DBuf<double> pull_c64;       //   and its coefficient w_um / d_u
     DBuf<float> pull_c32;
+    // level 0 only: the JL right-hand sides' own split of the rows (cfc.cu),
+    // rows longer than kJlRow in chunks of kJlChunk (one thread sums a chunk)
+    int32_t jl_n_chunks = 0, jl_n_long = 0;
+    DBuf<int32_t> jl_chunk_row, jl_chunk_begin, jl_long_first;
     // pull lists longer than kLongRow split into chunks of kChunk, as the rows of a level
     int32_t pull_n_chunks = 0, pull_n_long = 0;
     DBuf<int32_t> pull_chunk_row, pull_chunk_begin, pull_chunk_long, pull_long_first, pull_long_of_row;
 };
 
 constexpr int kDenseMax = 2048;  // largest coarsest level solved by a dense inverse
-constexpr int kLongRow = 64;     // rows with more nonzeros are split into chunks
-constexpr int kChunk = 32;       // nonzeros per chunk of a split row
+constexpr int kLongRow = 128;    // rows with more nonzeros are split into chunks
+constexpr int kChunk = 64;       // nonzeros per chunk of a split row
+constexpr int kJlRow = 32;       // the JL right-hand sides: rows with more entries are split
+constexpr int kJlChunk = 32;     //   into chunks of this many (one thread each)
 constexpr int kMaxTiles = 64;    // column tiles per launch (k <= 64 * 64)
 constexpr int kBlock = 256;
 
@@ -264,6 +270,7 @@ void ingest(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const 
 // ------------------------------------------------------------------ hierarchy (amg.cu)
 void init_levels(lap_hierarchy &h, Csr64 &fine, const lap_hier_opts_t &o, cudaStream_t s);
 void grow_levels(lap_hierarchy &h, int target, cudaStream_t s);  // target 0: all
+void build_jl_chunks(Level &L, cudaStream_t s);                   // Level::jl_* of level 0
 int effective_coarse_max(const lap_hierarchy &h);                 // the option, or its automatic value
 // Makes L.wbf / degbf / dinvbf (no-op when present): each weight rounded to
 // FP32 and then to BF16 (nearest, ties to even); the degrees are the FP64

@@ -178,23 +178,30 @@ int64_t scan_impl(const T *in, T *out, int64_t n, cudaStream_t s) {
 
 // ------------------------------------------------------------------ radix sort
 // LSD radix sort of (64-bit key, 32-bit value) pairs, 8-bit digits.  A block
-// owns a tile of 16384 consecutive pairs (32 warps x 16 rounds x 32).  Its scatter stages the tile in
-// shared memory in digit order (stable) and then writes each digit's run to
-// its place in one pass over the staged tile, so the global writes come in
-// runs (64 pairs per digit on average) instead of single 8-byte stores.
+// owns a tile of consecutive pairs (16384, or 4096 for small sorts).  Its
+// scatter stages the tile in shared memory in digit order (stable) and then
+// writes each digit's run to its place in one pass over the staged tile, so
+// the global writes come in runs (64 pairs per digit on average for the large
+// tile) instead of single 8-byte stores.
 constexpr int kRsBits = 8;
 constexpr int kRsDigits = 1 << kRsBits;
 constexpr int kRsThreads = 1024;
 constexpr int kRsWarps = kRsThreads / 32;
-constexpr int kRsRounds = 16;                     // rounds of 32 pairs per warp
-constexpr int kRsSub = 32 * kRsRounds;            // pairs per warp (a contiguous sub-tile)
-constexpr int kRsTile = kRsWarps * kRsSub;        // 16384 pairs per block
-constexpr size_t kRsSmem = (size_t)kRsTile * 12   // staged keys and values
-                           + (size_t)kRsWarps * kRsDigits * 2  // per-warp digit counts, then offsets (u16)
-                           + (size_t)3 * kRsDigits * 4;        // tile offsets, global starts, totals
+// R rounds of 32 pairs per warp: a tile of 32 x 32 x R pairs (16 384 at R = 16
+// for large sorts, 4 096 at R = 4 when the large tiles would not fill the GPU)
+template <int R>
+__host__ __device__ constexpr int rs_tile() { return kRsWarps * 32 * R; }
+template <int R>
+constexpr size_t rs_smem() {
+    return (size_t)rs_tile<R>() * 12                    // staged keys and values
+           + (size_t)kRsWarps * kRsDigits * 2           // per-warp digit counts, then offsets (u16)
+           + (size_t)3 * kRsDigits * 4;                 // tile offsets, global starts, totals
+}
 
+template <int R>
 __global__ void __launch_bounds__(kRsThreads) k_rs_hist(const uint64_t *__restrict__ keys, int64_t n, int shift,
                                                         int32_t *__restrict__ hist, int nblocks) {
+    constexpr int kRsTile = rs_tile<R>();
     __shared__ uint32_t h[kRsDigits];
     for (int d = threadIdx.x; d < kRsDigits; d += kRsThreads) h[d] = 0;
     __syncthreads();
@@ -214,13 +221,17 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_hist(const uint64_t *__restri
 
 // offs[d * nblocks + b]: exclusive scan of the histograms in digit-major
 // order, i.e. where block b's run of digit d starts in the output.
+template <int R>
 __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t *__restrict__ kin,
                                                            const uint32_t *__restrict__ vin,
                                                            uint64_t *__restrict__ kout,
                                                            uint32_t *__restrict__ vout, int64_t n, int shift,
                                                            const int32_t *__restrict__ offs, int nblocks) {
-    extern __shared__ __align__(16) unsigned char rs_smem[];
-    uint64_t *sk = reinterpret_cast<uint64_t *>(rs_smem);                // [kRsTile]
+    constexpr int kRsTile = rs_tile<R>();
+    constexpr int kRsRounds = R;
+    constexpr int kRsSub = 32 * R;
+    extern __shared__ __align__(16) unsigned char rs_smem_raw[];
+    uint64_t *sk = reinterpret_cast<uint64_t *>(rs_smem_raw);            // [kRsTile]
     uint32_t *sv = reinterpret_cast<uint32_t *>(sk + kRsTile);           // [kRsTile]
     uint16_t *wpos = reinterpret_cast<uint16_t *>(sv + kRsTile);         // [kRsWarps][kRsDigits]
     uint32_t *loc = reinterpret_cast<uint32_t *>(wpos + kRsWarps * kRsDigits);  // [kRsDigits]
@@ -315,17 +326,18 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t *__res
     }
 }
 
+template <int R>
 void radix_passes(uint64_t *&ka, uint32_t *&va, uint64_t *&kb, uint32_t *&vb, int32_t *hist, int64_t n,
                   int nblocks, int bits, cudaStream_t s) {
     // the staged tile needs more than the default 48 KB of shared memory (set on the current device)
-    CFC_CUDA(cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRsSmem));
+    CFC_CUDA(cudaFuncSetAttribute(k_rs_scatter<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem<R>()));
     const int passes = (bits + kRsBits - 1) / kRsBits;
     for (int p = 0; p < passes; ++p) {
         const int shift = kRsBits * p;
-        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_rs_hist, nblocks, kRsThreads, 0, ka, n, shift, hist, nblocks);
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_rs_hist<R>, nblocks, kRsThreads, 0, ka, n, shift, hist, nblocks);
         scan_rec<int32_t>(hist, hist, (int64_t)kRsDigits * nblocks, s);
-        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_rs_scatter, nblocks, kRsThreads, kRsSmem, ka, va, kb, vb, n, shift, hist,
-                   nblocks);
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_rs_scatter<R>, nblocks, kRsThreads, rs_smem<R>(), ka, va, kb, vb, n, shift,
+                   hist, nblocks);
         std::swap(ka, kb);
         std::swap(va, vb);
     }
@@ -372,13 +384,17 @@ int64_t scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, cudaStrea
 void radix_sort_pairs(uint64_t *keys, uint32_t *vals, int64_t n, int bits, cudaStream_t s) {
     if (n <= 1 || bits <= 0) return;
     CFC_REQUIRE(n < (int64_t(1) << 31), LAP_EBUDGET, "sort too large");
-    const int nblocks = (int)((n + kRsTile - 1) / kRsTile);
+    // large tiles once they give every SM two blocks, small ones below
+    const bool big = (n + rs_tile<16>() - 1) / rs_tile<16>() >= 2 * num_sms_public();
+    const int tile = big ? rs_tile<16>() : rs_tile<4>();
+    const int nblocks = (int)((n + tile - 1) / tile);
     DBuf<uint64_t> k2(n, s);
     DBuf<uint32_t> v2(n, s);
     DBuf<int32_t> hist((size_t)kRsDigits * nblocks, s);
     uint64_t *ka = keys, *kb = k2.get();
     uint32_t *va = vals, *vb = v2.get();
-    radix_passes(ka, va, kb, vb, hist.get(), n, nblocks, bits, s);
+    if (big) radix_passes<16>(ka, va, kb, vb, hist.get(), n, nblocks, bits, s);
+    else radix_passes<4>(ka, va, kb, vb, hist.get(), n, nblocks, bits, s);
     if (ka != keys) {
         CFC_CUDA(cudaMemcpyAsync(keys, ka, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
         CFC_CUDA(cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
