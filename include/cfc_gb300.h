@@ -191,14 +191,17 @@ void lap_default_solve_opts(lap_solve_opts_t *o);
  * lap_build_hierarchy -- ingest G and build the multigrid hierarchy.
  * Sec. 2 (graph model, L = D - A), Sec. 3.1 and Sec. 6.1 (an algebraic
  * multigrid Laplacian solver; the paper's LAMG coarsens by elimination and
- * affinity-based aggregation -- this library aggregates by pairwise matching
- * on edge strength w_ij / max(D_ii, D_jj)).
+ * affinity-based aggregation -- this library eliminates nodes with one or two
+ * neighbours and aggregates by pairwise matching, see lap_hier_opts_t).
  *   n           number of nodes, 2 <= n < 2^31
  *   m           number of input edges (m >= 1)
  *   src, dst    int32[m], host or device: edge endpoints in [0, n).
  *               Self-loops are dropped; edge direction is ignored;
  *               repeated pairs are merged with their weights summed
- *               (parallel conductances) (Sec. 6.3).
+ *               (parallel conductances) (Sec. 6.3).  Page-locked host
+ *               buffers (cudaHostAlloc, cudaHostRegister) are read in place
+ *               by the first kernels, other host buffers are copied first;
+ *               either way they are not read after the call returns.
  *   w           double[m], host or device, or NULL for unit weights; each
  *               weight a conductance (Sec. 2) with 1e-150 <= w <= 1e150, a
  *               range in which the FP64 sums and products of the solver

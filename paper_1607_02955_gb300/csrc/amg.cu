@@ -433,12 +433,19 @@ __global__ void k_nchunk(const int32_t *__restrict__ rowptr, int32_t n, int32_t 
     }
 }
 
-// the JL split of level 0's rows: chunks per row, then each chunk's row and start
-__global__ void k_jl_nchunk(const int32_t *__restrict__ rowptr, int32_t n, int32_t *__restrict__ nchunk) {
+// the JL split of level 0's rows: chunks per row, then each chunk's row and
+// start; also counts the rows with one or two entries (the candidates of the
+// low-degree elimination) into *low
+__global__ void k_jl_nchunk(const int32_t *__restrict__ rowptr, int32_t n, int32_t *__restrict__ nchunk,
+                            unsigned long long *__restrict__ low) {
+    unsigned long long c = 0;
     GRID_LOOP(i, n) {
         const int len = rowptr[i + 1] - rowptr[i];
         nchunk[i] = len > kJlRow ? (len + kJlChunk - 1) / kJlChunk : 0;
+        c += (len >= 1 && len <= 2) ? 1ull : 0ull;
     }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(low, c);
 }
 __global__ void k_jl_fill(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ nchunk,
                           const int32_t *__restrict__ cfirst, const int32_t *__restrict__ lidx, int32_t n,
@@ -1339,35 +1346,38 @@ void init_levels(lap_hierarchy &h, Csr64 &fine, const lap_hier_opts_t &o, cudaSt
     h.wexp = max_exponent(L0.w64.get(), std::max<int64_t>(L0.nnz, 1), s);
     h.fingerprint = graph_fingerprint(L0, s);
     finish_level(L0, h.wexp, o.reorder, s);
-    build_jl_chunks(L0, s);
+    const int64_t low = build_jl_chunks(L0, s);
     h.p0 = 0;
-    // low-degree elimination when it removes at least 5 % of the nodes
-    if (o.eliminate && L0.n > 256 && eliminate_level(h, 0.05, s)) h.p0 = 1;
+    // low-degree elimination when it removes at least 5 % of the nodes (the
+    // nodes with one or two neighbours bound what it can remove)
+    if (o.eliminate && L0.n > 256 && low >= 0.05 * L0.n && eliminate_level(h, 0.05, s)) h.p0 = 1;
     h.lv[0].row_of.release();
     const Level &T = h.lv.back();
     if (T.n <= effective_coarse_max(h) || o.max_levels <= 1) grow_levels(h, 0, s);
 }
 
-void build_jl_chunks(Level &L, cudaStream_t s) {
+int64_t build_jl_chunks(Level &L, cudaStream_t s) {
     const int32_t n = L.n;
     DBuf<int32_t> nchunk(n, s), cfirst(n, s), isl(n, s), lidx(n, s);
-    DBuf<int64_t> ct(2, s);
+    DBuf<int64_t> ct(3, s);
     ct.zero(s);
-    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_jl_nchunk, grid_for(n), kBlock, 0, L.rowptr.get(), n, nchunk.get());
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_jl_nchunk, grid_for(n), kBlock, 0, L.rowptr.get(), n, nchunk.get(),
+               reinterpret_cast<unsigned long long *>(ct.get() + 2));
     scan_exclusive_i32_total(nchunk.get(), cfirst.get(), n, ct.get(), s);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_long_index, grid_for(n), kBlock, 0, nchunk.get(), n, isl.get());
     scan_exclusive_i32_total(isl.get(), lidx.get(), n, ct.get() + 1, s);
-    int64_t hc[2];
-    read_totals(ct.get(), 2, hc, s);
+    int64_t hc[3];
+    read_totals(ct.get(), 3, hc, s);
     L.jl_n_chunks = (int32_t)hc[0];
     L.jl_n_long = (int32_t)hc[1];
-    if (L.jl_n_chunks == 0) return;
+    if (L.jl_n_chunks == 0) return hc[2];
     L.jl_chunk_row.alloc_persistent(L.jl_n_chunks);
     L.jl_chunk_begin.alloc_persistent(L.jl_n_chunks);
     L.jl_long_first.alloc_persistent(L.jl_n_long + 1);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_jl_fill, grid_for(n), kBlock, 0, L.rowptr.get(), nchunk.get(), cfirst.get(),
                lidx.get(), n, L.jl_chunk_row.get(), L.jl_chunk_begin.get(), L.jl_long_first.get());
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_set_last, 1, 1, 0, L.jl_long_first.get(), L.jl_n_long, L.jl_n_chunks);
+    return hc[2];
 }
 
 // coarse_max in effect: the option, or (0) n_top / 4096 clamped to [256, 1024]

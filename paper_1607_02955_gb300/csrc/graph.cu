@@ -132,23 +132,70 @@ __global__ void k_uf_init(const int32_t *__restrict__ rowptr, const int32_t *__r
     }
 }
 
-__global__ void k_uf_hook(const int32_t *__restrict__ row_of, const int32_t *__restrict__ col, int64_t nnz,
-                          int32_t *par) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t u = row_of[i], v = col[i];
-        if (u > v) continue;
-        int32_t ru = uf_find(par, u), rv = uf_find(par, v);
-        while (ru != rv) {
-            if (ru < rv) {
-                int32_t t = ru;
-                ru = rv;
-                rv = t;
-            }
-            const int32_t old = atomicCAS(par + ru, ru, rv);
-            if (old == ru) break;
-            ru = uf_find(par, ru);
-            rv = uf_find(par, rv);
+// Afforest's order (Sutton, Ben-Nun, Bar-Barak, IPDPS 2018): first hook every
+// node to its first `rounds` neighbours, then let the rest of the entries
+// only of nodes outside the largest tree so far hook.  Correct whichever tree
+// is skipped: the entries are symmetric, so an edge between the skipped tree
+// and another one is seen from the other side.
+__device__ __forceinline__ void uf_hook(int32_t *par, int32_t u, int32_t v) {
+    int32_t ru = uf_find(par, u), rv = uf_find(par, v);
+    while (ru != rv) {
+        if (ru < rv) {
+            const int32_t t = ru;
+            ru = rv;
+            rv = t;
         }
+        const int32_t old = atomicCAS(par + ru, ru, rv);
+        if (old == ru) break;
+        ru = uf_find(par, ru);
+        rv = uf_find(par, rv);
+    }
+}
+
+__global__ void k_uf_sample(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, int32_t n,
+                            int r, int32_t *par) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e = rowptr[i] + r;
+        if (e < rowptr[i + 1]) uf_hook(par, (int32_t)i, col[e]);
+    }
+}
+
+__global__ void k_uf_compress(int32_t *par, int32_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        __stcg(par + i, uf_find(par, (int32_t)i));
+}
+
+// the most frequent root among 32 evenly spaced nodes (one warp)
+__global__ void k_uf_giant(const int32_t *par, int32_t n, int32_t *giant) {
+    const int lane = threadIdx.x & 31;
+    const int32_t r = uf_find(const_cast<int32_t *>(par), (int32_t)(((int64_t)n * lane) / 32));
+    const uint32_t peers = __match_any_sync(0xffffffffu, r);
+    int c = __popc(peers), best = r;
+    for (int o = 16; o > 0; o >>= 1) {
+        const int oc = __shfl_xor_sync(0xffffffffu, c, o), ob = __shfl_xor_sync(0xffffffffu, best, o);
+        if (oc > c || (oc == c && ob < best)) {
+            c = oc;
+            best = ob;
+        }
+    }
+    if (lane == 0) *giant = best;
+}
+
+// giant == nullptr: every upper entry (row < column) hooks, no sampling before
+__global__ void k_uf_rest(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ row_of,
+                          const int32_t *__restrict__ col, int64_t nnz, int r0, const int32_t *__restrict__ giant,
+                          int32_t *par) {
+    const int32_t g = giant ? *giant : -1;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = row_of[e];
+        if (!giant) {
+            const int32_t v = col[e];
+            if (u < v) uf_hook(par, u, v);
+            continue;
+        }
+        if (e < (int64_t)rowptr[u] + r0) continue;  // hooked in the sampling rounds
+        if (uf_find(par, u) == g) continue;
+        uf_hook(par, u, col[e]);
     }
 }
 
@@ -190,8 +237,11 @@ void ingest(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const 
     CFC_REQUIRE(m >= 1 && 2 * m < (int64_t(1) << 31) - 1, LAP_EINVAL, "need 1 <= m and 2m < 2^31");
     DBuf<int32_t> ts, td;
     DBuf<double> tw;
-    const int32_t *ds = to_device(src, m, ts, s);
-    const int32_t *dd = to_device(dst, m, td, s);
+    // endpoints in page-locked host memory are read in place (twice, by the
+    // validation and the pair emission): no staging copy
+    const void *ms = mapped_host_pointer(src), *md = mapped_host_pointer(dst);
+    const int32_t *ds = ms ? static_cast<const int32_t *>(ms) : to_device(src, m, ts, s);
+    const int32_t *dd = md ? static_cast<const int32_t *>(md) : to_device(dst, m, td, s);
     const double *dw = to_device(w, m, tw, s);
 
     // device scalars read back in batches: [0] invalid-edge flag, [1] kept
@@ -264,8 +314,22 @@ void ingest(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const 
     int32_t *roots = reinterpret_cast<int32_t *>(tot.get() + 3);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_uf_init, grid_for(n), kBlock, 0, out.rowptr.get(), out.col.get(), par.get(),
                (int32_t)n);
-    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_uf_hook, grid_for(nnz), kBlock, 0, row_of, out.col.get(), nnz,
-               par.get());
+    if (nnz < (int64_t(1) << 24)) {
+        // small graphs: one pass over the upper entries (the sampling rounds
+        // contend on the hubs' roots when ids follow arrival order, as in BA)
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_uf_rest, grid_for(nnz), kBlock, 0, out.rowptr.get(), row_of,
+                   out.col.get(), nnz, 0, (const int32_t *)nullptr, par.get());
+    } else {
+        constexpr int kSample = 2;
+        for (int r = 0; r < kSample; ++r)
+            CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_uf_sample, grid_for(n), kBlock, 0, out.rowptr.get(), out.col.get(),
+                       (int32_t)n, r, par.get());
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_uf_compress, grid_for(n), kBlock, 0, par.get(), (int32_t)n);
+        DBuf<int32_t> giant(1, s);
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_uf_giant, 1, 32, 0, par.get(), (int32_t)n, giant.get());
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_uf_rest, grid_for(nnz), kBlock, 0, out.rowptr.get(), row_of,
+                   out.col.get(), nnz, kSample, giant.get(), par.get());
+    }
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_uf_count_roots, grid_for(n), kBlock, 0, par.get(), (int32_t)n, roots);
     read_totals(tot.get() + 3, 1, h + 3, s);
     CFC_REQUIRE(h[3] == 1, LAP_ENOTCONN, "graph is not connected");

@@ -146,6 +146,9 @@ struct DBuf {
 };
 
 bool is_device_pointer(const void *p);
+// The device address of a page-locked host buffer (read in place by kernels
+// over the host link), or nullptr for any other pointer.
+const void *mapped_host_pointer(const void *p);
 
 // ------------------------------------------------------------------ graph levels
 // One level of the multigrid hierarchy: the Laplacian L = D - A of a graph in
@@ -270,7 +273,7 @@ void ingest(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const 
 // ------------------------------------------------------------------ hierarchy (amg.cu)
 void init_levels(lap_hierarchy &h, Csr64 &fine, const lap_hier_opts_t &o, cudaStream_t s);
 void grow_levels(lap_hierarchy &h, int target, cudaStream_t s);  // target 0: all
-void build_jl_chunks(Level &L, cudaStream_t s);                   // Level::jl_* of level 0
+int64_t build_jl_chunks(Level &L, cudaStream_t s);  // Level::jl_* of level 0; returns its rows of length 1 or 2
 int effective_coarse_max(const lap_hierarchy &h);                 // the option, or its automatic value
 // Makes L.wbf / degbf / dinvbf (no-op when present): each weight rounded to
 // FP32 and then to BF16 (nearest, ties to even); the degrees are the FP64
