@@ -148,6 +148,10 @@ typedef struct {
                              (one launch instead of one per kernel); 0: plain launches.
                              Plain launches are also used while lap_stats timing or the
                              launch log is on, so that those see every kernel */
+    int32_t first_residual_ff; /* 1 (default): the first refinement step's residual is formed
+                             in two FP32 words where that is exact enough (FP32 modes, FP32
+                             weights exactly 2^-e w; see lap_solve_info_t); 0: every residual
+                             in FP64.  The stopping test uses an FP64 residual either way */
 } lap_solve_opts_t;
 
 typedef struct {
@@ -161,6 +165,12 @@ typedef struct {
     int32_t k_tile, levels_used, nu_coarse, cycle;
     double coarse_scale;
     int32_t w_levels;
+    int32_t first_residual_ff;  /* 1 when the first refinement step's residual (x = the first
+                                   correction) was formed in two FP32 words from exact FP32
+                                   weights (about 48 bits) instead of FP64; it only feeds the
+                                   next inner solve, and the stopping test always uses an FP64
+                                   residual.  0 otherwise (FP64 mode, weights not exact in
+                                   FP32, max_outer <= 1, or no second step) */
 } lap_solve_info_t;
 
 typedef struct {

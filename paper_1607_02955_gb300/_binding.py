@@ -42,13 +42,13 @@ class SolveOpts(C.Structure):
                 ("smoother", C.c_int32), ("nu_pre", C.c_int32), ("nu_post", C.c_int32),
                 ("check_every", C.c_int32), ("levels_used", C.c_int32), ("nu_coarse", C.c_int32),
                 ("cycle", C.c_int32), ("coarse_scale", C.c_double), ("w_levels", C.c_int32),
-                ("graphs", C.c_int32)]
+                ("graphs", C.c_int32), ("first_residual_ff", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
     _fields_ = [("outer_iters", C.c_int32), ("inner_iters", C.c_int32), ("max_rel_residual", C.c_double),
                 ("k_tile", C.c_int32), ("levels_used", C.c_int32), ("nu_coarse", C.c_int32), ("cycle", C.c_int32),
-                ("coarse_scale", C.c_double), ("w_levels", C.c_int32)]
+                ("coarse_scale", C.c_double), ("w_levels", C.c_int32), ("first_residual_ff", C.c_int32)]
 
 
 class HierInfo(C.Structure):
@@ -294,7 +294,7 @@ def lap_solve_multi(h: Hierarchy, B, X, opts: SolveOpts | None = None, stream=No
     return {"status": st, "outer_iters": info.outer_iters, "inner_iters": info.inner_iters,
             "max_rel_residual": info.max_rel_residual, "k_tile": info.k_tile, "levels_used": info.levels_used,
             "nu_coarse": info.nu_coarse, "cycle": info.cycle, "coarse_scale": info.coarse_scale,
-            "w_levels": info.w_levels}
+            "w_levels": info.w_levels, "first_residual_ff": info.first_residual_ff}
 
 
 def cfc_jl_rhs(h: Hierarchy, k: int, seed: int, Y, stream=None):

@@ -277,13 +277,28 @@ __global__ void k_set_last(int32_t *p, int32_t idx, int32_t v) {
     if (blockIdx.x == 0 && threadIdx.x == 0) p[idx] = v;
 }
 
-__global__ void k_row_sums(const int32_t *__restrict__ rowptr, const double *__restrict__ w, int32_t n,
-                           double *__restrict__ deg) {
+// D_ii = sum_j w_ij in CSR order: one thread per row of at most 32 entries
+// (most rows), one warp per longer row (lane-strided sums + a fixed tree);
+// both orders are fixed, so the sums are reproducible
+__global__ void k_row_sums_short(const int32_t *__restrict__ rowptr, const double *__restrict__ w, int32_t n,
+                                 double *__restrict__ deg) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int e0 = rowptr[r], e1 = rowptr[r + 1];
+        if (e1 - e0 > 32) continue;
+        double s = 0.0;
+        for (int e = e0; e < e1; ++e) s += w[e];
+        deg[r] = s;
+    }
+}
+__global__ void k_row_sums_long(const int32_t *__restrict__ rowptr, const double *__restrict__ w, int32_t n,
+                                double *__restrict__ deg) {
     const int lane = threadIdx.x & 31;
     for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n;
          r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int e0 = rowptr[r], e1 = rowptr[r + 1];
+        if (e1 - e0 <= 32) continue;
         double s = 0.0;
-        for (int e = rowptr[r] + lane; e < rowptr[r + 1]; e += 32) s += w[e];
+        for (int e = e0 + lane; e < e1; e += 32) s += w[e];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (lane == 0) deg[r] = s;
@@ -311,8 +326,17 @@ __global__ void k_u32_to_i32(const uint32_t *__restrict__ a, int32_t *__restrict
 __global__ void k_finish(const int32_t *__restrict__ rowptr, const double *__restrict__ w64,
                          const double *__restrict__ deg64, int32_t n, int64_t nnz, double sc,
                          float *__restrict__ w32, float *__restrict__ deg32, float *__restrict__ dinv32,
-                         double *__restrict__ dinv64, int32_t *__restrict__ nchunk) {
-    GRID_LOOP(e, nnz) w32[e] = (float)(w64[e] * sc);
+                         double *__restrict__ dinv64, int32_t *__restrict__ nchunk,
+                         unsigned long long *__restrict__ inexact) {
+    // inexact: set when some FP32 weight is not exactly the scaled FP64 one
+    bool bad = false;
+    GRID_LOOP(e, nnz) {
+        const double x = w64[e] * sc;
+        const float f = (float)x;
+        w32[e] = f;
+        bad = bad || ((double)f != x);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(inexact, 1ull);
     GRID_LOOP(i, n) {
         const double d = deg64[i];
         const double ds = d * sc;
@@ -349,6 +373,28 @@ __global__ void k_fingerprint(const int32_t *__restrict__ rowptr, const int32_t 
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if (lane == 0 && acc) atomicAdd(out, acc);
+}
+
+// The fingerprint's sum and the largest weight's bit pattern in one pass over
+// the entries, one thread each (the row of each entry from row_of)
+__global__ void k_fingerprint_flat(const int32_t *__restrict__ row_of, const int32_t *__restrict__ col,
+                                   const double *__restrict__ w, int64_t nnz, unsigned long long *__restrict__ out) {
+    unsigned long long acc = 0, m = 0;
+    GRID_LOOP(e, nnz) {
+        const unsigned long long wb = (unsigned long long)__double_as_longlong(w[e]);
+        const unsigned long long rc = ((unsigned long long)(uint32_t)row_of[e] << 32) | (uint32_t)col[e];
+        acc += fmix64(rc ^ fmix64(wb));
+        m = wb > m ? wb : m;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_down_sync(0xffffffffu, acc, o);
+        const unsigned long long t = __shfl_down_sync(0xffffffffu, m, o);
+        m = t > m ? t : m;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (acc) atomicAdd(out, acc);
+        if (m) atomicMax(out + 1, m);
+    }
 }
 
 // largest of n positive doubles: positive doubles order like their bit
@@ -401,8 +447,14 @@ __global__ void k_order_stats(const int32_t *__restrict__ rowptr, int32_t n, uns
         }
         wmax += m;
     }
-    atomicAdd(out, wmax);
-    atomicAdd(out + 1, rsum);
+    for (int o = 16; o > 0; o >>= 1) {  // one atomic per warp, not per thread
+        wmax += __shfl_down_sync(0xffffffffu, wmax, o);
+        rsum += __shfl_down_sync(0xffffffffu, rsum, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(out, wmax);
+        atomicAdd(out + 1, rsum);
+    }
 }
 
 // sort key of a row for the processing order: shorter rows later, rows longer
@@ -768,8 +820,10 @@ void contract(const int32_t *rowptr, const int32_t *col, const double *w, int32_
                hpos.get(), len, b, w, out.col.get(), out.w.get(), rowcnt.get());
     scan_exclusive_i32(rowcnt.get(), out.rowptr.get(), nc, s);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_set_last, 1, 1, 0, out.rowptr.get(), nc, (int32_t)cnnz);
-    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_row_sums, grid_for(32 * (int64_t)nc), kBlock, 0, out.rowptr.get(),
-               out.w.get(), nc, out.deg.get());
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_row_sums_short, grid_for(nc), kBlock, 0,
+               out.rowptr.get(), out.w.get(), nc, out.deg.get());
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_row_sums_long, grid_for(32 * (int64_t)nc), kBlock, 0,
+               out.rowptr.get(), out.w.get(), nc, out.deg.get());
 }
 
 // ---------------------------------------------------------------- low-degree elimination
@@ -1045,6 +1099,19 @@ uint64_t graph_fingerprint(const Level &L, cudaStream_t s) {
     return (uint64_t)h;
 }
 
+void fingerprint_and_exponent(const Level &L, uint64_t *fp, int *wexp, cudaStream_t s) {
+    DBuf<int64_t> f(2, s);
+    f.zero(s);
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_fingerprint_flat, grid_for(L.nnz), kBlock, 0, L.row_of.get(), L.col.get(),
+               L.w64.get(), L.nnz, reinterpret_cast<unsigned long long *>(f.get()));
+    int64_t h[2] = {0, 0};
+    read_totals(f.get(), 2, h, s);
+    *fp = (uint64_t)h[0];
+    double mx = 0.0;
+    std::memcpy(&mx, &h[1], sizeof(mx));
+    *wexp = mx > 0.0 ? std::ilogb(mx) : 0;
+}
+
 int max_exponent(const double *v, int64_t n, cudaStream_t s) {
     DBuf<int64_t> m(1, s);
     m.zero(s);
@@ -1065,21 +1132,23 @@ void finish_level(Level &L, int wexp, int reorder, cudaStream_t s) {
     L.dinv32.alloc_persistent(n);
     L.dinv64.alloc_persistent(n);
     DBuf<int32_t> nchunk(n, s), cfirst(n, s), isl(n, s), lidx(n, s);
+    // the counts, the round statistics and the FP32 weights' exactness come
+    // back with one synchronisation
+    DBuf<int64_t> tot(5, s);
+    tot.zero(s);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_finish, grid_for(std::max<int64_t>(nnz, n)), kBlock, 0, L.rowptr.get(),
                L.w64.get(), L.deg64.get(), n, nnz, std::ldexp(1.0, -wexp), L.w32.get(), L.deg32.get(),
-               L.dinv32.get(), L.dinv64.get(), nchunk.get());
-    // the counts and the round statistics come back with one synchronisation
-    DBuf<int64_t> tot(4, s);
-    tot.zero(s);
+               L.dinv32.get(), L.dinv64.get(), nchunk.get(), reinterpret_cast<unsigned long long *>(tot.get() + 4));
     scan_exclusive_i32_total(nchunk.get(), cfirst.get(), n, tot.get(), s);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_long_index, grid_for(n), kBlock, 0, nchunk.get(), n, isl.get());
     scan_exclusive_i32_total(isl.get(), lidx.get(), n, tot.get() + 1, s);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_order_stats, grid_for((n + 3) / 4), kBlock, 0, L.rowptr.get(), n,
                reinterpret_cast<unsigned long long *>(tot.get() + 2));
-    int64_t h[4];
-    read_totals(tot.get(), 4, h, s);
+    int64_t h[5];
+    read_totals(tot.get(), 5, h, s);
     L.n_chunks = (int32_t)h[0];
     L.n_long = (int32_t)h[1];
+    L.w32_exact = h[4] == 0;
     // When the row lengths are very uneven (power-law degrees), the row
     // kernels take the rows longest first (a stable sort by length), so that
     // the row groups of a warp get rows of about the same length and the
@@ -1229,8 +1298,10 @@ bool eliminate_level(lap_hierarchy &h, double min_frac, cudaStream_t s) {
         CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_elim_write_fills, grid_for(32 * (int64_t)nk), kBlock, 0, kcol.get(),
                    kstart.get(), ucol.get(), uw.get(), fptr.get(), fnew.get(), fnew_pref.get(), C.rowptr.get(), nk,
                    C.col.get(), C.w.get());
-        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_row_sums, grid_for(32 * (int64_t)nk), kBlock, 0, C.rowptr.get(),
-                   C.w.get(), nk, C.deg.get());
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_row_sums_short, grid_for(nk), kBlock, 0,
+                   C.rowptr.get(), C.w.get(), nk, C.deg.get());
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_row_sums_long, grid_for(32 * (int64_t)nk), kBlock, 0,
+                   C.rowptr.get(), C.w.get(), nk, C.deg.get());
     }
     // pull lists of the restriction, in ascending order of the eliminated node
     {
@@ -1343,8 +1414,8 @@ void init_levels(lap_hierarchy &h, Csr64 &fine, const lap_hier_opts_t &o, cudaSt
     h.hopts = o;
     h.complete = false;
     h.coarse_n = 0;
-    h.wexp = max_exponent(L0.w64.get(), std::max<int64_t>(L0.nnz, 1), s);
-    h.fingerprint = graph_fingerprint(L0, s);
+    // the same values as max_exponent and graph_fingerprint, with one pass and one synchronisation
+    fingerprint_and_exponent(L0, &h.fingerprint, &h.wexp, s);
     finish_level(L0, h.wexp, o.reorder, s);
     const int64_t low = build_jl_chunks(L0, s);
     h.p0 = 0;

@@ -267,6 +267,7 @@ void lap_default_solve_opts(lap_solve_opts_t *o) {
     o->cycle = 0;
     o->w_levels = 0;
     o->graphs = 1;
+    o->first_residual_ff = 1;
     o->coarse_scale = 0.0;
 }
 

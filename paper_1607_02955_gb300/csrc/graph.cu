@@ -77,14 +77,28 @@ __global__ void k_finish_rowptr(int32_t *rowptr, int32_t n, int32_t nnz) {
     if (blockIdx.x == 0 && threadIdx.x == 0) rowptr[n] = nnz;
 }
 
-// D_ii = sum_j w_ij: one warp per row, fixed-order lane-strided sums + tree
-__global__ void k_row_sums(const int32_t *__restrict__ rowptr, const double *__restrict__ w, int32_t n,
-                           double *__restrict__ deg) {
+// D_ii = sum_j w_ij in CSR order: one thread per row of at most 32 entries
+// (most rows), one warp per longer row (lane-strided sums + a fixed tree);
+// both orders are fixed, so the sums are reproducible
+__global__ void k_row_sums_short(const int32_t *__restrict__ rowptr, const double *__restrict__ w, int32_t n,
+                                 double *__restrict__ deg) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int e0 = rowptr[r], e1 = rowptr[r + 1];
+        if (e1 - e0 > 32) continue;
+        double s = 0.0;
+        for (int e = e0; e < e1; ++e) s += w[e];
+        deg[r] = s;
+    }
+}
+__global__ void k_row_sums_long(const int32_t *__restrict__ rowptr, const double *__restrict__ w, int32_t n,
+                                double *__restrict__ deg) {
     const int lane = threadIdx.x & 31;
     for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n;
          r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int e0 = rowptr[r], e1 = rowptr[r + 1];
+        if (e1 - e0 <= 32) continue;
         double s = 0.0;
-        for (int e = rowptr[r] + lane; e < rowptr[r + 1]; e += 32) s += w[e];
+        for (int e = e0 + lane; e < e1; e += 32) s += w[e];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (lane == 0) deg[r] = s;
@@ -296,8 +310,10 @@ void ingest(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const 
     hpos.release();
     scan_exclusive_i32_async(rowcnt.get(), out.rowptr.get(), n, s);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_finish_rowptr, 1, 1, 0, out.rowptr.get(), (int32_t)n, (int32_t)nnz);
-    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_row_sums, grid_for(32 * n), kBlock, 0, out.rowptr.get(), out.w.get(),
-               (int32_t)n, out.deg.get());
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_row_sums_short, grid_for(n), kBlock, 0,
+               out.rowptr.get(), out.w.get(), (int32_t)n, out.deg.get());
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_row_sums_long, grid_for(32 * (int64_t)n), kBlock, 0,
+               out.rowptr.get(), out.w.get(), (int32_t)n, out.deg.get());
 
     // edge ids: lexicographic rank among the upper entries (row < col)
     DBuf<int32_t> up(nnz, s);

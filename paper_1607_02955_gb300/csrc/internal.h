@@ -188,6 +188,7 @@ struct Level {
     //   restriction   b'(I) = b(keep_node[I]) + sum over the eliminated
     //                 neighbours u of keep_node[I] of (w_u,I / d_u) b(u)
     //   back-substitution  x(u) = b(u) / d_u + sum_m (w_um / d_u) x'(nb_m(u))
+    bool w32_exact = false;      // every FP32 weight is exactly 2^-wexp times the FP64 one
     bool elim = false;
     int32_t n_elim = 0;
     DBuf<int32_t> row_of;        // [nnz] row of each entry, level 0 during setup only
@@ -290,6 +291,9 @@ int max_exponent(const double *v, int64_t n, cudaStream_t s);
 // Order-free 64-bit fingerprint of a level's graph (its CSR entries and
 // weights): equal graphs give equal values.  Synchronises s.
 uint64_t graph_fingerprint(const Level &L, cudaStream_t s);
+// graph_fingerprint and max_exponent of the weights of level 0 in one pass
+// (needs L.row_of), one synchronisation of s
+void fingerprint_and_exponent(const Level &L, uint64_t *fp, int *wexp, cudaStream_t s);
 
 // dense SPD inverse (in place, FP64, row-major n x n) for the coarsest level
 // and cfc_exact_small: one block in shared memory for n <= 160, else blocked

@@ -420,6 +420,21 @@ __device__ __forceinline__ typename Vec<T>::V row_sum(const LevelView &A, const 
     return vadd(s0, s1);
 }
 
+// An Op with a member `custom_sum(A, e0, e1, c0, lane)` computes the sum
+// sum_{e in [e0, e1)} w_e x_{col(e)} itself (another arithmetic or operand
+// layout); every other Op takes row_sum.
+template <class Op, class = void>
+struct has_custom_sum : std::false_type {};
+template <class Op>
+struct has_custom_sum<Op, std::void_t<decltype(&Op::custom_sum)>> : std::true_type {};
+
+template <typename T, bool BF, int G, class Op>
+__device__ __forceinline__ typename Vec<T>::V row_sum_of(const LevelView &A, const Op &op, int e0, int e1, int c0,
+                                                        int lane) {
+    if constexpr (has_custom_sum<Op>::value) return op.custom_sum(A, e0, e1, c0, lane);
+    else return row_sum<T, BF, G>(A, op, e0, e1, c0, lane);
+}
+
 // ------------------------------------------------------------------ SpMM-like row operator
 // Op provides:
 //   V gather(int j, int c0) const              operand of node j, this lane's columns
@@ -444,7 +459,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_chunk_sums(LevelView A, Op op, T 
     const int i = __ldg(A.chunk_row + ch);
     const int e0 = __ldg(A.chunk_begin + ch);
     const int e1 = min(e0 + kChunk, __ldg(A.rowptr + i + 1));
-    vst<T>(chunk_part + (size_t)ch * ld_part + c0, row_sum<T, BF, G>(A, op, e0, e1, c0, lane));
+    vst<T>(chunk_part + (size_t)ch * ld_part + c0, row_sum_of<T, BF, G>(A, op, e0, e1, c0, lane));
 }
 
 // How rows longer than kLongRow are handled:
@@ -484,7 +499,7 @@ __global__ void __launch_bounds__(kBlock, (NR >= 3 ? 3 : 4)) k_rowop(LevelView A
                 const int e0 = __ldg(A.rowptr + i), e1 = __ldg(A.rowptr + i + 1);
                 if (e1 - e0 <= kLongRow) {
                     const auto pr = op.pre(i, c0);  // own-row operands, in flight with the gathers
-                    const V s = row_sum<T, BF, G>(A, op, e0, e1, c0, lane);
+                    const V s = row_sum_of<T, BF, G>(A, op, e0, e1, c0, lane);
                     op.epi(i, c0, s, pr, acc);
                 } else if (PRE) {
                     const auto pr = op.pre(i, c0);
@@ -504,7 +519,7 @@ __global__ void __launch_bounds__(kBlock, (NR >= 3 ? 3 : 4)) k_rowop(LevelView A
                 i = __ldg(A.chunk_row + ch);
                 const int e0 = __ldg(A.chunk_begin + ch);
                 const int e1 = min(e0 + kChunk, __ldg(A.rowptr + i + 1));
-                const V s = row_sum<T, BF, G>(A, op, e0, e1, c0, lane);
+                const V s = row_sum_of<T, BF, G>(A, op, e0, e1, c0, lane);
                 vst<T>(chunk_part + (size_t)ch * ld_part + c0, s);
                 __threadfence();
             }

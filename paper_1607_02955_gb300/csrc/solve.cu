@@ -129,6 +129,110 @@ struct OpResid64 {
     }
 };
 
+// hi + lo += w * x with error-free transformations in FP32 (the product by
+// an FMA, the sum by Knuth's two-sum); explicit roundings keep the compiler
+// from contracting them
+__device__ __forceinline__ void ff_acc(float &hi, float &lo, float w, float x) {
+    const float p = __fmul_rn(w, x);
+    const float pe = __fmaf_rn(w, x, -p);  // w x = p + pe exactly
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));  // hi + p = s + err
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(err, pe));
+}
+
+// The residual of the first refinement step, when x is still the first
+// correction alone: x = 2^-(wexp + rexp0) d with d the FP32 inner solution on
+// G.  With FP32 weights that are exactly 2^-wexp w (Level::w32_exact) every
+// product w_ij d_j is exact in two FP32 words, and the row sums are carried
+// in two FP32 words (about 48 bits), then finished in FP64:
+//   r = b - 2^-rexp0 (2^-wexp D d - sum_j w32_ij d_j).
+// The gathers move FP32 rows (half of the FP64 residual's bytes) and the
+// arithmetic runs on the FP32 pipes, not on GB300's narrow FP64 one.  This
+// residual only feeds the second inner solve: a column is never declared
+// converged here; the step that can converge uses OpResid64.
+template <typename Tin>
+struct OpResidFirst {
+    using V = typename Vec<double>::V;
+    static constexpr int VW = Vec<double>::W;
+    LevelView A;
+    const float *d;
+    const double *b;
+    Tin *r;
+    int ld;
+    const double *bnorm;
+    double *relres;
+    int32_t *active;
+    int wexp;
+    const int32_t *rexp0;  // exponent of the step that produced d
+    const int32_t *rexp;   // exponent of this residual's scaled copy
+    int32_t *rexp_next;
+    double pred;
+    __device__ float4 drow(int j, int c0) const {
+        return __ldg(reinterpret_cast<const float4 *>(d + (size_t)j * ld + c0));
+    }
+    __device__ V custom_sum(const LevelView &Av, int e0, int e1, int c0, int) const {
+        float hi[VW] = {0.f, 0.f, 0.f, 0.f}, lo[VW] = {0.f, 0.f, 0.f, 0.f};
+        for (int e = e0; e < e1; e += 4) {
+            int j[4];
+            float w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool ok = e + u < e1;
+                j[u] = ok ? __ldg(Av.col + e + u) : -1;
+                w[u] = ok ? __ldg(Av.w32 + e + u) : 0.f;
+            }
+            float4 x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = j[u] >= 0 ? drow(j[u], c0) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                ff_acc(hi[0], lo[0], w[u], x[u].x);
+                ff_acc(hi[1], lo[1], w[u], x[u].y);
+                ff_acc(hi[2], lo[2], w[u], x[u].z);
+                ff_acc(hi[3], lo[3], w[u], x[u].w);
+            }
+        }
+        V out;
+#pragma unroll
+        for (int v = 0; v < VW; ++v) vel(out, v) = (double)hi[v] + (double)lo[v];
+        return out;
+    }
+    __device__ V gather(int j, int c0) const {  // d as FP64 (the generic sum is not used)
+        const float4 x = drow(j, c0);
+        V o;
+        vel(o, 0) = x.x;
+        vel(o, 1) = x.y;
+        vel(o, 2) = x.z;
+        vel(o, 3) = x.w;
+        return o;
+    }
+    struct Pre {
+        double ds;  // 2^-wexp D_ii
+    };
+    __device__ Pre pre(int i, int) const { return Pre{scale2(ldeg<double>(A, i), -wexp)}; }
+    template <class Acc>
+    __device__ void epi(int i, int c0, V s, const Pre &pr, Acc &acc) const {
+        const V di = gather(i, c0);
+        const V bi = vldg<double>(b + (size_t)i * ld + c0);
+#pragma unroll
+        for (int v = 0; v < VW; ++v) {
+            const double q = pr.ds * vel(di, v) - vel(s, v);  // (2^-wexp L d)_i
+            const double rv = vel(bi, v) - scale2(q, -__ldg(rexp0 + c0 + v));
+            acc.add(0, v, rv * rv);
+            r[(size_t)i * ld + c0 + v] = from_double<Tin>(scale2(rv, __ldg(rexp + c0 + v)));
+        }
+    }
+    __device__ void fin(int c, const double *sums) const {
+        const double bn = bnorm[c];
+        const double rn = sqrt(sums[0]);
+        relres[c] = bn > 0.0 ? rn / bn : 0.0;
+        active[c] = bn > 0.0 ? 1 : 0;  // never converged here
+        rexp_next[c] = (rn * pred > 0.0 && isfinite(rn)) ? -ilogb(rn * pred) : rexp[c];
+    }
+};
+
 // PCG scalars from the sums r.z, sum z, sum r (and r.r at the start):
 // mu = mean(z) (the projection of z onto 1-perp), rz = r.(z - mu),
 // beta = rz / rz_old; Init also records rr0 = r.r and the active columns.
@@ -1197,7 +1301,7 @@ struct Solver {
         CFC_CUDA(cudaMemsetAsync(x64, 0, (size_t)n * ld * 8, s));
 
         int outer = 0, inner_total = 0;
-        bool converged = false;
+        bool converged = false, used_ff = false;
         double maxrel = 0.0;
         std::vector<double> hrel(ld), hbn(ld);
         for (outer = 0;; ++outer) {
@@ -1218,22 +1322,36 @@ struct Solver {
                 const int nvb_long = (L0.n_chunks + RPB - 1) / RPB;
                 const int nvb = nvb_short + nvb_long;
                 dim3 grid(red_grid(nvb), ntiles64);
-                using Op = OpResid64<Tin>;
                 LevelView v0 = view(L0);
                 v0.long_count = nullptr;  // FP64 sweeps finish long rows from chunk sums: no counters
-                Op op{v0, x64, b64, rfine, ld, cs.bnorm, cs.relres, cs.active_out, o.tol, rx_cur,
-                      kScaled ? cs.rexp[(outer + 1) & 1] : nullptr, pred};
-                const double bytes = mat_bytes(L0, 8) + 2 * v64 + vec_bytes(n, ld, 1, sizeof(Tin));
-                if (L0.n_chunks > 0) {
-                    CFC_LAUNCH(LAP_KF_RESID64, s, 0.0, (k_chunk_sums<double, K64, Op>), dim3(nvb_long, ntiles64),
-                               kBlock, 0, v0, op, chunk_part64, ld);
-                    CFC_LAUNCH(LAP_KF_RESID64, s, bytes, (k_rowop<double, K64, 1, Op, kLongPre>),
-                               dim3(red_grid(nvb_short), ntiles64), kBlock, 0, v0, op, nvb_short, nvb_short,
-                               chunk_part64, ld, rb);
-                } else {
-                    CFC_LAUNCH(LAP_KF_RESID64, s, bytes, (k_rowop<double, K64, 1, Op>), grid, kBlock, 0, v0, op,
-                               nvb_short, nvb, chunk_part64, ld, rb);
+                // x is still the first correction alone: its residual in two FP32 words
+                const bool first_ff =
+                    kScaled && outer == 1 && L0.w32_exact && o.max_outer > 1 && o.first_residual_ff != 0;
+                auto launch = [&](const auto &op, double bytes) {
+                    using Op = std::decay_t<decltype(op)>;
+                    if (L0.n_chunks > 0) {
+                        CFC_LAUNCH(LAP_KF_RESID64, s, 0.0, (k_chunk_sums<double, K64, Op>),
+                                   dim3(nvb_long, ntiles64), kBlock, 0, v0, op, chunk_part64, ld);
+                        CFC_LAUNCH(LAP_KF_RESID64, s, bytes, (k_rowop<double, K64, 1, Op, kLongPre>),
+                                   dim3(red_grid(nvb_short), ntiles64), kBlock, 0, v0, op, nvb_short, nvb_short,
+                                   chunk_part64, ld, rb);
+                    } else {
+                        CFC_LAUNCH(LAP_KF_RESID64, s, bytes, (k_rowop<double, K64, 1, Op>), grid, kBlock, 0, v0, op,
+                                   nvb_short, nvb, chunk_part64, ld, rb);
+                    }
+                };
+                used_ff = used_ff || first_ff;
+                if constexpr (kScaled) {
+                    if (first_ff) {
+                        launch(OpResidFirst<Tin>{v0, p0 ? d0 : dbuf, b64, rfine, ld, cs.bnorm, cs.relres,
+                                                 cs.active_out, h->wexp, cs.rexp[0], rx_cur, cs.rexp[0], pred},
+                               mat_bytes(L0, 4) + v64 + 2 * vec_bytes(n, ld, 1, sizeof(Tin)));
+                    }
                 }
+                if (!first_ff)
+                    launch(OpResid64<Tin>{v0, x64, b64, rfine, ld, cs.bnorm, cs.relres, cs.active_out, o.tol, rx_cur,
+                                          kScaled ? cs.rexp[(outer + 1) & 1] : nullptr, pred},
+                           mat_bytes(L0, 8) + 2 * v64 + vec_bytes(n, ld, 1, sizeof(Tin)));
             }
             if (p0) elim_restrict();
             CFC_CUDA(cudaMemcpyAsync(h_active, cs.active_out, ld * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -1286,6 +1404,7 @@ struct Solver {
             info->cycle = cycle;
             info->coarse_scale = gamma;
             info->w_levels = cycle == 2 ? w_levels : 0;
+            info->first_residual_ff = used_ff ? 1 : 0;
         }
         return converged ? LAP_OK : LAP_ENOCONV;
     }

@@ -44,7 +44,7 @@ def test_status_strings_and_defaults(P):
     assert h.aggregation == 0 and h.hub_factor == 0
     # options the autotuner fills in are left open; cycles are replayed as graphs
     assert (o.levels_used, o.nu_coarse, o.cycle, o.coarse_scale, o.w_levels, o.k_tile) == (0, 0, 0, 0.0, 0, 0)
-    assert o.graphs == 1
+    assert o.graphs == 1 and o.first_residual_ff == 1
     assert "not finished" in P.lap_status_string(P.LAP_EPENDING)
     sv = P.cfc_server_default_opts()
     assert sv.slots == 4 and sv.hbm_budget == 0 and sv.resident_pivots == 0

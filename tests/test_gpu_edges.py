@@ -284,3 +284,38 @@ def test_aggregation_options_are_validated(P):
     for bad in (dict(aggregation=2), dict(aggregation=-1), dict(hub_factor=-1), dict(hub_factor=2000000)):
         with pytest.raises(P.LapError):
             P.lap_build_hierarchy(n, s, d, None, P.lap_default_hier_opts(**bad))
+
+
+# ------------------------------------------------------------------ first residual in two FP32 words
+@pytest.mark.parametrize("weights", ["unit", "pow2", "uniform"])
+def test_first_residual_in_two_fp32_words(P, weights):
+    # with weights that FP32 holds exactly (unit, or powers of two over 8
+    # octaves) the first refinement step's residual is formed in two FP32
+    # words; the result is still certified by the FP64 residual, matches the
+    # oracle's farness, and takes as many steps as with every residual in
+    # FP64.  Other weights take the FP64 residual throughout.
+    import torch
+    n, s, d, _ = synth.rmat(14, seed=3)
+    rng = np.random.default_rng(12)
+    w = {"unit": None, "pow2": 2.0 ** rng.integers(-4, 5, s.size).astype(np.float64),
+         "uniform": synth.uniform_weights(s.size, seed=5)}[weights]
+    g = canonical_graph(n, s, d, w)
+    h = P.lap_build_hierarchy(n, s, d, w)
+    B = rng.standard_normal((n, 40))
+    X = torch.empty((n, 40), dtype=torch.float64, device="cuda")
+    info = P.lap_solve_multi(h, torch.tensor(B, device="cuda"), X, P.lap_default_solve_opts(precision=1))
+    assert info["first_residual_ff"] == (0 if weights == "uniform" else 1)
+    assert info["outer_iters"] >= 2 and info["max_rel_residual"] <= 1e-8
+    _certify(g, B, X.cpu().numpy())
+    X64 = torch.empty_like(X)
+    ref = P.lap_solve_multi(h, torch.tensor(B, device="cuda"), X64,
+                            P.lap_default_solve_opts(precision=1, first_residual_ff=0))
+    assert ref["first_residual_ff"] == 0 and ref["outer_iters"] == info["outer_iters"]
+    np.testing.assert_allclose(X.cpu().numpy(), X64.cpu().numpy(), rtol=0, atol=1e-6 * np.abs(X64.cpu().numpy()).max())
+    nodes = np.array([2, n // 2], np.int32)
+    f = P.cfc_farness_jl(h, 32, 4, nodes)
+    fo = jl.jl_farness(g, 32, 4, nodes.tolist(), solver="cg", tol=1e-12)
+    assert _rel(f, fo) <= FARNESS_RTOL
+    # FP64 mode never takes it
+    info64 = P.lap_solve_multi(h, torch.tensor(B, device="cuda"), X, P.lap_default_solve_opts(precision=0))
+    assert info64["first_residual_ff"] == 0
