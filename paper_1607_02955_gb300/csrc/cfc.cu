@@ -113,60 +113,123 @@ __device__ __forceinline__ JlRow jl_row(const int32_t *rowptr, const double *deg
     return JlRow{sc, llrint(sc)};
 }
 
-// sum over entries [e0, e1) of row u of a_e * q_{i,e} for the 32 rows
-// i = cb*32 .., with a_e = sgn * round(sqrt(w_e) * 2^S_u / sqrt(k)) computed on
-// the spot (a unit weight skips the square root: sqrt(1) = 1 exactly)
-__device__ __forceinline__ void jl_accum(const int32_t *eid, const int32_t *col, const double *w, int u,
-                                         const JlRow &jr, int e0, int e1, int cb, uint64_t seed,
-                                         long long (&acc)[32]) {
-    for (int e = e0; e < e1; ++e) {
-        const double we = __ldg(w + e);
-        long long t = we == 1.0 ? jr.t1 : llrint(sqrt(we) * jr.sc);
-        if (u > __ldg(col + e)) t = -t;
-        const uint32_t bits = jl_bits32((uint64_t)__ldg(eid + e), cb, seed);
-#pragma unroll
-        for (int q = 0; q < 32; ++q) acc[q] += ((bits >> q) & 1u) ? -t : t;
-    }
-}
+// The JL sums of 32 units per warp, a unit being a row of at most kJlRow
+// entries (k_jl_short) or a kJlChunk-entry chunk of a longer row
+// (k_jl_chunks); lane l owns unit l.  The warp first stages the units'
+// entries in shared memory, one unit at a time with the lanes over its
+// entries (coalesced loads of the edge ids, columns and weights), as the
+// fixed-point terms a_e = sgn * round(sqrt(w_e) * 2^S_u / sqrt(k)) (a unit
+// weight skips the square root: sqrt(1) = 1 exactly).  Then every lane sums
+// its own unit, for each 32-row block of Q in turn:
+//   acc_q = sum_e (bit q of the block's Philox word for e) ? -a_e : a_e.
+constexpr int kJlWarps = 2;  // warps per block
+struct JlStage {
+    int32_t id[32][33];
+    long long t[32][33];
+};
 
-__global__ void k_jl_short(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ eid,
-                           const int32_t *__restrict__ col, const double *__restrict__ w,
-                           const double *__restrict__ deg, int32_t n, int k, int ld, int cb_off, uint64_t seed,
-                           double inv_k, double inv_sqrt_k, double *__restrict__ Y) {
-    const int ncb = (ld + 31) / 32;
-    GRID_LOOP(t, (int64_t)n * ncb) {
-        const int u = (int)(t / ncb), cb = (int)(t - (int64_t)u * ncb);
-        const int e0 = rowptr[u], e1 = rowptr[u + 1];
-        if (e1 - e0 > kJlRow) continue;
-        long long acc[32];
-#pragma unroll
-        for (int q = 0; q < 32; ++q) acc[q] = 0;
-        jl_accum(eid, col, w, u, jl_row(rowptr, deg, u, inv_k, inv_sqrt_k), e0, e1, cb_off + cb, seed, acc);
-        const int sh = -jl_row_shift(rowptr, deg, u, inv_k);
-#pragma unroll
-        for (int q = 0; q < 32; ++q) {
-            const int c = cb * 32 + q;
-            if (c < ld) Y[(size_t)u * ld + c] = c < k ? i64_scaled_to_double(acc[q], sh) : 0.0;
+template <class Emit>
+__device__ __forceinline__ void jl_warp_units(const int32_t *eid, const int32_t *col, const double *w, int u,
+                                              const JlRow &jr, int e0, int len, int ncb, int cb_off, uint64_t seed,
+                                              JlStage &st, Emit emit) {
+    const int lane = threadIdx.x & 31;
+    for (int r = 0; r < 32; ++r) {
+        const int e0r = __shfl_sync(0xffffffffu, e0, r), lr = __shfl_sync(0xffffffffu, len, r);
+        const int ur = __shfl_sync(0xffffffffu, u, r);
+        const double scr = __shfl_sync(0xffffffffu, jr.sc, r);
+        const long long t1r = __shfl_sync(0xffffffffu, jr.t1, r);
+        if (lane < lr) {
+            const int e = e0r + lane;
+            const double we = __ldg(w + e);
+            long long t = we == 1.0 ? t1r : llrint(sqrt(we) * scr);
+            if (ur > __ldg(col + e)) t = -t;
+            st.id[lane][r] = __ldg(eid + e);
+            st.t[lane][r] = t;
         }
     }
-}
-
-__global__ void k_jl_chunks(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ eid,
-                            const int32_t *__restrict__ col, const double *__restrict__ w,
-                            const double *__restrict__ deg, const int32_t *__restrict__ chunk_row,
-                            const int32_t *__restrict__ chunk_begin, int32_t n_chunks, int ld, int cb_off,
-                            uint64_t seed, double inv_k, double inv_sqrt_k, long long *__restrict__ part) {
-    const int ncb = (ld + 31) / 32;
-    GRID_LOOP(t, (int64_t)n_chunks * ncb) {
-        const int ch = (int)(t / ncb), cb = (int)(t - (int64_t)ch * ncb);
-        const int u = chunk_row[ch];
-        const int e0 = chunk_begin[ch], e1 = min(e0 + kJlChunk, rowptr[u + 1]);
+    __syncwarp();
+    for (int cb = 0; cb < ncb; ++cb) {
         long long acc[32];
 #pragma unroll
         for (int q = 0; q < 32; ++q) acc[q] = 0;
-        jl_accum(eid, col, w, u, jl_row(rowptr, deg, u, inv_k, inv_sqrt_k), e0, e1, cb_off + cb, seed, acc);
+        for (int j = 0; j < len; ++j) {
+            const long long t = st.t[j][lane];
+            const uint32_t bits = jl_bits32((uint64_t)(uint32_t)st.id[j][lane], cb_off + cb, seed);
 #pragma unroll
-        for (int q = 0; q < 32; ++q) part[((size_t)ch * ncb + cb) * 32 + q] = acc[q];
+            for (int q = 0; q < 32; ++q) acc[q] += ((bits >> q) & 1u) ? -t : t;
+        }
+        emit(cb, acc);
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(32 * kJlWarps) k_jl_short(const int32_t *__restrict__ rowptr,
+                                                           const int32_t *__restrict__ eid,
+                                                           const int32_t *__restrict__ col,
+                                                           const double *__restrict__ w,
+                                                           const double *__restrict__ deg, int32_t n, int k, int ld,
+                                                           int cb_off, uint64_t seed, double inv_k,
+                                                           double inv_sqrt_k, double *__restrict__ Y) {
+    __shared__ JlStage stage[kJlWarps];
+    JlStage &st = stage[threadIdx.x >> 5];
+    const int ncb = (ld + 31) / 32;
+    const int64_t nwarp = (n + 31) / 32;
+    for (int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wg < nwarp;
+         wg += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int u = (int)(wg * 32 + (threadIdx.x & 31));
+        int e0 = 0, len = 0;
+        JlRow jr{0.0, 0};
+        if (u < n) {
+            e0 = rowptr[u];
+            len = rowptr[u + 1] - e0;
+            if (len > kJlRow) len = 0;  // split rows: k_jl_chunks
+            jr = jl_row(rowptr, deg, u, inv_k, inv_sqrt_k);
+        }
+        const bool mine = u < n && rowptr[u + 1] - e0 <= kJlRow;
+        const int sh = mine ? -jl_row_shift(rowptr, deg, u, inv_k) : 0;
+        jl_warp_units(eid, col, w, u, jr, e0, len, ncb, cb_off, seed, st,
+                      [&](int cb, const long long(&acc)[32]) {
+                          if (!mine) return;
+#pragma unroll
+                          for (int q = 0; q < 32; ++q) {
+                              const int c = cb * 32 + q;
+                              if (c < ld) Y[(size_t)u * ld + c] = c < k ? i64_scaled_to_double(acc[q], sh) : 0.0;
+                          }
+                      });
+    }
+}
+
+__global__ void __launch_bounds__(32 * kJlWarps) k_jl_chunks(const int32_t *__restrict__ rowptr,
+                                                            const int32_t *__restrict__ eid,
+                                                            const int32_t *__restrict__ col,
+                                                            const double *__restrict__ w,
+                                                            const double *__restrict__ deg,
+                                                            const int32_t *__restrict__ chunk_row,
+                                                            const int32_t *__restrict__ chunk_begin,
+                                                            int32_t n_chunks, int ld, int cb_off, uint64_t seed,
+                                                            double inv_k, double inv_sqrt_k,
+                                                            long long *__restrict__ part) {
+    __shared__ JlStage stage[kJlWarps];
+    JlStage &st = stage[threadIdx.x >> 5];
+    const int ncb = (ld + 31) / 32;
+    const int64_t nwarp = (n_chunks + 31) / 32;
+    for (int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wg < nwarp;
+         wg += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int ch = (int)(wg * 32 + (threadIdx.x & 31));
+        int u = 0, e0 = 0, len = 0;
+        JlRow jr{0.0, 0};
+        if (ch < n_chunks) {
+            u = chunk_row[ch];
+            e0 = chunk_begin[ch];
+            len = min(kJlChunk, rowptr[u + 1] - e0);
+            jr = jl_row(rowptr, deg, u, inv_k, inv_sqrt_k);
+        }
+        jl_warp_units(eid, col, w, u, jr, e0, len, ncb, cb_off, seed, st,
+                      [&](int cb, const long long(&acc)[32]) {
+                          if (ch >= n_chunks) return;
+#pragma unroll
+                          for (int q = 0; q < 32; ++q) part[((size_t)ch * ncb + cb) * 32 + q] = acc[q];
+                      });
     }
 }
 
@@ -384,11 +447,11 @@ void jl_rhs(lap_hierarchy *h, int k_total, int row0, int k, int ld, uint64_t see
     const int cb_off = row0 / 32;
     // entries: eid, col, weight (16 B); rows: rowptr, degree; the block of Y
     const double bytes = (double)L.nnz * 16 + (double)n * 12 + (double)n * ld * 8;
-    CFC_LAUNCH(LAP_KF_CFC, s, bytes, k_jl_short, grid_for((int64_t)n * ncb, 128), 128, 0, L.rowptr.get(),
+    CFC_LAUNCH(LAP_KF_CFC, s, bytes, k_jl_short, grid_for((int64_t)n, 32 * kJlWarps), 32 * kJlWarps, 0, L.rowptr.get(),
                h->eid.get(), L.col.get(), L.w64.get(), L.deg64.get(), n, k, ld, cb_off, seed, inv_k, inv_sqrt_k, Y);
     if (L.jl_n_chunks > 0) {  // rows longer than kJlRow: chunk partials, then exact sums per row
         DBuf<long long> part((size_t)L.jl_n_chunks * ncb * 32, s);
-        CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_jl_chunks, grid_for((int64_t)L.jl_n_chunks * ncb, 128), 128, 0,
+        CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_jl_chunks, grid_for((int64_t)L.jl_n_chunks, 32 * kJlWarps), 32 * kJlWarps, 0,
                    L.rowptr.get(), h->eid.get(), L.col.get(), L.w64.get(), L.deg64.get(), L.jl_chunk_row.get(),
                    L.jl_chunk_begin.get(), L.jl_n_chunks, ld, cb_off, seed, inv_k, inv_sqrt_k, part.get());
         CFC_LAUNCH(LAP_KF_CFC, s, 0.0, k_jl_long, grid_for((int64_t)L.jl_n_long * ld, 128), 128, 0,
