@@ -167,13 +167,13 @@ def run_serving(P, specs, n_queries, loads, seed=4, n_pivots=200, slots=4, resid
 
 
 def kernel_source_digest():
-    """Digest of the solver kernels' sources, the row-kernel templates and the
-    solver (comments and blank lines left out, so that documentation edits
-    keep stored counters valid)."""
+    """Digest of the solver kernels' sources: the row-kernel templates, the
+    solver and the shared header with their constants (comments and blank
+    lines left out, so that documentation edits keep stored counters valid)."""
     import hashlib
     import re
     h = hashlib.sha256()
-    for f in ("rowops.cuh", "solve.cu"):
+    for f in ("rowops.cuh", "solve.cu", "internal.h"):
         with open(os.path.join(ROOT, "paper_1607_02955_gb300", "csrc", f)) as fh:
             text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
         for line in text.splitlines():

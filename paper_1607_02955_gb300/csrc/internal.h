@@ -216,7 +216,7 @@ struct Level {
 
 constexpr int kDenseMax = 2048;  // largest coarsest level solved by a dense inverse
 constexpr int kLongRow = 128;    // rows with more nonzeros are split into chunks
-constexpr int kChunk = 64;       // nonzeros per chunk of a split row
+constexpr int kChunk = 128;      // nonzeros per chunk of a split row
 constexpr int kJlRow = 32;       // the JL right-hand sides: rows with more entries are split
 constexpr int kJlChunk = 32;     //   into chunks of this many (one thread each)
 constexpr int kMaxTiles = 64;    // column tiles per launch (k <= 64 * 64)
