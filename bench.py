@@ -610,6 +610,8 @@ def hier_opts(P, args):
         kw["aggregation"] = {"strength": 0, "affinity": 1}[args.aggregation]
     if getattr(args, "hub_factor", None) is not None:
         kw["hub_factor"] = args.hub_factor
+    if getattr(args, "chunking", None) is not None:
+        kw["chunking"] = args.chunking
     return P.lap_default_hier_opts(**kw)
 
 
@@ -868,6 +870,8 @@ def main():
                     help="hierarchy option aggregation (default: strength)")
     ap.add_argument("--hub-factor", type=int, default=None,
                     help="hierarchy option hub_factor (default 0: no hub rule)")
+    ap.add_argument("--chunking", type=int, default=None, choices=[0, 1, 2],
+                    help="hierarchy option chunking (default 0: by level size)")
     ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS),
                     help="arithmetic of the solve (fp32: FP32 PCG + V-cycle in FP64 refinement)")
     ap.add_argument("--launch-log", default=None,
@@ -934,7 +938,8 @@ def main():
                        "levels_built": hinfo["levels"], "level_n": hinfo["level_n"], "setup_ms": hinfo["setup_ms"],
                        "level_row_order": hinfo["level_row_order"], "elim_levels": hinfo["elim_levels"],
                        "hier_opts": {"coarse_max": hopts.coarse_max, "aggregation": hopts.aggregation,
-                                     "hub_factor": hopts.hub_factor, "eliminate": hopts.eliminate},
+                                     "hub_factor": hopts.hub_factor, "eliminate": hopts.eliminate,
+                                     "chunking": hopts.chunking},
                        "solve": {key: sinfo[key] for key in ("outer_iters", "inner_iters", "max_rel_residual",
                                                               "k_tile", "levels_used", "nu_coarse", "cycle",
                                                               "coarse_scale", "w_levels")},

@@ -33,7 +33,8 @@ SYMBOLS = [
 class HierOpts(C.Structure):
     _fields_ = [("coarse_max", C.c_int32), ("max_levels", C.c_int32), ("agg_passes", C.c_int32),
                 ("match_rounds", C.c_int32), ("eager", C.c_int32), ("eliminate", C.c_int32),
-                ("reorder", C.c_int32), ("aggregation", C.c_int32), ("hub_factor", C.c_int32)]
+                ("reorder", C.c_int32), ("aggregation", C.c_int32), ("chunking", C.c_int32),
+                ("hub_factor", C.c_int32)]
 
 
 class SolveOpts(C.Structure):

@@ -327,7 +327,7 @@ __global__ void k_finish(const int32_t *__restrict__ rowptr, const double *__res
                          const double *__restrict__ deg64, int32_t n, int64_t nnz, double sc,
                          float *__restrict__ w32, float *__restrict__ deg32, float *__restrict__ dinv32,
                          double *__restrict__ dinv64, int32_t *__restrict__ nchunk,
-                         unsigned long long *__restrict__ inexact) {
+                         unsigned long long *__restrict__ inexact, int long_row, int chunk) {
     // inexact: set when some FP32 weight is not exactly the scaled FP64 one
     bool bad = false;
     GRID_LOOP(e, nnz) {
@@ -345,7 +345,7 @@ __global__ void k_finish(const int32_t *__restrict__ rowptr, const double *__res
         dinv32[i] = (deg32[i] > 0.f && di <= 3.0e38) ? (float)di : 0.f;
         dinv64[i] = 1.0 / d;
         const int len = rowptr[i + 1] - rowptr[i];
-        nchunk[i] = len > kLongRow ? (len + kChunk - 1) / kChunk : 0;
+        nchunk[i] = len > long_row ? (len + chunk - 1) / chunk : 0;
     }
 }
 
@@ -431,16 +431,17 @@ __global__ void k_bf16_level(const int32_t *__restrict__ rowptr, const double *_
 }
 
 // gather rounds of the row kernels (4 neighbours per round, rows up to
-// kLongRow) in the natural order, four rows sharing a warp: [0] the sum over
+// long_row) in the natural order, four rows sharing a warp: [0] the sum over
 // warps of their longest row's rounds, [1] the sum over rows of their rounds
-__global__ void k_order_stats(const int32_t *__restrict__ rowptr, int32_t n, unsigned long long *__restrict__ out) {
+__global__ void k_order_stats(const int32_t *__restrict__ rowptr, int32_t n, int long_row,
+                              unsigned long long *__restrict__ out) {
     unsigned long long wmax = 0, rsum = 0;
     GRID_LOOP(w, ((int64_t)n + 3) / 4) {
         unsigned long long m = 0;
         for (int j = 0; j < 4; ++j) {
             const int64_t i = 4 * w + j;
             if (i >= n) break;
-            const int len = min(rowptr[i + 1] - rowptr[i], kLongRow + 1);
+            const int len = min(rowptr[i + 1] - rowptr[i], long_row + 1);
             const unsigned long long rounds = (unsigned long long)((len + 3) / 4);
             m = rounds > m ? rounds : m;
             rsum += rounds;
@@ -458,12 +459,12 @@ __global__ void k_order_stats(const int32_t *__restrict__ rowptr, int32_t n, uns
 }
 
 // sort key of a row for the processing order: shorter rows later, rows longer
-// than kLongRow (handled in chunks) first, equal lengths in row order
-__global__ void k_order_keys(const int32_t *__restrict__ rowptr, int32_t n, uint64_t *__restrict__ keys,
-                             uint32_t *__restrict__ vals) {
+// than long_row first, equal lengths in row order
+__global__ void k_order_keys(const int32_t *__restrict__ rowptr, int32_t n, int long_row,
+                             uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
     GRID_LOOP(i, n) {
         const int len = rowptr[i + 1] - rowptr[i];
-        keys[i] = (uint64_t)(kLongRow + 1 - min(len, kLongRow + 1));
+        keys[i] = (uint64_t)(long_row + 1 - min(len, long_row + 1));
         vals[i] = (uint32_t)i;
     }
 }
@@ -477,11 +478,12 @@ __global__ void k_chunk_keys(const int32_t *__restrict__ col, const int32_t *__r
     }
 }
 
-// chunks of each row of (rowptr, n): rows longer than kLongRow take ceil(len / kChunk)
-__global__ void k_nchunk(const int32_t *__restrict__ rowptr, int32_t n, int32_t *__restrict__ nchunk) {
+// chunks of each row of (rowptr, n): rows longer than long_row take ceil(len / chunk)
+__global__ void k_nchunk(const int32_t *__restrict__ rowptr, int32_t n, int long_row, int chunk,
+                         int32_t *__restrict__ nchunk) {
     GRID_LOOP(i, n) {
         const int len = rowptr[i + 1] - rowptr[i];
-        nchunk[i] = len > kLongRow ? (len + kChunk - 1) / kChunk : 0;
+        nchunk[i] = len > long_row ? (len + chunk - 1) / chunk : 0;
     }
 }
 
@@ -521,6 +523,7 @@ __global__ void k_long_index(const int32_t *__restrict__ nchunk, int32_t n, int3
 
 __global__ void k_fill_chunks(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ nchunk,
                               const int32_t *__restrict__ cfirst, const int32_t *__restrict__ lidx, int32_t n,
+                              int chunk,
                               int32_t *__restrict__ chunk_row, int32_t *__restrict__ chunk_begin,
                               int32_t *__restrict__ chunk_long, int32_t *__restrict__ long_first,
                               int32_t *__restrict__ long_of_row) {
@@ -532,7 +535,7 @@ __global__ void k_fill_chunks(const int32_t *__restrict__ rowptr, const int32_t 
         long_first[l] = f;
         for (int t = 0; t < c; ++t) {
             chunk_row[f + t] = (int32_t)i;
-            chunk_begin[f + t] = rowptr[i] + t * kChunk;
+            chunk_begin[f + t] = rowptr[i] + t * chunk;
             chunk_long[f + t] = l;
         }
     }
@@ -1124,9 +1127,10 @@ int max_exponent(const double *v, int64_t n, cudaStream_t s) {
     return mx > 0.0 ? std::ilogb(mx) : 0;
 }
 
-void finish_level(Level &L, int wexp, int reorder, cudaStream_t s) {
+void finish_level(Level &L, int wexp, int reorder, int chunking, cudaStream_t s) {
     const int32_t n = L.n;
     const int64_t nnz = L.nnz;
+    chunk_params(n, chunking, &L.long_row, &L.chunk);
     L.w32.alloc_persistent(std::max<int64_t>(nnz, 1));
     L.deg32.alloc_persistent(n);
     L.dinv32.alloc_persistent(n);
@@ -1138,11 +1142,12 @@ void finish_level(Level &L, int wexp, int reorder, cudaStream_t s) {
     tot.zero(s);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_finish, grid_for(std::max<int64_t>(nnz, n)), kBlock, 0, L.rowptr.get(),
                L.w64.get(), L.deg64.get(), n, nnz, std::ldexp(1.0, -wexp), L.w32.get(), L.deg32.get(),
-               L.dinv32.get(), L.dinv64.get(), nchunk.get(), reinterpret_cast<unsigned long long *>(tot.get() + 4));
+               L.dinv32.get(), L.dinv64.get(), nchunk.get(), reinterpret_cast<unsigned long long *>(tot.get() + 4),
+               L.long_row, L.chunk);
     scan_exclusive_i32_total(nchunk.get(), cfirst.get(), n, tot.get(), s);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_long_index, grid_for(n), kBlock, 0, nchunk.get(), n, isl.get());
     scan_exclusive_i32_total(isl.get(), lidx.get(), n, tot.get() + 1, s);
-    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_order_stats, grid_for((n + 3) / 4), kBlock, 0, L.rowptr.get(), n,
+    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_order_stats, grid_for((n + 3) / 4), kBlock, 0, L.rowptr.get(), n, L.long_row,
                reinterpret_cast<unsigned long long *>(tot.get() + 2));
     int64_t h[5];
     read_totals(tot.get(), 5, h, s);
@@ -1163,9 +1168,10 @@ void finish_level(Level &L, int wexp, int reorder, cudaStream_t s) {
     if (reorder == 2 || (reorder == 0 && uneven)) {
         DBuf<uint64_t> keys(n, s);
         L.order.alloc_persistent(n);
-        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_order_keys, grid_for(n), kBlock, 0, L.rowptr.get(), n, keys.get(),
-                   reinterpret_cast<uint32_t *>(L.order.get()));
-        radix_sort_pairs(keys.get(), reinterpret_cast<uint32_t *>(L.order.get()), n, 6, s);
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_order_keys, grid_for(n), kBlock, 0, L.rowptr.get(), n, L.long_row,
+                   keys.get(), reinterpret_cast<uint32_t *>(L.order.get()));
+        // keys in [0, long_row + 1]
+        radix_sort_pairs(keys.get(), reinterpret_cast<uint32_t *>(L.order.get()), n, bits_for(L.long_row + 2), s);
     }
     if (L.n_chunks == 0) return;
     L.chunk_row.alloc_persistent(L.n_chunks);
@@ -1174,7 +1180,7 @@ void finish_level(Level &L, int wexp, int reorder, cudaStream_t s) {
     L.long_first.alloc_persistent(L.n_long + 1);
     L.long_of_row.alloc_persistent(n);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_fill_chunks, grid_for(n), kBlock, 0, L.rowptr.get(), nchunk.get(),
-               cfirst.get(), lidx.get(), n, L.chunk_row.get(), L.chunk_begin.get(), L.chunk_long.get(),
+               cfirst.get(), lidx.get(), n, L.chunk, L.chunk_row.get(), L.chunk_begin.get(), L.chunk_long.get(),
                L.long_first.get(), L.long_of_row.get());
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_set_last, 1, 1, 0, L.long_first.get(), L.n_long, L.n_chunks);
     // chunks in ascending order of their first column (stable: row order among equals)
@@ -1328,7 +1334,9 @@ bool eliminate_level(lap_hierarchy &h, double min_frac, cudaStream_t s) {
         DBuf<int32_t> nchunk(nk, s), cfirst(nk, s), isl(nk, s), lidx(nk, s);
         DBuf<int64_t> ct(2, s);
         ct.zero(s);
-        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_nchunk, grid_for(nk), kBlock, 0, F.pull_ptr.get(), nk, nchunk.get());
+        chunk_params(nk, h.hopts.chunking, &F.pull_long_row, &F.pull_chunk);
+        CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_nchunk, grid_for(nk), kBlock, 0, F.pull_ptr.get(), nk, F.pull_long_row,
+                   F.pull_chunk, nchunk.get());
         scan_exclusive_i32_total(nchunk.get(), cfirst.get(), nk, ct.get(), s);
         CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_long_index, grid_for(nk), kBlock, 0, nchunk.get(), nk, isl.get());
         scan_exclusive_i32_total(isl.get(), lidx.get(), nk, ct.get() + 1, s);
@@ -1343,7 +1351,7 @@ bool eliminate_level(lap_hierarchy &h, double min_frac, cudaStream_t s) {
             F.pull_long_first.alloc_persistent(F.pull_n_long + 1);
             F.pull_long_of_row.alloc_persistent(nk);
             CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_fill_chunks, grid_for(nk), kBlock, 0, F.pull_ptr.get(), nchunk.get(),
-                       cfirst.get(), lidx.get(), nk, F.pull_chunk_row.get(), F.pull_chunk_begin.get(),
+                       cfirst.get(), lidx.get(), nk, F.pull_chunk, F.pull_chunk_row.get(), F.pull_chunk_begin.get(),
                        F.pull_chunk_long.get(), F.pull_long_first.get(), F.pull_long_of_row.get());
             CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_set_last, 1, 1, 0, F.pull_long_first.get(), F.pull_n_long,
                        F.pull_n_chunks);
@@ -1357,7 +1365,7 @@ bool eliminate_level(lap_hierarchy &h, double min_frac, cudaStream_t s) {
     Cl.w64 = std::move(C.w);
     Cl.deg64 = std::move(C.deg);
     h.lv.push_back(std::move(Cl));
-    finish_level(h.lv.back(), h.wexp, h.hopts.reorder, s);
+    finish_level(h.lv.back(), h.wexp, h.hopts.reorder, h.hopts.chunking, s);
     return true;
 }
 
@@ -1416,7 +1424,7 @@ void init_levels(lap_hierarchy &h, Csr64 &fine, const lap_hier_opts_t &o, cudaSt
     h.coarse_n = 0;
     // the same values as max_exponent and graph_fingerprint, with one pass and one synchronisation
     fingerprint_and_exponent(L0, &h.fingerprint, &h.wexp, s);
-    finish_level(L0, h.wexp, o.reorder, s);
+    finish_level(L0, h.wexp, o.reorder, o.chunking, s);
     const int64_t low = build_jl_chunks(L0, s);
     h.p0 = 0;
     // low-degree elimination when it removes at least 5 % of the nodes (the
@@ -1532,7 +1540,7 @@ void grow_levels(lap_hierarchy &h, int target, cudaStream_t s) {
         Cl.w64 = std::move(C.w);
         Cl.deg64 = std::move(C.deg);
         h.lv.push_back(std::move(Cl));
-        finish_level(h.lv.back(), h.wexp, o.reorder, s);
+        finish_level(h.lv.back(), h.wexp, o.reorder, o.chunking, s);
         CFC_CUDA(cudaEventRecord(ev1, s));
         CFC_CUDA(cudaEventSynchronize(ev1));
         float ms = 0.f;

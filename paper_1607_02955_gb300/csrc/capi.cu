@@ -173,6 +173,8 @@ LevelView view(const Level &L) {
     v.dinv64 = L.dinv64.get();
     v.n_chunks = L.n_chunks;
     v.n_long = L.n_long;
+    v.long_row = L.long_row;
+    v.chunk = L.chunk;
     v.chunk_row = L.chunk_row.get();
     v.chunk_begin = L.chunk_begin.get();
     v.chunk_long = L.chunk_long.get();
@@ -201,6 +203,8 @@ LevelView pull_view(const Level &E) {
     v.w64 = E.pull_c64.get();
     v.n_chunks = E.pull_n_chunks;
     v.n_long = E.pull_n_long;
+    v.long_row = E.pull_long_row;
+    v.chunk = E.pull_chunk;
     v.chunk_row = E.pull_chunk_row.get();
     v.chunk_begin = E.pull_chunk_begin.get();
     v.chunk_long = E.pull_chunk_long.get();
@@ -248,6 +252,7 @@ void lap_default_hier_opts(lap_hier_opts_t *o) {
     o->reorder = 0;
     o->aggregation = LAP_AGG_STRENGTH;
     o->hub_factor = 0;
+    o->chunking = 0;
 }
 
 void lap_default_solve_opts(lap_solve_opts_t *o) {
@@ -303,6 +308,7 @@ lap_status_t lap_build_hierarchy(int64_t n, int64_t m, const int32_t *src, const
         CFC_REQUIRE(o.aggregation == LAP_AGG_STRENGTH || o.aggregation == LAP_AGG_AFFINITY, LAP_EINVAL,
                     "aggregation must be LAP_AGG_STRENGTH or LAP_AGG_AFFINITY");
         CFC_REQUIRE(o.hub_factor >= 0 && o.hub_factor <= 1000000, LAP_EINVAL, "hub_factor must be in [0, 1e6]");
+        CFC_REQUIRE(o.chunking >= 0 && o.chunking <= 2, LAP_EINVAL, "chunking must be 0, 1 or 2");
         cudaStream_t s = (cudaStream_t)stream;
         auto *h = new lap_hierarchy();
         try {

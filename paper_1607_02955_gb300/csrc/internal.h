@@ -164,7 +164,9 @@ struct Level {
     // rounded weights, made on first use by a solve in the BF16-coarse mode
     DBuf<uint16_t> wbf;
     DBuf<float> degbf, dinvbf;
-    // rows longer than kLongRow nonzeros are split into chunks of kChunk
+    // rows longer than long_row nonzeros are split into chunks of `chunk`
+    // (chunk_params: short chunks on levels whose blocks stay in L2)
+    int32_t long_row = 0, chunk = 0;
     int32_t n_long = 0, n_chunks = 0;
     DBuf<int32_t> chunk_row;     // [n_chunks] row of each chunk
     DBuf<int32_t> chunk_begin;   // [n_chunks] first nonzero of the chunk
@@ -209,14 +211,29 @@ struct Level {
     // rows longer than kJlRow in chunks of kJlChunk (one thread sums a chunk)
     int32_t jl_n_chunks = 0, jl_n_long = 0;
     DBuf<int32_t> jl_chunk_row, jl_chunk_begin, jl_long_first;
-    // pull lists longer than kLongRow split into chunks of kChunk, as the rows of a level
+    // pull lists longer than pull_long_row split into chunks of pull_chunk, as the rows of a level
+    int32_t pull_long_row = 0, pull_chunk = 0;
     int32_t pull_n_chunks = 0, pull_n_long = 0;
     DBuf<int32_t> pull_chunk_row, pull_chunk_begin, pull_chunk_long, pull_long_first, pull_long_of_row;
 };
 
 constexpr int kDenseMax = 2048;  // largest coarsest level solved by a dense inverse
-constexpr int kLongRow = 128;    // rows with more nonzeros are split into chunks
-constexpr int kChunk = 128;      // nonzeros per chunk of a split row
+// Long rows are split into chunks, per level: a level with at most
+// kBigLevelRows rows (its 64-column FP32 blocks, at most 128 MB, stay in the
+// L2) splits rows longer than 32 into chunks of 16, for parallelism; a larger
+// one splits rows longer than 128 into chunks of 128, which cuts the chunk
+// partials that go through DRAM (measured: BA 100k 18.9k RHS/s with the short
+// chunks against 16.1k with the long ones; R-MAT 24's SpMV 118 ms per step
+// with the long ones against 186 with the short ones).  mode (the hierarchy
+// option `chunking`): 0 by size, 1 short, 2 long.
+constexpr int kLongRowSmall = 32, kChunkSmall = 16;
+constexpr int kLongRowBig = 128, kChunkBig = 128;
+constexpr int64_t kBigLevelRows = int64_t(1) << 19;
+inline void chunk_params(int64_t rows, int mode, int32_t *long_row, int32_t *chunk) {
+    const bool big = mode == 2 || (mode == 0 && rows > kBigLevelRows);
+    *long_row = big ? kLongRowBig : kLongRowSmall;
+    *chunk = big ? kChunkBig : kChunkSmall;
+}
 constexpr int kJlRow = 32;       // the JL right-hand sides: rows with more entries are split
 constexpr int kJlChunk = 32;     //   into chunks of this many (one thread each)
 constexpr int kMaxTiles = 64;    // column tiles per launch (k <= 64 * 64)
@@ -230,6 +247,7 @@ struct LevelView {
     const uint16_t *wbf;  // BF16 weights, read by the kernels instantiated for them
     const double *w64, *deg64, *dinv64;
     int32_t n_chunks, n_long;
+    int32_t long_row, chunk;  // rows longer than long_row are split into chunks of `chunk`
     const int32_t *chunk_row, *chunk_begin, *chunk_long, *long_first, *long_of_row, *order, *chunk_order;
     uint32_t *long_count;  // [n_long * kMaxTiles] arrival counters of the launching solve
 };
@@ -284,7 +302,7 @@ int effective_coarse_max(const lap_hierarchy &h);                 // the option,
 // w * 2^-wexp (see lap_hierarchy::wexp)
 void ensure_bf16(Level &L, int wexp, cudaStream_t s);
 // FP32 copies, inverse degrees, long-row split, row order (reorder as lap_hier_opts_t)
-void finish_level(Level &L, int wexp, int reorder, cudaStream_t s);
+void finish_level(Level &L, int wexp, int reorder, int chunking, cudaStream_t s);
 // Exponent of the largest of n positive FP64 values (device array): the e with
 // 2^e <= max < 2^(e+1).  Synchronises s.
 int max_exponent(const double *v, int64_t n, cudaStream_t s);

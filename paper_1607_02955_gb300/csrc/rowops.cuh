@@ -8,7 +8,7 @@
 // grid-stride; on levels with very uneven row lengths the rows are taken in a
 // fixed longest-first order (LevelView::order).
 //
-// Rows with more than kLongRow nonzeros are split into chunks of kChunk.
+// Rows with more than A.long_row nonzeros are split into chunks of A.chunk.
 // Without reductions the group that finishes a row's last chunk (arrival
 // counter) adds the chunk sums in chunk order and runs the row's epilogue;
 // with reductions the chunk sums come from a k_chunk_sums launch just before
@@ -458,11 +458,11 @@ __global__ void __launch_bounds__(kBlock, 4) k_chunk_sums(LevelView A, Op op, T 
     const int ch = A.chunk_order ? __ldg(A.chunk_order + slot) : slot;
     const int i = __ldg(A.chunk_row + ch);
     const int e0 = __ldg(A.chunk_begin + ch);
-    const int e1 = min(e0 + kChunk, __ldg(A.rowptr + i + 1));
+    const int e1 = min(e0 + A.chunk, __ldg(A.rowptr + i + 1));
     vst<T>(chunk_part + (size_t)ch * ld_part + c0, row_sum_of<T, BF, G>(A, op, e0, e1, c0, lane));
 }
 
-// How rows longer than kLongRow are handled:
+// How rows longer than A.long_row are handled:
 //   kLongLast  chunks are spread over groups; the group finishing a row's last
 //              chunk (arrival counter) adds the chunk sums and finishes the row
 //   kLongPre   chunk sums come from k_chunk_sums, launched just before, and the
@@ -497,7 +497,7 @@ __global__ void __launch_bounds__(kBlock, (NR >= 3 ? 3 : 4)) k_rowop(LevelView A
             if (slot < A.n) {
                 const int i = A.order ? __ldg(A.order + slot) : slot;
                 const int e0 = __ldg(A.rowptr + i), e1 = __ldg(A.rowptr + i + 1);
-                if (e1 - e0 <= kLongRow) {
+                if (e1 - e0 <= A.long_row) {
                     const auto pr = op.pre(i, c0);  // own-row operands, in flight with the gathers
                     const V s = row_sum_of<T, BF, G>(A, op, e0, e1, c0, lane);
                     op.epi(i, c0, s, pr, acc);
@@ -518,7 +518,7 @@ __global__ void __launch_bounds__(kBlock, (NR >= 3 ? 3 : 4)) k_rowop(LevelView A
             if (has) {
                 i = __ldg(A.chunk_row + ch);
                 const int e0 = __ldg(A.chunk_begin + ch);
-                const int e1 = min(e0 + kChunk, __ldg(A.rowptr + i + 1));
+                const int e1 = min(e0 + A.chunk, __ldg(A.rowptr + i + 1));
                 const V s = row_sum_of<T, BF, G>(A, op, e0, e1, c0, lane);
                 vst<T>(chunk_part + (size_t)ch * ld_part + c0, s);
                 __threadfence();

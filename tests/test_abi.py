@@ -41,7 +41,7 @@ def test_status_strings_and_defaults(P):
     assert o.tol == 1e-8 and o.precision == P.LAP_FP32_REFINED
     h = P.lap_default_hier_opts()
     assert h.coarse_max == 0 and h.agg_passes == 2 and h.eliminate == 1 and h.reorder == 0
-    assert h.aggregation == 0 and h.hub_factor == 0
+    assert h.aggregation == 0 and h.hub_factor == 0 and h.chunking == 0
     # options the autotuner fills in are left open; cycles are replayed as graphs
     assert (o.levels_used, o.nu_coarse, o.cycle, o.coarse_scale, o.w_levels, o.k_tile) == (0, 0, 0, 0.0, 0, 0)
     assert o.graphs == 1 and o.first_residual_ff == 1

@@ -281,7 +281,8 @@ def test_hub_rule_keeps_a_star_centre_out_of_every_aggregate(P, aggregation):
 
 def test_aggregation_options_are_validated(P):
     n, s, d, _ = synth.grid2d(8)
-    for bad in (dict(aggregation=2), dict(aggregation=-1), dict(hub_factor=-1), dict(hub_factor=2000000)):
+    for bad in (dict(aggregation=2), dict(aggregation=-1), dict(hub_factor=-1), dict(hub_factor=2000000),
+                dict(chunking=3), dict(chunking=-1)):
         with pytest.raises(P.LapError):
             P.lap_build_hierarchy(n, s, d, None, P.lap_default_hier_opts(**bad))
 
@@ -319,3 +320,25 @@ def test_first_residual_in_two_fp32_words(P, weights):
     # FP64 mode never takes it
     info64 = P.lap_solve_multi(h, torch.tensor(B, device="cuda"), X, P.lap_default_solve_opts(precision=0))
     assert info64["first_residual_ff"] == 0
+
+
+# ------------------------------------------------------------------ long-row chunking modes
+@pytest.mark.parametrize("chunking", [1, 2])
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "fp32_all_levels", "bf16coarse"])
+def test_rmat_with_each_chunking(P, rmat14, chunking, precision):
+    # 1: rows longer than 32 in chunks of 16 (small levels); 2: rows longer
+    # than 128 in chunks of 128 (large levels, R-MAT 24's fine level): the
+    # SpMV, the residuals and the elimination's pull lists take them
+    import torch
+    n, s, d, w, g = rmat14
+    assert np.bincount(np.concatenate([s, d])).max() > 2 * 128  # hubs span several long chunks
+    h = P.lap_build_hierarchy(n, s, d, w, P.lap_default_hier_opts(chunking=chunking))
+    B = np.random.default_rng(4).standard_normal((n, 24))
+    X = torch.empty((n, 24), dtype=torch.float64, device="cuda")
+    info = P.lap_solve_multi(h, torch.tensor(B, device="cuda"), X, P.lap_default_solve_opts(**PRECISIONS[precision]))
+    assert info["max_rel_residual"] <= 1e-8
+    _certify(g, B, X.cpu().numpy())
+    nodes = np.array([0, n - 1], np.int32)
+    f = P.cfc_farness_jl(h, 32, 9, nodes, opts=P.lap_default_solve_opts(**PRECISIONS[precision]))
+    fo = jl.jl_farness(g, 32, 9, nodes.tolist(), solver="cg", tol=1e-12)
+    assert _rel(f, fo) <= FARNESS_RTOL
