@@ -11,9 +11,19 @@ namespace cfc {
 
 namespace {
 
-__global__ void k_validate(const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
-                           const double *__restrict__ w, int64_t m, int32_t n, int32_t *__restrict__ flag,
-                           int32_t *__restrict__ keep) {
+// One pass over the input edges: validation, and two CSR candidates per
+// kept edge, (u, v) and (v, u) with key = row * 2^b + col, at slots 2e and
+// 2e + 1.  A dropped edge (self-loop or invalid) gets the key 2^(2b) - 1 in
+// both slots, above every real key (a real key is at most
+// (n-1) 2^b + (n-2) < 2^(2b) - 1), so it sorts to the end.  The kept count
+// and an invalid-edge flag come back in out[0..1].
+__global__ void k_validate_emit(const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+                                const double *__restrict__ w, int64_t m, int32_t n, int b,
+                                uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                                unsigned long long *__restrict__ out) {
+    const uint64_t drop = (uint64_t(1) << (2 * b)) - 1;
+    unsigned long long kept = 0;
+    bool bad = false;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
         const int32_t u = src[e], v = dst[e];
         bool ok = u >= 0 && v >= 0 && u < n && v < n;
@@ -21,23 +31,19 @@ __global__ void k_validate(const int32_t *__restrict__ src, const int32_t *__res
             const double x = w[e];
             ok = ok && x >= 1e-150 && x <= 1e150;
         }
-        if (!ok) atomicOr(flag, 1);
-        keep[e] = (ok && u != v) ? 1 : 0;
+        bad = bad || !ok;
+        const bool keep = ok && u != v;
+        kept += keep ? 1ull : 0ull;
+        keys[2 * e] = keep ? ((uint64_t)(uint32_t)u << b) | (uint32_t)v : drop;
+        keys[2 * e + 1] = keep ? ((uint64_t)(uint32_t)v << b) | (uint32_t)u : drop;
+        vals[2 * e] = (uint32_t)e;
+        vals[2 * e + 1] = (uint32_t)e;
     }
-}
-
-// two CSR candidates per kept edge: (u, v) and (v, u); key = row * 2^b + col
-__global__ void k_emit_pairs(const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
-                             const int32_t *__restrict__ keep, const int32_t *__restrict__ pos, int64_t m, int b,
-                             uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
-        if (!keep[e]) continue;
-        const uint64_t u = (uint32_t)src[e], v = (uint32_t)dst[e];
-        const int64_t p = 2 * (int64_t)pos[e];
-        keys[p] = (u << b) | v;
-        vals[p] = (uint32_t)e;
-        keys[p + 1] = (v << b) | u;
-        vals[p + 1] = (uint32_t)e;
+    for (int o = 16; o > 0; o >>= 1) kept += __shfl_down_sync(0xffffffffu, kept, o);
+    const bool anybad = __any_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0) {
+        if (kept) atomicAdd(out + 1, kept);
+        if (anybad) atomicOr(out, 1ull);
     }
 }
 
@@ -251,8 +257,8 @@ void ingest(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const 
     CFC_REQUIRE(m >= 1 && 2 * m < (int64_t(1) << 31) - 1, LAP_EINVAL, "need 1 <= m and 2m < 2^31");
     DBuf<int32_t> ts, td;
     DBuf<double> tw;
-    // endpoints in page-locked host memory are read in place (twice, by the
-    // validation and the pair emission): no staging copy
+    // endpoints in page-locked host memory are read in place, once, by the
+    // validation and pair emission: no staging copy
     const void *ms = mapped_host_pointer(src), *md = mapped_host_pointer(dst);
     const int32_t *ds = ms ? static_cast<const int32_t *>(ms) : to_device(src, m, ts, s);
     const int32_t *dd = md ? static_cast<const int32_t *>(md) : to_device(dst, m, td, s);
@@ -262,26 +268,21 @@ void ingest(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const 
     // edges, [2] merged entries, [3] union-find roots
     DBuf<int64_t> tot(4, s);
     tot.zero(s);
-    DBuf<int32_t> keep(m, s), pos(m, s);
-    const double eb = (double)m * (8.0 + (w ? 8.0 : 0.0));
-    // invalid edges get keep = 0, so nothing downstream reads them before the flag is checked
-    CFC_LAUNCH(LAP_KF_SETUP, s, eb, k_validate, grid_for(m), kBlock, 0, ds, dd, dw, m, (int32_t)n,
-               reinterpret_cast<int32_t *>(tot.get()), keep.get());
-    scan_exclusive_i32_total(keep.get(), pos.get(), m, tot.get() + 1, s);
+    const int b = bits_for(n);
+    DBuf<uint64_t> keys(2 * m, s);
+    DBuf<uint32_t> vals(2 * m, s);
+    const double eb = (double)m * (8.0 + (w ? 8.0 : 0.0) + 24.0);
+    // dropped edges sort behind the 2 kept candidates of every kept edge
+    CFC_LAUNCH(LAP_KF_SETUP, s, eb, k_validate_emit, grid_for(m), kBlock, 0, ds, dd, dw, m, (int32_t)n, b,
+               keys.get(), vals.get(), reinterpret_cast<unsigned long long *>(tot.get()));
     int64_t h[4];
     read_totals(tot.get(), 2, h, s);
     CFC_REQUIRE(h[0] == 0, LAP_EINVAL, "edge endpoint out of range or weight outside [1e-150, 1e150]");
     const int64_t kept = h[1];
     CFC_REQUIRE(kept > 0, LAP_ENOTCONN, "graph has no edges besides self-loops");
     const int64_t len = 2 * kept;
-    const int b = bits_for(n);
-    DBuf<uint64_t> keys(len, s);
-    DBuf<uint32_t> vals(len, s);
-    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_emit_pairs, grid_for(m), kBlock, 0, ds, dd, keep.get(), pos.get(), m, b,
-               keys.get(), vals.get());
-    keep.release();
-    pos.release();
-    radix_sort_pairs(keys.get(), vals.get(), len, 2 * b, s);
+    // the dropped edges' slots have the largest key: the sort moves them past len
+    radix_sort_pairs(keys.get(), vals.get(), 2 * m, 2 * b, s);
 
     DBuf<int32_t> head(len, s), hpos(len, s);
     CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_heads, grid_for(len), kBlock, 0, keys.get(), len, head.get());
