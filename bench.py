@@ -534,51 +534,58 @@ def _ranks(x):
     return r
 
 
+def accuracy_rows(P, torch, spec, eps_list, piv_list, rng):
+    """The farness of every node of one graph by the projection estimator
+    (k = ceil(ln n / eps^2), Sec. 6.4) and the sampling estimator (|S| pivots),
+    against the exact farness (dense, on the device): per setting the device
+    time, the largest relative error, the Spearman correlation of the
+    closeness ranking with the exact one and the fraction of node pairs whose
+    order flips."""
+    n, s, d, w = make_graph(spec)
+    f_exact, _ = P.cfc_exact_small(n, s, d, w)
+    h = P.lap_build_hierarchy(n, s, d, w)
+    nodes = np.arange(n, dtype=np.int32)
+    pairs = rng.integers(0, n, size=(200000, 2))
+    ex_order = np.sign(f_exact[pairs[:, 0]] - f_exact[pairs[:, 1]])
+    rows = []
+
+    def record(kind, param, fn):
+        fn()  # first call: autotuning for this column count
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        f = fn()
+        ms = (time.perf_counter() - t0) * 1e3
+        rel = float(np.max(np.abs(f - f_exact) / f_exact))
+        rho = float(np.corrcoef(_ranks(f), _ranks(f_exact))[0, 1])
+        flips = float(np.mean(np.sign(f[pairs[:, 0]] - f[pairs[:, 1]]) != ex_order))
+        rows.append({"estimator": kind, **param, "ms": ms, "max_rel_err": rel, "spearman": rho,
+                     "pair_flips": flips})
+
+    for eps in eps_list:
+        k = int(np.ceil(np.log(n) / eps ** 2))
+        record("projection", {"eps": eps, "k": k}, lambda k=k: P.cfc_farness_jl(h, k, 1, nodes))
+    for piv in piv_list:
+        # the sampling estimate scales a sum over |S| pivots by n/|S| (Proposition 1)
+        record("sampling", {"pivots": piv}, lambda piv=piv: P.cfc_farness_sampled(h, piv, 1, nodes))
+    h.destroy()
+    return {"n": n, "m": int(s.size), "rows": rows}
+
+
+ACCURACY_GRAPHS = {"ba3000": dict(kind="ba", n=3000, m_per=5, seed=2), "grid48": dict(kind="grid", a=48)}
+
+
 def accuracy_main(args):
     """Accuracy against time of the two estimators on synthetic graphs (the
-    shape of Sec. 6.4): the exact farness of every node (dense, on the device)
-    against the projection estimator at eps = 0.5 .. 0.05 (k = ceil(ln n /
-    eps^2), Sec. 6.4) and the sampling estimator with |S| = 10 .. 1000 pivots,
-    every node queried.  Reports per setting the device time, the largest
-    relative farness error, the Spearman correlation of the closeness ranking
-    with the exact one, and the fraction of node pairs whose order flips."""
+    shape of Sec. 6.4): eps = 0.5 .. 0.05 and |S| = 10 .. 1000, every node
+    queried (accuracy_rows)."""
     import torch
     torch.cuda.init()
     import paper_1607_02955_gb300 as P
     from paper_1607_02955_gb300 import build_ext
     build_ext.build()
-    graphs = {"ba3000": dict(kind="ba", n=3000, m_per=5, seed=2), "grid48": dict(kind="grid", a=48)}
-    out = {}
     rng = np.random.default_rng(4)
-    for name, spec in graphs.items():
-        n, s, d, w = make_graph(spec)
-        f_exact, _ = P.cfc_exact_small(n, s, d, w)
-        h = P.lap_build_hierarchy(n, s, d, w)
-        nodes = np.arange(n, dtype=np.int32)
-        pairs = rng.integers(0, n, size=(200000, 2))
-        ex_order = np.sign(f_exact[pairs[:, 0]] - f_exact[pairs[:, 1]])
-        rows = []
-
-        def record(kind, param, fn):
-            fn()  # first call: autotuning for this column count
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            f = fn()
-            ms = (time.perf_counter() - t0) * 1e3
-            rel = float(np.max(np.abs(f - f_exact) / f_exact))
-            rho = float(np.corrcoef(_ranks(f), _ranks(f_exact))[0, 1])
-            flips = float(np.mean(np.sign(f[pairs[:, 0]] - f[pairs[:, 1]]) != ex_order))
-            rows.append({"estimator": kind, **param, "ms": ms, "max_rel_err": rel, "spearman": rho,
-                         "pair_flips": flips})
-
-        for eps in (0.5, 0.4, 0.3, 0.2, 0.1, 0.05):
-            k = int(np.ceil(np.log(n) / eps ** 2))
-            record("projection", {"eps": eps, "k": k}, lambda k=k: P.cfc_farness_jl(h, k, 1, nodes))
-        for piv in (10, 30, 100, 300, 1000):
-            # the sampling estimate scales a sum over |S| pivots by n/|S| (Proposition 1)
-            record("sampling", {"pivots": piv}, lambda piv=piv: P.cfc_farness_sampled(h, piv, 1, nodes))
-        h.destroy()
-        out[name] = {"n": n, "m": int(s.size), "rows": rows}
+    out = {name: accuracy_rows(P, torch, spec, (0.5, 0.4, 0.3, 0.2, 0.1, 0.05), (10, 30, 100, 300, 1000), rng)
+           for name, spec in ACCURACY_GRAPHS.items()}
     print(json.dumps({"metric": "estimator accuracy vs device time", "data": "synthetic", "n_gpus": 1,
                       "config": {"workload": "accuracy", "queried": "every node"}, "accuracy": out}), flush=True)
 
@@ -973,6 +980,12 @@ def main():
                 res2 = gpu_workload(P, torch, args.workload, args, 1, 1, local, 1, full=False)
                 line["precision_comparison"] = precision_comparison(P, torch, res2, args)
                 del res2
+        if world == 1 and not args.no_compare:
+            # the accuracy experiment (Sec. 6.4's shape) at two settings of each estimator
+            line["accuracy"] = {"ba3000": accuracy_rows(P, torch, ACCURACY_GRAPHS["ba3000"], (0.3, 0.1), (10, 100),
+                                                         np.random.default_rng(4)),
+                                "note": "every node queried; exact farness from the dense pseudoinverse on the "
+                                        "device; `--workload accuracy` runs the full sweep on two graphs"}
         if world == 1 and not args.no_serving:
             line["serving"] = run_serving(P, SERVE_SMALL, n_queries=48, loads=(0.5,))
             line["serving_resident_pivots"] = run_serving(P, SERVE_SMALL, n_queries=48, loads=(0.5,),
