@@ -351,8 +351,8 @@ __global__ void k_finish(const int32_t *__restrict__ rowptr, const double *__res
 
 // Order-free fingerprint of a level's graph: the sum (mod 2^64) over its CSR
 // entries of the MurmurHash3 finaliser (fmix64) of (row, column) mixed with
-// the weight's bit pattern; one warp per row, lanes striding its entries.
-// Integer sums commute, so the value does not depend on scheduling.
+// the weight's bit pattern.  Integer sums commute, so the value does not
+// depend on scheduling.
 __device__ __forceinline__ unsigned long long fmix64(unsigned long long x) {
     x ^= x >> 33;
     x *= 0xff51afd7ed558ccdull;
@@ -360,19 +360,6 @@ __device__ __forceinline__ unsigned long long fmix64(unsigned long long x) {
     x *= 0xc4ceb9fe1a85ec53ull;
     x ^= x >> 33;
     return x;
-}
-__global__ void k_fingerprint(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                              const double *__restrict__ w, int32_t n, unsigned long long *__restrict__ out) {
-    const int lane = threadIdx.x & 31;
-    unsigned long long acc = 0;
-    WARP_ROW_LOOP(i, n) {
-        for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) {
-            const unsigned long long rc = ((unsigned long long)(uint32_t)i << 32) | (uint32_t)col[e];
-            acc += fmix64(rc ^ fmix64((unsigned long long)__double_as_longlong(w[e])));
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0 && acc) atomicAdd(out, acc);
 }
 
 // The fingerprint's sum and the largest weight's bit pattern in one pass over
@@ -1092,16 +1079,6 @@ __global__ void k_elim_emit_pull(const int32_t *__restrict__ e_nb, const int32_t
 
 }  // namespace
 
-uint64_t graph_fingerprint(const Level &L, cudaStream_t s) {
-    DBuf<int64_t> f(1, s);
-    f.zero(s);
-    CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_fingerprint, grid_for(32 * (int64_t)L.n), kBlock, 0, L.rowptr.get(),
-               L.col.get(), L.w64.get(), L.n, reinterpret_cast<unsigned long long *>(f.get()));
-    int64_t h = 0;
-    read_totals(f.get(), 1, &h, s);
-    return (uint64_t)h;
-}
-
 void fingerprint_and_exponent(const Level &L, uint64_t *fp, int *wexp, cudaStream_t s) {
     DBuf<int64_t> f(2, s);
     f.zero(s);
@@ -1422,7 +1399,7 @@ void init_levels(lap_hierarchy &h, Csr64 &fine, const lap_hier_opts_t &o, cudaSt
     h.hopts = o;
     h.complete = false;
     h.coarse_n = 0;
-    // the same values as max_exponent and graph_fingerprint, with one pass and one synchronisation
+    // the graph's fingerprint and the largest weight's exponent, with one pass and one synchronisation
     fingerprint_and_exponent(L0, &h.fingerprint, &h.wexp, s);
     finish_level(L0, h.wexp, o.reorder, o.chunking, s);
     const int64_t low = build_jl_chunks(L0, s);

@@ -306,11 +306,9 @@ void finish_level(Level &L, int wexp, int reorder, int chunking, cudaStream_t s)
 // Exponent of the largest of n positive FP64 values (device array): the e with
 // 2^e <= max < 2^(e+1).  Synchronises s.
 int max_exponent(const double *v, int64_t n, cudaStream_t s);
-// Order-free 64-bit fingerprint of a level's graph (its CSR entries and
-// weights): equal graphs give equal values.  Synchronises s.
-uint64_t graph_fingerprint(const Level &L, cudaStream_t s);
-// graph_fingerprint and max_exponent of the weights of level 0 in one pass
-// (needs L.row_of), one synchronisation of s
+// Order-free 64-bit fingerprint of level 0's graph (its CSR entries and
+// weights: equal graphs give equal values) and max_exponent of its weights,
+// in one pass (needs L.row_of) and one synchronisation of s
 void fingerprint_and_exponent(const Level &L, uint64_t *fp, int *wexp, cudaStream_t s);
 
 // dense SPD inverse (in place, FP64, row-major n x n) for the coarsest level
