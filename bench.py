@@ -623,6 +623,8 @@ def hier_opts(P, args):
         kw["hub_factor"] = args.hub_factor
     if getattr(args, "chunking", None) is not None:
         kw["chunking"] = args.chunking
+    if getattr(args, "reorder", None) is not None:
+        kw["reorder"] = args.reorder
     return P.lap_default_hier_opts(**kw)
 
 
@@ -883,6 +885,8 @@ def main():
                     help="hierarchy option hub_factor (default 0: no hub rule)")
     ap.add_argument("--resident-pivots", action="store_true",
                     help="serve_mix: one resident pivot set per graph (requests solve only their nodes)")
+    ap.add_argument("--reorder", type=int, default=None, choices=[0, 1, 2],
+                    help="hierarchy option reorder (default 0: longest rows first where row lengths are uneven)")
     ap.add_argument("--chunking", type=int, default=None, choices=[0, 1, 2],
                     help="hierarchy option chunking (default 0: by level size)")
     ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS),
@@ -952,7 +956,7 @@ def main():
                        "level_row_order": hinfo["level_row_order"], "elim_levels": hinfo["elim_levels"],
                        "hier_opts": {"coarse_max": hopts.coarse_max, "aggregation": hopts.aggregation,
                                      "hub_factor": hopts.hub_factor, "eliminate": hopts.eliminate,
-                                     "chunking": hopts.chunking},
+                                     "chunking": hopts.chunking, "reorder": hopts.reorder},
                        "solve": {key: sinfo[key] for key in ("outer_iters", "inner_iters", "max_rel_residual",
                                                               "k_tile", "levels_used", "nu_coarse", "cycle",
                                                               "coarse_scale", "w_levels")},
