@@ -110,11 +110,11 @@ typedef struct {
                              elsewhere; 1 natural order; 2 longest first everywhere */
     int32_t aggregation;  /* LAP_AGG_STRENGTH (default) | LAP_AGG_AFFINITY */
     int32_t chunking;     /* how the row kernels split long rows (the hubs): 1 rows longer
-                             than 32 entries in chunks of 16 (many small work units: best
-                             while a level's 64-column block stays in the 129 MB L2), 2
+                             than 32 entries in chunks of 16 (many small work units: best on
+                             small levels, whose short sweeps a long chunk would dominate), 2
                              rows longer than 128 in chunks of 128 (fewer partial sums through
-                             DRAM: best above that); 0 (default): 1 for levels of at most 2^19
-                             rows, 2 above */
+                             DRAM: best on large levels); 0 (default): 1 for levels (and the
+                             elimination's pull lists) of at most 2^22 entries, 2 above */
     int32_t hub_factor;   /* > 0: a node with more than hub_factor x the mean row length of
                              its level neither joins nor absorbs an aggregate (it stays a
                              singleton); 0 (default): no hub rule.  At most 1000000 */

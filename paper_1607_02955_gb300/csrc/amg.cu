@@ -1107,7 +1107,7 @@ int max_exponent(const double *v, int64_t n, cudaStream_t s) {
 void finish_level(Level &L, int wexp, int reorder, int chunking, cudaStream_t s) {
     const int32_t n = L.n;
     const int64_t nnz = L.nnz;
-    chunk_params(n, chunking, &L.long_row, &L.chunk);
+    chunk_params(nnz, chunking, &L.long_row, &L.chunk);
     L.w32.alloc_persistent(std::max<int64_t>(nnz, 1));
     L.deg32.alloc_persistent(n);
     L.dinv32.alloc_persistent(n);
@@ -1311,7 +1311,7 @@ bool eliminate_level(lap_hierarchy &h, double min_frac, cudaStream_t s) {
         DBuf<int32_t> nchunk(nk, s), cfirst(nk, s), isl(nk, s), lidx(nk, s);
         DBuf<int64_t> ct(2, s);
         ct.zero(s);
-        chunk_params(nk, h.hopts.chunking, &F.pull_long_row, &F.pull_chunk);
+        chunk_params(npull, h.hopts.chunking, &F.pull_long_row, &F.pull_chunk);
         CFC_LAUNCH(LAP_KF_SETUP, s, 0.0, k_nchunk, grid_for(nk), kBlock, 0, F.pull_ptr.get(), nk, F.pull_long_row,
                    F.pull_chunk, nchunk.get());
         scan_exclusive_i32_total(nchunk.get(), cfirst.get(), nk, ct.get(), s);

@@ -165,7 +165,7 @@ struct Level {
     DBuf<uint16_t> wbf;
     DBuf<float> degbf, dinvbf;
     // rows longer than long_row nonzeros are split into chunks of `chunk`
-    // (chunk_params: short chunks on levels whose blocks stay in L2)
+    // (chunk_params: short chunks on levels with few entries)
     int32_t long_row = 0, chunk = 0;
     int32_t n_long = 0, n_chunks = 0;
     DBuf<int32_t> chunk_row;     // [n_chunks] row of each chunk
@@ -218,19 +218,21 @@ struct Level {
 };
 
 constexpr int kDenseMax = 2048;  // largest coarsest level solved by a dense inverse
-// Long rows are split into chunks, per level: a level with at most
-// kBigLevelRows rows (its 64-column FP32 blocks, at most 128 MB, stay in the
-// L2) splits rows longer than 32 into chunks of 16, for parallelism; a larger
-// one splits rows longer than 128 into chunks of 128, which cuts the chunk
-// partials that go through DRAM (measured: BA 100k 18.9k RHS/s with the short
-// chunks against 16.1k with the long ones; R-MAT 24's SpMV 118 ms per step
-// with the long ones against 186 with the short ones).  mode (the hierarchy
-// option `chunking`): 0 by size, 1 short, 2 long.
+// Long rows are split into chunks, per level (or per set of pull lists): one
+// with at most kBigLevelEntries entries splits rows longer than 32 into
+// chunks of 16: its sweeps take tens of microseconds, and a 128-entry chunk
+// (32 rounds of gathers by one row group) would be their critical path.  A
+// larger one splits rows longer than 128 into chunks of 128, which cuts the
+// chunk partials that go through DRAM.  Measured: BA 100k (1M entries) 18.9k
+// RHS/s with the short chunks against 16.1k with the long ones; R-MAT 20's
+// PCG level (15.6M entries) SpMV 7.0 against 13.0 ms per step, R-MAT 24's 118
+// against 186.  mode (the hierarchy option `chunking`): 0 by size, 1 short,
+// 2 long.
 constexpr int kLongRowSmall = 32, kChunkSmall = 16;
 constexpr int kLongRowBig = 128, kChunkBig = 128;
-constexpr int64_t kBigLevelRows = int64_t(1) << 19;
-inline void chunk_params(int64_t rows, int mode, int32_t *long_row, int32_t *chunk) {
-    const bool big = mode == 2 || (mode == 0 && rows > kBigLevelRows);
+constexpr int64_t kBigLevelEntries = int64_t(1) << 22;
+inline void chunk_params(int64_t entries, int mode, int32_t *long_row, int32_t *chunk) {
+    const bool big = mode == 2 || (mode == 0 && entries > kBigLevelEntries);
     *long_row = big ? kLongRowBig : kLongRowSmall;
     *chunk = big ? kChunkBig : kChunkSmall;
 }
