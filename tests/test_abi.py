@@ -70,3 +70,36 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(_binding, "_lib", None)
     with pytest.raises(RuntimeError, match="missing"):
         _binding.lib()
+
+
+def test_tune_table_round_trip(P, tmp_path):
+    # host logic only (no GPU): a table read from JSON is written back entry
+    # for entry, loading it twice adds nothing, and a malformed line is
+    # rejected with LAP_EINVAL
+    before = P.lap_tune_entries()
+    src = tmp_path / "tune.json"
+    keys = [("00000000deadbeef", 1000, 5000, 64, 1, 64, 1, 2, 2, 1, 1, 1.0, 0, 64, 1, 1, 1, 1.0, 0),
+            ("0123456789abcdef", 2304, 9024, 32, 0, 32, 1, 2, 2, 4, 2, 1.5, 2, 32, 5, 4, 2, 1.5, 2)]
+    lines = ['{"format": "lap_tune_v1", "entries": [']
+    for i, e in enumerate(keys):
+        k = '"%s", %d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %.17g, %d' % e[:13]
+        c = "%d, %d, %d, %d, %.17g, %d" % e[13:]
+        lines.append('{"key": [%s], "choice": [%s]}%s' % (k, c, "," if i + 1 < len(keys) else ""))
+    lines.append("]}")
+    src.write_text("\n".join(lines) + "\n")
+    assert P.lap_tune_load(str(src)) == 2
+    assert P.lap_tune_load(str(src)) == 0  # already there
+    assert P.lap_tune_entries() == before + 2
+    out = tmp_path / "out.json"
+    P.lap_tune_save(str(out))
+    text = out.read_text()
+    for e in keys:
+        assert '"%s", %d, %d' % e[:3] in text
+    assert P.lap_tune_load(str(out)) == 0
+    bad = tmp_path / "bad.json"
+    bad.write_text('{"key": ["00ff", 1, 2], "choice": [1]}\n')
+    with pytest.raises(P.LapError) as err:
+        P.lap_tune_load(str(bad))
+    assert err.value.status == P.LAP_EINVAL
+    with pytest.raises(P.LapError):
+        P.lap_tune_load(str(tmp_path / "missing.json"))
