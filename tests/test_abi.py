@@ -103,3 +103,16 @@ def test_tune_table_round_trip(P, tmp_path):
     assert err.value.status == P.LAP_EINVAL
     with pytest.raises(P.LapError):
         P.lap_tune_load(str(tmp_path / "missing.json"))
+
+
+def test_hierarchy_options_are_checked_before_device_work(P):
+    # option checks run before any CUDA call, so they hold without a GPU
+    import numpy as np
+    src = np.array([0, 1], np.int32)
+    dst = np.array([1, 2], np.int32)
+    for bad in (dict(agg_passes=0), dict(agg_passes=5), dict(eliminate=2), dict(reorder=3), dict(aggregation=2),
+                dict(hub_factor=-1), dict(chunking=3), dict(coarse_max=-1)):
+        with pytest.raises(P.LapError) as err:
+            P.lap_build_hierarchy(3, src, dst, None, P.lap_default_hier_opts(**bad))
+        assert err.value.status == P.LAP_EINVAL, bad
+        assert P.lap_last_error(), bad
