@@ -342,3 +342,20 @@ def test_rmat_with_each_chunking(P, rmat14, chunking, precision):
     f = P.cfc_farness_jl(h, 32, 9, nodes, opts=P.lap_default_solve_opts(**PRECISIONS[precision]))
     fo = jl.jl_farness(g, 32, 9, nodes.tolist(), solver="cg", tol=1e-12)
     assert _rel(f, fo) <= FARNESS_RTOL
+
+
+
+def test_first_residual_in_two_fp32_words_without_elimination(P):
+    # a unit-weight grid has no node with fewer than two neighbours: no
+    # elimination level, so the first correction lives at the PCG level itself
+    import torch
+    n, s, d, _ = synth.grid2d(40, 30)
+    g = canonical_graph(n, s, d, None)
+    h = P.lap_build_hierarchy(n, s, d, None)
+    assert P.lap_hierarchy_info(h)["elim_levels"] == 0
+    B = np.random.default_rng(21).standard_normal((n, 24))
+    X = torch.empty((n, 24), dtype=torch.float64, device="cuda")
+    info = P.lap_solve_multi(h, torch.tensor(B, device="cuda"), X, P.lap_default_solve_opts(precision=1))
+    assert info["first_residual_ff"] == 1
+    assert info["outer_iters"] >= 2 and info["max_rel_residual"] <= 1e-8
+    _certify(g, B, X.cpu().numpy())
